@@ -1,0 +1,268 @@
+"""Seeded synthetic contact scenes shaped like the paper's workloads.
+
+This module only makes inputs: node clouds of finite-element-like bodies
+(lattice boxes, lattice balls, ellipsoids), their masses, outward normals,
+rigid-body velocities and the matching affine matrices C = skew(omega).  It
+holds none of the contact method's arithmetic and is shared by the oracle
+tests, the CUDA tests and the benchmark.
+
+Conventions (same as the library): x[n,3] float64, v[n,3], C[n,3,3] with
+C[p, a, b] = d v_a / d x_b, m[n], nrm[n,3] (unit outward normal for surface
+nodes, zero for interior nodes), body[n] int32.
+
+Normals follow Sec. 2.3 of the paper (area-weighted outward normals of the
+boundary faces adjacent to a node): on a lattice box a face node gets the
+face normal, an edge node the normalised sum of two, a corner node of three;
+on a ball or ellipsoid the normal is the normalised gradient of the implicit
+surface at the node.  Interior nodes get 0.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 2108_0225
+
+
+@dataclass
+class Scene:
+    x: np.ndarray
+    v: np.ndarray
+    C: np.ndarray
+    m: np.ndarray
+    nrm: np.ndarray
+    body: np.ndarray
+    n_bodies: int
+    h: float
+    mu: float
+    n_iter: int
+    mu_pair: np.ndarray | None = None
+    name: str = ""
+    info: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+    def astype(self, dt) -> "Scene":
+        """Copy with v, C, m, nrm in dtype dt (x stays float64)."""
+        return Scene(self.x.copy(), self.v.astype(dt), self.C.astype(dt), self.m.astype(dt),
+                     self.nrm.astype(dt), self.body.copy(), self.n_bodies, self.h, self.mu,
+                     self.n_iter, None if self.mu_pair is None else self.mu_pair.copy(),
+                     self.name, dict(self.info))
+
+
+def skew(w):
+    """Matrix of the cross product: skew(w) @ r == cross(w, r)."""
+    w = np.asarray(w, np.float64)
+    return np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+
+
+def haar_rotation(rng) -> np.ndarray:
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def random_direction(rng) -> np.ndarray:
+    d = rng.standard_normal(3)
+    return d / np.linalg.norm(d)
+
+
+def _box_lattice(nx, ny, nz, s):
+    """Lattice box centred at 0 with spacing s, and its area-weighted normals."""
+    I, J, K = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    I, J, K = I.ravel(), J.ravel(), K.ravel()
+    pts = np.stack([(I - (nx - 1) / 2) * s, (J - (ny - 1) / 2) * s, (K - (nz - 1) / 2) * s], 1)
+    nrm = np.zeros_like(pts)
+    for ax, (idx, nmax) in enumerate(((I, nx), (J, ny), (K, nz))):
+        nrm[idx == 0, ax] -= 1.0
+        nrm[idx == nmax - 1, ax] += 1.0
+    ln = np.linalg.norm(nrm, axis=1)
+    nz_ = ln > 0
+    nrm[nz_] /= ln[nz_, None]
+    return pts, nrm
+
+
+def _implicit_lattice(count, s, axes, shape, jitter, rng):
+    """The `count` lattice points (spacing s) innermost in an ellipsoid or box
+    with semi-axis ratios `axes`; surface points get outward normals."""
+    axes = np.asarray(axes, np.float64)
+    vol_unit = (4.0 / 3.0 * np.pi) if shape == "ellipsoid" else 8.0
+    R = (count * s**3 / (vol_unit * np.prod(axes))) ** (1.0 / 3.0) * 1.15
+    ext = np.ceil(R * axes / s).astype(int) + 2
+    gi = [np.arange(-e, e + 1) for e in ext]
+    I, J, K = np.meshgrid(*gi, indexing="ij")
+    lat = np.stack([I.ravel(), J.ravel(), K.ravel()], 1)
+    pts = lat * s
+
+    def level(p):
+        q = p / (axes * R)
+        if shape == "ellipsoid":
+            return np.sqrt((q**2).sum(1))
+        return np.abs(q).max(1)
+
+    lev = level(pts)
+    order = np.argsort(lev, kind="stable")[:count]
+    lat, pts, lev = lat[order], pts[order], lev[order]
+    # surface = lattice points with a missing 6-neighbour
+    occ = np.zeros(tuple(2 * ext + 3), bool)
+    li = lat + ext + 1
+    occ[li[:, 0], li[:, 1], li[:, 2]] = True
+    surf = np.zeros(count, bool)
+    for d in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+        nb = li + np.array(d)
+        surf |= ~occ[nb[:, 0], nb[:, 1], nb[:, 2]]
+    nrm = np.zeros_like(pts)
+    if shape == "ellipsoid":
+        g = pts / (axes * R) ** 2
+    else:
+        q = pts / (axes * R)
+        g = np.zeros_like(pts)
+        amax = np.abs(q).max(1, keepdims=True)
+        g = np.where(np.abs(q) >= amax - 1e-12, np.sign(q), 0.0)
+    g = g / np.maximum(np.linalg.norm(g, axis=1, keepdims=True), 1e-300)
+    nrm[surf] = g[surf]
+    if jitter > 0:
+        pts = pts + rng.uniform(-jitter, jitter, pts.shape)
+    return pts, nrm
+
+
+def _rigid(pts, nrm, R, center, v0, w):
+    x = pts @ R.T + center
+    n = nrm @ R.T
+    v = v0 + np.cross(w, x - center)
+    C = np.broadcast_to(skew(w), (x.shape[0], 3, 3)).copy()
+    return x, n, v, C
+
+
+def _assemble(parts, h, mu, n_iter, name, mu_pair=None, info=None):
+    x = np.concatenate([p[0] for p in parts])
+    nrm = np.concatenate([p[1] for p in parts])
+    v = np.concatenate([p[2] for p in parts])
+    C = np.concatenate([p[3] for p in parts])
+    m = np.concatenate([p[4] for p in parts])
+    body = np.concatenate([np.full(p[0].shape[0], b, np.int32) for b, p in enumerate(parts)])
+    return Scene(x, v, C, m, nrm, body, len(parts), h, mu, n_iter, mu_pair, name, info or {})
+
+
+def two_cubes(mu: float = 0.3, n_iter: int = 10, approach: bool = True) -> Scene:
+    """Two 8x8x8-node cubes (spacing 1/32, 1/512 mass per node), centres at
+    x = 0.35 and 0.65 moving head-on at +-1 (C = 0), h = 1/32."""
+    s = 1.0 / 32
+    pts, nrm = _box_lattice(8, 8, 8, s)
+    sign = 1.0 if approach else -1.0
+    parts = []
+    for cx, vx in ((0.35, sign), (0.65, -sign)):
+        x = pts + np.array([cx, 0.5, 0.5])
+        v = np.tile([vx, 0.0, 0.0], (x.shape[0], 1))
+        parts.append((x, nrm.copy(), v, np.zeros((x.shape[0], 3, 3)), np.full(x.shape[0], 1.0 / 512)))
+    return _assemble(parts, 1.0 / 32, mu, n_iter, "two_cubes_8x8x8_h1/32")
+
+
+def four_bodies(seed: int = SEED_BASE + 2, scale: float = 1.0, mu: float = 0.3, n_iter: int = 8,
+                h: float = 1.0 / 256) -> Scene:
+    """Two lattice boxes (50x40x25 nodes) and two lattice balls (50,000
+    nodes), spacing h/2, jittered by U(-0.1h, 0.1h), Haar-random rotations,
+    random rigid velocities |v| <= 2 and |omega| <= 5, placed as two facing
+    pairs with surface gaps U(0, 2h).  `scale` < 1 shrinks the node counts
+    (for tests); 1 gives 200,000 nodes."""
+    rng = np.random.default_rng(seed)
+    s = h / 2
+    jit = 0.1 * h
+    nb = max(int(round(50 * scale ** (1 / 3))), 2), max(int(round(40 * scale ** (1 / 3))), 2), max(int(round(25 * scale ** (1 / 3))), 2)
+    nball = int(nb[0] * nb[1] * nb[2])
+    shapes = []
+    for kind in ("box", "ball", "box", "ball"):
+        if kind == "box":
+            pts, nrm = _box_lattice(*nb, s)
+            pts = pts + rng.uniform(-jit, jit, pts.shape)
+        else:
+            pts, nrm = _implicit_lattice(nball, s, (1, 1, 1), "ellipsoid", jit, rng)
+        shapes.append((pts, nrm))
+    parts = []
+    for pair in range(2):
+        A, B = shapes[2 * pair], shapes[2 * pair + 1]
+        RA, RB = haar_rotation(rng), haar_rotation(rng)
+        pa, pb = A[0] @ RA.T, B[0] @ RB.T
+        gap = rng.uniform(0, 2 * h)
+        yc = 0.3 + 0.4 * pair
+        ca = np.array([0.5 - pa[:, 0].max() - gap / 2, yc, 0.5])
+        cb = np.array([0.5 - pb[:, 0].min() + gap / 2, yc, 0.5])
+        for (pts, nrm), R, c, side in (((A[0], A[1]), RA, ca, 1.0), ((B[0], B[1]), RB, cb, -1.0)):
+            v0 = random_direction(rng) * rng.uniform(0, 2)
+            v0[0] = side * abs(v0[0])  # the pair approaches along x
+            w = random_direction(rng) * rng.uniform(0, 5)
+            x, n, v, Cm = _rigid(pts, nrm, R, c, v0, w)
+            m = np.full(x.shape[0], 1.0 / x.shape[0])
+            parts.append((x, n, v, Cm, m))
+    return _assemble(parts, h, mu, n_iter, f"four_bodies_{sum(p[0].shape[0] for p in parts)}_h1/{round(1 / h)}",
+                     info=dict(seed=seed))
+
+
+def eight_bodies(seed: int = SEED_BASE + 3, per_body: int = 500_000, n_iter: int = 8,
+                 h: float = 1.0 / 512) -> Scene:
+    """Eight tetrahedral-mesh-like node clouds: jittered lattices (spacing
+    h/2, jitter U(-h/8, h/8)) inside ellipsoids or boxes with axis ratios
+    U(0.6, 1), the `per_body` innermost points each; four approaching pairs
+    whose surfaces overlap by up to h; lognormal masses (sigma 0.3) scaled to
+    unit mass per body; mu(b, b') ~ U[0.1, 0.5], symmetric."""
+    rng = np.random.default_rng(seed)
+    s = h / 2
+    parts = []
+    centres = [(0.3, 0.3), (0.3, 0.7), (0.7, 0.3), (0.7, 0.7)]
+    for pair in range(4):
+        shp = []
+        for _ in range(2):
+            kind = "ellipsoid" if rng.uniform() < 0.5 else "box"
+            axes = rng.uniform(0.6, 1.0, 3)
+            pts, nrm = _implicit_lattice(per_body, s, axes, kind, 0.25 * s, rng)
+            R = haar_rotation(rng)
+            shp.append((pts @ R.T, nrm @ R.T))
+        overlap = rng.uniform(0, h)
+        yc, zc = centres[pair]
+        ca = np.array([0.5 - shp[0][0][:, 0].max() + overlap / 2, yc, zc])
+        cb = np.array([0.5 - shp[1][0][:, 0].min() - overlap / 2, yc, zc])
+        for (pts, nrm), c, side in ((shp[0], ca, 1.0), (shp[1], cb, -1.0)):
+            v0 = random_direction(rng) * rng.uniform(0, 2)
+            v0[0] = side * abs(v0[0])
+            w = random_direction(rng) * rng.uniform(0, 5)
+            x = pts + c
+            v = v0 + np.cross(w, pts)
+            Cm = np.broadcast_to(skew(w), (x.shape[0], 3, 3)).copy()
+            m = rng.lognormal(0.0, 0.3, x.shape[0])
+            m = m / m.sum()
+            parts.append((x, nrm, v, Cm, m))
+    nb = len(parts)
+    mp = rng.uniform(0.1, 0.5, (nb, nb))
+    mp = np.triu(mp) + np.triu(mp, 1).T
+    return _assemble(parts, h, 0.3, n_iter, f"eight_bodies_{nb * per_body}_h1/{round(1 / h)}",
+                     mu_pair=mp, info=dict(seed=seed))
+
+
+def random_cloud(n: int, n_bodies: int = 2, seed: int = 0, h: float = 0.1, affine: bool = False,
+                 spread: float = 1.0, mu: float = 0.3, n_iter: int = 3, origin=(0.0, 0.0, 0.0),
+                 interior_frac: float = 0.3) -> Scene:
+    """Random non-affine state on a random cloud (test input): uniform
+    positions in a cube of side `spread`, random masses in [0.5, 1.5],
+    random unit normals (a fraction zeroed as interior), and either random
+    v, C or one shared affine field v = v0 + L x, C = L."""
+    rng = np.random.default_rng(seed)
+    x = np.asarray(origin) + rng.uniform(0, spread, (n, 3))
+    m = rng.uniform(0.5, 1.5, n)
+    nrm = rng.standard_normal((n, 3))
+    nrm /= np.maximum(np.linalg.norm(nrm, axis=1, keepdims=True), 1e-300)
+    nrm[rng.uniform(size=n) < interior_frac] = 0.0
+    body = rng.integers(0, n_bodies, n).astype(np.int32)
+    if affine:
+        v0 = rng.standard_normal(3)
+        L = rng.standard_normal((3, 3))
+        v = v0 + x @ L.T
+        Cm = np.broadcast_to(L, (n, 3, 3)).copy()
+    else:
+        v = rng.standard_normal((n, 3))
+        Cm = rng.standard_normal((n, 3, 3)) / h
+    return Scene(x, v, Cm, m, nrm, body, n_bodies, h, mu, n_iter, None, f"random_cloud_{n}", dict(seed=seed))
