@@ -1,0 +1,363 @@
+"""Benchmark of the APIC augury contact step (arXiv 2108.02259) on GB300.
+
+One "step" is one full contact step through the C ABI: keys, sort, sparse
+grid activation, mass P2G, then N + 1 fused transfer passes (the paper's
+series with the Coulomb projection), on one synthetic scene resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Prints one JSON line.  The metric is contact particle-iterations per second,
+P * (N + 1) per step (each particle through each transfer pair).
+
+Workloads (seeded, synthetic, shaped like the paper's bodies):
+  four_bodies   4 bodies, 200,000 FE nodes, h = 1/256, mu = 0.3, N = 8, FP32 (default)
+  two_cubes     2 cubes of 8^3 nodes, h = 1/32, mu = 0.3, N = 10, FP64
+  eight_bodies  8 bodies, 4,000,000 nodes, h = 1/512, per-pair mu, N = 8, FP32
+
+Multi-GPU (torchrun): every rank steps its own copy of the scene (the scenes
+are independent; no collective on the data path); value = all ranks'
+particle-iterations / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "contact particle-iters/s"
+UNIT = "particle-iters/s"
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def make_scene(name):
+    from paper_2108_02259_gb300 import scenes
+
+    if name == "four_bodies":
+        return scenes.four_bodies(), np.float32
+    if name == "two_cubes":
+        return scenes.two_cubes(mu=0.3, n_iter=10), np.float64
+    if name == "eight_bodies":
+        return scenes.eight_bodies(), np.float32
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(name, s, dt):
+    return {
+        "workload": f"{name}: {s.n_bodies} bodies, {s.n} FE nodes, h=1/{round(1 / s.h)}, N={s.n_iter}, "
+                    + ("mu per body pair" if s.mu_pair is not None else f"mu={s.mu}"),
+        "particles": s.n,
+        "bodies": s.n_bodies,
+        "h": s.h,
+        "n_iter": s.n_iter,
+        "transfer_pairs_per_step": s.n_iter + 1,
+        "precision": "fp64" if dt == np.float64 else "fp32 (fp64 node momentum at multi-body nodes)",
+        "l2": "flushed before every timed step (256 MiB write)",
+    }
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during timing."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return float(json.load(open(p))["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes_per_pass(P, G):
+    """Bytes one fused transfer pass must move: per particle read the offset
+    and mass (16 B), normal (12 B) and cell tag (4 B), read and write the
+    12-float change Delta (96 B) = 128 B; per active node read v_i and
+    accumulate p_i (24 B)."""
+    return 128.0 * P + 24.0 * G
+
+
+def cpu_baseline(s, budget_s=12.0):
+    """The FP64 oracle as it stands, single-threaded, on the host cores."""
+    import oracle
+
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        oracle.contact_step(s.x, s.v, s.C, s.m, s.nrm, s.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
+                            mu_pair=s.mu_pair)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or steps >= 8:
+            break
+    return {"value": s.n * (s.n_iter + 1) * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full step(s) of the same scene ({s.n} particles, N={s.n_iter}), "
+                      f"{el:.1f} s single-threaded FP64"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    s, dt = make_scene(args.workload)
+    for _ in range(args.warmup):
+        oracle.contact_step(s.x, s.v, s.C, s.m, s.nrm, s.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
+                            mu_pair=s.mu_pair)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.contact_step(s.x, s.v, s.C, s.m, s.nrm, s.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
+                            mu_pair=s.mu_pair)
+    el = time.perf_counter() - t0
+    value = s.n * (s.n_iter + 1) * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args.workload, s, dt),
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                         "sample": f"the whole scene each step ({s.n} particles), single-threaded FP64 oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="four_bodies", choices=["four_bodies", "two_cubes", "eight_bodies"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}" if ws > 1 else "cuda:0")
+    torch.cuda.set_device(dev)
+
+    from paper_2108_02259_gb300 import apic, build
+
+    build.build()
+    s, dt = make_scene(args.workload)
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    f = s.astype(dt)
+
+    def t(a, d):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=d).to(dev)
+
+    X = t(f.x, torch.float64)
+    Vv, Cc, M, NR = t(f.v, tdt), t(f.C, tdt), t(f.m, tdt), t(f.nrm, tdt)
+    B = t(f.body, torch.int32)
+    Vo, Co = torch.empty_like(Vv), torch.empty_like(Cc)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = apic.Context(dev.index)
+
+    def step():
+        apic.contact_step(ctx, X, Vv, Cc, M, NR, B, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies, mu_pair=s.mu_pair,
+                          v_out=Vo, C_out=Co, stream=stream)
+
+    # one checked step: the device's own momentum balance
+    r = apic.contact_step(ctx, X, Vv, Cc, M, NR, B, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies, mu_pair=s.mu_pair,
+                          v_out=Vo, C_out=Co, stream=stream, stats=True)
+    st = r.stats
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    try:  # nvidia-smi wants the physical GPU: address it by UUID
+        clocks = Clocks("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
+    except Exception:
+        clocks = Clocks(dev.index)
+    ctx.set_profiling(True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    ck = clocks.stop()
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    t_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    if ws > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    units = s.n * (s.n_iter + 1) * args.steps * ws
+    value = units / (t_ms / 1e3)
+
+    # roofline of the fused transfer kernel (timed live with events on the launch stream)
+    G = prof["active_nodes"]
+    iter_avg_ms = prof["iter_ms"] / max(prof["iter_launches"], 1)
+    alg = algorithmic_bytes_per_pass(s.n, G)
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg / (iter_avg_ms / 1e3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
+    if os.path.exists(tfile):
+        try:
+            tj = json.load(open(tfile))
+            if tj.get("kernel_source_hash") == kernel_source_hash():
+                traffic = tj.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # end to end: the same step through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        def pin(a, d):
+            return torch.as_tensor(np.ascontiguousarray(a), dtype=d).pin_memory().numpy()
+
+        hx, hv, hC, hm, hn = pin(f.x, torch.float64), pin(f.v, tdt), pin(f.C, tdt), pin(f.m, tdt), pin(f.nrm, tdt)
+        hb = pin(f.body, torch.int32)
+        hvo, hCo = pin(np.zeros_like(f.v), tdt), pin(np.zeros_like(f.C), tdt)
+        for _ in range(2):
+            apic.contact_step(ctx, hx, hv, hC, hm, hn, hb, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
+                              mu_pair=s.mu_pair, v_out=hvo, C_out=hCo, stream=stream)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            apic.contact_step(ctx, hx, hv, hC, hm, hn, hb, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
+                              mu_pair=s.mu_pair, v_out=hvo, C_out=hCo, stream=stream)
+        torch.cuda.synchronize(dev)
+        el = time.perf_counter() - t0
+        if ws > 1:
+            tt = torch.tensor([el], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            el = float(tt.item())
+        isz = np.dtype(dt).itemsize
+        e2e = {"value": units / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(s.n * (24 + 4 + isz * (3 + 9 + 1 + 3))),
+               "d2h_bytes_per_step": int(s.n * isz * (3 + 9))}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    sP = float(np.sum(s.m * np.linalg.norm(s.v, axis=1)))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if dt == np.float64 else "f32", "data": "synthetic",
+        "config": workload_config(args.workload, s, dt),
+        "e2e": e2e,
+        "gpu_launches": int(prof["kernel_launches"]),
+        "sort_primitive_calls": int(prof["sort_launches"]),
+        "roofline": {"bound": "hbm", "kernel": "k_items (fused G2P + projection + P2G pass)",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg, "avg_launch_ms": iter_avg_ms,
+                     "launches": int(prof["iter_launches"]), "active_nodes": int(G)},
+        "step_breakdown_ms": {"prep_incl_mass_p2g": prof["prep_ms"] / max(prof["steps"], 1),
+                              "transfer_passes": prof["iter_ms"] / max(prof["steps"], 1),
+                              "step": prof["step_ms"] / max(prof["steps"], 1)},
+        "momentum_check": {"P_drift_rel": float(np.abs(st["P_out"] - st["P_in"]).max() / sP),
+                           "multibody_nodes": st["multibody_nodes"], "active_blocks": st["active_blocks"],
+                           "work_items": st["work_items"]},
+        "clocks": ck,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(s)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def kernel_source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "api.cu", "apic_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2108_02259_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,160 @@
+/*
+ * libapiccontact — the APIC augury contact step of Tupek, Koester & Mosby,
+ * "A momentum preserving frictional contact algorithm based on affine
+ * particle-in-cell grid transfers" (arXiv 2108.02259), on NVIDIA GB300.
+ *
+ * One call maps the predicted generalized velocity V = {v_p, C_p} of the
+ * contact particles (finite-element boundary nodes, Sec. 2 intro) to the
+ * preferred velocity
+ *
+ *     V_hat = V + G V + sum_{n=1..N} G W_n,        G = H - I        (Sec. 2.3)
+ *
+ * where H is one APIC particle-to-grid / grid-to-particle transfer pair on a
+ * quadratic B-spline background grid of spacing h (Sec. 2.1.2, App. B) and
+ * W_{m+1} is the undesirable part of V_hat_m - V under the Coulomb-friction
+ * cone (Sec. 2.4).  The caller forms the augury acceleration
+ * (V_hat - V) / tau itself (Sec. 2.2, eq. apic_accel).
+ *
+ * C_p is the APIC affine matrix B_p D_p^{-1}; with the quadratic B-splines
+ * D_p = (h^2/2) I (App. B), so B_p = (h^2/2) C_p.  C is row-major 3x3:
+ * C[9p + 3a + b] = d v_a / d x_b.
+ *
+ * Conventions for every entry point:
+ *   - No exceptions cross the ABI.  Every call returns an apic_status;
+ *     on failure apic_last_error() holds a message for the calling thread.
+ *   - The caller owns every pointer it passes.  The library keeps none past
+ *     the call.  Scratch (grid, sort buffers) is owned by the context and
+ *     grows on demand; it counts against the context's HBM budget.
+ *   - Array pointers are device pointers on the context's device unless the
+ *     APIC_HOST_PTRS flag is set.  Work is queued on the caller's CUDA stream
+ *     (cudaStream_t passed as void*, NULL = legacy default stream).
+ *   - A context is not thread-safe; use one per thread.
+ */
+#ifndef APICCONTACT_H
+#define APICCONTACT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t apic_status;
+#define APIC_OK 0
+#define APIC_ERR_INVALID_ARG (-1)   /* bad size, pointer, flag or value   */
+#define APIC_ERR_OUT_OF_MEMORY (-2) /* device allocation or budget failed */
+#define APIC_ERR_CUDA (-3)          /* a CUDA runtime call failed         */
+#define APIC_ERR_TIMEOUT (-4)       /* a bounded device wait gave up      */
+
+/* Flags of apic_step_args.flags */
+#define APIC_FP64 (1u << 0)          /* v, C, m, nrm (in and out) are double; all arithmetic FP64.
+                                        Without it they are float and the transfers run in FP32
+                                        (positions as int cell + FP32 offset, FP64 node momentum
+                                        at nodes two or more bodies touch).                        */
+#define APIC_HOST_PTRS (1u << 1)     /* every array pointer is host memory: the call copies in,
+                                        computes, copies out and synchronises the stream.          */
+#define APIC_VARIANT_PIC (1u << 2)   /* PIC transfers (Sec. 2.1.1): no affine term, C unchanged.   */
+#define APIC_VARIANT_SEP23 (1u << 3) /* Sec. 2.3 separation rule instead of the Sec. 2.4 cone:
+                                        W = Delta if Delta_v . n > 0, else 0.                      */
+
+typedef struct apic_ctx apic_ctx;
+
+/* One contact step of one scene.
+ *   n         number of particles (>= 0; 0 is a no-op).
+ *   n_bodies  1..32; body[p] in [0, n_bodies).  Bodies only matter for the
+ *             multi-body node bookkeeping and the per-pair friction table.
+ *   n_iter    N >= 0 augury iterations: N + 1 transfer pairs (Sec. 2.3).
+ *   body      [n] int32.
+ *   x         [n*3] double positions, xyz interleaved.  Grid nodes sit at
+ *             h * (i, j, k) for all integers (unbounded grid, App. B).
+ *   v, C      [n*3], [n*9] predicted velocity and affine matrix (float, or
+ *             double with APIC_FP64).
+ *   m         [n] masses, > 0.
+ *   nrm       [n*3] outward unit normals of surface nodes, 0 for interior
+ *             nodes (Sec. 2.3).
+ *   v_out, C_out  [n*3], [n*9] results; may alias v, C.
+ *   h         grid spacing > 0.   mu  scalar friction coefficient >= 0.
+ *   mu_pair   NULL, or HOST pointer to n_bodies*n_bodies doubles (symmetric):
+ *             per-body-pair friction, blended per particle by the mass of the
+ *             other bodies its stencil sees (the paper has one scalar mu).
+ *   flags     APIC_* above.
+ */
+typedef struct {
+  int64_t n;
+  int32_t n_bodies;
+  int32_t n_iter;
+  const int32_t* body;
+  const double* x;
+  const void* v;
+  const void* C;
+  const void* m;
+  const void* nrm;
+  void* v_out;
+  void* C_out;
+  double h;
+  double mu;
+  const double* mu_pair;
+  uint32_t flags;
+} apic_step_args;
+
+/* Diagnostics of one step (FP64 reductions on the device).
+ *   P = sum m v;  L = sum m [ x cross v + (h^2/2) axial(C) ],
+ *   axial(C) = (C_zy - C_yz, C_xz - C_zx, C_yx - C_xy)  — the angular
+ *   momentum the grid sees (Sec. 2.1.2).  Requesting stats synchronises. */
+typedef struct {
+  double P_in[3], P_out[3], L_in[3], L_out[3];
+  int64_t multibody_nodes; /* grid nodes with mass from two or more bodies */
+  int64_t active_blocks;   /* 4x4x4-node grid blocks allocated this step   */
+  int64_t work_items;      /* (grid block, body) particle segments         */
+} apic_stats;
+
+/* Per-context kernel timing (CUDA events on the caller's stream), for the
+ * benchmark's roofline figure.  Enabled by apic_set_profiling. */
+typedef struct {
+  int64_t steps;
+  int64_t iter_launches;   /* launches of the fused transfer kernel           */
+  double iter_ms;          /* their summed durations                           */
+  double prep_ms;          /* keys, sort, gather, grid activation              */
+  double step_ms;          /* whole steps                                      */
+  int64_t particles;       /* particles of the last step                      */
+  int64_t active_nodes;    /* grid nodes of the last step                     */
+  int64_t kernel_launches; /* launches of this library's own kernels          */
+  int64_t sort_launches;   /* device sort / scan primitive calls (CUB)        */
+} apic_profile;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* apic_last_error(void);
+
+/* Library version string. */
+const char* apic_version(void);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * scratch the context may hold (0 = no cap).  Returns INVALID_ARG for a bad
+ * device, CUDA on a runtime failure. */
+apic_status apic_create(apic_ctx** out, int32_t device, size_t hbm_budget_bytes);
+
+/* Free a context and all its scratch.  NULL is accepted. */
+apic_status apic_destroy(apic_ctx* ctx);
+
+/* One contact step (Sec. 2.3 series with the Sec. 2.4 projection).
+ * Asynchronous on `stream` except: it synchronises the stream twice while
+ * sizing the sparse grid, and at the end when `stats` is non-NULL or
+ * APIC_HOST_PTRS is set.  Invalid particle data (body out of range, m <= 0,
+ * non-finite or out-of-range positions) returns INVALID_ARG. */
+apic_status apic_contact_step(apic_ctx* ctx, const apic_step_args* args, void* stream, apic_stats* stats);
+
+/* Turn kernel timing on (1) or off (0) and reset the counters. */
+apic_status apic_set_profiling(apic_ctx* ctx, int32_t on);
+
+/* Read the counters (synchronises the device work they cover). */
+apic_status apic_get_profile(apic_ctx* ctx, apic_profile* out);
+
+/* Bytes of device scratch the context currently holds. */
+apic_status apic_scratch_bytes(apic_ctx* ctx, size_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APICCONTACT_H */

@@ -1,0 +1,224 @@
+"""Thin ctypes binding of libapiccontact (include/apiccontact.h).
+
+Argument marshalling only: every step of the contact computation runs in the
+library's CUDA kernels.  Device arrays are torch CUDA tensors (pointers and
+the current torch stream are passed through); host arrays are numpy arrays
+(the call sets APIC_HOST_PTRS and the library copies in and out).
+
+The library must have been built (``paper_2108_02259_gb300.build.build()``);
+loading fails loudly otherwise.  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libapiccontact.so")
+
+APIC_OK = 0
+APIC_ERR_INVALID_ARG = -1
+APIC_ERR_OUT_OF_MEMORY = -2
+APIC_ERR_CUDA = -3
+APIC_ERR_TIMEOUT = -4
+
+APIC_FP64 = 1 << 0
+APIC_HOST_PTRS = 1 << 1
+APIC_VARIANT_PIC = 1 << 2
+APIC_VARIANT_SEP23 = 1 << 3
+
+EXPORTED = [
+    "apic_last_error", "apic_version", "apic_create", "apic_destroy", "apic_contact_step",
+    "apic_set_profiling", "apic_get_profile", "apic_scratch_bytes",
+]
+
+
+class StepArgs(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64), ("n_bodies", C.c_int32), ("n_iter", C.c_int32),
+        ("body", C.c_void_p), ("x", C.c_void_p), ("v", C.c_void_p), ("C", C.c_void_p),
+        ("m", C.c_void_p), ("nrm", C.c_void_p), ("v_out", C.c_void_p), ("C_out", C.c_void_p),
+        ("h", C.c_double), ("mu", C.c_double), ("mu_pair", C.c_void_p), ("flags", C.c_uint32),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("P_in", C.c_double * 3), ("P_out", C.c_double * 3), ("L_in", C.c_double * 3),
+        ("L_out", C.c_double * 3), ("multibody_nodes", C.c_int64), ("active_blocks", C.c_int64),
+        ("work_items", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return dict(P_in=np.array(self.P_in[:]), P_out=np.array(self.P_out[:]), L_in=np.array(self.L_in[:]),
+                    L_out=np.array(self.L_out[:]), multibody_nodes=int(self.multibody_nodes),
+                    active_blocks=int(self.active_blocks), work_items=int(self.work_items))
+
+
+class Profile(C.Structure):
+    _fields_ = [
+        ("steps", C.c_int64), ("iter_launches", C.c_int64), ("iter_ms", C.c_double), ("prep_ms", C.c_double),
+        ("step_ms", C.c_double), ("particles", C.c_int64), ("active_nodes", C.c_int64),
+        ("kernel_launches", C.c_int64), ("sort_launches", C.c_int64),
+    ]
+
+
+_lib = None
+
+
+class ApicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libapiccontact error {code}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with paper_2108_02259_gb300.build.build()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.apic_last_error.restype = C.c_char_p
+    lib.apic_version.restype = C.c_char_p
+    lib.apic_create.argtypes = [C.POINTER(P), C.c_int32, C.c_size_t]
+    lib.apic_destroy.argtypes = [P]
+    lib.apic_contact_step.argtypes = [P, C.POINTER(StepArgs), P, C.POINTER(Stats)]
+    lib.apic_set_profiling.argtypes = [P, C.c_int32]
+    lib.apic_get_profile.argtypes = [P, C.POINTER(Profile)]
+    lib.apic_scratch_bytes.argtypes = [P, C.POINTER(C.c_size_t)]
+    for f in ("apic_create", "apic_destroy", "apic_contact_step", "apic_set_profiling", "apic_get_profile",
+              "apic_scratch_bytes"):
+        getattr(lib, f).restype = C.c_int32
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != APIC_OK:
+        raise ApicError(code, load().apic_last_error().decode())
+
+
+class Context:
+    """An apic_ctx on one CUDA device (scratch grows on demand)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.apic_create(C.byref(h), int(device), int(hbm_budget_bytes)))
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().apic_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_profiling(self, on: bool):
+        _check(load().apic_set_profiling(self._h, 1 if on else 0))
+
+    def profile(self) -> dict:
+        p = Profile()
+        _check(load().apic_get_profile(self._h, C.byref(p)))
+        return {k: getattr(p, k) for k, _ in Profile._fields_}
+
+    def scratch_bytes(self) -> int:
+        v = C.c_size_t()
+        _check(load().apic_scratch_bytes(self._h, C.byref(v)))
+        return int(v.value)
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+@dataclass
+class StepResult:
+    v: object
+    C: object
+    stats: dict | None
+
+
+def contact_step(ctx: Context, x, v, Cm, m, nrm, body, h: float, mu: float, n_iter: int, n_bodies: int | None = None,
+                 mu_pair=None, flags: int = 0, v_out=None, C_out=None, stream=None, stats: bool = False) -> StepResult:
+    """One contact step through the C ABI.
+
+    Device path: x float64 [n,3], v [n,3], C [n,3,3], m [n], nrm [n,3] (all float32,
+    or all float64 for the FP64 build), body int32 [n] -- torch CUDA tensors,
+    contiguous.  Host path: the same as numpy arrays.  Outputs are allocated when
+    not given (in place is allowed).  `stream` is a torch.cuda.Stream (default:
+    the current one)."""
+    lib = load()
+    dev = _is_torch(x)
+    n = int(x.shape[0])
+    dt = v.dtype
+    if dev:
+        import torch
+
+        fp64 = dt == torch.float64
+        for t in (x, v, Cm, m, nrm, body):
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("device path wants contiguous CUDA tensors")
+        if x.dtype != torch.float64 or body.dtype != torch.int32:
+            raise ValueError("x must be float64 and body int32")
+        if any(t.dtype != dt for t in (Cm, m, nrm)):
+            raise ValueError("v, C, m, nrm must share one dtype")
+        if v_out is None:
+            v_out = torch.empty_like(v)
+        if C_out is None:
+            C_out = torch.empty_like(Cm)
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        sptr = stream.cuda_stream
+    else:
+        fp64 = dt == np.float64
+        x = np.ascontiguousarray(x, np.float64)
+        body = np.ascontiguousarray(body, np.int32)
+        v, Cm, m, nrm = (np.ascontiguousarray(a, dt) for a in (v, Cm, m, nrm))
+        if v_out is None:
+            v_out = np.empty_like(v)
+        if C_out is None:
+            C_out = np.empty_like(Cm)
+        sptr = None if stream is None else stream.cuda_stream
+        flags |= APIC_HOST_PTRS
+    if fp64:
+        flags |= APIC_FP64
+    if n_bodies is None:
+        n_bodies = (int(body.max()) + 1) if n else 1
+    mp = None
+    if mu_pair is not None:
+        mp = np.ascontiguousarray(np.asarray(mu_pair, np.float64).reshape(n_bodies, n_bodies))
+    a = StepArgs(n, int(n_bodies), int(n_iter), _ptr(body), _ptr(x), _ptr(v), _ptr(Cm), _ptr(m), _ptr(nrm),
+                 _ptr(v_out), _ptr(C_out), float(h), float(mu), None if mp is None else mp.ctypes.data, int(flags))
+    st = Stats() if stats else None
+    _check(lib.apic_contact_step(ctx.handle, C.byref(a), sptr, C.byref(st) if stats else None))
+    return StepResult(v_out, C_out, st.as_dict() if stats else None)

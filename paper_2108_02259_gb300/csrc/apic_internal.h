@@ -1,0 +1,123 @@
+// Internal types and launchers of libapiccontact (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace apic {
+
+// 4-wide vector with natural alignment (16 B for float, 32 B for double).
+template <class T>
+struct alignas(4 * sizeof(T)) V4 {
+  T x, y, z, w;
+};
+
+// The background grid is stored in blocks of 4x4x4 nodes.  A work item is
+// the run of sorted particles whose cell lies in one grid block and that
+// belong to one body.  Its particles touch nodes [4B-1, 4B+5] per dimension:
+// a 7x7x7 node tile spanning the 3x3x3 blocks around B.
+constexpr int kBlk = 4;
+constexpr int kTile = 7;
+constexpr int kTile3 = kTile * kTile * kTile;
+constexpr int kNodesPerBlock = kBlk * kBlk * kBlk;
+// A work item holds at most kChunk particles (one per thread of its CTA).
+constexpr int kChunk = 128;
+
+// Error bits raised by the validation pass.
+constexpr int kErrBody = 1;
+constexpr int kErrMass = 2;
+constexpr int kErrPos = 4;
+
+// Device-side scalars the host reads back while sizing the grid.
+struct DevScalars {
+  int bbox[6];   // min (bx, by, bz), max (bx, by, bz) of particle blocks
+  int err;       // kErr* bits
+  int n_items;   // work items
+  int n_blocks;  // active grid blocks
+  int pad;
+  double mom[12];  // P_in, L_in, P_out, L_out accumulators
+  unsigned long long multibody;
+};
+
+// Dense page table over a box of grid blocks (block coordinates relative to
+// the box origin).  The box has a one-block margin around every particle
+// block so that a particle's stencil never leaves it.
+struct Box {
+  int ox, oy, oz;  // origin block coordinates
+  int nx, ny, nz;  // extent in blocks
+};
+
+// Iteration-kernel modes (one transfer pair each; Sec. 2.3).
+enum Mode : int {
+  kModeMass = 0,   // m_i and the body mask (once per step)
+  kModeP2GV = 1,   // P2G of V (first half of H V)
+  kModeFirst = 2,  // G2P -> Delta_0 = H V - V -> W_1 -> P2G(W_1)
+  kModeMid = 3,    // G2P -> Delta_m = Delta_{m-1} + H W_m - W_m -> W_{m+1} -> P2G
+  kModeLast = 4,   // G2P -> Delta_N -> V_hat = V + Delta_N in caller order
+  kModeOnly = 5,   // N = 0: G2P -> V_hat = H V in caller order
+  kModeMu = 6,     // per-particle friction blend from a body-pair table
+};
+
+// Everything the per-item kernel needs, by value.
+template <class T>
+struct IterParams {
+  int n_items;
+  int n_particles;
+  int n_bodies;
+  Box box;
+  const int* item_start;   // [n_items] first sorted particle of each item
+  const int2* item_info;   // [n_items] (block linear index in the box, body)
+  const int* page;         // [box volume] compact block id or -1
+  const V4<T>* pt;         // [n] (t_x, t_y, t_z, m) sorted
+  const V4<T>* pn;         // [n] (n_x, n_y, n_z, local cell bits) sorted
+  const T* mup;            // [n] per-particle mu or nullptr
+  T mu;                    // scalar mu
+  const T* mu_pair;        // [n_bodies^2] device copy of the pair table (kModeMu)
+  T* gmb;                  // [n_bodies * nodes] per-body node mass, or nullptr
+  T* mup_out;              // [n] written by kModeMu
+  int64_t n_nodes;
+  const V4<T>* V;          // [3n] sorted V = (v, h C) as 3 planes of n
+  V4<T>* D;                // [3n] Delta planes
+  const V4<T>* gv;         // grid velocity (normalised), [nodes]
+  V4<T>* gp;               // grid momentum accumulators, [nodes]
+  T* gm;                   // grid mass, [nodes]
+  uint32_t* gmask;         // body bits, [nodes]
+  V4<double>* gp64;        // FP64 momentum at multi-body nodes (FP32 path), [nodes]
+  const int* perm;         // sorted -> caller index
+  void* v_out;             // caller order outputs (T)
+  void* C_out;
+  T inv_h;
+  int pic;                 // PIC transfers
+  int sep23;               // Sec. 2.3 rule
+};
+
+template <class T>
+cudaError_t launch_cells(int64_t n, const double* x, const int32_t* body, const T* m, double inv_h,
+                         int n_bodies, int4* cellb, DevScalars* ds, cudaStream_t s);
+template <class K>
+cudaError_t launch_keys(int64_t n, const int4* cellb, Box box, int n_bodies, K* keys, int* vals,
+                        cudaStream_t s);
+template <class T>
+cudaError_t launch_gather(int64_t n, const int* perm, const int4* cellb, const double* x, const T* v,
+                          const T* C, const T* m, const T* nrm, double h, double inv_h, V4<T>* pt,
+                          V4<T>* pn, V4<T>* V, cudaStream_t s);
+template <class K>
+cudaError_t launch_heads(int64_t n, const K* keys, int* flags, cudaStream_t s);
+template <class K>
+cudaError_t launch_item_info(const int* item_start, const int* n_items, const K* keys, int n_bodies,
+                             int2* item_info, int max_items, cudaStream_t s);
+cudaError_t launch_mark(int64_t n, const int4* cellb, Box box, int* flags, cudaStream_t s);
+cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* list, int* page,
+                           int* count, cudaStream_t s);
+template <class T>
+cudaError_t launch_items(const IterParams<T>& p, int mode, int threads, cudaStream_t s);
+template <class T>
+cudaError_t launch_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask, V4<T>* gp,
+                             V4<double>* gp64, V4<T>* gv, cudaStream_t s);
+template <class T>
+cudaError_t launch_momentum(int64_t n, const double* x, const T* v, const T* C, const T* m, double h,
+                            double* out6, cudaStream_t s);
+cudaError_t launch_count_multibody(int64_t n_nodes, const uint32_t* gmask,
+                                   unsigned long long* out, cudaStream_t s);
+
+}  // namespace apic

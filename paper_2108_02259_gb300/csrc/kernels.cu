@@ -1,0 +1,779 @@
+// CUDA kernels of libapiccontact (sm_103a).
+//
+// The per-step pipeline (host side in api.cu):
+//   cells -> keys -> radix sort -> gather SoA -> item heads -> grid-block
+//   activation -> mass P2G -> P2G(V) -> N+1 fused transfer passes, each
+//   followed by a node normalisation (v_i = p_i / m_i).
+//
+// Notation follows the paper: particles p, background nodes i, weights N_i
+// (App. B), generalized velocity V = {v, B} with B_p = C_p D_p and
+// D_p = (h^2/2) I, the series V_hat = V + G V + sum G W_n (Sec. 2.3) and the
+// undesirable part of Sec. 2.4.  Inside the kernels C is carried as
+// Ch = h C (velocity units) and node offsets in cell units d = (x_i - x_p)/h,
+// so P2G adds N m (v + Ch d) and G2P gives Ch_hat = 2 sum N v_i (x) d.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "apic_internal.h"
+
+namespace apic {
+namespace {
+
+__device__ __forceinline__ float bits_to(float, uint32_t b) { return __uint_as_float(b); }
+__device__ __forceinline__ double bits_to(double, uint32_t b) {
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ uint32_t to_bits(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ uint32_t to_bits(double v) { return (uint32_t)__double_as_longlong(v); }
+
+// App. B quadratic B-spline weights of the nodes i-1, i, i+1, i+2 for the
+// in-cell offset t = x/h - floor(x/h), written out (with the 1/4 factor on
+// the middle two, the reading under which they sum to one):
+//   (1-t)^2/4,  (2-t^2)/4,  (1+2t-t^2)/4,  t^2/4
+// and the node offsets d_k = (x_{i-1+k} - x_p)/h = k - 1 - t.
+template <class T>
+__device__ __forceinline__ void bspline(T t, T w[4], T d[4]) {
+  const T s = T(1) - t;
+  w[0] = T(0.25) * s * s;
+  w[1] = T(0.25) * (T(2) - t * t);
+  w[2] = T(0.25) * (T(1) + t * (T(2) - t));
+  w[3] = T(0.25) * t * t;
+  d[0] = -T(1) - t;
+  d[1] = -t;
+  d[2] = T(1) - t;
+  d[3] = T(2) - t;
+}
+
+// Sec. 2.4: the undesirable part of the proposed change (dv, dCh).  dCh is
+// always undesirable; dv loses its admissible part inside the Coulomb cone
+// when dv.n <= 0.  With sep23 the Sec. 2.3 rule is used instead.
+template <class T>
+__device__ __forceinline__ void undesirable(const T dv[3], const T dC[9], const T n[3], T mu,
+                                            int sep23, T wv[3], T wC[9]) {
+  const T dn = dv[0] * n[0] + dv[1] * n[1] + dv[2] * n[2];
+  if (sep23) {
+    const T f = dn > T(0) ? T(1) : T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) wv[a] = f * dv[a];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) wC[a] = f * dC[a];
+    return;
+  }
+  if (dn <= T(0)) {
+    T vt[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) vt[a] = dv[a] - dn * n[a];
+    const T nt = sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
+    const T s = fmin(nt, -mu * dn);
+    const T keep = nt > T(0) ? s / nt : T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) wv[a] = vt[a] - keep * vt[a];
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) wv[a] = dv[a];
+  }
+#pragma unroll
+  for (int a = 0; a < 9; ++a) wC[a] = dC[a];
+}
+
+template <class T>
+__device__ __forceinline__ void load12(const V4<T>* planes, int n, int s, T v[3], T C[9]) {
+  const V4<T> a = planes[s], b = planes[n + s], c = planes[2 * n + s];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z;
+  C[0] = a.w; C[1] = b.x; C[2] = b.y;
+  C[3] = b.z; C[4] = b.w; C[5] = c.x;
+  C[6] = c.y; C[7] = c.z; C[8] = c.w;
+}
+
+template <class T>
+__device__ __forceinline__ void store12(V4<T>* planes, int n, int s, const T v[3], const T C[9]) {
+  planes[s] = V4<T>{v[0], v[1], v[2], C[0]};
+  planes[n + s] = V4<T>{C[1], C[2], C[3], C[4]};
+  planes[2 * n + s] = V4<T>{C[5], C[6], C[7], C[8]};
+}
+
+// Node index of tile node t (tile coordinates (a, b, c) in [0,7)^3 relative
+// to node 4B-1), or -1 when its block is not active.
+__device__ __forceinline__ int tile_node(const int* snb, int t) {
+  const int a = t % kTile, b = (t / kTile) % kTile, c = t / (kTile * kTile);
+  const int nb = snb[((c + 3) >> 2) * 9 + ((b + 3) >> 2) * 3 + ((a + 3) >> 2)];
+  if (nb < 0) return -1;
+  return nb * kNodesPerBlock + (((c + 3) & 3) << 4) + (((b + 3) & 3) << 2) + ((a + 3) & 3);
+}
+
+// G2P from the shared tile: v_hat = sum N v_i, Ch_hat = 2 sum N v_i (x) d,
+// sum-factorised over x, then y, then z.
+template <class T, bool AFF>
+__device__ __forceinline__ void g2p_tile(const V4<T>* sv, int base, const T wx[4], const T dx[4],
+                                         const T wy[4], const T dy[4], const T wz[4],
+                                         const T dz[4], T hv[3], T hC[9]) {
+  T s0[3] = {0, 0, 0}, sx[3] = {0, 0, 0}, sy[3] = {0, 0, 0}, sz[3] = {0, 0, 0};
+  T wdx[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) wdx[k] = wx[k] * dx[k];
+#pragma unroll
+  for (int kz = 0; kz < 4; ++kz) {
+#pragma unroll
+    for (int ky = 0; ky < 4; ++ky) {
+      T ax[3] = {0, 0, 0}, adx[3] = {0, 0, 0};
+#pragma unroll
+      for (int kx = 0; kx < 4; ++kx) {
+        const V4<T> g = sv[base + kz * (kTile * kTile) + ky * kTile + kx];
+        ax[0] += wx[kx] * g.x;
+        ax[1] += wx[kx] * g.y;
+        ax[2] += wx[kx] * g.z;
+        if (AFF) {
+          adx[0] += wdx[kx] * g.x;
+          adx[1] += wdx[kx] * g.y;
+          adx[2] += wdx[kx] * g.z;
+        }
+      }
+      const T wyz = wy[ky] * wz[kz];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) s0[a] += wyz * ax[a];
+      if (AFF) {
+        const T wyzdy = wyz * dy[ky], wyzdz = wyz * dz[kz];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          sx[a] += wyz * adx[a];
+          sy[a] += wyzdy * ax[a];
+          sz[a] += wyzdz * ax[a];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    hv[a] = s0[a];
+    hC[3 * a + 0] = T(2) * sx[a];
+    hC[3 * a + 1] = T(2) * sy[a];
+    hC[3 * a + 2] = T(2) * sz[a];
+  }
+}
+
+// Quadratic B-spline weight of one node row k (0..3, i.e. node i-1+k) as a
+// polynomial in t, N_k(t) = c0 + c1 t + c2 t^2 (the App. B functions expanded).
+template <class T>
+__device__ __forceinline__ void row_poly(int k, T& c0, T& c1, T& c2) {
+  c0 = k == 0 ? T(0.25) : k == 1 ? T(0.5) : k == 2 ? T(0.25) : T(0);
+  c1 = k == 0 ? T(-0.5) : k == 2 ? T(0.5) : T(0);
+  c2 = k == 0 ? T(0.25) : k == 3 ? T(0.25) : T(-0.25);
+}
+
+__device__ __forceinline__ void flush_mom(float*, V4<float>* gp, V4<double>* gp64,
+                                          const uint32_t* gmask, int node, float x, float y,
+                                          float z) {
+  if (gp64 != nullptr && __popc(gmask[node]) >= 2) {
+    atomicAdd(&gp64[node].x, (double)x);
+    atomicAdd(&gp64[node].y, (double)y);
+    atomicAdd(&gp64[node].z, (double)z);
+  } else {
+    atomicAdd(reinterpret_cast<float4*>(&gp[node]), make_float4(x, y, z, 0.f));
+  }
+}
+__device__ __forceinline__ void flush_mom(double*, V4<double>* gp, V4<double>*, const uint32_t*,
+                                          int node, double x, double y, double z) {
+  atomicAdd(&gp[node].x, x);
+  atomicAdd(&gp[node].y, y);
+  atomicAdd(&gp[node].z, z);
+}
+
+// One work item = up to kChunk sorted particles of one body whose cells lie
+// in one grid block.  A CTA of kChunk threads runs it in two phases:
+//
+//  phase 1, one thread per particle (lanes sorted by cell, so neighbouring
+//    lanes read the same tile nodes): G2P from the 7^3-node shared tile of
+//    grid velocities, the Sec. 2.3 series update of Delta, the Sec. 2.4
+//    projection giving W, and a stash of (t, m, W) in shared memory;
+//  phase 2, cell-centric P2G: each half-warp walks 16 consecutive stashed
+//    particles; lane (ky, kz) owns stencil row (., ky, kz) of the current
+//    cell and keeps its 4 nodes x 3 components in registers, adding them to
+//    the shared P2G tile only when the cell changes.  No two lanes of a
+//    half-warp ever add to the same node.
+//
+// The shared P2G tile is then added to the global grid (FP64 at nodes that
+// two or more bodies touch, on the FP32 path).
+template <class T, int MODE>
+__global__ void __launch_bounds__(kChunk, 4) k_items(const IterParams<T> p) {
+  constexpr bool kG2P = MODE == kModeFirst || MODE == kModeMid || MODE == kModeLast || MODE == kModeOnly;
+  constexpr bool kP2G = MODE == kModeMass || MODE == kModeP2GV || MODE == kModeFirst || MODE == kModeMid;
+  constexpr int kComp = MODE == kModeMass ? 1 : 3;
+  __shared__ V4<T> sv[kG2P ? kTile3 : 1];
+  __shared__ T sacc[kP2G ? kComp : 1][kTile3];
+  __shared__ V4<T> stash[kP2G ? 4 : 1][kP2G ? kChunk : 1];
+  __shared__ int sloc[kChunk];
+  __shared__ int snb[27];
+  const int tid = threadIdx.x;
+  const int n = p.n_particles;
+  const int item = blockIdx.x;
+  if (item >= p.n_items) return;
+  const int2 info = p.item_info[item];
+  const int bx = info.x % p.box.nx;
+  const int by = (info.x / p.box.nx) % p.box.ny;
+  const int bz = info.x / (p.box.nx * p.box.ny);
+  const int body = info.y;
+  const int s0 = p.item_start[item];
+  const int s1 = item + 1 < p.n_items ? p.item_start[item + 1] : n;
+  const int count = s1 - s0;  // <= kChunk
+  if (tid < 27) {
+    const int ox = tid % 3 - 1, oy = (tid / 3) % 3 - 1, oz = tid / 9 - 1;
+    snb[tid] = p.page[((bz + oz) * p.box.ny + (by + oy)) * p.box.nx + (bx + ox)];
+  }
+  if (kP2G)
+    for (int t = tid; t < kTile3; t += kChunk)
+#pragma unroll
+      for (int a = 0; a < kComp; ++a) sacc[a][t] = T(0);
+  __syncthreads();
+  if (kG2P) {
+    for (int t = tid; t < kTile3; t += kChunk) {
+      const int node = tile_node(snb, t);
+      sv[t] = node >= 0 ? p.gv[node] : V4<T>{T(0), T(0), T(0), T(0)};
+    }
+    __syncthreads();
+  }
+
+  // ---------------- phase 1: one thread per particle ----------------
+  if (tid < count) {
+    const int s = s0 + tid;
+    const V4<T> pt = p.pt[s];
+    const V4<T> pn = p.pn[s];
+    const uint32_t loc = to_bits(pn.w);
+    const int base = (int)(loc >> 4) * (kTile * kTile) + (int)((loc >> 2) & 3) * kTile + (int)(loc & 3);
+    sloc[tid] = base;
+    if (MODE == kModeMu) {
+      // mu_p = sum_{b' != b} mu(b,b') M_b'p / sum_{b' != b} M_b'p with
+      // M_b'p = sum_i N_ip m_{b',i}; mu(b,b) when no other body is near.
+      T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4];
+      bspline(pt.x, wx, dx);
+      bspline(pt.y, wy, dy);
+      bspline(pt.z, wz, dz);
+      T num = T(0), den = T(0);
+      const uint32_t own = 1u << body;
+#pragma unroll 1
+      for (int q = 0; q < 64; ++q) {
+        const int kx = q & 3, ky = (q >> 2) & 3, kz = q >> 4;
+        const int node = tile_node(snb, base + kz * (kTile * kTile) + ky * kTile + kx);
+        if (node < 0) continue;
+        uint32_t other = p.gmask[node] & ~own;
+        if (!other) continue;
+        T wxk = kx == 0 ? wx[0] : kx == 1 ? wx[1] : kx == 2 ? wx[2] : wx[3];
+        T wyk = ky == 0 ? wy[0] : ky == 1 ? wy[1] : ky == 2 ? wy[2] : wy[3];
+        T wzk = kz == 0 ? wz[0] : kz == 1 ? wz[1] : kz == 2 ? wz[2] : wz[3];
+        const T w = wxk * wyk * wzk;
+        while (other) {
+          const int bo = __ffs(other) - 1;
+          other &= other - 1;
+          const T M = p.gmb[(int64_t)bo * p.n_nodes + node];
+          num += w * p.mu_pair[body * p.n_bodies + bo] * M;
+          den += w * M;
+        }
+      }
+      p.mup_out[s] = den > T(0) ? num / den : p.mu_pair[body * p.n_bodies + body];
+    } else if (MODE == kModeMass) {
+      stash[0][tid] = pt;
+    } else if (MODE == kModeP2GV) {
+      stash[0][tid] = pt;
+      stash[1][tid] = p.V[s];
+      stash[2][tid] = p.V[n + s];
+      stash[3][tid] = p.V[2 * n + s];
+    } else {
+      T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4];
+      bspline(pt.x, wx, dx);
+      bspline(pt.y, wy, dy);
+      bspline(pt.z, wz, dz);
+      T hv[3], hC[9];
+      if (p.pic)
+        g2p_tile<T, false>(sv, base, wx, dx, wy, dy, wz, dz, hv, hC);
+      else
+        g2p_tile<T, true>(sv, base, wx, dx, wy, dy, wz, dz, hv, hC);
+      const T nrm[3] = {pn.x, pn.y, pn.z};
+      const T mu = p.mup ? p.mup[s] : p.mu;
+      T dv[3], dC[9];
+      bool out = false;
+      if (MODE == kModeFirst || MODE == kModeOnly) {
+        // Delta_0 = H V - V
+        T v[3], C[9];
+        load12(p.V, n, s, v, C);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dv[a] = hv[a] - v[a];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) dC[a] = p.pic ? T(0) : hC[a] - C[a];
+        out = MODE == kModeOnly;
+      } else {
+        // Delta_m = Delta_{m-1} + H W_m - W_m, W_m recomputed from Delta_{m-1}
+        T pv[3], pC[9], wv[3], wC[9];
+        load12(p.D, n, s, pv, pC);
+        undesirable(pv, pC, nrm, mu, p.sep23, wv, wC);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dv[a] = pv[a] + hv[a] - wv[a];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) dC[a] = p.pic ? T(0) : pC[a] + hC[a] - wC[a];
+        out = MODE == kModeLast;
+      }
+      if (out) {
+        // V_hat = V + Delta_N, back in caller order, C = Ch / h
+        T v[3], C[9];
+        load12(p.V, n, s, v, C);
+        const int64_t idx = p.perm[s];
+        T* vo = static_cast<T*>(p.v_out);
+        T* Co = static_cast<T*>(p.C_out);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) vo[3 * idx + a] = v[a] + dv[a];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) Co[9 * idx + a] = (C[a] + dC[a]) * p.inv_h;
+      } else {
+        store12(p.D, n, s, dv, dC);
+        T u[3], uC[9];
+        undesirable(dv, dC, nrm, mu, p.sep23, u, uC);
+        stash[0][tid] = pt;
+        stash[1][tid] = V4<T>{u[0], u[1], u[2], uC[0]};
+        stash[2][tid] = V4<T>{uC[1], uC[2], uC[3], uC[4]};
+        stash[3][tid] = V4<T>{uC[5], uC[6], uC[7], uC[8]};
+      }
+    }
+  }
+  if (!kP2G) return;
+  __syncthreads();
+
+  // ---------------- phase 2: cell-centric P2G ----------------
+  {
+    const int hw = tid >> 4, lane = tid & 15;
+    const int ky = lane & 3, kz = lane >> 2;
+    T cy0, cy1, cy2, cz0, cz1, cz2;
+    row_poly(ky, cy0, cy1, cy2);
+    row_poly(kz, cz0, cz1, cz2);
+    const T oy = T(ky - 1), oz = T(kz - 1);
+    const bool aff = !p.pic;
+    T acc[4][kComp];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int a = 0; a < kComp; ++a) acc[k][a] = T(0);
+    int cur = -1;
+    const int j0 = hw * 16, j1 = min(j0 + 16, count);
+    auto flush = [&](int base) {
+      const int row = base + kz * (kTile * kTile) + ky * kTile;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int a = 0; a < kComp; ++a) {
+          atomicAdd(&sacc[a][row + k], acc[k][a]);
+          acc[k][a] = T(0);
+        }
+    };
+    for (int j = j0; j < j1; ++j) {
+      const int base = sloc[j];
+      if (base != cur) {
+        if (cur >= 0) flush(cur);
+        cur = base;
+      }
+      const V4<T> a = stash[0][j];
+      const T wyzm = a.w * (cy0 + a.y * (cy1 + a.y * cy2)) * (cz0 + a.z * (cz1 + a.z * cz2));
+      T wx[4], dx[4];
+      bspline(a.x, wx, dx);
+      if (MODE == kModeMass) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k][0] += wyzm * wx[k];
+      } else {
+        const V4<T> w0 = stash[1][j], w1 = stash[2][j], w2 = stash[3][j];
+        // W = (u, Ch) with Ch rows (w0.w w1.x w1.y) (w1.z w1.w w2.x) (w2.y w2.z w2.w)
+        const T dy = oy - a.y, dz = oz - a.z;
+        T b[3], c0[3];
+        if (aff) {
+          b[0] = w0.x + w1.x * dy + w1.y * dz;
+          b[1] = w0.y + w1.w * dy + w2.x * dz;
+          b[2] = w0.z + w2.z * dy + w2.w * dz;
+          c0[0] = w0.w;
+          c0[1] = w1.z;
+          c0[2] = w2.y;
+        } else {
+          b[0] = w0.x;
+          b[1] = w0.y;
+          b[2] = w0.z;
+          c0[0] = c0[1] = c0[2] = T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const T w = wyzm * wx[k];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) acc[k][c] += w * (b[c] + c0[c] * dx[k]);
+        }
+      }
+    }
+    if (cur >= 0) flush(cur);
+  }
+  __syncthreads();
+
+  // ---------------- add the tile to the global grid ----------------
+  for (int t = tid; t < kTile3; t += kChunk) {
+    const int node = tile_node(snb, t);
+    if (node < 0) continue;
+    if (MODE == kModeMass) {
+      const T mv = sacc[0][t];
+      if (mv != T(0)) {
+        atomicAdd(&p.gm[node], mv);
+        atomicOr(&p.gmask[node], 1u << body);
+        if (p.gmb) atomicAdd(&p.gmb[(int64_t)body * p.n_nodes + node], mv);
+      }
+    } else {
+      const T x = sacc[0][t], y = sacc[kComp > 1 ? 1 : 0][t], z = sacc[kComp > 2 ? 2 : 0][t];
+      if (x != T(0) || y != T(0) || z != T(0))
+        flush_mom(static_cast<T*>(nullptr), p.gp, p.gp64, p.gmask, node, x, y, z);
+    }
+  }
+}
+
+// v_i = p_i / m_i (0 where m_i = 0), then clear p_i for the next pass.
+// Nodes that two or more bodies touch take their momentum from the FP64
+// accumulators (FP32 path).
+template <class T>
+__global__ void k_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask, V4<T>* gp,
+                            V4<double>* gp64, V4<T>* gv) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  const T m = gm[i];
+  V4<T> v{T(0), T(0), T(0), T(0)};
+  if (gp64 != nullptr && __popc(gmask[i]) >= 2) {
+    const V4<double> q = gp64[i];
+    if (m > T(0)) {
+      const double md = (double)m;
+      v = V4<T>{(T)(q.x / md), (T)(q.y / md), (T)(q.z / md), T(0)};
+    }
+    gp64[i] = V4<double>{0.0, 0.0, 0.0, 0.0};
+  } else {
+    const V4<T> q = gp[i];
+    if (m > T(0)) v = V4<T>{q.x / m, q.y / m, q.z / m, T(0)};
+  }
+  gp[i] = V4<T>{T(0), T(0), T(0), T(0)};
+  gv[i] = v;
+}
+
+template <class T>
+__device__ __forceinline__ bool bad_mass(T m) {
+  return !(m > T(0)) || !isfinite((double)m);
+}
+
+template <class T>
+__global__ void k_cells(int64_t n, const double* __restrict__ x, const int32_t* __restrict__ body,
+                        const T* __restrict__ m, double inv_h, int n_bodies, int4* cellb,
+                        DevScalars* ds) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+  int err = 0;
+  if (p < n) {
+    int c[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double xs = x[3 * p + d] * inv_h;
+      // |x/h| < 2^29 keeps cells, blocks and their margins inside int32
+      if (!(fabs(xs) < 536870912.0)) {
+        err |= kErrPos;
+        c[d] = 0;
+      } else {
+        c[d] = (int)floor(xs);
+      }
+      lo[d] = hi[d] = c[d] >> 2;
+    }
+    const int b = body[p];
+    if (b < 0 || b >= n_bodies) err |= kErrBody;
+    if (bad_mass(m[p])) err |= kErrMass;
+    cellb[p] = make_int4(c[0], c[1], c[2], b);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], off));
+      hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], off));
+    }
+    err |= __shfl_xor_sync(0xffffffffu, err, off);
+  }
+  // block reduction, then one set of atomics per block
+  __shared__ int red[7][32];
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      red[d][w] = lo[d];
+      red[3 + d][w] = hi[d];
+    }
+    red[6][w] = err;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int l = threadIdx.x;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = l < nw ? red[d][l] : INT32_MAX;
+      hi[d] = l < nw ? red[3 + d][l] : INT32_MIN;
+    }
+    err = l < nw ? red[6][l] : 0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], off));
+        hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], off));
+      }
+      err |= __shfl_xor_sync(0xffffffffu, err, off);
+    }
+    if (l == 0 && lo[0] != INT32_MAX) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        atomicMin(&ds->bbox[d], lo[d]);
+        atomicMax(&ds->bbox[3 + d], hi[d]);
+      }
+      if (err) atomicOr(&ds->err, err);
+    }
+  }
+}
+
+template <class K>
+__global__ void k_keys(int64_t n, const int4* __restrict__ cellb, Box box, int n_bodies, K* keys,
+                       int* vals) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int4 c = cellb[p];
+  const int bx = (c.x >> 2) - box.ox, by = (c.y >> 2) - box.oy, bz = (c.z >> 2) - box.oz;
+  const int64_t blin = ((int64_t)bz * box.ny + by) * box.nx + bx;
+  const uint32_t loc = (uint32_t)(((c.z & 3) << 4) | ((c.y & 3) << 2) | (c.x & 3));
+  keys[p] = (K)((((uint64_t)blin * (uint64_t)n_bodies + (uint64_t)c.w) << 6) | loc);
+  vals[p] = (int)p;
+}
+
+template <class T>
+__global__ void k_gather(int64_t n, const int* __restrict__ perm, const int4* __restrict__ cellb,
+                         const double* __restrict__ x, const T* __restrict__ v,
+                         const T* __restrict__ C, const T* __restrict__ m,
+                         const T* __restrict__ nrm, double h, double inv_h, V4<T>* pt, V4<T>* pn,
+                         V4<T>* V) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int64_t i = perm[s];
+  const int4 c = cellb[i];
+  const T tx = (T)(x[3 * i + 0] * inv_h - (double)c.x);
+  const T ty = (T)(x[3 * i + 1] * inv_h - (double)c.y);
+  const T tz = (T)(x[3 * i + 2] * inv_h - (double)c.z);
+  pt[s] = V4<T>{tx, ty, tz, m[i]};
+  const uint32_t loc = (uint32_t)(((c.z & 3) << 4) | ((c.y & 3) << 2) | (c.x & 3));
+  pn[s] = V4<T>{nrm[3 * i + 0], nrm[3 * i + 1], nrm[3 * i + 2], bits_to(T(0), loc)};
+  const T hh = (T)h;
+  T vv[3], Ch[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) vv[a] = v[3 * i + a];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) Ch[a] = C[9 * i + a] * hh;
+  store12(V, (int)n, (int)s, vv, Ch);
+}
+
+template <class K>
+__global__ void k_heads(int64_t n, const K* __restrict__ keys, int* flags) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  // a new item at every (grid block, body) change and every kChunk particles
+  flags[s] = (s % kChunk == 0 || (keys[s] >> 6) != (keys[s - 1] >> 6)) ? 1 : 0;
+}
+
+template <class K>
+__global__ void k_item_info(const int* __restrict__ item_start, const int* __restrict__ n_items,
+                            const K* __restrict__ keys, int n_bodies, int2* info) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *n_items) return;
+  const uint64_t q = (uint64_t)(keys[item_start[i]] >> 6);
+  info[i] = make_int2((int)(q / (uint64_t)n_bodies), (int)(q % (uint64_t)n_bodies));
+}
+
+// Mark every grid block a particle's 4x4x4-node stencil reaches.
+__global__ void k_mark(int64_t n, const int4* __restrict__ cellb, Box box, int* flags) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int4 c = cellb[p];
+  const int x0 = ((c.x - 1) >> 2) - box.ox, x1 = ((c.x + 2) >> 2) - box.ox;
+  const int y0 = ((c.y - 1) >> 2) - box.oy, y1 = ((c.y + 2) >> 2) - box.oy;
+  const int z0 = ((c.z - 1) >> 2) - box.oz, z1 = ((c.z + 2) >> 2) - box.oz;
+  for (int bz = z0; bz <= z1; ++bz)
+    for (int by = y0; by <= y1; ++by)
+      for (int bx = x0; bx <= x1; ++bx)
+        flags[((int64_t)bz * box.ny + by) * box.nx + bx] = 1;
+}
+
+// Stream compaction after an exclusive scan of 0/1 flags: list the flagged
+// indices in order, optionally write each index's compact id (or -1) into
+// `page`, and store the count.
+__global__ void k_compact(int64_t n, const int* __restrict__ flags, const int* __restrict__ offs,
+                          int* list, int* page, int* count) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int f = flags[i], o = offs[i];
+  if (f) list[o] = (int)i;
+  if (page) page[i] = f ? o : -1;
+  if (i == n - 1) *count = o + f;
+}
+
+// FP64 totals P = sum m v and L = sum m [x cross v + (h^2/2) axial(C)].
+template <class T>
+__global__ void k_momentum(int64_t n, const double* __restrict__ x, const T* __restrict__ v,
+                           const T* __restrict__ C, const T* __restrict__ m, double h2half,
+                           double* out6) {
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const double mm = (double)m[p];
+    const double x0 = x[3 * p], x1 = x[3 * p + 1], x2 = x[3 * p + 2];
+    const double v0 = (double)v[3 * p], v1 = (double)v[3 * p + 1], v2 = (double)v[3 * p + 2];
+    const T* c = C + 9 * p;
+    acc[0] += mm * v0;
+    acc[1] += mm * v1;
+    acc[2] += mm * v2;
+    acc[3] += mm * (x1 * v2 - x2 * v1 + h2half * ((double)c[7] - (double)c[5]));
+    acc[4] += mm * (x2 * v0 - x0 * v2 + h2half * ((double)c[2] - (double)c[6]));
+    acc[5] += mm * (x0 * v1 - x1 * v0 + h2half * ((double)c[3] - (double)c[1]));
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+  __shared__ double red[6][32];
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) red[k][w] = acc[k];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      double v = threadIdx.x < nw ? red[k][threadIdx.x] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (threadIdx.x == 0) atomicAdd(&out6[k], v);
+    }
+  }
+}
+
+__global__ void k_count_multibody(int64_t n_nodes, const uint32_t* __restrict__ gmask,
+                                  unsigned long long* out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool mb = i < n_nodes && __popc(gmask[i]) >= 2;
+  const unsigned ball = __ballot_sync(0xffffffffu, mb);
+  if ((threadIdx.x & 31) == 0 && ball) atomicAdd(out, (unsigned long long)__popc(ball));
+}
+
+inline unsigned grid_for(int64_t n, int threads) {
+  return (unsigned)((n + threads - 1) / threads);
+}
+
+}  // namespace
+
+template <class T>
+cudaError_t launch_cells(int64_t n, const double* x, const int32_t* body, const T* m, double inv_h,
+                         int n_bodies, int4* cellb, DevScalars* ds, cudaStream_t s) {
+  k_cells<T><<<grid_for(n, 256), 256, 0, s>>>(n, x, body, m, inv_h, n_bodies, cellb, ds);
+  return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t launch_keys(int64_t n, const int4* cellb, Box box, int n_bodies, K* keys, int* vals,
+                        cudaStream_t s) {
+  k_keys<K><<<grid_for(n, 256), 256, 0, s>>>(n, cellb, box, n_bodies, keys, vals);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_gather(int64_t n, const int* perm, const int4* cellb, const double* x, const T* v,
+                          const T* C, const T* m, const T* nrm, double h, double inv_h, V4<T>* pt,
+                          V4<T>* pn, V4<T>* V, cudaStream_t s) {
+  k_gather<T><<<grid_for(n, 256), 256, 0, s>>>(n, perm, cellb, x, v, C, m, nrm, h, inv_h, pt, pn, V);
+  return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t launch_heads(int64_t n, const K* keys, int* flags, cudaStream_t s) {
+  k_heads<K><<<grid_for(n, 256), 256, 0, s>>>(n, keys, flags);
+  return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t launch_item_info(const int* item_start, const int* n_items, const K* keys, int n_bodies,
+                             int2* item_info, int max_items, cudaStream_t s) {
+  k_item_info<K><<<grid_for(max_items, 256), 256, 0, s>>>(item_start, n_items, keys, n_bodies, item_info);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mark(int64_t n, const int4* cellb, Box box, int* flags, cudaStream_t s) {
+  k_mark<<<grid_for(n, 256), 256, 0, s>>>(n, cellb, box, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* list, int* page,
+                           int* count, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_compact<<<grid_for(n, 256), 256, 0, s>>>(n, flags, offs, list, page, count);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_items(const IterParams<T>& p, int mode, int threads, cudaStream_t s) {
+  if (p.n_items <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)p.n_items;
+  (void)threads;
+  switch (mode) {
+    case kModeMass: k_items<T, kModeMass><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeP2GV: k_items<T, kModeP2GV><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeFirst: k_items<T, kModeFirst><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeMid: k_items<T, kModeMid><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeLast: k_items<T, kModeLast><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeOnly: k_items<T, kModeOnly><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeMu: k_items<T, kModeMu><<<grid, kChunk, 0, s>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask, V4<T>* gp,
+                             V4<double>* gp64, V4<T>* gv, cudaStream_t s) {
+  if (n_nodes <= 0) return cudaSuccess;
+  k_normalize<T><<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, gm, gmask, gp, gp64, gv);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_momentum(int64_t n, const double* x, const T* v, const T* C, const T* m, double h,
+                            double* out6, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  unsigned g = grid_for(n, 256);
+  if (g > 608) g = 608;
+  k_momentum<T><<<g, 256, 0, s>>>(n, x, v, C, m, 0.5 * h * h, out6);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_multibody(int64_t n_nodes, const uint32_t* gmask, unsigned long long* out,
+                                   cudaStream_t s) {
+  if (n_nodes <= 0) return cudaSuccess;
+  k_count_multibody<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, gmask, out);
+  return cudaGetLastError();
+}
+
+#define APIC_INST_T(T)                                                                            \
+  template cudaError_t launch_cells<T>(int64_t, const double*, const int32_t*, const T*, double, \
+                                       int, int4*, DevScalars*, cudaStream_t);                    \
+  template cudaError_t launch_gather<T>(int64_t, const int*, const int4*, const double*,          \
+                                        const T*, const T*, const T*, const T*, double, double,   \
+                                        V4<T>*, V4<T>*, V4<T>*, cudaStream_t);                     \
+  template cudaError_t launch_items<T>(const IterParams<T>&, int, int, cudaStream_t);             \
+  template cudaError_t launch_normalize<T>(int64_t, const T*, const uint32_t*, V4<T>*,            \
+                                           V4<double>*, V4<T>*, cudaStream_t);                    \
+  template cudaError_t launch_momentum<T>(int64_t, const double*, const T*, const T*, const T*,   \
+                                          double, double*, cudaStream_t);
+APIC_INST_T(float)
+APIC_INST_T(double)
+
+#define APIC_INST_K(K)                                                                          \
+  template cudaError_t launch_keys<K>(int64_t, const int4*, Box, int, K*, int*, cudaStream_t);  \
+  template cudaError_t launch_heads<K>(int64_t, const K*, int*, cudaStream_t);              \
+  template cudaError_t launch_item_info<K>(const int*, const int*, const K*, int, int2*, int,   \
+                                           cudaStream_t);
+APIC_INST_K(uint32_t)
+APIC_INST_K(uint64_t)
+
+}  // namespace apic
