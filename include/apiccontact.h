@@ -144,6 +144,31 @@ apic_status apic_destroy(apic_ctx* ctx);
  * non-finite or out-of-range positions) returns INVALID_ARG. */
 apic_status apic_contact_step(apic_ctx* ctx, const apic_step_args* args, void* stream, apic_stats* stats);
 
+/* The contact step for callers that cannot allocate device memory.
+ * (The paper has no counterpart; this is a deployment variant.)
+ *
+ * Some hosts may not call cudaMalloc during a step: an application whose own
+ * memory pool has already reserved (nearly) all of the GPU and hands out
+ * nothing else, or a real-time loop that cannot afford the device-wide
+ * synchronisation cudaMalloc and cudaFree imply.  This call computes exactly
+ * what apic_contact_step computes, on the same apic_step_args and apic_stats,
+ * but takes every scratch buffer from one static device array of 32 MiB that
+ * the library defines (one per GPU that loads the library, held until the
+ * process exits).  It allocates nothing and needs no context.
+ *   - Device pointers only (APIC_HOST_PTRS is rejected).
+ *   - A scene whose scratch would exceed the 32 MiB array (roughly 100,000
+ *     FP32 particles in compact bodies; fewer for sparse scenes or FP64) is
+ *     rejected with APIC_ERR_INVALID_ARG and a message naming the limit.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins.
+ *   - Every call uses the same array and leaves its data there; each call
+ *     clears what must start at zero.  Calls whose GPU work overlaps (other
+ *     streams, other host threads) race on the array: serialise them.
+ *   - Synchronises the stream twice while sizing the grid, and at the end
+ *     when stats is non-NULL.  Errors are reported by apic_last_error(). */
+apic_status apic_contact_step_static(const apic_step_args* args, void* stream, apic_stats* stats);
+
 /* Turn kernel timing on (1) or off (0) and reset the counters. */
 apic_status apic_set_profiling(apic_ctx* ctx, int32_t on);
 

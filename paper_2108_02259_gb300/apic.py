@@ -32,7 +32,7 @@ APIC_VARIANT_SEP23 = 1 << 3
 
 EXPORTED = [
     "apic_last_error", "apic_version", "apic_create", "apic_destroy", "apic_contact_step",
-    "apic_set_profiling", "apic_get_profile", "apic_scratch_bytes",
+    "apic_set_profiling", "apic_get_profile", "apic_scratch_bytes", "apic_contact_step_static",
 ]
 
 
@@ -89,6 +89,8 @@ def load(path: str = LIB_PATH):
     lib.apic_create.argtypes = [C.POINTER(P), C.c_int32, C.c_size_t]
     lib.apic_destroy.argtypes = [P]
     lib.apic_contact_step.argtypes = [P, C.POINTER(StepArgs), P, C.POINTER(Stats)]
+    lib.apic_contact_step_static.argtypes = [C.POINTER(StepArgs), P, C.POINTER(Stats)]
+    lib.apic_contact_step_static.restype = C.c_int32
     lib.apic_set_profiling.argtypes = [P, C.c_int32]
     lib.apic_get_profile.argtypes = [P, C.POINTER(Profile)]
     lib.apic_scratch_bytes.argtypes = [P, C.POINTER(C.c_size_t)]
@@ -221,4 +223,38 @@ def contact_step(ctx: Context, x, v, Cm, m, nrm, body, h: float, mu: float, n_it
                  _ptr(v_out), _ptr(C_out), float(h), float(mu), None if mp is None else mp.ctypes.data, int(flags))
     st = Stats() if stats else None
     _check(lib.apic_contact_step(ctx.handle, C.byref(a), sptr, C.byref(st) if stats else None))
+    return StepResult(v_out, C_out, st.as_dict() if stats else None)
+
+
+def contact_step_static(x, v, Cm, m, nrm, body, h: float, mu: float, n_iter: int, n_bodies: int | None = None,
+                        mu_pair=None, flags: int = 0, v_out=None, C_out=None, stream=None,
+                        stats: bool = False) -> StepResult:
+    """apic_contact_step_static: the same step with no device allocation at all
+    (scratch from the library's fixed static device array).  Torch CUDA
+    tensors only, same layouts as contact_step."""
+    import torch
+
+    lib = load()
+    n = int(x.shape[0])
+    dt = v.dtype
+    for t in (x, v, Cm, m, nrm, body):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("apic_contact_step_static wants contiguous CUDA tensors")
+    if dt == torch.float64:
+        flags |= APIC_FP64
+    if v_out is None:
+        v_out = torch.empty_like(v)
+    if C_out is None:
+        C_out = torch.empty_like(Cm)
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    if n_bodies is None:
+        n_bodies = (int(body.max()) + 1) if n else 1
+    mp = None
+    if mu_pair is not None:
+        mp = np.ascontiguousarray(np.asarray(mu_pair, np.float64).reshape(n_bodies, n_bodies))
+    a = StepArgs(n, int(n_bodies), int(n_iter), _ptr(body), _ptr(x), _ptr(v), _ptr(Cm), _ptr(m), _ptr(nrm),
+                 _ptr(v_out), _ptr(C_out), float(h), float(mu), None if mp is None else mp.ctypes.data, int(flags))
+    st = Stats() if stats else None
+    _check(lib.apic_contact_step_static(C.byref(a), stream.cuda_stream, C.byref(st) if stats else None))
     return StepResult(v_out, C_out, st.as_dict() if stats else None)

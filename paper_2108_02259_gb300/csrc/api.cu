@@ -61,6 +61,8 @@ constexpr int64_t kMaxPageEntries = int64_t(1) << 28;  // dense page table limit
 
 }  // namespace
 
+void apic::set_last_error(const char* msg) { g_last_error = msg; }
+
 struct apic_ctx {
   int device = 0;
   int num_sms = 0;

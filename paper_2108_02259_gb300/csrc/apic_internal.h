@@ -117,6 +117,9 @@ cudaError_t launch_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask
 template <class T>
 cudaError_t launch_momentum(int64_t n, const double* x, const T* v, const T* C, const T* m, double h,
                             double* out6, cudaStream_t s);
+// Set the calling thread's message returned by apic_last_error().
+void set_last_error(const char* msg);
+
 cudaError_t launch_count_multibody(int64_t n_nodes, const uint32_t* gmask,
                                    unsigned long long* out, cudaStream_t s);
 
