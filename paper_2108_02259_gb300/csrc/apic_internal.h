@@ -21,7 +21,10 @@ constexpr int kTile = 7;
 constexpr int kTile3 = kTile * kTile * kTile;
 constexpr int kNodesPerBlock = kBlk * kBlk * kBlk;
 // A work item holds at most kChunk particles (one per thread of its CTA).
-constexpr int kChunk = 128;
+#ifndef APIC_CHUNK
+#define APIC_CHUNK 128
+#endif
+constexpr int kChunk = APIC_CHUNK;
 
 // Error bits raised by the validation pass.
 constexpr int kErrBody = 1;

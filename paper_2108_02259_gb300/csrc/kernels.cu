@@ -16,6 +16,11 @@
 
 #include "apic_internal.h"
 
+// Resident CTAs per SM the fused kernel is compiled for (register cap).
+#ifndef APIC_ITEMS_MIN_BLOCKS
+#define APIC_ITEMS_MIN_BLOCKS 8
+#endif
+
 namespace apic {
 namespace {
 
@@ -92,13 +97,30 @@ __device__ __forceinline__ void store12(V4<T>* planes, int n, int s, const T v[3
   planes[2 * n + s] = V4<T>{C[5], C[6], C[7], C[8]};
 }
 
-// Node index of tile node t (tile coordinates (a, b, c) in [0,7)^3 relative
-// to node 4B-1), or -1 when its block is not active.
+// Tile node t = (a, b, c) in [0,7)^3, relative to node 4B-1 of the item's
+// block B, lies in neighbour block ((a+3)>>2, (b+3)>>2, (c+3)>>2) of the
+// 3x3x3 around B at local node ((a+3)&3, (b+3)&3, (c+3)&3).  The table packs
+// (neighbour << 6 | local) for all 343 tile nodes.
+struct TileTable {
+  unsigned short e[kTile3];
+};
+constexpr TileTable make_tile_table() {
+  TileTable t{};
+  for (int i = 0; i < kTile3; ++i) {
+    const int a = i % kTile, b = (i / kTile) % kTile, c = i / (kTile * kTile);
+    const int nb = ((c + 3) >> 2) * 9 + ((b + 3) >> 2) * 3 + ((a + 3) >> 2);
+    const int local = (((c + 3) & 3) << 4) | (((b + 3) & 3) << 2) | ((a + 3) & 3);
+    t.e[i] = (unsigned short)((nb << 6) | local);
+  }
+  return t;
+}
+__device__ const TileTable g_tile = make_tile_table();
+
+// Node index of tile node t, or -1 when its block is not active.
 __device__ __forceinline__ int tile_node(const int* snb, int t) {
-  const int a = t % kTile, b = (t / kTile) % kTile, c = t / (kTile * kTile);
-  const int nb = snb[((c + 3) >> 2) * 9 + ((b + 3) >> 2) * 3 + ((a + 3) >> 2)];
-  if (nb < 0) return -1;
-  return nb * kNodesPerBlock + (((c + 3) & 3) << 4) + (((b + 3) & 3) << 2) + ((a + 3) & 3);
+  const int e = g_tile.e[t];
+  const int nb = snb[e >> 6];
+  return nb < 0 ? -1 : nb * kNodesPerBlock + (e & 63);
 }
 
 // G2P from the shared tile: v_hat = sum N v_i, Ch_hat = 2 sum N v_i (x) d,
@@ -178,6 +200,56 @@ __device__ __forceinline__ void flush_mom(double*, V4<double>* gp, V4<double>*, 
   atomicAdd(&gp[node].z, z);
 }
 
+// Phase-2 register accumulators of one lane: nodes kx = 0..3 of its stencil
+// row, K components.  A particle adds wx_k A_c + (wx_k dx_k) B_c to node k,
+// component c.  The FP32 form packs node pairs (0,1) and (2,3) into float2
+// and uses the paired FP32 FMA of sm_100+.
+template <class T, int K>
+struct RowAcc {
+  T a[4][K];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int c = 0; c < K; ++c) a[k][c] = T(0);
+  }
+  __device__ __forceinline__ void add(const V4<T>& X, const V4<T>& XD, const T* A, const T* B) {
+    const T wx[4] = {X.x, X.y, X.z, X.w}, wd[4] = {XD.x, XD.y, XD.z, XD.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int c = 0; c < K; ++c) a[k][c] += wx[k] * A[c] + (B ? wd[k] * B[c] : T(0));
+  }
+  __device__ __forceinline__ T get(int k, int c) const { return a[k][c]; }
+};
+
+template <int K>
+struct RowAcc<float, K> {
+  float2 a01[K], a23[K];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int c = 0; c < K; ++c) a01[c] = a23[c] = make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ void add(const V4<float>& X, const V4<float>& XD, const float* A, const float* B) {
+    const float2 x01 = make_float2(X.x, X.y), x23 = make_float2(X.z, X.w);
+    const float2 d01 = make_float2(XD.x, XD.y), d23 = make_float2(XD.z, XD.w);
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      const float2 Ac = make_float2(A[c], A[c]);
+      a01[c] = __ffma2_rn(x01, Ac, a01[c]);
+      a23[c] = __ffma2_rn(x23, Ac, a23[c]);
+      if (B) {
+        const float2 Bc = make_float2(B[c], B[c]);
+        a01[c] = __ffma2_rn(d01, Bc, a01[c]);
+        a23[c] = __ffma2_rn(d23, Bc, a23[c]);
+      }
+    }
+  }
+  __device__ __forceinline__ float get(int k, int c) const {
+    return k == 0 ? a01[c].x : k == 1 ? a01[c].y : k == 2 ? a23[c].x : a23[c].y;
+  }
+};
+
 // One work item = up to kChunk sorted particles of one body whose cells lie
 // in one grid block.  A CTA of kChunk threads runs it in two phases:
 //
@@ -194,13 +266,13 @@ __device__ __forceinline__ void flush_mom(double*, V4<double>* gp, V4<double>*, 
 // The shared P2G tile is then added to the global grid (FP64 at nodes that
 // two or more bodies touch, on the FP32 path).
 template <class T, int MODE>
-__global__ void __launch_bounds__(kChunk, 4) k_items(const IterParams<T> p) {
+__global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const IterParams<T> p) {
   constexpr bool kG2P = MODE == kModeFirst || MODE == kModeMid || MODE == kModeLast || MODE == kModeOnly;
   constexpr bool kP2G = MODE == kModeMass || MODE == kModeP2GV || MODE == kModeFirst || MODE == kModeMid;
   constexpr int kComp = MODE == kModeMass ? 1 : 3;
   __shared__ V4<T> sv[kG2P ? kTile3 : 1];
   __shared__ T sacc[kP2G ? kComp : 1][kTile3];
-  __shared__ V4<T> stash[kP2G ? 4 : 1][kP2G ? kChunk : 1];
+  __shared__ V4<T> stash[kP2G ? 6 : 1][kP2G ? kChunk : 1];
   __shared__ int sloc[kChunk];
   __shared__ int snb[27];
   const int tid = threadIdx.x;
@@ -215,6 +287,22 @@ __global__ void __launch_bounds__(kChunk, 4) k_items(const IterParams<T> p) {
   const int s0 = p.item_start[item];
   const int s1 = item + 1 < p.n_items ? p.item_start[item + 1] : n;
   const int count = s1 - s0;  // <= kChunk
+  // Issue this thread's particle loads first so that they are in flight
+  // while the CTA fetches its grid tile.
+  constexpr bool kReadD = MODE == kModeMid || MODE == kModeLast;
+  constexpr bool kReadV = MODE == kModeP2GV || MODE == kModeFirst || MODE == kModeOnly;
+  V4<T> pt{}, pn{}, q0{}, q1{}, q2{};
+  if (tid < count) {
+    const int s = s0 + tid;
+    pt = p.pt[s];
+    pn = p.pn[s];
+    if (kReadD || kReadV) {
+      const V4<T>* planes = kReadD ? p.D : p.V;
+      q0 = planes[s];
+      q1 = planes[n + s];
+      q2 = planes[2 * n + s];
+    }
+  }
   if (tid < 27) {
     const int ox = tid % 3 - 1, oy = (tid / 3) % 3 - 1, oz = tid / 9 - 1;
     snb[tid] = p.page[((bz + oz) * p.box.ny + (by + oy)) * p.box.nx + (bx + ox)];
@@ -235,8 +323,6 @@ __global__ void __launch_bounds__(kChunk, 4) k_items(const IterParams<T> p) {
   // ---------------- phase 1: one thread per particle ----------------
   if (tid < count) {
     const int s = s0 + tid;
-    const V4<T> pt = p.pt[s];
-    const V4<T> pn = p.pn[s];
     const uint32_t loc = to_bits(pn.w);
     const int base = (int)(loc >> 4) * (kTile * kTile) + (int)((loc >> 2) & 3) * kTile + (int)(loc & 3);
     sloc[tid] = base;
@@ -269,13 +355,17 @@ __global__ void __launch_bounds__(kChunk, 4) k_items(const IterParams<T> p) {
         }
       }
       p.mup_out[s] = den > T(0) ? num / den : p.mu_pair[body * p.n_bodies + body];
-    } else if (MODE == kModeMass) {
+    } else if (MODE == kModeMass || MODE == kModeP2GV) {
+      T wx[4], dx[4];
+      bspline(pt.x, wx, dx);
       stash[0][tid] = pt;
-    } else if (MODE == kModeP2GV) {
-      stash[0][tid] = pt;
-      stash[1][tid] = p.V[s];
-      stash[2][tid] = p.V[n + s];
-      stash[3][tid] = p.V[2 * n + s];
+      stash[4][tid] = V4<T>{wx[0], wx[1], wx[2], wx[3]};
+      stash[5][tid] = V4<T>{wx[0] * dx[0], wx[1] * dx[1], wx[2] * dx[2], wx[3] * dx[3]};
+      if (MODE == kModeP2GV) {
+        stash[1][tid] = q0;
+        stash[2][tid] = q1;
+        stash[3][tid] = q2;
+      }
     } else {
       T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4];
       bspline(pt.x, wx, dx);
@@ -292,8 +382,8 @@ __global__ void __launch_bounds__(kChunk, 4) k_items(const IterParams<T> p) {
       bool out = false;
       if (MODE == kModeFirst || MODE == kModeOnly) {
         // Delta_0 = H V - V
-        T v[3], C[9];
-        load12(p.V, n, s, v, C);
+        const T v[3] = {q0.x, q0.y, q0.z};
+        const T C[9] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
 #pragma unroll
         for (int a = 0; a < 3; ++a) dv[a] = hv[a] - v[a];
 #pragma unroll
@@ -301,8 +391,9 @@ __global__ void __launch_bounds__(kChunk, 4) k_items(const IterParams<T> p) {
         out = MODE == kModeOnly;
       } else {
         // Delta_m = Delta_{m-1} + H W_m - W_m, W_m recomputed from Delta_{m-1}
-        T pv[3], pC[9], wv[3], wC[9];
-        load12(p.D, n, s, pv, pC);
+        const T pv[3] = {q0.x, q0.y, q0.z};
+        const T pC[9] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+        T wv[3], wC[9];
         undesirable(pv, pC, nrm, mu, p.sep23, wv, wC);
 #pragma unroll
         for (int a = 0; a < 3; ++a) dv[a] = pv[a] + hv[a] - wv[a];
@@ -329,6 +420,8 @@ __global__ void __launch_bounds__(kChunk, 4) k_items(const IterParams<T> p) {
         stash[1][tid] = V4<T>{u[0], u[1], u[2], uC[0]};
         stash[2][tid] = V4<T>{uC[1], uC[2], uC[3], uC[4]};
         stash[3][tid] = V4<T>{uC[5], uC[6], uC[7], uC[8]};
+        stash[4][tid] = V4<T>{wx[0], wx[1], wx[2], wx[3]};
+        stash[5][tid] = V4<T>{wx[0] * dx[0], wx[1] * dx[1], wx[2] * dx[2], wx[3] * dx[3]};
       }
     }
   }
@@ -344,11 +437,8 @@ __global__ void __launch_bounds__(kChunk, 4) k_items(const IterParams<T> p) {
     row_poly(kz, cz0, cz1, cz2);
     const T oy = T(ky - 1), oz = T(kz - 1);
     const bool aff = !p.pic;
-    T acc[4][kComp];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int a = 0; a < kComp; ++a) acc[k][a] = T(0);
+    RowAcc<T, kComp> acc;
+    acc.zero();
     int cur = -1;
     const int j0 = hw * 16, j1 = min(j0 + 16, count);
     auto flush = [&](int base) {
@@ -356,10 +446,8 @@ __global__ void __launch_bounds__(kChunk, 4) k_items(const IterParams<T> p) {
 #pragma unroll
       for (int k = 0; k < 4; ++k)
 #pragma unroll
-        for (int a = 0; a < kComp; ++a) {
-          atomicAdd(&sacc[a][row + k], acc[k][a]);
-          acc[k][a] = T(0);
-        }
+        for (int c = 0; c < kComp; ++c) atomicAdd(&sacc[c][row + k], acc.get(k, c));
+      acc.zero();
     };
     for (int j = j0; j < j1; ++j) {
       const int base = sloc[j];
@@ -368,35 +456,31 @@ __global__ void __launch_bounds__(kChunk, 4) k_items(const IterParams<T> p) {
         cur = base;
       }
       const V4<T> a = stash[0][j];
+      const V4<T> X = stash[4][j], XD = stash[5][j];
       const T wyzm = a.w * (cy0 + a.y * (cy1 + a.y * cy2)) * (cz0 + a.z * (cz1 + a.z * cz2));
-      T wx[4], dx[4];
-      bspline(a.x, wx, dx);
       if (MODE == kModeMass) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k][0] += wyzm * wx[k];
+        const T A[1] = {wyzm};
+        acc.add(X, XD, A, nullptr);
       } else {
         const V4<T> w0 = stash[1][j], w1 = stash[2][j], w2 = stash[3][j];
-        // W = (u, Ch) with Ch rows (w0.w w1.x w1.y) (w1.z w1.w w2.x) (w2.y w2.z w2.w)
+        // W = (u, Ch); Ch rows (w0.w w1.x w1.y) (w1.z w1.w w2.x) (w2.y w2.z w2.w).
+        // Node k of this row gets wx_k A + wx_k dx_k B with
+        //   A_c = m wy wz (u_c + Ch_c1 dy + Ch_c2 dz),  B_c = m wy wz Ch_c0.
         const T dy = oy - a.y, dz = oz - a.z;
-        T b[3], c0[3];
+        T A[3], B[3];
         if (aff) {
-          b[0] = w0.x + w1.x * dy + w1.y * dz;
-          b[1] = w0.y + w1.w * dy + w2.x * dz;
-          b[2] = w0.z + w2.z * dy + w2.w * dz;
-          c0[0] = w0.w;
-          c0[1] = w1.z;
-          c0[2] = w2.y;
+          A[0] = wyzm * (w0.x + w1.x * dy + w1.y * dz);
+          A[1] = wyzm * (w0.y + w1.w * dy + w2.x * dz);
+          A[2] = wyzm * (w0.z + w2.z * dy + w2.w * dz);
+          B[0] = wyzm * w0.w;
+          B[1] = wyzm * w1.z;
+          B[2] = wyzm * w2.y;
+          acc.add(X, XD, A, B);
         } else {
-          b[0] = w0.x;
-          b[1] = w0.y;
-          b[2] = w0.z;
-          c0[0] = c0[1] = c0[2] = T(0);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const T w = wyzm * wx[k];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) acc[k][c] += w * (b[c] + c0[c] * dx[k]);
+          A[0] = wyzm * w0.x;
+          A[1] = wyzm * w0.y;
+          A[2] = wyzm * w0.z;
+          acc.add(X, XD, A, nullptr);
         }
       }
     }
