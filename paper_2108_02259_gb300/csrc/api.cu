@@ -58,6 +58,7 @@ struct Buf {
 
 constexpr int kMaxBodies = 32;
 constexpr int64_t kMaxPageEntries = int64_t(1) << 28;  // dense page table limit (1 GiB)
+constexpr int kBoxSlack = 2;  // blocks of room for motion when a page-table box is reused
 
 }  // namespace
 
@@ -72,6 +73,8 @@ struct apic_ctx {
   Buf cellb, keys_a, keys_b, vals_a, perm, pt, pn, V, D, mup, heads, offs, item_start, item_info;
   Buf bflags, boffs, blist, page, gm, gmask, gp, gp64, gv, gmb, mu_pair, cub_tmp;
   Buf h_x, h_body, h_v, h_C, h_m, h_nrm, h_vo, h_Co;  // staging for APIC_HOST_PTRS
+  Box box{};                      // page-table box of the last step
+  bool have_box = false;
   DevScalars* ds = nullptr;       // device
   DevScalars* hs = nullptr;       // pinned host mirror
   // profiling
@@ -240,13 +243,14 @@ apic_status validate(const apic_step_args* a) {
 template <class K>
 apic_status keys_sort(apic_ctx* c, int64_t n, const int4* cellb, Box box, int n_bodies, int end_bit,
                       int** perm_out, const void** keys_out, cudaStream_t s) {
+  // particles outside the (possibly reused) box raise kErrBox
   K *ka, *kb;
   int *va, *vb;
   APIC_TRY(get(c, c->keys_a, n, &ka));
   APIC_TRY(get(c, c->keys_b, n, &kb));
   APIC_TRY(get(c, c->vals_a, n, &va));
   APIC_TRY(get(c, c->perm, n, &vb));
-  KLAUNCH(c, launch_keys<K>(n, cellb, box, n_bodies, ka, va, s));
+  KLAUNCH(c, launch_keys<K>(n, cellb, box, n_bodies, ka, va, &c->ds->err, s));
   APIC_TRY(sort_pairs<K>(c, ka, kb, va, vb, (int)n, end_bit, s));
   *perm_out = vb;
   *keys_out = kb;
@@ -290,88 +294,119 @@ apic_status step_impl(apic_ctx* c, const apic_step_args* a, cudaStream_t s, apic
     x = dx; body = db; v = dv; C = dC; m = dm; nrm = dn; vo = dvo; Co = dCo;
   }
 
-  // 1. cells, validation, bounding box of particle blocks; momentum of V.
+  // Steps 1-5 size the sparse grid.  The page-table box of the previous step
+  // (kept with a margin) is reused when every particle still fits in it;
+  // otherwise the kernels flag kErrBox and the steps are redone with a box
+  // fitted to this step's particles.  Nothing is written to the outputs
+  // before the grid is sized, so redoing is safe.
   int4* cellb;
   APIC_TRY(get(c, c->cellb, n, &cellb));
-  DevScalars init{};
-  init.bbox[0] = init.bbox[1] = init.bbox[2] = INT32_MAX;
-  init.bbox[3] = init.bbox[4] = init.bbox[5] = INT32_MIN;
-  *c->hs = init;
-  CUDA_TRY(cudaMemcpyAsync(c->ds, c->hs, sizeof(DevScalars), cudaMemcpyHostToDevice, s));
   const double inv_h = 1.0 / a->h;
-  KLAUNCH(c, launch_cells<T>(n, x, body, m, inv_h, a->n_bodies, cellb, c->ds, s));
-  if (stats) KLAUNCH(c, launch_momentum<T>(n, x, v, C, m, a->h, &c->ds->mom[0], s));
-  CUDA_TRY(cudaMemcpyAsync(c->hs, c->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
-  if (c->hs->err) {
-    const int e = c->hs->err;
-    return fail(APIC_ERR_INVALID_ARG, "invalid particle data:%s%s%s", (e & kErrBody) ? " body id out of range" : "",
-                (e & kErrMass) ? " mass not finite and > 0" : "",
-                (e & kErrPos) ? " position not finite or |x/h| >= 2^29" : "");
-  }
-
-  // 2. page-table box with a one-block margin; keys; radix sort.
-  Box box;
-  box.ox = c->hs->bbox[0] - 1;
-  box.oy = c->hs->bbox[1] - 1;
-  box.oz = c->hs->bbox[2] - 1;
-  box.nx = c->hs->bbox[3] - c->hs->bbox[0] + 3;
-  box.ny = c->hs->bbox[4] - c->hs->bbox[1] + 3;
-  box.nz = c->hs->bbox[5] - c->hs->bbox[2] + 3;
-  const int64_t NB = (int64_t)box.nx * box.ny * box.nz;
-  if (NB > kMaxPageEntries)
-    return fail(APIC_ERR_INVALID_ARG,
-                "the particles span %lld grid blocks of 4^3 nodes; the dense page table is limited to %lld",
-                (long long)NB, (long long)kMaxPageEntries);
-  const int end_bit = bits_for((uint64_t)NB * (uint64_t)a->n_bodies - 1) + 6;
+  Box box{};
+  int64_t NB = 0;
   int* perm = nullptr;
   const void* keys = nullptr;
-  const bool k64 = end_bit > 32;
-  if (k64)
-    APIC_TRY(keys_sort<uint64_t>(c, n, cellb, box, a->n_bodies, end_bit, &perm, &keys, s));
-  else
-    APIC_TRY(keys_sort<uint32_t>(c, n, cellb, box, a->n_bodies, end_bit, &perm, &keys, s));
-
-  // 3. sorted SoA.
+  bool k64 = false;
   V4<T> *pt, *pn, *V, *D;
-  APIC_TRY(get(c, c->pt, n, &pt));
-  APIC_TRY(get(c, c->pn, n, &pn));
-  APIC_TRY(get(c, c->V, 3 * n, &V));
-  APIC_TRY(get(c, c->D, 3 * n, &D));
-  KLAUNCH(c, launch_gather<T>(n, perm, cellb, x, v, C, m, nrm, a->h, inv_h, pt, pn, V, s));
-
-  // 4. work items: runs of equal (grid block, body).
   int *heads, *offs, *item_start;
   int2* item_info;
-  APIC_TRY(get(c, c->heads, n, &heads));
-  APIC_TRY(get(c, c->offs, n, &offs));
-  APIC_TRY(get(c, c->item_start, n, &item_start));
-  APIC_TRY(get(c, c->item_info, n, &item_info));
-  if (k64)
-    KLAUNCH(c, launch_heads<uint64_t>(n, static_cast<const uint64_t*>(keys), heads, s));
-  else
-    KLAUNCH(c, launch_heads<uint32_t>(n, static_cast<const uint32_t*>(keys), heads, s));
-  APIC_TRY(exclusive_sum(c, heads, offs, n, s));
-  KLAUNCH(c, launch_compact(n, heads, offs, item_start, nullptr, &c->ds->n_items, s));
-  if (k64)
-    KLAUNCH(c, launch_item_info<uint64_t>(item_start, &c->ds->n_items, static_cast<const uint64_t*>(keys),
-                                        a->n_bodies, item_info, (int)n, s));
-  else
-    KLAUNCH(c, launch_item_info<uint32_t>(item_start, &c->ds->n_items, static_cast<const uint32_t*>(keys),
-                                        a->n_bodies, item_info, (int)n, s));
+  int* page = nullptr;
+  for (int attempt = 0;; ++attempt) {
+    // 1. cells, validation, bounding box of particle blocks; momentum of V.
+    DevScalars init{};
+    init.bbox[0] = init.bbox[1] = init.bbox[2] = INT32_MAX;
+    init.bbox[3] = init.bbox[4] = init.bbox[5] = INT32_MIN;
+    *c->hs = init;
+    CUDA_TRY(cudaMemcpyAsync(c->ds, c->hs, sizeof(DevScalars), cudaMemcpyHostToDevice, s));
+    KLAUNCH(c, launch_cells<T>(n, x, body, m, inv_h, a->n_bodies, cellb, c->ds, s));
+    if (stats) KLAUNCH(c, launch_momentum<T>(n, x, v, C, m, a->h, &c->ds->mom[0], s));
+    const bool fresh = !c->have_box || attempt > 0;
+    if (fresh) {
+      CUDA_TRY(cudaMemcpyAsync(c->hs, c->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      if (c->hs->err) break;  // reported below
+      // 2. page-table box: one block of stencil margin plus kBoxSlack blocks of
+      //    room for motion in later steps.
+      const int g = 1 + kBoxSlack;
+      c->box.ox = c->hs->bbox[0] - g;
+      c->box.oy = c->hs->bbox[1] - g;
+      c->box.oz = c->hs->bbox[2] - g;
+      c->box.nx = c->hs->bbox[3] - c->hs->bbox[0] + 1 + 2 * g;
+      c->box.ny = c->hs->bbox[4] - c->hs->bbox[1] + 1 + 2 * g;
+      c->box.nz = c->hs->bbox[5] - c->hs->bbox[2] + 1 + 2 * g;
+      c->have_box = true;
+    }
+    box = c->box;
+    NB = (int64_t)box.nx * box.ny * box.nz;
+    if (NB > kMaxPageEntries) {
+      c->have_box = false;
+      return fail(APIC_ERR_INVALID_ARG,
+                  "the particles span %lld grid blocks of 4^3 nodes; the dense page table is limited to %lld",
+                  (long long)NB, (long long)kMaxPageEntries);
+    }
+    const int end_bit = bits_for((uint64_t)NB * (uint64_t)a->n_bodies - 1) + 6;
+    k64 = end_bit > 32;
+    if (k64)
+      APIC_TRY(keys_sort<uint64_t>(c, n, cellb, box, a->n_bodies, end_bit, &perm, &keys, s));
+    else
+      APIC_TRY(keys_sort<uint32_t>(c, n, cellb, box, a->n_bodies, end_bit, &perm, &keys, s));
 
-  // 5. active grid blocks: every block some stencil reaches; page table.
-  int *bflags, *boffs, *blist, *page;
-  APIC_TRY(get(c, c->bflags, NB, &bflags));
-  APIC_TRY(get(c, c->boffs, NB, &boffs));
-  APIC_TRY(get(c, c->blist, NB, &blist));
-  APIC_TRY(get(c, c->page, NB, &page));
-  CUDA_TRY(cudaMemsetAsync(bflags, 0, NB * sizeof(int), s));
-  KLAUNCH(c, launch_mark(n, cellb, box, bflags, s));
-  APIC_TRY(exclusive_sum(c, bflags, boffs, NB, s));
-  KLAUNCH(c, launch_compact(NB, bflags, boffs, blist, page, &c->ds->n_blocks, s));
-  CUDA_TRY(cudaMemcpyAsync(&c->hs->n_items, &c->ds->n_items, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
+    // 3. sorted SoA.
+    APIC_TRY(get(c, c->pt, n, &pt));
+    APIC_TRY(get(c, c->pn, n, &pn));
+    APIC_TRY(get(c, c->V, 3 * n, &V));
+    APIC_TRY(get(c, c->D, 3 * n, &D));
+    KLAUNCH(c, launch_gather<T>(n, perm, cellb, x, v, C, m, nrm, a->h, inv_h, pt, pn, V, s));
+
+    // 4. work items: runs of equal (grid block, body), at most kChunk long.
+    APIC_TRY(get(c, c->heads, n, &heads));
+    APIC_TRY(get(c, c->offs, n, &offs));
+    APIC_TRY(get(c, c->item_start, n, &item_start));
+    APIC_TRY(get(c, c->item_info, n, &item_info));
+    if (k64)
+      KLAUNCH(c, launch_heads<uint64_t>(n, static_cast<const uint64_t*>(keys), heads, s));
+    else
+      KLAUNCH(c, launch_heads<uint32_t>(n, static_cast<const uint32_t*>(keys), heads, s));
+    APIC_TRY(exclusive_sum(c, heads, offs, n, s));
+    KLAUNCH(c, launch_compact(n, heads, offs, item_start, nullptr, &c->ds->n_items, s));
+    if (k64)
+      KLAUNCH(c, launch_item_info<uint64_t>(item_start, &c->ds->n_items, static_cast<const uint64_t*>(keys),
+                                          a->n_bodies, item_info, (int)n, s));
+    else
+      KLAUNCH(c, launch_item_info<uint32_t>(item_start, &c->ds->n_items, static_cast<const uint32_t*>(keys),
+                                          a->n_bodies, item_info, (int)n, s));
+
+    // 5. active grid blocks: every block some stencil reaches; page table.
+    int *bflags, *boffs, *blist;
+    APIC_TRY(get(c, c->bflags, NB, &bflags));
+    APIC_TRY(get(c, c->boffs, NB, &boffs));
+    APIC_TRY(get(c, c->blist, NB, &blist));
+    APIC_TRY(get(c, c->page, NB, &page));
+    CUDA_TRY(cudaMemsetAsync(bflags, 0, NB * sizeof(int), s));
+    if (k64)
+      KLAUNCH(c, launch_mark_items<uint64_t>(item_start, item_info, &c->ds->n_items,
+                                           static_cast<const uint64_t*>(keys), n, (int)n, box, bflags, s));
+    else
+      KLAUNCH(c, launch_mark_items<uint32_t>(item_start, item_info, &c->ds->n_items,
+                                           static_cast<const uint32_t*>(keys), n, (int)n, box, bflags, s));
+    APIC_TRY(exclusive_sum(c, bflags, boffs, NB, s));
+    KLAUNCH(c, launch_compact(NB, bflags, boffs, blist, page, &c->ds->n_blocks, s));
+    CUDA_TRY(cudaMemcpyAsync(c->hs, c->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if ((c->hs->err & kErrBox) && !(c->hs->err & ~kErrBox) && attempt == 0) {
+      c->have_box = false;  // a particle left the reused box: size a fresh one
+      continue;
+    }
+    break;
+  }
+  if (c->hs->err) {
+    const int e = c->hs->err;
+    c->have_box = false;
+    return fail(APIC_ERR_INVALID_ARG, "invalid particle data:%s%s%s%s", (e & kErrBody) ? " body id out of range" : "",
+                (e & kErrMass) ? " mass not finite and > 0" : "",
+                (e & kErrPos) ? " position not finite or |x/h| >= 2^29" : "",
+                (e & kErrBox) ? " (internal: page-table box)" : "");
+  }
   const int n_items = c->hs->n_items;
   const int n_blocks = c->hs->n_blocks;
   const int64_t n_nodes = (int64_t)n_blocks * kNodesPerBlock;
@@ -439,13 +474,12 @@ apic_status step_impl(apic_ctx* c, const apic_step_args* a, cudaStream_t s, apic
   const int threads = 128;
 
   // 7. mass, optional friction blend, P2G(V), then the N+1 transfer passes.
-  KLAUNCH(c, launch_items<T>(p, kModeMass, threads, s));
+  KLAUNCH(c, launch_items<T>(p, kModeMassV, threads, s));
   if (a->mu_pair) {
     KLAUNCH(c, launch_items<T>(p, kModeMu, threads, s));
     p.mup = mup;
   }
-  KLAUNCH(c, launch_items<T>(p, kModeP2GV, threads, s));
-  KLAUNCH(c, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, s));
+  KLAUNCH(c, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 1, s));
   t_prep.stop();
   const int N = a->n_iter;
   for (int pass = 0; pass <= N; ++pass) {
@@ -454,7 +488,7 @@ apic_status step_impl(apic_ctx* c, const apic_step_args* a, cudaStream_t s, apic
       Timer t_it(c, s, 2);
       KLAUNCH(c, launch_items<T>(p, mode, threads, s));
     }
-    if (pass < N) KLAUNCH(c, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, s));
+    if (pass < N) KLAUNCH(c, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 0, s));
   }
   t_step.stop();
 

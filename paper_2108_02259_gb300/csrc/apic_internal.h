@@ -30,6 +30,7 @@ constexpr int kChunk = APIC_CHUNK;
 constexpr int kErrBody = 1;
 constexpr int kErrMass = 2;
 constexpr int kErrPos = 4;
+constexpr int kErrBox = 8;  // a particle lies outside a page-table box reused from an earlier step
 
 // Device-side scalars the host reads back while sizing the grid.
 struct DevScalars {
@@ -59,6 +60,7 @@ enum Mode : int {
   kModeLast = 4,   // G2P -> Delta_N -> V_hat = V + Delta_N in caller order
   kModeOnly = 5,   // N = 0: G2P -> V_hat = H V in caller order
   kModeMu = 6,     // per-particle friction blend from a body-pair table
+  kModeMassV = 7,  // m_i, body mask and P2G of V in one pass (momentum to FP64)
 };
 
 // Everything the per-item kernel needs, by value.
@@ -99,7 +101,7 @@ cudaError_t launch_cells(int64_t n, const double* x, const int32_t* body, const 
                          int n_bodies, int4* cellb, DevScalars* ds, cudaStream_t s);
 template <class K>
 cudaError_t launch_keys(int64_t n, const int4* cellb, Box box, int n_bodies, K* keys, int* vals,
-                        cudaStream_t s);
+                        int* err, cudaStream_t s);
 template <class T>
 cudaError_t launch_gather(int64_t n, const int* perm, const int4* cellb, const double* x, const T* v,
                           const T* C, const T* m, const T* nrm, double h, double inv_h, V4<T>* pt,
@@ -109,14 +111,18 @@ cudaError_t launch_heads(int64_t n, const K* keys, int* flags, cudaStream_t s);
 template <class K>
 cudaError_t launch_item_info(const int* item_start, const int* n_items, const K* keys, int n_bodies,
                              int2* item_info, int max_items, cudaStream_t s);
-cudaError_t launch_mark(int64_t n, const int4* cellb, Box box, int* flags, cudaStream_t s);
+cudaError_t launch_mark(int64_t n, const int4* cellb, Box box, int* flags, int* err, cudaStream_t s);
 cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* list, int* page,
                            int* count, cudaStream_t s);
+template <class K>
+cudaError_t launch_mark_items(const int* item_start, const int2* item_info, const int* n_items, const K* keys,
+                              int64_t n, int max_items, Box box, int* flags, cudaStream_t s);
 template <class T>
 cudaError_t launch_items(const IterParams<T>& p, int mode, int threads, cudaStream_t s);
+// all64: take every node's momentum from the FP64 accumulators (after kModeMassV).
 template <class T>
 cudaError_t launch_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask, V4<T>* gp,
-                             V4<double>* gp64, V4<T>* gv, cudaStream_t s);
+                             V4<double>* gp64, V4<T>* gv, int all64, cudaStream_t s);
 template <class T>
 cudaError_t launch_momentum(int64_t n, const double* x, const T* v, const T* C, const T* m, double h,
                             double* out6, cudaStream_t s);

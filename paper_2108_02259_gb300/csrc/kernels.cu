@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "apic_internal.h"
 
 // Resident CTAs per SM the fused kernel is compiled for (register cap).
@@ -200,6 +202,11 @@ __device__ __forceinline__ void flush_mom(double*, V4<double>* gp, V4<double>*, 
   atomicAdd(&gp[node].z, z);
 }
 
+// Stash rows of particle j are padded by one slot every 16 particles, so the
+// two half-warps of a warp (16 particles apart) read different banks.
+constexpr int kStashN = kChunk + kChunk / 16;
+__device__ __forceinline__ int sidx(int j) { return j + (j >> 4); }
+
 // Phase-2 register accumulators of one lane: nodes kx = 0..3 of its stencil
 // row, K components.  A particle adds wx_k A_c + (wx_k dx_k) B_c to node k,
 // component c.  The FP32 form packs node pairs (0,1) and (2,3) into float2
@@ -268,11 +275,15 @@ struct RowAcc<float, K> {
 template <class T, int MODE>
 __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const IterParams<T> p) {
   constexpr bool kG2P = MODE == kModeFirst || MODE == kModeMid || MODE == kModeLast || MODE == kModeOnly;
-  constexpr bool kP2G = MODE == kModeMass || MODE == kModeP2GV || MODE == kModeFirst || MODE == kModeMid;
-  constexpr int kComp = MODE == kModeMass ? 1 : 3;
+  constexpr bool kP2G = MODE == kModeMass || MODE == kModeP2GV || MODE == kModeMassV || MODE == kModeFirst ||
+                        MODE == kModeMid;
+  constexpr bool kMass = MODE == kModeMass || MODE == kModeMassV;  // accumulates m_i and the body mask
+  constexpr bool kMom = MODE != kModeMass;                          // accumulates momentum
+  constexpr int kComp = MODE == kModeMass ? 1 : MODE == kModeMassV ? 4 : 3;
   __shared__ V4<T> sv[kG2P ? kTile3 : 1];
+  __shared__ uint32_t smask[MODE == kModeMu ? kTile3 : 1];
   __shared__ T sacc[kP2G ? kComp : 1][kTile3];
-  __shared__ V4<T> stash[kP2G ? 6 : 1][kP2G ? kChunk : 1];
+  __shared__ V4<T> stash[kP2G ? 6 : 1][kP2G ? kStashN : 1];
   __shared__ int sloc[kChunk];
   __shared__ int snb[27];
   const int tid = threadIdx.x;
@@ -290,7 +301,7 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
   // Issue this thread's particle loads first so that they are in flight
   // while the CTA fetches its grid tile.
   constexpr bool kReadD = MODE == kModeMid || MODE == kModeLast;
-  constexpr bool kReadV = MODE == kModeP2GV || MODE == kModeFirst || MODE == kModeOnly;
+  constexpr bool kReadV = MODE == kModeP2GV || MODE == kModeMassV || MODE == kModeFirst || MODE == kModeOnly;
   V4<T> pt{}, pn{}, q0{}, q1{}, q2{};
   if (tid < count) {
     const int s = s0 + tid;
@@ -319,6 +330,13 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
     }
     __syncthreads();
   }
+  if (MODE == kModeMu) {
+    for (int t = tid; t < kTile3; t += kChunk) {
+      const int node = tile_node(snb, t);
+      smask[t] = node >= 0 ? p.gmask[node] : 0u;
+    }
+    __syncthreads();
+  }
 
   // ---------------- phase 1: one thread per particle ----------------
   if (tid < count) {
@@ -338,10 +356,10 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
 #pragma unroll 1
       for (int q = 0; q < 64; ++q) {
         const int kx = q & 3, ky = (q >> 2) & 3, kz = q >> 4;
-        const int node = tile_node(snb, base + kz * (kTile * kTile) + ky * kTile + kx);
-        if (node < 0) continue;
-        uint32_t other = p.gmask[node] & ~own;
+        const int tq = base + kz * (kTile * kTile) + ky * kTile + kx;
+        uint32_t other = smask[tq] & ~own;
         if (!other) continue;
+        const int node = tile_node(snb, tq);
         T wxk = kx == 0 ? wx[0] : kx == 1 ? wx[1] : kx == 2 ? wx[2] : wx[3];
         T wyk = ky == 0 ? wy[0] : ky == 1 ? wy[1] : ky == 2 ? wy[2] : wy[3];
         T wzk = kz == 0 ? wz[0] : kz == 1 ? wz[1] : kz == 2 ? wz[2] : wz[3];
@@ -355,16 +373,16 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
         }
       }
       p.mup_out[s] = den > T(0) ? num / den : p.mu_pair[body * p.n_bodies + body];
-    } else if (MODE == kModeMass || MODE == kModeP2GV) {
+    } else if (MODE == kModeMass || MODE == kModeP2GV || MODE == kModeMassV) {
       T wx[4], dx[4];
       bspline(pt.x, wx, dx);
-      stash[0][tid] = pt;
-      stash[4][tid] = V4<T>{wx[0], wx[1], wx[2], wx[3]};
-      stash[5][tid] = V4<T>{wx[0] * dx[0], wx[1] * dx[1], wx[2] * dx[2], wx[3] * dx[3]};
-      if (MODE == kModeP2GV) {
-        stash[1][tid] = q0;
-        stash[2][tid] = q1;
-        stash[3][tid] = q2;
+      stash[0][sidx(tid)] = pt;
+      stash[4][sidx(tid)] = V4<T>{wx[0], wx[1], wx[2], wx[3]};
+      stash[5][sidx(tid)] = V4<T>{wx[0] * dx[0], wx[1] * dx[1], wx[2] * dx[2], wx[3] * dx[3]};
+      if (MODE != kModeMass) {
+        stash[1][sidx(tid)] = q0;
+        stash[2][sidx(tid)] = q1;
+        stash[3][sidx(tid)] = q2;
       }
     } else {
       T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4];
@@ -416,12 +434,12 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
         store12(p.D, n, s, dv, dC);
         T u[3], uC[9];
         undesirable(dv, dC, nrm, mu, p.sep23, u, uC);
-        stash[0][tid] = pt;
-        stash[1][tid] = V4<T>{u[0], u[1], u[2], uC[0]};
-        stash[2][tid] = V4<T>{uC[1], uC[2], uC[3], uC[4]};
-        stash[3][tid] = V4<T>{uC[5], uC[6], uC[7], uC[8]};
-        stash[4][tid] = V4<T>{wx[0], wx[1], wx[2], wx[3]};
-        stash[5][tid] = V4<T>{wx[0] * dx[0], wx[1] * dx[1], wx[2] * dx[2], wx[3] * dx[3]};
+        stash[0][sidx(tid)] = pt;
+        stash[1][sidx(tid)] = V4<T>{u[0], u[1], u[2], uC[0]};
+        stash[2][sidx(tid)] = V4<T>{uC[1], uC[2], uC[3], uC[4]};
+        stash[3][sidx(tid)] = V4<T>{uC[5], uC[6], uC[7], uC[8]};
+        stash[4][sidx(tid)] = V4<T>{wx[0], wx[1], wx[2], wx[3]};
+        stash[5][sidx(tid)] = V4<T>{wx[0] * dx[0], wx[1] * dx[1], wx[2] * dx[2], wx[3] * dx[3]};
       }
     }
   }
@@ -437,17 +455,22 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
     row_poly(kz, cz0, cz1, cz2);
     const T oy = T(ky - 1), oz = T(kz - 1);
     const bool aff = !p.pic;
-    RowAcc<T, kComp> acc;
+    RowAcc<T, kMom ? 3 : 1> acc;
+    RowAcc<T, 1> macc;  // mass, when this pass also scatters mass (kModeMassV)
     acc.zero();
+    macc.zero();
     int cur = -1;
     const int j0 = hw * 16, j1 = min(j0 + 16, count);
     auto flush = [&](int base) {
       const int row = base + kz * (kTile * kTile) + ky * kTile;
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+      for (int k = 0; k < 4; ++k) {
 #pragma unroll
-        for (int c = 0; c < kComp; ++c) atomicAdd(&sacc[c][row + k], acc.get(k, c));
+        for (int c = 0; c < (kMom ? 3 : 1); ++c) atomicAdd(&sacc[c][row + k], acc.get(k, c));
+        if constexpr (MODE == kModeMassV) atomicAdd(&sacc[3][row + k], macc.get(k, 0));
+      }
       acc.zero();
+      macc.zero();
     };
     for (int j = j0; j < j1; ++j) {
       const int base = sloc[j];
@@ -455,14 +478,18 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
         if (cur >= 0) flush(cur);
         cur = base;
       }
-      const V4<T> a = stash[0][j];
-      const V4<T> X = stash[4][j], XD = stash[5][j];
+      const V4<T> a = stash[0][sidx(j)];
+      const V4<T> X = stash[4][sidx(j)], XD = stash[5][sidx(j)];
       const T wyzm = a.w * (cy0 + a.y * (cy1 + a.y * cy2)) * (cz0 + a.z * (cz1 + a.z * cz2));
-      if (MODE == kModeMass) {
+      if (kMass) {
         const T A[1] = {wyzm};
-        acc.add(X, XD, A, nullptr);
-      } else {
-        const V4<T> w0 = stash[1][j], w1 = stash[2][j], w2 = stash[3][j];
+        if constexpr (MODE == kModeMass)
+          acc.add(X, XD, A, nullptr);
+        else
+          macc.add(X, XD, A, nullptr);
+      }
+      if constexpr (kMom) {
+        const V4<T> w0 = stash[1][sidx(j)], w1 = stash[2][sidx(j)], w2 = stash[3][sidx(j)];
         // W = (u, Ch); Ch rows (w0.w w1.x w1.y) (w1.z w1.w w2.x) (w2.y w2.z w2.w).
         // Node k of this row gets wx_k A + wx_k dx_k B with
         //   A_c = m wy wz (u_c + Ch_c1 dy + Ch_c2 dz),  B_c = m wy wz Ch_c0.
@@ -492,17 +519,26 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
   for (int t = tid; t < kTile3; t += kChunk) {
     const int node = tile_node(snb, t);
     if (node < 0) continue;
-    if (MODE == kModeMass) {
-      const T mv = sacc[0][t];
+    if constexpr (kMass) {
+      const T mv = sacc[MODE == kModeMassV ? 3 : 0][t];
       if (mv != T(0)) {
         atomicAdd(&p.gm[node], mv);
         atomicOr(&p.gmask[node], 1u << body);
         if (p.gmb) atomicAdd(&p.gmb[(int64_t)body * p.n_nodes + node], mv);
       }
-    } else {
-      const T x = sacc[0][t], y = sacc[kComp > 1 ? 1 : 0][t], z = sacc[kComp > 2 ? 2 : 0][t];
-      if (x != T(0) || y != T(0) || z != T(0))
-        flush_mom(static_cast<T*>(nullptr), p.gp, p.gp64, p.gmask, node, x, y, z);
+    }
+    if constexpr (kMom) {
+      const T x = sacc[0][t], y = sacc[1][t], z = sacc[2][t];
+      if (x != T(0) || y != T(0) || z != T(0)) {
+        if (MODE == kModeMassV && p.gp64 != nullptr) {
+          // the body mask is not final yet: P2G of V goes to FP64 everywhere
+          atomicAdd(&p.gp64[node].x, (double)x);
+          atomicAdd(&p.gp64[node].y, (double)y);
+          atomicAdd(&p.gp64[node].z, (double)z);
+        } else {
+          flush_mom(static_cast<T*>(nullptr), p.gp, p.gp64, p.gmask, node, x, y, z);
+        }
+      }
     }
   }
 }
@@ -512,12 +548,12 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
 // accumulators (FP32 path).
 template <class T>
 __global__ void k_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask, V4<T>* gp,
-                            V4<double>* gp64, V4<T>* gv) {
+                            V4<double>* gp64, V4<T>* gv, int all64) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n_nodes) return;
   const T m = gm[i];
   V4<T> v{T(0), T(0), T(0), T(0)};
-  if (gp64 != nullptr && __popc(gmask[i]) >= 2) {
+  if (gp64 != nullptr && (all64 || __popc(gmask[i]) >= 2)) {
     const V4<double> q = gp64[i];
     if (m > T(0)) {
       const double md = (double)m;
@@ -614,11 +650,18 @@ __global__ void k_cells(int64_t n, const double* __restrict__ x, const int32_t* 
 
 template <class K>
 __global__ void k_keys(int64_t n, const int4* __restrict__ cellb, Box box, int n_bodies, K* keys,
-                       int* vals) {
+                       int* vals, int* err) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int4 c = cellb[p];
-  const int bx = (c.x >> 2) - box.ox, by = (c.y >> 2) - box.oy, bz = (c.z >> 2) - box.oz;
+  int bx = (c.x >> 2) - box.ox, by = (c.y >> 2) - box.oy, bz = (c.z >> 2) - box.oz;
+  // every particle block must keep a one-block margin inside the box
+  if (bx < 1 || by < 1 || bz < 1 || bx > box.nx - 2 || by > box.ny - 2 || bz > box.nz - 2) {
+    atomicOr(err, kErrBox);
+    bx = min(max(bx, 1), box.nx - 2);
+    by = min(max(by, 1), box.ny - 2);
+    bz = min(max(bz, 1), box.nz - 2);
+  }
   const int64_t blin = ((int64_t)bz * box.ny + by) * box.nx + bx;
   const uint32_t loc = (uint32_t)(((c.z & 3) << 4) | ((c.y & 3) << 2) | (c.x & 3));
   keys[p] = (K)((((uint64_t)blin * (uint64_t)n_bodies + (uint64_t)c.w) << 6) | loc);
@@ -661,24 +704,66 @@ __global__ void k_heads(int64_t n, const K* __restrict__ keys, int* flags) {
 template <class K>
 __global__ void k_item_info(const int* __restrict__ item_start, const int* __restrict__ n_items,
                             const K* __restrict__ keys, int n_bodies, int2* info) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *n_items) return;
-  const uint64_t q = (uint64_t)(keys[item_start[i]] >> 6);
-  info[i] = make_int2((int)(q / (uint64_t)n_bodies), (int)(q % (uint64_t)n_bodies));
+  const int count = *n_items;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const uint64_t q = (uint64_t)(keys[item_start[i]] >> 6);
+    info[i] = make_int2((int)(q / (uint64_t)n_bodies), (int)(q % (uint64_t)n_bodies));
+  }
 }
 
 // Mark every grid block a particle's 4x4x4-node stencil reaches.
-__global__ void k_mark(int64_t n, const int4* __restrict__ cellb, Box box, int* flags) {
+__global__ void k_mark(int64_t n, const int4* __restrict__ cellb, Box box, int* flags, int* err) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int4 c = cellb[p];
   const int x0 = ((c.x - 1) >> 2) - box.ox, x1 = ((c.x + 2) >> 2) - box.ox;
   const int y0 = ((c.y - 1) >> 2) - box.oy, y1 = ((c.y + 2) >> 2) - box.oy;
   const int z0 = ((c.z - 1) >> 2) - box.oz, z1 = ((c.z + 2) >> 2) - box.oz;
+  if (x0 < 0 || y0 < 0 || z0 < 0 || x1 >= box.nx || y1 >= box.ny || z1 >= box.nz) {
+    atomicOr(err, kErrBox);
+    return;
+  }
   for (int bz = z0; bz <= z1; ++bz)
     for (int by = y0; by <= y1; ++by)
       for (int bx = x0; bx <= x1; ++bx)
         flags[((int64_t)bz * box.ny + by) * box.nx + bx] = 1;
+}
+
+// Mark the grid blocks the stencils of one work item reach: one warp per
+// item.  Particles of an item share a block B; a particle in cell-in-block l
+// reaches block B-1 along an axis when l = 0 and B+1 when l >= 2, so the
+// warp ORs those six conditions over its particles and marks the implied
+// subset of the 3x3x3 blocks around B (once per item, not per particle).
+template <class K>
+__global__ void k_mark_items(const int* __restrict__ item_start, const int2* __restrict__ item_info,
+                             const int* __restrict__ n_items_p, const K* __restrict__ keys, int64_t n,
+                             Box box, int* flags) {
+  const int lane = threadIdx.x & 31;
+  const int n_items = *n_items_p;
+  const int warps = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
+  for (int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); i < n_items; i += warps) {
+    const int s0 = item_start[i];
+    const int s1 = i + 1 < n_items ? item_start[i + 1] : (int)n;
+    unsigned need = 0;
+    for (int s = s0 + lane; s < s1; s += 32) {
+      const unsigned loc = (unsigned)(keys[s] & 63);
+      const unsigned lx = loc & 3, ly = (loc >> 2) & 3, lz = loc >> 4;
+      need |= (lx == 0) | ((lx >= 2) << 1) | ((ly == 0) << 2) | ((ly >= 2) << 3) | ((lz == 0) << 4) |
+              ((lz >= 2) << 5);
+    }
+    need = __reduce_or_sync(0xffffffffu, need);
+    if (lane < 27) {
+      const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+      const bool ok = (dx == 0 || (dx < 0 ? (need & 1) : (need & 2))) &&
+                      (dy == 0 || (dy < 0 ? (need & 4) : (need & 8))) &&
+                      (dz == 0 || (dz < 0 ? (need & 16) : (need & 32)));
+      if (ok) {
+        const int blin = item_info[i].x;
+        const int bx = blin % box.nx, by = (blin / box.nx) % box.ny, bz = blin / (box.nx * box.ny);
+        flags[((int64_t)(bz + dz) * box.ny + (by + dy)) * box.nx + (bx + dx)] = 1;
+      }
+    }
+  }
 }
 
 // Stream compaction after an exclusive scan of 0/1 flags: list the flagged
@@ -757,8 +842,8 @@ cudaError_t launch_cells(int64_t n, const double* x, const int32_t* body, const 
 
 template <class K>
 cudaError_t launch_keys(int64_t n, const int4* cellb, Box box, int n_bodies, K* keys, int* vals,
-                        cudaStream_t s) {
-  k_keys<K><<<grid_for(n, 256), 256, 0, s>>>(n, cellb, box, n_bodies, keys, vals);
+                        int* err, cudaStream_t s) {
+  k_keys<K><<<grid_for(n, 256), 256, 0, s>>>(n, cellb, box, n_bodies, keys, vals, err);
   return cudaGetLastError();
 }
 
@@ -779,12 +864,23 @@ cudaError_t launch_heads(int64_t n, const K* keys, int* flags, cudaStream_t s) {
 template <class K>
 cudaError_t launch_item_info(const int* item_start, const int* n_items, const K* keys, int n_bodies,
                              int2* item_info, int max_items, cudaStream_t s) {
-  k_item_info<K><<<grid_for(max_items, 256), 256, 0, s>>>(item_start, n_items, keys, n_bodies, item_info);
+  const unsigned grid = (unsigned)std::min<int64_t>(grid_for(max_items, 256), 152 * 8);
+  k_item_info<K><<<grid, 256, 0, s>>>(item_start, n_items, keys, n_bodies, item_info);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mark(int64_t n, const int4* cellb, Box box, int* flags, cudaStream_t s) {
-  k_mark<<<grid_for(n, 256), 256, 0, s>>>(n, cellb, box, flags);
+cudaError_t launch_mark(int64_t n, const int4* cellb, Box box, int* flags, int* err, cudaStream_t s) {
+  k_mark<<<grid_for(n, 256), 256, 0, s>>>(n, cellb, box, flags, err);
+  return cudaGetLastError();
+}
+
+template <class K>
+cudaError_t launch_mark_items(const int* item_start, const int2* item_info, const int* n_items, const K* keys,
+                              int64_t n, int max_items, Box box, int* flags, cudaStream_t s) {
+  if (max_items <= 0) return cudaSuccess;
+  const int64_t warps = std::min<int64_t>(max_items, 152 * 64);
+  k_mark_items<K><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(item_start, item_info, n_items, keys, n,
+                                                                       box, flags);
   return cudaGetLastError();
 }
 
@@ -808,6 +904,7 @@ cudaError_t launch_items(const IterParams<T>& p, int mode, int threads, cudaStre
     case kModeLast: k_items<T, kModeLast><<<grid, kChunk, 0, s>>>(p); break;
     case kModeOnly: k_items<T, kModeOnly><<<grid, kChunk, 0, s>>>(p); break;
     case kModeMu: k_items<T, kModeMu><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeMassV: k_items<T, kModeMassV><<<grid, kChunk, 0, s>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -815,9 +912,9 @@ cudaError_t launch_items(const IterParams<T>& p, int mode, int threads, cudaStre
 
 template <class T>
 cudaError_t launch_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask, V4<T>* gp,
-                             V4<double>* gp64, V4<T>* gv, cudaStream_t s) {
+                             V4<double>* gp64, V4<T>* gv, int all64, cudaStream_t s) {
   if (n_nodes <= 0) return cudaSuccess;
-  k_normalize<T><<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, gm, gmask, gp, gp64, gv);
+  k_normalize<T><<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, gm, gmask, gp, gp64, gv, all64);
   return cudaGetLastError();
 }
 
@@ -846,15 +943,17 @@ cudaError_t launch_count_multibody(int64_t n_nodes, const uint32_t* gmask, unsig
                                         V4<T>*, V4<T>*, V4<T>*, cudaStream_t);                     \
   template cudaError_t launch_items<T>(const IterParams<T>&, int, int, cudaStream_t);             \
   template cudaError_t launch_normalize<T>(int64_t, const T*, const uint32_t*, V4<T>*,            \
-                                           V4<double>*, V4<T>*, cudaStream_t);                    \
+                                           V4<double>*, V4<T>*, int, cudaStream_t);               \
   template cudaError_t launch_momentum<T>(int64_t, const double*, const T*, const T*, const T*,   \
                                           double, double*, cudaStream_t);
 APIC_INST_T(float)
 APIC_INST_T(double)
 
 #define APIC_INST_K(K)                                                                          \
-  template cudaError_t launch_keys<K>(int64_t, const int4*, Box, int, K*, int*, cudaStream_t);  \
+  template cudaError_t launch_keys<K>(int64_t, const int4*, Box, int, K*, int*, int*, cudaStream_t); \
   template cudaError_t launch_heads<K>(int64_t, const K*, int*, cudaStream_t);              \
+  template cudaError_t launch_mark_items<K>(const int*, const int2*, const int*, const K*, int64_t, int, \
+                                            Box, int*, cudaStream_t);                        \
   template cudaError_t launch_item_info<K>(const int*, const int*, const K*, int, int2*, int,   \
                                            cudaStream_t);
 APIC_INST_K(uint32_t)

@@ -115,14 +115,14 @@ int bits_needed(uint64_t v) {
 
 template <class K>
 apic_status sort_static(Carve& cv, int64_t n, const int4* cellb, Box box, int n_bodies, int end_bit,
-                        int** perm, const void** keys_sorted, cudaStream_t s) {
+                        int** perm, const void** keys_sorted, int* err, cudaStream_t s) {
   K *ka, *kb;
   int *va, *vb;
   S_TRY(cv.take(n, &ka, "sort keys"));
   S_TRY(cv.take(n, &kb, "sorted keys"));
   S_TRY(cv.take(n, &va, "sort values"));
   S_TRY(cv.take(n, &vb, "permutation"));
-  S_CUDA(launch_keys<K>(n, cellb, box, n_bodies, ka, va, s));
+  S_CUDA(launch_keys<K>(n, cellb, box, n_bodies, ka, va, err, s));
   size_t tmp = 0;
   S_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, ka, kb, va, vb, (int)n, 0, end_bit, s));
   char* t;
@@ -186,9 +186,9 @@ apic_status static_impl(const apic_step_args* a, cudaStream_t s, apic_stats* sta
   int* perm = nullptr;
   const void* keys = nullptr;
   if (k64)
-    S_TRY(sort_static<uint64_t>(cv, n, cellb, box, a->n_bodies, end_bit, &perm, &keys, s));
+    S_TRY(sort_static<uint64_t>(cv, n, cellb, box, a->n_bodies, end_bit, &perm, &keys, &ds->err, s));
   else
-    S_TRY(sort_static<uint32_t>(cv, n, cellb, box, a->n_bodies, end_bit, &perm, &keys, s));
+    S_TRY(sort_static<uint32_t>(cv, n, cellb, box, a->n_bodies, end_bit, &perm, &keys, &ds->err, s));
 
   V4<T> *pt, *pn, *V, *D;
   S_TRY(cv.take(n, &pt, "particle offsets"));
@@ -222,7 +222,7 @@ apic_status static_impl(const apic_step_args* a, cudaStream_t s, apic_stats* sta
   S_TRY(cv.take(NB, &blist, "block list"));
   S_TRY(cv.take(NB, &page, "page table"));
   S_CUDA(cudaMemsetAsync(bflags, 0, NB * sizeof(int), s));
-  S_CUDA(launch_mark(n, cellb, box, bflags, s));
+  S_CUDA(launch_mark(n, cellb, box, bflags, &ds->err, s));
   S_TRY(scan_static(cv, bflags, boffs, NB, s));
   S_CUDA(launch_compact(NB, bflags, boffs, blist, page, &ds->n_blocks, s));
   S_CUDA(cudaMemcpyAsync(&hs.n_items, &ds->n_items, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -293,12 +293,12 @@ apic_status static_impl(const apic_step_args* a, cudaStream_t s, apic_stats* sta
     p.mup = mup;
   }
   S_CUDA(launch_items<T>(p, kModeP2GV, kChunk, s));
-  S_CUDA(launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, s));
+  S_CUDA(launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 0, s));
   const int N = a->n_iter;
   for (int pass = 0; pass <= N; ++pass) {
     const int mode = N == 0 ? kModeOnly : pass == 0 ? kModeFirst : pass == N ? kModeLast : kModeMid;
     S_CUDA(launch_items<T>(p, mode, kChunk, s));
-    if (pass < N) S_CUDA(launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, s));
+    if (pass < N) S_CUDA(launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 0, s));
   }
   if (stats) {
     S_CUDA(launch_momentum<T>(n, x, static_cast<const T*>(a->v_out), static_cast<const T*>(a->C_out), m, a->h,

@@ -243,3 +243,40 @@ def test_repeat_calls_reuse_scratch(ctx):
     assert ctx.scratch_bytes() == nbytes
     vs = np.abs(s.v).max()
     assert np.abs(a[0] - b[0]).max() <= 2 * TOL_V32 * vs
+
+
+def test_page_table_box_reuse_and_refit(ctx):
+    """The page-table box of one step is reused by the next when the
+    particles still fit (a small shift) and refitted when they do not (a
+    large shift); results match the oracle either way."""
+    base = scenes.four_bodies(scale=0.02)
+    for shift_cells in (0, 5, 3, 400, -7):
+        s = scenes.Scene(base.x + shift_cells * base.h, base.v, base.C, base.m, base.nrm, base.body, base.n_bodies,
+                         base.h, base.mu, 4)
+        check(s, run_gpu(ctx, s), run_oracle(s), TOL_V32, TOL_C32, TOL_MOM32, f"shift {shift_cells} cells")
+
+
+def _subset(s, keep, bodies):
+    """The particles of `bodies` only, renumbered 0.. (for the oracle)."""
+    remap = np.full(s.n_bodies, -1, np.int32)
+    remap[list(bodies)] = np.arange(len(bodies), dtype=np.int32)
+    mp = None if s.mu_pair is None else s.mu_pair[np.ix_(list(bodies), list(bodies))]
+    return scenes.Scene(s.x[keep], s.v[keep], s.C[keep], s.m[keep], s.nrm[keep], remap[s.body[keep]], len(bodies),
+                        s.h, s.mu, s.n_iter, mp)
+
+
+def test_eight_bodies_full_size(ctx):
+    """The 4,000,000-node 8-body scene (h = 1/512, per-pair mu, N = 8) as one
+    launch.  Its four approaching pairs are ~0.3 apart, far beyond the
+    2h stencil reach, so the oracle run on one pair alone gives exactly the
+    full-scene answer for that pair's 1,000,000 particles; the full scene
+    must also keep its momentum."""
+    s = scenes.eight_bodies()
+    v, Cm, st = run_gpu(ctx, s, mu_pair=s.mu_pair)
+    vs, _, sP, sL = scales(s, s.C)
+    assert np.abs(st["P_out"] - st["P_in"]).max() <= TOL_MOM32 * sP
+    assert np.abs(st["L_out"] - st["L_in"]).max() <= TOL_MOM32 * sL
+    keep = (s.body == 0) | (s.body == 1)
+    sub = _subset(s, keep, (0, 1))
+    rv, rC, rst = run_oracle(sub, mu_pair=sub.mu_pair)
+    check(sub, (v[keep], Cm[keep], None), (rv, rC, rst), TOL_V32, TOL_C32, None, "eight bodies, pair 0 of full scene")
