@@ -298,6 +298,11 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
   const int s0 = p.item_start[item];
   const int s1 = item + 1 < p.n_items ? p.item_start[item + 1] : n;
   const int count = s1 - s0;  // <= kChunk
+  // Particles are sorted by cell (z-major) inside an item, so its stencils
+  // reach only tile layers c in [lz(first), lz(last) + 3]: fetch, clear and
+  // flush just those.
+  const int t_lo = (int)(to_bits(p.pn[s0].w) >> 4) * (kTile * kTile);
+  const int t_hi = ((int)(to_bits(p.pn[s1 - 1].w) >> 4) + 4) * (kTile * kTile);
   // Issue this thread's particle loads first so that they are in flight
   // while the CTA fetches its grid tile.
   constexpr bool kReadD = MODE == kModeMid || MODE == kModeLast;
@@ -319,19 +324,19 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
     snb[tid] = p.page[((bz + oz) * p.box.ny + (by + oy)) * p.box.nx + (bx + ox)];
   }
   if (kP2G)
-    for (int t = tid; t < kTile3; t += kChunk)
+    for (int t = t_lo + tid; t < t_hi; t += kChunk)
 #pragma unroll
       for (int a = 0; a < kComp; ++a) sacc[a][t] = T(0);
   __syncthreads();
   if (kG2P) {
-    for (int t = tid; t < kTile3; t += kChunk) {
+    for (int t = t_lo + tid; t < t_hi; t += kChunk) {
       const int node = tile_node(snb, t);
       sv[t] = node >= 0 ? p.gv[node] : V4<T>{T(0), T(0), T(0), T(0)};
     }
     __syncthreads();
   }
   if (MODE == kModeMu) {
-    for (int t = tid; t < kTile3; t += kChunk) {
+    for (int t = t_lo + tid; t < t_hi; t += kChunk) {
       const int node = tile_node(snb, t);
       smask[t] = node >= 0 ? p.gmask[node] : 0u;
     }
@@ -516,7 +521,7 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
   __syncthreads();
 
   // ---------------- add the tile to the global grid ----------------
-  for (int t = tid; t < kTile3; t += kChunk) {
+  for (int t = t_lo + tid; t < t_hi; t += kChunk) {
     const int node = tile_node(snb, t);
     if (node < 0) continue;
     if constexpr (kMass) {
