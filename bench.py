@@ -13,6 +13,9 @@ Workloads (seeded, synthetic, shaped like the paper's bodies):
   four_bodies   4 bodies, 200,000 FE nodes, h = 1/256, mu = 0.3, N = 8, FP32 (default)
   two_cubes     2 cubes of 8^3 nodes, h = 1/32, mu = 0.3, N = 10, FP64
   eight_bodies  8 bodies, 4,000,000 nodes, h = 1/512, per-pair mu, N = 8, FP32
+  batched64     64 independent scenes, 1k-200k nodes and 2-6 bodies each, h in
+                {1/64, 1/128, 1/256}, mu = 0.3, N = 8, FP32, one batched call per
+                step; also reports the same scenes stepped one call each
 
 Multi-GPU (torchrun): every rank steps its own copy of the scene (the scenes
 are independent; no collective on the data path); value = all ranks'
@@ -50,7 +53,28 @@ def make_scene(name):
     raise SystemExit(f"unknown workload {name}")
 
 
-def workload_config(name, s, dt):
+def make_workload(name):
+    """(list of scenes, dtype, batched)."""
+    from paper_2108_02259_gb300 import scenes
+
+    if name == "batched64":
+        return scenes.batch_of_scenes(64), np.float32, True
+    s, dt = make_scene(name)
+    return [s], dt, False
+
+
+def workload_config(name, sc, dt):
+    if len(sc) > 1:
+        P = sum(s.n for s in sc)
+        return {"workload": f"{name}: {len(sc)} independent scenes, {P} FE nodes in total "
+                            f"({min(s.n for s in sc)}-{max(s.n for s in sc)} per scene, "
+                            f"{min(s.n_bodies for s in sc)}-{max(s.n_bodies for s in sc)} bodies), "
+                            f"h in {{1/64, 1/128, 1/256}}, N={sc[0].n_iter}, mu={sc[0].mu}, one batched call per step",
+                "particles": P, "scenes": len(sc), "n_iter": sc[0].n_iter,
+                "transfer_pairs_per_step": sc[0].n_iter + 1,
+                "precision": "fp32 (fp64 node momentum at multi-body nodes)",
+                "l2": "flushed before every timed step (256 MiB write)"}
+    s = sc[0]
     return {
         "workload": f"{name}: {s.n_bodies} bodies, {s.n} FE nodes, h=1/{round(1 / s.h)}, N={s.n_iter}, "
                     + ("mu per body pair" if s.mu_pair is not None else f"mu={s.mu}"),
@@ -152,22 +176,44 @@ def bounded_sample(s, max_particles=1_100_000):
     return sub, f"bodies 0 and 1 of the scene ({sub.n} of {s.n} particles)"
 
 
-def cpu_baseline(s, budget_s=12.0):
-    """The FP64 oracle as it stands, single-threaded, on the host cores."""
+def oracle_sample(sc):
+    """The oracle's bounded sample of a workload: whole scenes (the first
+    ones of a batch, up to ~300k particles), or for one large scene its
+    first approaching pair of bodies."""
+    if len(sc) == 1:
+        s, what = bounded_sample(sc[0])
+        return [s], what
+    out, P = [], 0
+    for s in sc:
+        if P + s.n > 300_000 and out:
+            break
+        out.append(s)
+        P += s.n
+    return out, f"the first {len(out)} of {len(sc)} scenes ({P} particles)"
+
+
+def run_oracle_steps(sample):
     import oracle
 
-    s, what = bounded_sample(s)
-    t0 = time.perf_counter()
-    steps = 0
-    while True:
+    for s in sample:
         oracle.contact_step(s.x, s.v, s.C, s.m, s.nrm, s.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
                             mu_pair=s.mu_pair)
+    return sum(s.n * (s.n_iter + 1) for s in sample)
+
+
+def cpu_baseline(sc, budget_s=12.0):
+    """The FP64 oracle as it stands, single-threaded, on the host cores."""
+    sample, what = oracle_sample(sc)
+    t0 = time.perf_counter()
+    steps = units = 0
+    while True:
+        units += run_oracle_steps(sample)
         steps += 1
         el = time.perf_counter() - t0
         if el > budget_s or steps >= 8:
             break
-    return {"value": s.n * (s.n_iter + 1) * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} step(s) of {what}, N={s.n_iter}, {el:.1f} s single-threaded FP64"}
+    return {"value": units / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} step(s) of {what}, N={sample[0].n_iter}, {el:.1f} s single-threaded FP64"}
 
 
 def run_reference(args):
@@ -177,21 +223,20 @@ def run_reference(args):
     import oracle
 
     oracle.build()
-    full, dt = make_scene(args.workload)
-    s, what = bounded_sample(full)
+    sc, dt, _ = make_workload(args.workload)
+    sample, what = oracle_sample(sc)
     for _ in range(args.warmup):
-        oracle.contact_step(s.x, s.v, s.C, s.m, s.nrm, s.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
-                            mu_pair=s.mu_pair)
+        run_oracle_steps(sample)
     t0 = time.perf_counter()
+    units = 0
     for _ in range(args.steps):
-        oracle.contact_step(s.x, s.v, s.C, s.m, s.nrm, s.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
-                            mu_pair=s.mu_pair)
+        units += run_oracle_steps(sample)
     el = time.perf_counter() - t0
-    value = s.n * (s.n_iter + 1) * args.steps / el
+    value = units / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args.workload, full, dt),
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args.workload, sc, dt),
         "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
                          "sample": f"each step: {what}, single-threaded FP64 oracle"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -205,7 +250,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="four_bodies", choices=["four_bodies", "two_cubes", "eight_bodies"])
+    ap.add_argument("--workload", default="four_bodies",
+                    choices=["four_bodies", "two_cubes", "eight_bodies", "batched64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -228,35 +274,50 @@ def main():
     from paper_2108_02259_gb300 import apic, build
 
     build.build()
-    s, dt = make_scene(args.workload)
+    sc, dt, batched = make_workload(args.workload)
     tdt = torch.float32 if dt == np.float32 else torch.float64
-    f = s.astype(dt)
+    N = sc[0].n_iter
+    P = sum(s.n for s in sc)
 
     def t(a, d):
         return torch.as_tensor(np.ascontiguousarray(a), dtype=d).to(dev)
 
-    X = t(f.x, torch.float64)
-    Vv, Cc, M, NR = t(f.v, tdt), t(f.C, tdt), t(f.m, tdt), t(f.nrm, tdt)
-    B = t(f.body, torch.int32)
-    Vo, Co = torch.empty_like(Vv), torch.empty_like(Cc)
+    bs = []
+    for s in sc:
+        f = s.astype(dt)
+        bs.append(apic.BatchScene(t(f.x, torch.float64), t(f.v, tdt), t(f.C, tdt), t(f.m, tdt), t(f.nrm, tdt),
+                                  t(f.body, torch.int32), s.h, s.mu, n_bodies=s.n_bodies, mu_pair=s.mu_pair))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     ctx = apic.Context(dev.index)
 
+    def step_one(b):
+        apic.contact_step(ctx, b.x, b.v, b.C, b.m, b.nrm, b.body, b.h, b.mu, N, n_bodies=b.n_bodies,
+                          mu_pair=b.mu_pair, v_out=b.v_out, C_out=b.C_out, stream=stream)
+
     def step():
-        apic.contact_step(ctx, X, Vv, Cc, M, NR, B, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies, mu_pair=s.mu_pair,
-                          v_out=Vo, C_out=Co, stream=stream)
+        if batched:
+            apic.contact_step_batched(ctx, bs, N, stream=stream)
+        else:
+            step_one(bs[0])
 
     # one checked step: the device's own momentum balance
-    r = apic.contact_step(ctx, X, Vv, Cc, M, NR, B, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies, mu_pair=s.mu_pair,
-                          v_out=Vo, C_out=Co, stream=stream, stats=True)
-    st = r.stats
+    st = apic.contact_step_batched(ctx, bs, N, stream=stream, stats=True)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    def timed(fn, steps):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            fn()
+            ends[i].record(stream)
+        torch.cuda.synchronize(dev)
+        return sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+
     try:  # nvidia-smi wants the physical GPU: address it by UUID
         clocks = Clocks("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
     except Exception:
@@ -266,29 +327,32 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     clocks.start()
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        starts[i].record(stream)
-        step()
-        ends[i].record(stream)
-    torch.cuda.synchronize(dev)
+    t_ms = timed(step, args.steps)
     if ws > 1:
         torch.distributed.barrier()
     ck = clocks.stop()
     prof = ctx.profile()
     ctx.set_profiling(False)
-    t_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     if ws > 1:
         tt = torch.tensor([t_ms], device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         t_ms = float(tt.item())
-    units = s.n * (s.n_iter + 1) * args.steps * ws
+    units = P * (N + 1) * args.steps * ws
     value = units / (t_ms / 1e3)
+
+    # the same scenes one call each (the plain single-scene path)
+    plain = None
+    if batched:
+        for b in bs:
+            step_one(b)
+        torch.cuda.synchronize(dev)
+        t_plain = timed(lambda: [step_one(b) for b in bs], max(2, args.steps // 4))
+        plain = P * (N + 1) * max(2, args.steps // 4) / (t_plain / 1e3)
 
     # roofline of the fused transfer kernel (timed live with events on the launch stream)
     G = prof["active_nodes"]
     iter_avg_ms = prof["iter_ms"] / max(prof["iter_launches"], 1)
-    alg = algorithmic_bytes_per_pass(s.n, G)
+    alg = algorithmic_bytes_per_pass(P, G)
     peak, peak_kind = measured_peak_hbm()
     achieved = alg / (iter_avg_ms / 1e3) / 1e9
     traffic = None
@@ -307,19 +371,30 @@ def main():
         def pin(a, d):
             return torch.as_tensor(np.ascontiguousarray(a), dtype=d).pin_memory().numpy()
 
-        hx, hv, hC, hm, hn = pin(f.x, torch.float64), pin(f.v, tdt), pin(f.C, tdt), pin(f.m, tdt), pin(f.nrm, tdt)
-        hb = pin(f.body, torch.int32)
-        hvo, hCo = pin(np.zeros_like(f.v), tdt), pin(np.zeros_like(f.C), tdt)
+        hs = []
+        for s in sc:
+            f = s.astype(dt)
+            hs.append(apic.BatchScene(pin(f.x, torch.float64), pin(f.v, tdt), pin(f.C, tdt), pin(f.m, tdt),
+                                      pin(f.nrm, tdt), pin(f.body, torch.int32), s.h, s.mu, n_bodies=s.n_bodies,
+                                      mu_pair=s.mu_pair, v_out=pin(np.zeros_like(f.v), tdt),
+                                      C_out=pin(np.zeros_like(f.C), tdt)))
+
+        def host_step():
+            if batched:
+                apic.contact_step_batched(ctx, hs, N, stream=stream)
+            else:
+                h = hs[0]
+                apic.contact_step(ctx, h.x, h.v, h.C, h.m, h.nrm, h.body, h.h, h.mu, N, n_bodies=h.n_bodies,
+                                  mu_pair=h.mu_pair, v_out=h.v_out, C_out=h.C_out, stream=stream)
+
         for _ in range(2):
-            apic.contact_step(ctx, hx, hv, hC, hm, hn, hb, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
-                              mu_pair=s.mu_pair, v_out=hvo, C_out=hCo, stream=stream)
+            host_step()
         torch.cuda.synchronize(dev)
         if ws > 1:
             torch.distributed.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            apic.contact_step(ctx, hx, hv, hC, hm, hn, hb, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
-                              mu_pair=s.mu_pair, v_out=hvo, C_out=hCo, stream=stream)
+            host_step()
         torch.cuda.synchronize(dev)
         el = time.perf_counter() - t0
         if ws > 1:
@@ -328,19 +403,20 @@ def main():
             el = float(tt.item())
         isz = np.dtype(dt).itemsize
         e2e = {"value": units / el, "unit": UNIT,
-               "h2d_bytes_per_step": int(s.n * (24 + 4 + isz * (3 + 9 + 1 + 3))),
-               "d2h_bytes_per_step": int(s.n * isz * (3 + 9))}
+               "h2d_bytes_per_step": int(P * (24 + 4 + isz * (3 + 9 + 1 + 3))),
+               "d2h_bytes_per_step": int(P * isz * (3 + 9))}
 
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return 0
-    sP = float(np.sum(s.m * np.linalg.norm(s.v, axis=1)))
+    sP = float(sum(np.sum(s.m * np.linalg.norm(s.v, axis=1)) for s in sc))
+    drift = float(sum(np.abs(x["P_out"] - x["P_in"]).max() for x in st)) / sP
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if dt == np.float64 else "f32", "data": "synthetic",
-        "config": workload_config(args.workload, s, dt),
+        "config": workload_config(args.workload, sc, dt),
         "e2e": e2e,
         "gpu_launches": int(prof["kernel_launches"]),
         "sort_primitive_calls": int(prof["sort_launches"]),
@@ -352,13 +428,18 @@ def main():
         "step_breakdown_ms": {"prep_incl_mass_p2g": prof["prep_ms"] / max(prof["steps"], 1),
                               "transfer_passes": prof["iter_ms"] / max(prof["steps"], 1),
                               "step": prof["step_ms"] / max(prof["steps"], 1)},
-        "momentum_check": {"P_drift_rel": float(np.abs(st["P_out"] - st["P_in"]).max() / sP),
-                           "multibody_nodes": st["multibody_nodes"], "active_blocks": st["active_blocks"],
-                           "work_items": st["work_items"]},
+        "momentum_check": {"P_drift_rel": drift,
+                           "multibody_nodes": int(sum(x["multibody_nodes"] for x in st)),
+                           "active_blocks": int(sum(x["active_blocks"] for x in st)),
+                           "work_items": int(sum(x["work_items"] for x in st))},
         "clocks": ck,
     }
+    if plain is not None:
+        line["plain_single_scene"] = {"value": plain, "unit": UNIT,
+                                      "what": "the same scenes, one apic_contact_step call each",
+                                      "batched_over_plain": value / plain}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(s)
+        line["cpu_baseline"] = cpu_baseline(sc)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -144,6 +144,17 @@ apic_status apic_destroy(apic_ctx* ctx);
  * non-finite or out-of-range positions) returns INVALID_ARG. */
 apic_status apic_contact_step(apic_ctx* ctx, const apic_step_args* args, void* stream, apic_stats* stats);
 
+/* Several independent scenes in one call (Sec. 2.3 series on each).
+ * Each scene keeps its own particles, grid spacing h, friction (mu or
+ * mu_pair) and outputs; the scenes share one sort, one sparse page table
+ * and one launch per transfer pass over the flattened work list, so small
+ * scenes fill the GPU together.  All scenes must share `flags` and
+ * `n_iter`.  `stats` is NULL or an array of n_scenes entries.  Host or
+ * device pointers, synchronisation and errors as apic_contact_step; an error
+ * message names the offending scene. */
+apic_status apic_contact_step_batched(apic_ctx* ctx, const apic_step_args* scenes, int32_t n_scenes,
+                                      void* stream, apic_stats* stats);
+
 /* The contact step for callers that cannot allocate device memory.
  * (The paper has no counterpart; this is a deployment variant.)
  *

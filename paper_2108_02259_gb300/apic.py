@@ -33,6 +33,7 @@ APIC_VARIANT_SEP23 = 1 << 3
 EXPORTED = [
     "apic_last_error", "apic_version", "apic_create", "apic_destroy", "apic_contact_step",
     "apic_set_profiling", "apic_get_profile", "apic_scratch_bytes", "apic_contact_step_static",
+    "apic_contact_step_batched",
 ]
 
 
@@ -89,6 +90,8 @@ def load(path: str = LIB_PATH):
     lib.apic_create.argtypes = [C.POINTER(P), C.c_int32, C.c_size_t]
     lib.apic_destroy.argtypes = [P]
     lib.apic_contact_step.argtypes = [P, C.POINTER(StepArgs), P, C.POINTER(Stats)]
+    lib.apic_contact_step_batched.argtypes = [P, C.POINTER(StepArgs), C.c_int32, P, C.POINTER(Stats)]
+    lib.apic_contact_step_batched.restype = C.c_int32
     lib.apic_contact_step_static.argtypes = [C.POINTER(StepArgs), P, C.POINTER(Stats)]
     lib.apic_contact_step_static.restype = C.c_int32
     lib.apic_set_profiling.argtypes = [P, C.c_int32]
@@ -258,3 +261,54 @@ def contact_step_static(x, v, Cm, m, nrm, body, h: float, mu: float, n_iter: int
     st = Stats() if stats else None
     _check(lib.apic_contact_step_static(C.byref(a), stream.cuda_stream, C.byref(st) if stats else None))
     return StepResult(v_out, C_out, st.as_dict() if stats else None)
+
+
+class BatchScene:
+    """One scene of a batched call: device tensors (or numpy arrays for the
+    host path) in the layouts of contact_step."""
+
+    def __init__(self, x, v, Cm, m, nrm, body, h, mu, n_bodies=None, mu_pair=None, v_out=None, C_out=None):
+        self.x, self.v, self.C, self.m, self.nrm, self.body = x, v, Cm, m, nrm, body
+        self.h, self.mu, self.mu_pair = float(h), float(mu), mu_pair
+        n = int(x.shape[0])
+        self.n_bodies = n_bodies if n_bodies is not None else ((int(body.max()) + 1) if n else 1)
+        if v_out is None:
+            v_out = v.new_empty(v.shape) if _is_torch(v) else np.empty_like(v)
+        if C_out is None:
+            C_out = Cm.new_empty(Cm.shape) if _is_torch(Cm) else np.empty_like(Cm)
+        self.v_out, self.C_out = v_out, C_out
+
+
+def contact_step_batched(ctx: Context, scenes, n_iter: int, flags: int = 0, stream=None, stats: bool = False):
+    """apic_contact_step_batched over a list of BatchScene (all device or all
+    host arrays, one precision).  Returns the per-scene stats (or None); the
+    results are in each scene's v_out / C_out."""
+    lib = load()
+    ns = len(scenes)
+    dev = _is_torch(scenes[0].x)
+    if dev:
+        import torch
+
+        fp64 = scenes[0].v.dtype == torch.float64
+        if stream is None:
+            stream = torch.cuda.current_stream(scenes[0].x.device)
+        sptr = stream.cuda_stream
+    else:
+        fp64 = scenes[0].v.dtype == np.float64
+        sptr = None if stream is None else stream.cuda_stream
+        flags |= APIC_HOST_PTRS
+    if fp64:
+        flags |= APIC_FP64
+    arr = (StepArgs * ns)()
+    keep = []
+    for i, sc in enumerate(scenes):
+        mp = None
+        if sc.mu_pair is not None:
+            mp = np.ascontiguousarray(np.asarray(sc.mu_pair, np.float64).reshape(sc.n_bodies, sc.n_bodies))
+            keep.append(mp)
+        arr[i] = StepArgs(int(sc.x.shape[0]), int(sc.n_bodies), int(n_iter), _ptr(sc.body), _ptr(sc.x), _ptr(sc.v),
+                          _ptr(sc.C), _ptr(sc.m), _ptr(sc.nrm), _ptr(sc.v_out), _ptr(sc.C_out), sc.h, sc.mu,
+                          None if mp is None else mp.ctypes.data, int(flags))
+    st = (Stats * ns)() if stats else None
+    _check(lib.apic_contact_step_batched(ctx.handle, arr, ns, sptr, st if stats else None))
+    return [st[i].as_dict() for i in range(ns)] if stats else None

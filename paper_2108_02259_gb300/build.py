@@ -17,7 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libapiccontact.so")
 SOURCES = ["kernels.cu", "api.cu", "static_step.cu"]
-HEADERS = [os.path.join(CSRC, "apic_internal.h"), os.path.join(ROOT, "include", "apiccontact.h")]
+HEADERS = [os.path.join(CSRC, "apic_internal.h"), os.path.join(CSRC, "pipeline.cuh"),
+           os.path.join(ROOT, "include", "apiccontact.h")]
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -34,13 +34,10 @@ constexpr int kErrBox = 8;  // a particle lies outside a page-table box reused f
 
 // Device-side scalars the host reads back while sizing the grid.
 struct DevScalars {
-  int bbox[6];   // min (bx, by, bz), max (bx, by, bz) of particle blocks
   int err;       // kErr* bits
   int n_items;   // work items
   int n_blocks;  // active grid blocks
   int pad;
-  double mom[12];  // P_in, L_in, P_out, L_out accumulators
-  unsigned long long multibody;
 };
 
 // Dense page table over a box of grid blocks (block coordinates relative to
@@ -49,6 +46,30 @@ struct DevScalars {
 struct Box {
   int ox, oy, oz;  // origin block coordinates
   int nx, ny, nz;  // extent in blocks
+};
+
+// One scene of a batch as the kernels see it.  Scenes are independent: each
+// has its own grid spacing, friction and page-table box; their boxes are
+// laid end to end in one page table and their particles end to end in one
+// index space.
+struct SceneDev {
+  const double* x;
+  const int32_t* body;
+  const void* v;
+  const void* C;
+  const void* m;
+  const void* nrm;
+  void* v_out;
+  void* C_out;
+  long long part_off;  // first particle of the scene in the batch
+  long long page_off;  // first page-table entry of the scene's box
+  int n;
+  int n_bodies;
+  int mu_off;          // offset of the scene's body-pair friction table, or -1
+  int pad;
+  Box box;
+  int pad2[2];
+  double h, inv_h, mu;
 };
 
 // Iteration-kernel modes (one transfer pair each; Sec. 2.3).
@@ -68,17 +89,17 @@ template <class T>
 struct IterParams {
   int n_items;
   int n_particles;
-  int n_bodies;
-  Box box;
+  int max_bodies;          // key multiplier: bodies of the largest scene
+  int n_scenes;
+  const SceneDev* sc;      // [n_scenes]
   const int* item_start;   // [n_items] first sorted particle of each item
-  const int2* item_info;   // [n_items] (block linear index in the box, body)
-  const int* page;         // [box volume] compact block id or -1
+  const int4* item_info;   // [n_items] (global page index of the block, body, scene, 0)
+  const int* page;         // page table: compact block id or -1
   const V4<T>* pt;         // [n] (t_x, t_y, t_z, m) sorted
   const V4<T>* pn;         // [n] (n_x, n_y, n_z, local cell bits) sorted
-  const T* mup;            // [n] per-particle mu or nullptr
-  T mu;                    // scalar mu
-  const T* mu_pair;        // [n_bodies^2] device copy of the pair table (kModeMu)
-  T* gmb;                  // [n_bodies * nodes] per-body node mass, or nullptr
+  const T* mup;            // [n] per-particle mu or nullptr (then the scene's mu)
+  const T* mu_table;       // concatenated body-pair friction tables (kModeMu)
+  T* gmb;                  // [max_bodies * nodes] per-body node mass, or nullptr
   T* mup_out;              // [n] written by kModeMu
   int64_t n_nodes;
   const V4<T>* V;          // [3n] sorted V = (v, h C) as 3 planes of n
@@ -88,48 +109,47 @@ struct IterParams {
   T* gm;                   // grid mass, [nodes]
   uint32_t* gmask;         // body bits, [nodes]
   V4<double>* gp64;        // FP64 momentum at multi-body nodes (FP32 path), [nodes]
-  const int* perm;         // sorted -> caller index
-  void* v_out;             // caller order outputs (T)
-  void* C_out;
-  T inv_h;
+  const int* perm;         // sorted -> batch particle index
   int pic;                 // PIC transfers
   int sep23;               // Sec. 2.3 rule
 };
 
+// Cells, validation, per-scene bounding boxes of particle blocks (sbbox[6 s]).
 template <class T>
-cudaError_t launch_cells(int64_t n, const double* x, const int32_t* body, const T* m, double inv_h,
-                         int n_bodies, int4* cellb, DevScalars* ds, cudaStream_t s);
+cudaError_t launch_cells(int64_t n, const SceneDev* sc, int ns, int4* cellb, int* sbbox, int* err,
+                         cudaStream_t s);
 template <class K>
-cudaError_t launch_keys(int64_t n, const int4* cellb, Box box, int n_bodies, K* keys, int* vals,
-                        int* err, cudaStream_t s);
+cudaError_t launch_keys(int64_t n, const SceneDev* sc, int ns, const int4* cellb, int max_bodies, K* keys,
+                        int* vals, int* err, cudaStream_t s);
 template <class T>
-cudaError_t launch_gather(int64_t n, const int* perm, const int4* cellb, const double* x, const T* v,
-                          const T* C, const T* m, const T* nrm, double h, double inv_h, V4<T>* pt,
+cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm, const int4* cellb, V4<T>* pt,
                           V4<T>* pn, V4<T>* V, cudaStream_t s);
 template <class K>
 cudaError_t launch_heads(int64_t n, const K* keys, int* flags, cudaStream_t s);
 template <class K>
-cudaError_t launch_item_info(const int* item_start, const int* n_items, const K* keys, int n_bodies,
-                             int2* item_info, int max_items, cudaStream_t s);
-cudaError_t launch_mark(int64_t n, const int4* cellb, Box box, int* flags, int* err, cudaStream_t s);
+cudaError_t launch_item_info(const int* item_start, const int* n_items, const K* keys, int max_bodies,
+                             const SceneDev* sc, int ns, int4* item_info, int max_items, cudaStream_t s);
 cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* list, int* page,
                            int* count, cudaStream_t s);
 template <class K>
-cudaError_t launch_mark_items(const int* item_start, const int2* item_info, const int* n_items, const K* keys,
-                              int64_t n, int max_items, Box box, int* flags, cudaStream_t s);
+cudaError_t launch_mark_items(const int* item_start, const int4* item_info, const int* n_items, const K* keys,
+                              int64_t n, int max_items, const SceneDev* sc, int* flags, cudaStream_t s);
 template <class T>
-cudaError_t launch_items(const IterParams<T>& p, int mode, int threads, cudaStream_t s);
+cudaError_t launch_items(const IterParams<T>& p, int mode, cudaStream_t s);
 // all64: take every node's momentum from the FP64 accumulators (after kModeMassV).
 template <class T>
 cudaError_t launch_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask, V4<T>* gp,
                              V4<double>* gp64, V4<T>* gv, int all64, cudaStream_t s);
+// FP64 totals of one scene: out6 = (P, L).
 template <class T>
 cudaError_t launch_momentum(int64_t n, const double* x, const T* v, const T* C, const T* m, double h,
                             double* out6, cudaStream_t s);
+// Per-scene counts: out[3 s] = (multi-body nodes, active blocks, work items).
+cudaError_t launch_scene_counts(int n_blocks, const int* blist, const uint32_t* gmask, int n_items,
+                                const int4* item_info, const SceneDev* sc, int ns, unsigned long long* out,
+                                cudaStream_t s);
+
 // Set the calling thread's message returned by apic_last_error().
 void set_last_error(const char* msg);
-
-cudaError_t launch_count_multibody(int64_t n_nodes, const uint32_t* gmask,
-                                   unsigned long long* out, cudaStream_t s);
 
 }  // namespace apic

@@ -290,10 +290,14 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
   const int n = p.n_particles;
   const int item = blockIdx.x;
   if (item >= p.n_items) return;
-  const int2 info = p.item_info[item];
-  const int bx = info.x % p.box.nx;
-  const int by = (info.x / p.box.nx) % p.box.ny;
-  const int bz = info.x / (p.box.nx * p.box.ny);
+  const int4 info = p.item_info[item];
+  const SceneDev& S = p.sc[info.z];
+  const Box box = S.box;
+  const long long page_off = S.page_off;
+  const int blin = (int)(info.x - page_off);
+  const int bx = blin % box.nx;
+  const int by = (blin / box.nx) % box.ny;
+  const int bz = blin / (box.nx * box.ny);
   const int body = info.y;
   const int s0 = p.item_start[item];
   const int s1 = item + 1 < p.n_items ? p.item_start[item + 1] : n;
@@ -321,7 +325,7 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
   }
   if (tid < 27) {
     const int ox = tid % 3 - 1, oy = (tid / 3) % 3 - 1, oz = tid / 9 - 1;
-    snb[tid] = p.page[((bz + oz) * p.box.ny + (by + oy)) * p.box.nx + (bx + ox)];
+    snb[tid] = p.page[page_off + ((bz + oz) * box.ny + (by + oy)) * box.nx + (bx + ox)];
   }
   if (kP2G)
     for (int t = t_lo + tid; t < t_hi; t += kChunk)
@@ -349,7 +353,9 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
     const uint32_t loc = to_bits(pn.w);
     const int base = (int)(loc >> 4) * (kTile * kTile) + (int)((loc >> 2) & 3) * kTile + (int)(loc & 3);
     sloc[tid] = base;
-    if (MODE == kModeMu) {
+    if (MODE == kModeMu && S.mu_off < 0) {
+      p.mup_out[s] = (T)S.mu;  // a scene with one scalar mu
+    } else if (MODE == kModeMu) {
       // mu_p = sum_{b' != b} mu(b,b') M_b'p / sum_{b' != b} M_b'p with
       // M_b'p = sum_i N_ip m_{b',i}; mu(b,b) when no other body is near.
       T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4];
@@ -373,11 +379,11 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
           const int bo = __ffs(other) - 1;
           other &= other - 1;
           const T M = p.gmb[(int64_t)bo * p.n_nodes + node];
-          num += w * p.mu_pair[body * p.n_bodies + bo] * M;
+          num += w * p.mu_table[S.mu_off + body * S.n_bodies + bo] * M;
           den += w * M;
         }
       }
-      p.mup_out[s] = den > T(0) ? num / den : p.mu_pair[body * p.n_bodies + body];
+      p.mup_out[s] = den > T(0) ? num / den : p.mu_table[S.mu_off + body * S.n_bodies + body];
     } else if (MODE == kModeMass || MODE == kModeP2GV || MODE == kModeMassV) {
       T wx[4], dx[4];
       bspline(pt.x, wx, dx);
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
       else
         g2p_tile<T, true>(sv, base, wx, dx, wy, dy, wz, dz, hv, hC);
       const T nrm[3] = {pn.x, pn.y, pn.z};
-      const T mu = p.mup ? p.mup[s] : p.mu;
+      const T mu = p.mup ? p.mup[s] : (T)S.mu;
       T dv[3], dC[9];
       bool out = false;
       if (MODE == kModeFirst || MODE == kModeOnly) {
@@ -428,13 +434,14 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
         // V_hat = V + Delta_N, back in caller order, C = Ch / h
         T v[3], C[9];
         load12(p.V, n, s, v, C);
-        const int64_t idx = p.perm[s];
-        T* vo = static_cast<T*>(p.v_out);
-        T* Co = static_cast<T*>(p.C_out);
+        const int64_t idx = p.perm[s] - S.part_off;
+        T* vo = static_cast<T*>(S.v_out);
+        T* Co = static_cast<T*>(S.C_out);
+        const T inv_h = (T)S.inv_h;
 #pragma unroll
         for (int a = 0; a < 3; ++a) vo[3 * idx + a] = v[a] + dv[a];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) Co[9 * idx + a] = (C[a] + dC[a]) * p.inv_h;
+        for (int a = 0; a < 9; ++a) Co[9 * idx + a] = (C[a] + dC[a]) * inv_h;
       } else {
         store12(p.D, n, s, dv, dC);
         T u[3], uC[9];
@@ -578,18 +585,51 @@ __device__ __forceinline__ bool bad_mass(T m) {
   return !(m > T(0)) || !isfinite((double)m);
 }
 
+// Scene of batch particle i / of global page-table entry g (binary search
+// over the scenes' offsets; empty scenes share the next scene's offset).
+__device__ __forceinline__ int scene_of_particle(const SceneDev* sc, int ns, long long i) {
+  int lo = 0, hi = ns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sc[mid].part_off <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int scene_of_page(const SceneDev* sc, int ns, long long g) {
+  int lo = 0, hi = ns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sc[mid].page_off <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Cell of every particle (x/h in FP64, floor), validation, and the bounding
+// box of each scene's particle blocks.  A CTA whose particles all belong to
+// one scene reduces the box in shared memory and adds it with one set of
+// atomics; CTAs that straddle scenes add per particle.
 template <class T>
-__global__ void k_cells(int64_t n, const double* __restrict__ x, const int32_t* __restrict__ body,
-                        const T* __restrict__ m, double inv_h, int n_bodies, int4* cellb,
-                        DevScalars* ds) {
+__global__ void k_cells(int64_t n, const SceneDev* __restrict__ sc, int ns, int4* cellb, int* sbbox, int* errp) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p_first = blockIdx.x * (int64_t)blockDim.x;
+  const int64_t p_last = min(p_first + blockDim.x, n) - 1;
+  __shared__ int uniform_scene;
+  if (threadIdx.x == 0) {
+    const int a = scene_of_particle(sc, ns, p_first), b = scene_of_particle(sc, ns, p_last);
+    uniform_scene = a == b ? a : -1;
+  }
+  __syncthreads();
   int lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
   int err = 0;
+  int scene = uniform_scene;
   if (p < n) {
+    if (scene < 0) scene = scene_of_particle(sc, ns, p);
+    const SceneDev& S = sc[scene];
+    const int64_t i = p - S.part_off;
     int c[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const double xs = x[3 * p + d] * inv_h;
+      const double xs = S.x[3 * i + d] * S.inv_h;
       // |x/h| < 2^29 keeps cells, blocks and their margins inside int32
       if (!(fabs(xs) < 536870912.0)) {
         err |= kErrPos;
@@ -599,10 +639,21 @@ __global__ void k_cells(int64_t n, const double* __restrict__ x, const int32_t* 
       }
       lo[d] = hi[d] = c[d] >> 2;
     }
-    const int b = body[p];
-    if (b < 0 || b >= n_bodies) err |= kErrBody;
-    if (bad_mass(m[p])) err |= kErrMass;
+    const int b = S.body[i];
+    if (b < 0 || b >= S.n_bodies) err |= kErrBody;
+    if (bad_mass(static_cast<const T*>(S.m)[i])) err |= kErrMass;
     cellb[p] = make_int4(c[0], c[1], c[2], b);
+    if (uniform_scene < 0) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        atomicMin(&sbbox[6 * scene + d], lo[d]);
+        atomicMax(&sbbox[6 * scene + 3 + d], hi[d]);
+      }
+    }
+  }
+  if (uniform_scene < 0) {
+    if (err) atomicOr(errp, err);
+    return;
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -613,7 +664,6 @@ __global__ void k_cells(int64_t n, const double* __restrict__ x, const int32_t* 
     }
     err |= __shfl_xor_sync(0xffffffffu, err, off);
   }
-  // block reduction, then one set of atomics per block
   __shared__ int red[7][32];
   const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if ((threadIdx.x & 31) == 0) {
@@ -645,19 +695,24 @@ __global__ void k_cells(int64_t n, const double* __restrict__ x, const int32_t* 
     if (l == 0 && lo[0] != INT32_MAX) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        atomicMin(&ds->bbox[d], lo[d]);
-        atomicMax(&ds->bbox[3 + d], hi[d]);
+        atomicMin(&sbbox[6 * uniform_scene + d], lo[d]);
+        atomicMax(&sbbox[6 * uniform_scene + 3 + d], hi[d]);
       }
-      if (err) atomicOr(&ds->err, err);
+      if (err) atomicOr(errp, err);
     }
   }
 }
 
+// Sort key: ((global page index of the cell's block) * max_bodies + body) << 6
+// | cell-in-block.  Sorting by it groups particles by scene, block and body,
+// and orders each group by cell (z-major).
 template <class K>
-__global__ void k_keys(int64_t n, const int4* __restrict__ cellb, Box box, int n_bodies, K* keys,
-                       int* vals, int* err) {
+__global__ void k_keys(int64_t n, const SceneDev* __restrict__ sc, int ns, const int4* __restrict__ cellb,
+                       int max_bodies, K* keys, int* vals, int* err) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
+  const SceneDev& S = sc[scene_of_particle(sc, ns, p)];
+  const Box box = S.box;
   const int4 c = cellb[p];
   int bx = (c.x >> 2) - box.ox, by = (c.y >> 2) - box.oy, bz = (c.z >> 2) - box.oz;
   // every particle block must keep a one-block margin inside the box
@@ -667,29 +722,34 @@ __global__ void k_keys(int64_t n, const int4* __restrict__ cellb, Box box, int n
     by = min(max(by, 1), box.ny - 2);
     bz = min(max(bz, 1), box.nz - 2);
   }
-  const int64_t blin = ((int64_t)bz * box.ny + by) * box.nx + bx;
+  const int64_t gpage = S.page_off + ((int64_t)bz * box.ny + by) * box.nx + bx;
   const uint32_t loc = (uint32_t)(((c.z & 3) << 4) | ((c.y & 3) << 2) | (c.x & 3));
-  keys[p] = (K)((((uint64_t)blin * (uint64_t)n_bodies + (uint64_t)c.w) << 6) | loc);
+  keys[p] = (K)((((uint64_t)gpage * (uint64_t)max_bodies + (uint64_t)c.w) << 6) | loc);
   vals[p] = (int)p;
 }
 
+// Sorted structure-of-arrays: offset in cell and mass, normal and cell bits,
+// and V = (v, h C) in three float4 planes.
 template <class T>
-__global__ void k_gather(int64_t n, const int* __restrict__ perm, const int4* __restrict__ cellb,
-                         const double* __restrict__ x, const T* __restrict__ v,
-                         const T* __restrict__ C, const T* __restrict__ m,
-                         const T* __restrict__ nrm, double h, double inv_h, V4<T>* pt, V4<T>* pn,
-                         V4<T>* V) {
+__global__ void k_gather(int64_t n, const SceneDev* __restrict__ sc, int ns, const int* __restrict__ perm,
+                         const int4* __restrict__ cellb, V4<T>* pt, V4<T>* pn, V4<T>* V) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
-  const int64_t i = perm[s];
-  const int4 c = cellb[i];
-  const T tx = (T)(x[3 * i + 0] * inv_h - (double)c.x);
-  const T ty = (T)(x[3 * i + 1] * inv_h - (double)c.y);
-  const T tz = (T)(x[3 * i + 2] * inv_h - (double)c.z);
-  pt[s] = V4<T>{tx, ty, tz, m[i]};
+  const int64_t g = perm[s];
+  const SceneDev& S = sc[scene_of_particle(sc, ns, g)];
+  const int64_t i = g - S.part_off;
+  const int4 c = cellb[g];
+  const double* x = S.x;
+  const T tx = (T)(x[3 * i + 0] * S.inv_h - (double)c.x);
+  const T ty = (T)(x[3 * i + 1] * S.inv_h - (double)c.y);
+  const T tz = (T)(x[3 * i + 2] * S.inv_h - (double)c.z);
+  pt[s] = V4<T>{tx, ty, tz, static_cast<const T*>(S.m)[i]};
   const uint32_t loc = (uint32_t)(((c.z & 3) << 4) | ((c.y & 3) << 2) | (c.x & 3));
+  const T* nrm = static_cast<const T*>(S.nrm);
   pn[s] = V4<T>{nrm[3 * i + 0], nrm[3 * i + 1], nrm[3 * i + 2], bits_to(T(0), loc)};
-  const T hh = (T)h;
+  const T hh = (T)S.h;
+  const T* v = static_cast<const T*>(S.v);
+  const T* C = static_cast<const T*>(S.C);
   T vv[3], Ch[9];
 #pragma unroll
   for (int a = 0; a < 3; ++a) vv[a] = v[3 * i + a];
@@ -708,30 +768,14 @@ __global__ void k_heads(int64_t n, const K* __restrict__ keys, int* flags) {
 
 template <class K>
 __global__ void k_item_info(const int* __restrict__ item_start, const int* __restrict__ n_items,
-                            const K* __restrict__ keys, int n_bodies, int2* info) {
+                            const K* __restrict__ keys, int max_bodies, const SceneDev* __restrict__ sc, int ns,
+                            int4* info) {
   const int count = *n_items;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     const uint64_t q = (uint64_t)(keys[item_start[i]] >> 6);
-    info[i] = make_int2((int)(q / (uint64_t)n_bodies), (int)(q % (uint64_t)n_bodies));
+    const long long gpage = (long long)(q / (uint64_t)max_bodies);
+    info[i] = make_int4((int)gpage, (int)(q % (uint64_t)max_bodies), scene_of_page(sc, ns, gpage), 0);
   }
-}
-
-// Mark every grid block a particle's 4x4x4-node stencil reaches.
-__global__ void k_mark(int64_t n, const int4* __restrict__ cellb, Box box, int* flags, int* err) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p >= n) return;
-  const int4 c = cellb[p];
-  const int x0 = ((c.x - 1) >> 2) - box.ox, x1 = ((c.x + 2) >> 2) - box.ox;
-  const int y0 = ((c.y - 1) >> 2) - box.oy, y1 = ((c.y + 2) >> 2) - box.oy;
-  const int z0 = ((c.z - 1) >> 2) - box.oz, z1 = ((c.z + 2) >> 2) - box.oz;
-  if (x0 < 0 || y0 < 0 || z0 < 0 || x1 >= box.nx || y1 >= box.ny || z1 >= box.nz) {
-    atomicOr(err, kErrBox);
-    return;
-  }
-  for (int bz = z0; bz <= z1; ++bz)
-    for (int by = y0; by <= y1; ++by)
-      for (int bx = x0; bx <= x1; ++bx)
-        flags[((int64_t)bz * box.ny + by) * box.nx + bx] = 1;
 }
 
 // Mark the grid blocks the stencils of one work item reach: one warp per
@@ -740,9 +784,9 @@ __global__ void k_mark(int64_t n, const int4* __restrict__ cellb, Box box, int* 
 // warp ORs those six conditions over its particles and marks the implied
 // subset of the 3x3x3 blocks around B (once per item, not per particle).
 template <class K>
-__global__ void k_mark_items(const int* __restrict__ item_start, const int2* __restrict__ item_info,
+__global__ void k_mark_items(const int* __restrict__ item_start, const int4* __restrict__ item_info,
                              const int* __restrict__ n_items_p, const K* __restrict__ keys, int64_t n,
-                             Box box, int* flags) {
+                             const SceneDev* __restrict__ sc, int* flags) {
   const int lane = threadIdx.x & 31;
   const int n_items = *n_items_p;
   const int warps = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
@@ -763,9 +807,12 @@ __global__ void k_mark_items(const int* __restrict__ item_start, const int2* __r
                       (dy == 0 || (dy < 0 ? (need & 4) : (need & 8))) &&
                       (dz == 0 || (dz < 0 ? (need & 16) : (need & 32)));
       if (ok) {
-        const int blin = item_info[i].x;
+        const int4 info = item_info[i];
+        const SceneDev& S = sc[info.z];
+        const Box box = S.box;
+        const int blin = (int)(info.x - S.page_off);
         const int bx = blin % box.nx, by = (blin / box.nx) % box.ny, bz = blin / (box.nx * box.ny);
-        flags[((int64_t)(bz + dz) * box.ny + (by + dy)) * box.nx + (bx + dx)] = 1;
+        flags[S.page_off + ((int64_t)(bz + dz) * box.ny + (by + dy)) * box.nx + (bx + dx)] = 1;
       }
     }
   }
@@ -824,12 +871,21 @@ __global__ void k_momentum(int64_t n, const double* __restrict__ x, const T* __r
   }
 }
 
-__global__ void k_count_multibody(int64_t n_nodes, const uint32_t* __restrict__ gmask,
-                                  unsigned long long* out) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const bool mb = i < n_nodes && __popc(gmask[i]) >= 2;
-  const unsigned ball = __ballot_sync(0xffffffffu, mb);
-  if ((threadIdx.x & 31) == 0 && ball) atomicAdd(out, (unsigned long long)__popc(ball));
+// Per-scene diagnostics: multi-body nodes and active blocks (from the
+// compact block list) and work items.
+__global__ void k_scene_counts(int n_blocks, const int* __restrict__ blist, const uint32_t* __restrict__ gmask,
+                               int n_items, const int4* __restrict__ item_info, const SceneDev* __restrict__ sc,
+                               int ns, unsigned long long* out) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < n_blocks; b += stride) {
+    const int scene = scene_of_page(sc, ns, blist[b]);
+    int mb = 0;
+    for (int k = 0; k < kNodesPerBlock; ++k) mb += __popc(gmask[(int64_t)b * kNodesPerBlock + k]) >= 2;
+    if (mb) atomicAdd(&out[3 * scene + 0], (unsigned long long)mb);
+    atomicAdd(&out[3 * scene + 1], 1ull);
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_items; i += stride)
+    atomicAdd(&out[3 * item_info[i].z + 2], 1ull);
 }
 
 inline unsigned grid_for(int64_t n, int threads) {
@@ -839,68 +895,66 @@ inline unsigned grid_for(int64_t n, int threads) {
 }  // namespace
 
 template <class T>
-cudaError_t launch_cells(int64_t n, const double* x, const int32_t* body, const T* m, double inv_h,
-                         int n_bodies, int4* cellb, DevScalars* ds, cudaStream_t s) {
-  k_cells<T><<<grid_for(n, 256), 256, 0, s>>>(n, x, body, m, inv_h, n_bodies, cellb, ds);
+cudaError_t launch_cells(int64_t n, const SceneDev* sc, int ns, int4* cellb, int* sbbox, int* err,
+                         cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_cells<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, cellb, sbbox, err);
   return cudaGetLastError();
 }
 
 template <class K>
-cudaError_t launch_keys(int64_t n, const int4* cellb, Box box, int n_bodies, K* keys, int* vals,
-                        int* err, cudaStream_t s) {
-  k_keys<K><<<grid_for(n, 256), 256, 0, s>>>(n, cellb, box, n_bodies, keys, vals, err);
+cudaError_t launch_keys(int64_t n, const SceneDev* sc, int ns, const int4* cellb, int max_bodies, K* keys,
+                        int* vals, int* err, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_keys<K><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, cellb, max_bodies, keys, vals, err);
   return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t launch_gather(int64_t n, const int* perm, const int4* cellb, const double* x, const T* v,
-                          const T* C, const T* m, const T* nrm, double h, double inv_h, V4<T>* pt,
+cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm, const int4* cellb, V4<T>* pt,
                           V4<T>* pn, V4<T>* V, cudaStream_t s) {
-  k_gather<T><<<grid_for(n, 256), 256, 0, s>>>(n, perm, cellb, x, v, C, m, nrm, h, inv_h, pt, pn, V);
+  if (n <= 0) return cudaSuccess;
+  k_gather<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, perm, cellb, pt, pn, V);
   return cudaGetLastError();
 }
 
 template <class K>
 cudaError_t launch_heads(int64_t n, const K* keys, int* flags, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
   k_heads<K><<<grid_for(n, 256), 256, 0, s>>>(n, keys, flags);
   return cudaGetLastError();
 }
 
 template <class K>
-cudaError_t launch_item_info(const int* item_start, const int* n_items, const K* keys, int n_bodies,
-                             int2* item_info, int max_items, cudaStream_t s) {
+cudaError_t launch_item_info(const int* item_start, const int* n_items, const K* keys, int max_bodies,
+                             const SceneDev* sc, int ns, int4* item_info, int max_items, cudaStream_t s) {
+  if (max_items <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)std::min<int64_t>(grid_for(max_items, 256), 152 * 8);
-  k_item_info<K><<<grid, 256, 0, s>>>(item_start, n_items, keys, n_bodies, item_info);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_mark(int64_t n, const int4* cellb, Box box, int* flags, int* err, cudaStream_t s) {
-  k_mark<<<grid_for(n, 256), 256, 0, s>>>(n, cellb, box, flags, err);
+  k_item_info<K><<<grid, 256, 0, s>>>(item_start, n_items, keys, max_bodies, sc, ns, item_info);
   return cudaGetLastError();
 }
 
 template <class K>
-cudaError_t launch_mark_items(const int* item_start, const int2* item_info, const int* n_items, const K* keys,
-                              int64_t n, int max_items, Box box, int* flags, cudaStream_t s) {
+cudaError_t launch_mark_items(const int* item_start, const int4* item_info, const int* n_items, const K* keys,
+                              int64_t n, int max_items, const SceneDev* sc, int* flags, cudaStream_t s) {
   if (max_items <= 0) return cudaSuccess;
   const int64_t warps = std::min<int64_t>(max_items, 152 * 64);
   k_mark_items<K><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(item_start, item_info, n_items, keys, n,
-                                                                       box, flags);
+                                                                       sc, flags);
   return cudaGetLastError();
 }
 
-cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* list, int* page,
-                           int* count, cudaStream_t s) {
+cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* list, int* page, int* count,
+                           cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_compact<<<grid_for(n, 256), 256, 0, s>>>(n, flags, offs, list, page, count);
   return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t launch_items(const IterParams<T>& p, int mode, int threads, cudaStream_t s) {
+cudaError_t launch_items(const IterParams<T>& p, int mode, cudaStream_t s) {
   if (p.n_items <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)p.n_items;
-  (void)threads;
   switch (mode) {
     case kModeMass: k_items<T, kModeMass><<<grid, kChunk, 0, s>>>(p); break;
     case kModeP2GV: k_items<T, kModeP2GV><<<grid, kChunk, 0, s>>>(p); break;
@@ -933,34 +987,36 @@ cudaError_t launch_momentum(int64_t n, const double* x, const T* v, const T* C, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_count_multibody(int64_t n_nodes, const uint32_t* gmask, unsigned long long* out,
-                                   cudaStream_t s) {
-  if (n_nodes <= 0) return cudaSuccess;
-  k_count_multibody<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, gmask, out);
+cudaError_t launch_scene_counts(int n_blocks, const int* blist, const uint32_t* gmask, int n_items,
+                                const int4* item_info, const SceneDev* sc, int ns, unsigned long long* out,
+                                cudaStream_t s) {
+  const int work = std::max(n_blocks, n_items);
+  if (work <= 0) return cudaSuccess;
+  const unsigned g = (unsigned)std::min<int64_t>(grid_for(work, 256), 152 * 8);
+  k_scene_counts<<<g, 256, 0, s>>>(n_blocks, blist, gmask, n_items, item_info, sc, ns, out);
   return cudaGetLastError();
 }
 
-#define APIC_INST_T(T)                                                                            \
-  template cudaError_t launch_cells<T>(int64_t, const double*, const int32_t*, const T*, double, \
-                                       int, int4*, DevScalars*, cudaStream_t);                    \
-  template cudaError_t launch_gather<T>(int64_t, const int*, const int4*, const double*,          \
-                                        const T*, const T*, const T*, const T*, double, double,   \
-                                        V4<T>*, V4<T>*, V4<T>*, cudaStream_t);                     \
-  template cudaError_t launch_items<T>(const IterParams<T>&, int, int, cudaStream_t);             \
-  template cudaError_t launch_normalize<T>(int64_t, const T*, const uint32_t*, V4<T>*,            \
-                                           V4<double>*, V4<T>*, int, cudaStream_t);               \
-  template cudaError_t launch_momentum<T>(int64_t, const double*, const T*, const T*, const T*,   \
-                                          double, double*, cudaStream_t);
+#define APIC_INST_T(T)                                                                                  \
+  template cudaError_t launch_cells<T>(int64_t, const SceneDev*, int, int4*, int*, int*, cudaStream_t); \
+  template cudaError_t launch_gather<T>(int64_t, const SceneDev*, int, const int*, const int4*, V4<T>*,  \
+                                        V4<T>*, V4<T>*, cudaStream_t);                                  \
+  template cudaError_t launch_items<T>(const IterParams<T>&, int, cudaStream_t);                        \
+  template cudaError_t launch_normalize<T>(int64_t, const T*, const uint32_t*, V4<T>*, V4<double>*,     \
+                                           V4<T>*, int, cudaStream_t);                                  \
+  template cudaError_t launch_momentum<T>(int64_t, const double*, const T*, const T*, const T*, double, \
+                                          double*, cudaStream_t);
 APIC_INST_T(float)
 APIC_INST_T(double)
 
-#define APIC_INST_K(K)                                                                          \
-  template cudaError_t launch_keys<K>(int64_t, const int4*, Box, int, K*, int*, int*, cudaStream_t); \
-  template cudaError_t launch_heads<K>(int64_t, const K*, int*, cudaStream_t);              \
-  template cudaError_t launch_mark_items<K>(const int*, const int2*, const int*, const K*, int64_t, int, \
-                                            Box, int*, cudaStream_t);                        \
-  template cudaError_t launch_item_info<K>(const int*, const int*, const K*, int, int2*, int,   \
-                                           cudaStream_t);
+#define APIC_INST_K(K)                                                                                     \
+  template cudaError_t launch_keys<K>(int64_t, const SceneDev*, int, const int4*, int, K*, int*, int*,     \
+                                      cudaStream_t);                                                       \
+  template cudaError_t launch_heads<K>(int64_t, const K*, int*, cudaStream_t);                             \
+  template cudaError_t launch_item_info<K>(const int*, const int*, const K*, int, const SceneDev*, int,    \
+                                           int4*, int, cudaStream_t);                                      \
+  template cudaError_t launch_mark_items<K>(const int*, const int4*, const int*, const K*, int64_t, int,   \
+                                            const SceneDev*, int*, cudaStream_t);
 APIC_INST_K(uint32_t)
 APIC_INST_K(uint64_t)
 

@@ -1,0 +1,505 @@
+// The per-step pipeline of libapiccontact, shared by the context-backed
+// entry points (api.cu) and the no-allocation entry point (static_step.cu).
+//
+// A call steps a batch of independent scenes (one scene is a batch of one):
+//   1. cells + validation + per-scene bounding boxes      (k_cells)
+//   2. per-scene page-table boxes laid end to end          (host, or reused)
+//   3. keys and one radix sort over all scenes              (k_keys, CUB)
+//   4. sorted SoA planes                                    (k_gather)
+//   5. work items of <= kChunk particles of one (block, body)
+//   6. active blocks and the page table                     (k_mark_items, scan, k_compact)
+//   7. mass, body mask and P2G(V); optional friction blend; normalise
+//   8. N + 1 fused transfer passes (Sec. 2.3 series, Sec. 2.4 projection)
+// Everything runs on the caller's stream; the host synchronises while the
+// sparse grid is sized (after 2 when no box can be reused, and after 6).
+//
+// The environment `Env` supplies device scratch by slot, a host mirror of
+// the device counters, an optional per-scene box cache and profiling hooks.
+#pragma once
+
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "../../include/apiccontact.h"
+#include "apic_internal.h"
+
+namespace apic {
+
+enum Slot : int {
+  kSlotCells = 0, kSlotKeysA, kSlotKeysB, kSlotVals, kSlotPerm, kSlotPt, kSlotPn, kSlotV, kSlotD, kSlotMup,
+  kSlotHeads, kSlotOffs, kSlotItemStart, kSlotItemInfo, kSlotBFlags, kSlotBOffs, kSlotBList, kSlotPage,
+  kSlotGm, kSlotGmask, kSlotGp, kSlotGp64, kSlotGv, kSlotGmb, kSlotMuTable, kSlotCubTmp, kSlotScenes,
+  kSlotSBbox, kSlotSMom, kSlotSCount, kSlotHX, kSlotHBody, kSlotHV, kSlotHC, kSlotHM, kSlotHN, kSlotHVo,
+  kSlotHCo, kSlotDS, kSlotCount
+};
+
+constexpr int kMaxBodies = 32;
+constexpr int64_t kMaxPageEntries = int64_t(1) << 28;  // dense page table limit (1 GiB)
+constexpr int kBoxSlack = 2;  // blocks of room for motion when a page-table box is reused
+
+apic_status pfail(apic_status code, const char* fmt, ...);
+
+#define P_CUDA(expr)                                                                              \
+  do {                                                                                            \
+    cudaError_t e_ = (expr);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return ::apic::pfail(e_ == cudaErrorMemoryAllocation ? APIC_ERR_OUT_OF_MEMORY : APIC_ERR_CUDA, \
+                           "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__);  \
+  } while (0)
+
+#define P_TRY(expr)               \
+  do {                            \
+    apic_status s_ = (expr);      \
+    if (s_ != APIC_OK) return s_; \
+  } while (0)
+
+#define P_LAUNCH(env, expr) \
+  do {                      \
+    (env).launched();       \
+    P_CUDA(expr);           \
+  } while (0)
+
+inline apic_status pfail(apic_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  set_last_error(buf);
+  return code;
+}
+
+inline int bits_for(uint64_t v) {  // bits needed to represent 0..v
+  int b = 0;
+  while (b < 64 && (v >> b) != 0) ++b;
+  return b;
+}
+
+// Checks shared by every entry point, for one scene.
+inline apic_status validate_scene(const apic_step_args* a, int idx, uint32_t allowed_flags) {
+  if (!a) return pfail(APIC_ERR_INVALID_ARG, "scene %d: args is NULL", idx);
+  if (a->n < 0) return pfail(APIC_ERR_INVALID_ARG, "scene %d: n = %lld < 0", idx, (long long)a->n);
+  if (a->n > (int64_t)INT32_MAX / 4)
+    return pfail(APIC_ERR_INVALID_ARG, "scene %d: n = %lld exceeds the per-call limit %d", idx, (long long)a->n,
+                 INT32_MAX / 4);
+  if (a->n_bodies < 1 || a->n_bodies > kMaxBodies)
+    return pfail(APIC_ERR_INVALID_ARG, "scene %d: n_bodies = %d outside [1, %d]", idx, a->n_bodies, kMaxBodies);
+  if (a->n_iter < 0) return pfail(APIC_ERR_INVALID_ARG, "scene %d: n_iter = %d < 0", idx, a->n_iter);
+  if (!(a->h > 0.0) || !std::isfinite(a->h))
+    return pfail(APIC_ERR_INVALID_ARG, "scene %d: h = %g must be finite and > 0", idx, a->h);
+  if (!(a->mu >= 0.0) || !std::isfinite(a->mu))
+    return pfail(APIC_ERR_INVALID_ARG, "scene %d: mu = %g must be finite and >= 0", idx, a->mu);
+  if (a->flags & ~allowed_flags)
+    return pfail(APIC_ERR_INVALID_ARG, "scene %d: flag bits 0x%x not accepted here", idx, a->flags & ~allowed_flags);
+  if (a->n > 0 && (!a->body || !a->x || !a->v || !a->C || !a->m || !a->nrm || !a->v_out || !a->C_out))
+    return pfail(APIC_ERR_INVALID_ARG, "scene %d: a required array pointer is NULL", idx);
+  if (a->mu_pair) {
+    const int nb = a->n_bodies;
+    for (int i = 0; i < nb * nb; ++i)
+      if (!(a->mu_pair[i] >= 0.0) || !std::isfinite(a->mu_pair[i]))
+        return pfail(APIC_ERR_INVALID_ARG, "scene %d: mu_pair[%d] = %g must be finite and >= 0", idx, i,
+                     a->mu_pair[i]);
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j)
+        if (a->mu_pair[i * nb + j] != a->mu_pair[j * nb + i])
+          return pfail(APIC_ERR_INVALID_ARG, "scene %d: mu_pair is not symmetric at (%d, %d)", idx, i, j);
+  }
+  return APIC_OK;
+}
+
+template <class Env, class K>
+apic_status sort_keys(Env& env, int64_t n, const SceneDev* sc, int ns, const int4* cellb, int max_bodies,
+                      int end_bit, int* err, int** perm_out, const void** keys_out, cudaStream_t s) {
+  K *ka, *kb;
+  int *va, *vb;
+  P_TRY(env.take(kSlotKeysA, n, &ka, "sort keys"));
+  P_TRY(env.take(kSlotKeysB, n, &kb, "sorted keys"));
+  P_TRY(env.take(kSlotVals, n, &va, "sort values"));
+  P_TRY(env.take(kSlotPerm, n, &vb, "permutation"));
+  P_LAUNCH(env, launch_keys<K>(n, sc, ns, cellb, max_bodies, ka, va, err, s));
+  size_t tmp = 0;
+  P_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, ka, kb, va, vb, (int)n, 0, end_bit, s));
+  char* t = nullptr;
+  P_TRY(env.take(kSlotCubTmp, tmp, &t, "sort temporaries"));
+  P_CUDA(cub::DeviceRadixSort::SortPairs(t, tmp, ka, kb, va, vb, (int)n, 0, end_bit, s));
+  env.sorted();
+  *perm_out = vb;
+  *keys_out = kb;
+  return APIC_OK;
+}
+
+template <class Env>
+apic_status exclusive_sum(Env& env, const int* in, int* out, int64_t n, cudaStream_t s) {
+  size_t tmp = 0;
+  P_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, in, out, n, s));
+  char* t = nullptr;
+  P_TRY(env.take(kSlotCubTmp, tmp, &t, "scan temporaries"));
+  P_CUDA(cub::DeviceScan::ExclusiveSum(t, tmp, in, out, n, s));
+  env.sorted();
+  return APIC_OK;
+}
+
+// Steps `ns` scenes in one batch.  All scenes share the precision and
+// variant flags of scene 0 and its n_iter (checked by the caller).
+template <class T, class Env>
+apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream_t s, apic_stats* stats) {
+  const uint32_t flags = scenes[0].flags;
+  const bool host = (flags & APIC_HOST_PTRS) != 0;
+  const int N = scenes[0].n_iter;
+  typename Env::Span span_step(env, s, 0);
+  typename Env::Span span_prep(env, s, 1);
+
+  // Scene table: particle offsets, caller pointers (staged for host arrays).
+  SceneDev* hsc = env.host_scenes(ns);
+  int64_t n = 0;
+  int max_bodies = 1, n_mu = 0;
+  bool any_mu = false;
+  for (int i = 0; i < ns; ++i) {
+    const apic_step_args& a = scenes[i];
+    SceneDev d{};
+    d.x = a.x;
+    d.body = a.body;
+    d.v = a.v;
+    d.C = a.C;
+    d.m = a.m;
+    d.nrm = a.nrm;
+    d.v_out = a.v_out;
+    d.C_out = a.C_out;
+    d.part_off = n;
+    d.n = (int)a.n;
+    d.n_bodies = a.n_bodies;
+    d.mu_off = -1;
+    if (a.mu_pair) {
+      d.mu_off = n_mu;
+      n_mu += a.n_bodies * a.n_bodies;
+      any_mu = true;
+    }
+    d.h = a.h;
+    d.inv_h = 1.0 / a.h;
+    d.mu = a.mu;
+    hsc[i] = d;
+    n += a.n;
+    if (a.n_bodies > max_bodies) max_bodies = a.n_bodies;
+  }
+  if (stats) std::memset(stats, 0, sizeof(apic_stats) * ns);
+  if (n == 0) return APIC_OK;
+  if (n > (int64_t)INT32_MAX / 4)
+    return pfail(APIC_ERR_INVALID_ARG, "the batch holds %lld particles, beyond the per-call limit %d", (long long)n,
+                 INT32_MAX / 4);
+
+  if (host) {
+    double* dx;
+    int32_t* db;
+    T *dv, *dC, *dm, *dn, *dvo, *dCo;
+    P_TRY(env.take(kSlotHX, 3 * n, &dx, "staged x"));
+    P_TRY(env.take(kSlotHBody, n, &db, "staged body"));
+    P_TRY(env.take(kSlotHV, 3 * n, &dv, "staged v"));
+    P_TRY(env.take(kSlotHC, 9 * n, &dC, "staged C"));
+    P_TRY(env.take(kSlotHM, n, &dm, "staged m"));
+    P_TRY(env.take(kSlotHN, 3 * n, &dn, "staged normals"));
+    P_TRY(env.take(kSlotHVo, 3 * n, &dvo, "staged v_out"));
+    P_TRY(env.take(kSlotHCo, 9 * n, &dCo, "staged C_out"));
+    for (int i = 0; i < ns; ++i) {
+      const apic_step_args& a = scenes[i];
+      const int64_t o = hsc[i].part_off, m = a.n;
+      if (m == 0) continue;
+      P_CUDA(cudaMemcpyAsync(dx + 3 * o, a.x, 3 * m * sizeof(double), cudaMemcpyHostToDevice, s));
+      P_CUDA(cudaMemcpyAsync(db + o, a.body, m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      P_CUDA(cudaMemcpyAsync(dv + 3 * o, a.v, 3 * m * sizeof(T), cudaMemcpyHostToDevice, s));
+      P_CUDA(cudaMemcpyAsync(dC + 9 * o, a.C, 9 * m * sizeof(T), cudaMemcpyHostToDevice, s));
+      P_CUDA(cudaMemcpyAsync(dm + o, a.m, m * sizeof(T), cudaMemcpyHostToDevice, s));
+      P_CUDA(cudaMemcpyAsync(dn + 3 * o, a.nrm, 3 * m * sizeof(T), cudaMemcpyHostToDevice, s));
+      hsc[i].x = dx + 3 * o;
+      hsc[i].body = db + o;
+      hsc[i].v = dv + 3 * o;
+      hsc[i].C = dC + 9 * o;
+      hsc[i].m = dm + o;
+      hsc[i].nrm = dn + 3 * o;
+      hsc[i].v_out = dvo + 3 * o;
+      hsc[i].C_out = dCo + 9 * o;
+    }
+  }
+
+  DevScalars* ds = env.ds();
+  DevScalars* hs = env.hs();
+  SceneDev* sc;
+  int* sbbox;
+  int4* cellb;
+  P_TRY(env.take(kSlotScenes, ns, &sc, "scene table"));
+  P_TRY(env.take(kSlotSBbox, 6 * ns, &sbbox, "scene boxes"));
+  P_TRY(env.take(kSlotCells, n, &cellb, "cells"));
+  int* hbbox = env.host_bbox(ns);
+  Box* boxes = env.box_cache(ns);  // persistent per-scene boxes (or scratch)
+
+  int64_t NB = 0;
+  int* perm = nullptr;
+  const void* keys = nullptr;
+  bool k64 = false;
+  V4<T> *pt, *pn, *V, *D;
+  int *heads, *offs, *item_start;
+  int4* item_info;
+  int* page = nullptr;
+  int* blist = nullptr;
+  for (int attempt = 0;; ++attempt) {
+    // 1. cells, validation, bounding boxes of particle blocks.
+    const bool fresh = !env.have_box() || attempt > 0;
+    if (fresh) {
+      for (int i = 0; i < ns; ++i) {
+        int* b = hbbox + 6 * i;
+        b[0] = b[1] = b[2] = INT32_MAX;
+        b[3] = b[4] = b[5] = INT32_MIN;
+      }
+      P_CUDA(cudaMemcpyAsync(sbbox, hbbox, 6 * ns * sizeof(int), cudaMemcpyHostToDevice, s));
+    } else {
+      // boxes reused from the previous step: the table already holds them
+      for (int i = 0; i < ns; ++i) {
+        hsc[i].box = boxes[i];
+      }
+    }
+    *hs = DevScalars{};
+    P_CUDA(cudaMemcpyAsync(ds, hs, sizeof(DevScalars), cudaMemcpyHostToDevice, s));
+    if (!fresh) {
+      NB = 0;
+      for (int i = 0; i < ns; ++i) {
+        hsc[i].page_off = NB;
+        NB += (int64_t)hsc[i].box.nx * hsc[i].box.ny * hsc[i].box.nz;
+      }
+    }
+    P_CUDA(cudaMemcpyAsync(sc, hsc, ns * sizeof(SceneDev), cudaMemcpyHostToDevice, s));
+    P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, sbbox, &ds->err, s));
+    if (fresh) {
+      // 2. page-table boxes: one block of stencil margin plus kBoxSlack
+      //    blocks of room for motion in later steps; laid end to end.
+      P_CUDA(cudaMemcpyAsync(hbbox, sbbox, 6 * ns * sizeof(int), cudaMemcpyDeviceToHost, s));
+      P_CUDA(cudaMemcpyAsync(hs, ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+      P_CUDA(cudaStreamSynchronize(s));
+      if (hs->err) break;  // reported below
+      const int g = 1 + kBoxSlack;
+      NB = 0;
+      for (int i = 0; i < ns; ++i) {
+        const int* b = hbbox + 6 * i;
+        Box bx{};
+        if (hsc[i].n > 0) {
+          bx.ox = b[0] - g;
+          bx.oy = b[1] - g;
+          bx.oz = b[2] - g;
+          bx.nx = b[3] - b[0] + 1 + 2 * g;
+          bx.ny = b[4] - b[1] + 1 + 2 * g;
+          bx.nz = b[5] - b[2] + 1 + 2 * g;
+        }
+        hsc[i].box = bx;
+        boxes[i] = bx;
+        hsc[i].page_off = NB;
+        NB += (int64_t)bx.nx * bx.ny * bx.nz;
+        if (NB > kMaxPageEntries) {
+          env.forget_box();
+          return pfail(APIC_ERR_INVALID_ARG,
+                       "the scenes span more than %lld grid blocks of 4^3 nodes (dense page-table limit)",
+                       (long long)kMaxPageEntries);
+        }
+      }
+      env.keep_box();
+      P_CUDA(cudaMemcpyAsync(sc, hsc, ns * sizeof(SceneDev), cudaMemcpyHostToDevice, s));
+    }
+    // 3. keys and one radix sort over all scenes.
+    const int end_bit = bits_for((uint64_t)NB * (uint64_t)max_bodies - 1) + 6;
+    k64 = end_bit > 32;
+    if (k64)
+      P_TRY((sort_keys<Env, uint64_t>(env, n, sc, ns, cellb, max_bodies, end_bit, &ds->err, &perm, &keys, s)));
+    else
+      P_TRY((sort_keys<Env, uint32_t>(env, n, sc, ns, cellb, max_bodies, end_bit, &ds->err, &perm, &keys, s)));
+
+    // 4. sorted SoA.
+    P_TRY(env.take(kSlotPt, n, &pt, "particle offsets"));
+    P_TRY(env.take(kSlotPn, n, &pn, "particle normals"));
+    P_TRY(env.take(kSlotV, 3 * n, &V, "sorted V"));
+    P_TRY(env.take(kSlotD, 3 * n, &D, "Delta"));
+    P_LAUNCH(env, launch_gather<T>(n, sc, ns, perm, cellb, pt, pn, V, s));
+
+    // 5. work items: runs of equal (grid block, body), at most kChunk long.
+    P_TRY(env.take(kSlotHeads, n, &heads, "item heads"));
+    P_TRY(env.take(kSlotOffs, n, &offs, "item offsets"));
+    P_TRY(env.take(kSlotItemStart, n, &item_start, "item starts"));
+    P_TRY(env.take(kSlotItemInfo, n, &item_info, "item info"));
+    if (k64)
+      P_LAUNCH(env, launch_heads<uint64_t>(n, static_cast<const uint64_t*>(keys), heads, s));
+    else
+      P_LAUNCH(env, launch_heads<uint32_t>(n, static_cast<const uint32_t*>(keys), heads, s));
+    P_TRY(exclusive_sum(env, heads, offs, n, s));
+    P_LAUNCH(env, launch_compact(n, heads, offs, item_start, nullptr, &ds->n_items, s));
+    if (k64)
+      P_LAUNCH(env, launch_item_info<uint64_t>(item_start, &ds->n_items, static_cast<const uint64_t*>(keys),
+                                               max_bodies, sc, ns, item_info, (int)n, s));
+    else
+      P_LAUNCH(env, launch_item_info<uint32_t>(item_start, &ds->n_items, static_cast<const uint32_t*>(keys),
+                                               max_bodies, sc, ns, item_info, (int)n, s));
+
+    // 6. active grid blocks: every block some stencil reaches; page table.
+    int *bflags, *boffs;
+    P_TRY(env.take(kSlotBFlags, NB, &bflags, "block flags"));
+    P_TRY(env.take(kSlotBOffs, NB, &boffs, "block offsets"));
+    P_TRY(env.take(kSlotBList, NB, &blist, "block list"));
+    P_TRY(env.take(kSlotPage, NB, &page, "page table"));
+    P_CUDA(cudaMemsetAsync(bflags, 0, NB * sizeof(int), s));
+    if (k64)
+      P_LAUNCH(env, launch_mark_items<uint64_t>(item_start, item_info, &ds->n_items,
+                                                static_cast<const uint64_t*>(keys), n, (int)n, sc, bflags, s));
+    else
+      P_LAUNCH(env, launch_mark_items<uint32_t>(item_start, item_info, &ds->n_items,
+                                                static_cast<const uint32_t*>(keys), n, (int)n, sc, bflags, s));
+    P_TRY(exclusive_sum(env, bflags, boffs, NB, s));
+    P_LAUNCH(env, launch_compact(NB, bflags, boffs, blist, page, &ds->n_blocks, s));
+    P_CUDA(cudaMemcpyAsync(hs, ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    P_CUDA(cudaStreamSynchronize(s));
+    if ((hs->err & kErrBox) && !(hs->err & ~kErrBox) && attempt == 0) {
+      env.forget_box();  // a particle left a reused box: size fresh ones
+      continue;
+    }
+    break;
+  }
+  if (hs->err) {
+    const int e = hs->err;
+    env.forget_box();
+    return pfail(APIC_ERR_INVALID_ARG, "invalid particle data:%s%s%s%s", (e & kErrBody) ? " body id out of range" : "",
+                 (e & kErrMass) ? " mass not finite and > 0" : "",
+                 (e & kErrPos) ? " position not finite or |x/h| >= 2^29" : "",
+                 (e & kErrBox) ? " (internal: page-table box)" : "");
+  }
+  const int n_items = hs->n_items;
+  const int n_blocks = hs->n_blocks;
+  const int64_t n_nodes = (int64_t)n_blocks * kNodesPerBlock;
+
+  // 7. node arrays; mass, body mask and P2G(V); friction blend; normalise.
+  T* gm;
+  uint32_t* gmask;
+  V4<T>*gp, *gv;
+  V4<double>* gp64 = nullptr;
+  T* gmb = nullptr;
+  T* mu_table = nullptr;
+  T* mup = nullptr;
+  P_TRY(env.take(kSlotGm, n_nodes, &gm, "grid mass"));
+  P_TRY(env.take(kSlotGmask, n_nodes, &gmask, "grid body mask"));
+  P_TRY(env.take(kSlotGp, n_nodes, &gp, "grid momentum"));
+  P_TRY(env.take(kSlotGv, n_nodes, &gv, "grid velocity"));
+  P_CUDA(cudaMemsetAsync(gm, 0, n_nodes * sizeof(T), s));
+  P_CUDA(cudaMemsetAsync(gmask, 0, n_nodes * sizeof(uint32_t), s));
+  P_CUDA(cudaMemsetAsync(gp, 0, n_nodes * sizeof(V4<T>), s));
+  if (sizeof(T) == 4) {
+    P_TRY(env.take(kSlotGp64, n_nodes, &gp64, "FP64 node momentum"));
+    P_CUDA(cudaMemsetAsync(gp64, 0, n_nodes * sizeof(V4<double>), s));
+  }
+  if (any_mu) {
+    P_TRY(env.take(kSlotGmb, (size_t)max_bodies * n_nodes, &gmb, "per-body grid mass"));
+    P_CUDA(cudaMemsetAsync(gmb, 0, (size_t)max_bodies * n_nodes * sizeof(T), s));
+    P_TRY(env.take(kSlotMuTable, (size_t)n_mu, &mu_table, "friction tables"));
+    P_TRY(env.take(kSlotMup, n, &mup, "particle friction"));
+    T* hmu = static_cast<T*>(env.host_buf((size_t)n_mu * sizeof(T)));
+    if (!hmu) return pfail(APIC_ERR_INVALID_ARG, "friction tables too large for this entry point");
+    for (int i = 0; i < ns; ++i)
+      if (scenes[i].mu_pair)
+        for (int k = 0; k < scenes[i].n_bodies * scenes[i].n_bodies; ++k)
+          hmu[hsc[i].mu_off + k] = (T)scenes[i].mu_pair[k];
+    P_CUDA(cudaMemcpyAsync(mu_table, hmu, (size_t)n_mu * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+
+  IterParams<T> p{};
+  p.n_items = n_items;
+  p.n_particles = (int)n;
+  p.max_bodies = max_bodies;
+  p.n_scenes = ns;
+  p.sc = sc;
+  p.item_start = item_start;
+  p.item_info = item_info;
+  p.page = page;
+  p.pt = pt;
+  p.pn = pn;
+  p.mup = nullptr;
+  p.mu_table = mu_table;
+  p.gmb = gmb;
+  p.mup_out = mup;
+  p.n_nodes = n_nodes;
+  p.V = V;
+  p.D = D;
+  p.gv = gv;
+  p.gp = gp;
+  p.gm = gm;
+  p.gmask = gmask;
+  p.gp64 = gp64;
+  p.perm = perm;
+  p.pic = (flags & APIC_VARIANT_PIC) ? 1 : 0;
+  p.sep23 = (flags & APIC_VARIANT_SEP23) ? 1 : 0;
+
+  P_LAUNCH(env, launch_items<T>(p, kModeMassV, s));
+  if (any_mu) {
+    P_LAUNCH(env, launch_items<T>(p, kModeMu, s));
+    p.mup = mup;
+  }
+  P_LAUNCH(env, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 1, s));
+  span_prep.stop();
+
+  // 8. the N + 1 transfer passes.
+  for (int pass = 0; pass <= N; ++pass) {
+    const int mode = N == 0 ? kModeOnly : pass == 0 ? kModeFirst : pass == N ? kModeLast : kModeMid;
+    {
+      typename Env::Span span_pass(env, s, 2);
+      P_LAUNCH(env, launch_items<T>(p, mode, s));
+    }
+    if (pass < N) P_LAUNCH(env, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 0, s));
+  }
+  span_step.stop();
+
+  if (stats) {
+    double* smom;
+    unsigned long long* scount;
+    P_TRY(env.take(kSlotSMom, 12 * ns, &smom, "scene momenta"));
+    P_TRY(env.take(kSlotSCount, 3 * ns, &scount, "scene counts"));
+    P_CUDA(cudaMemsetAsync(smom, 0, 12 * ns * sizeof(double), s));
+    P_CUDA(cudaMemsetAsync(scount, 0, 3 * ns * sizeof(unsigned long long), s));
+    for (int i = 0; i < ns; ++i) {
+      const SceneDev& d = hsc[i];
+      if (d.n == 0) continue;
+      const double* x = d.x;
+      const T* m = static_cast<const T*>(d.m);
+      P_LAUNCH(env, launch_momentum<T>(d.n, x, static_cast<const T*>(d.v), static_cast<const T*>(d.C), m, d.h,
+                                       smom + 12 * i, s));
+      P_LAUNCH(env, launch_momentum<T>(d.n, x, static_cast<const T*>(d.v_out), static_cast<const T*>(d.C_out),
+                                       m, d.h, smom + 12 * i + 6, s));
+    }
+    P_LAUNCH(env, launch_scene_counts(n_blocks, blist, gmask, n_items, item_info, sc, ns, scount, s));
+    double* hm = static_cast<double*>(env.host_buf(12 * ns * sizeof(double) + 3 * ns * sizeof(unsigned long long)));
+    if (!hm) return pfail(APIC_ERR_INVALID_ARG, "too many scenes for statistics on this entry point");
+    unsigned long long* hc = reinterpret_cast<unsigned long long*>(hm + 12 * ns);
+    P_CUDA(cudaMemcpyAsync(hm, smom, 12 * ns * sizeof(double), cudaMemcpyDeviceToHost, s));
+    P_CUDA(cudaMemcpyAsync(hc, scount, 3 * ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    P_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < ns; ++i) {
+      for (int k = 0; k < 3; ++k) {
+        stats[i].P_in[k] = hm[12 * i + k];
+        stats[i].L_in[k] = hm[12 * i + 3 + k];
+        stats[i].P_out[k] = hm[12 * i + 6 + k];
+        stats[i].L_out[k] = hm[12 * i + 9 + k];
+      }
+      stats[i].multibody_nodes = (int64_t)hc[3 * i];
+      stats[i].active_blocks = (int64_t)hc[3 * i + 1];
+      stats[i].work_items = (int64_t)hc[3 * i + 2];
+    }
+  }
+  if (host) {
+    for (int i = 0; i < ns; ++i) {
+      const apic_step_args& a = scenes[i];
+      if (a.n == 0) continue;
+      P_CUDA(cudaMemcpyAsync(a.v_out, hsc[i].v_out, 3 * a.n * sizeof(T), cudaMemcpyDeviceToHost, s));
+      P_CUDA(cudaMemcpyAsync(a.C_out, hsc[i].C_out, 9 * a.n * sizeof(T), cudaMemcpyDeviceToHost, s));
+    }
+    P_CUDA(cudaStreamSynchronize(s));
+  }
+  env.done(n, n_nodes);
+  return APIC_OK;
+}
+
+}  // namespace apic

@@ -266,3 +266,57 @@ def random_cloud(n: int, n_bodies: int = 2, seed: int = 0, h: float = 0.1, affin
         v = rng.standard_normal((n, 3))
         Cm = rng.standard_normal((n, 3, 3)) / h
     return Scene(x, v, Cm, m, nrm, body, n_bodies, h, mu, n_iter, None, f"random_cloud_{n}", dict(seed=seed))
+
+
+def multi_body_scene(rng, total_nodes: int, n_bodies: int, h: float, mu: float = 0.3, n_iter: int = 8,
+                     name: str = "") -> Scene:
+    """`n_bodies` lattice boxes and balls (alternating) of total_nodes /
+    n_bodies nodes each, spacing h/2, jitter U(-0.1h, 0.1h), Haar-random
+    rotations, rigid velocities |v| <= 2, |omega| <= 5, placed as approaching
+    pairs along x (gaps U(0, 2h)) stacked along y."""
+    s = h / 2
+    per = max(int(total_nodes // n_bodies), 8)
+    parts = []
+    y = 0.0
+    for b in range(0, n_bodies, 2):
+        pair = []
+        for k in range(b, min(b + 2, n_bodies)):
+            if k % 2 == 0:
+                e = max(int(round(per ** (1 / 3))), 2)
+                pts, nrm = _box_lattice(e, e, max(per // (e * e), 1), s)
+                pts = pts + rng.uniform(-0.1 * h, 0.1 * h, pts.shape)
+            else:
+                pts, nrm = _implicit_lattice(per, s, (1, 1, 1), "ellipsoid", 0.1 * h, rng)
+            R = haar_rotation(rng)
+            pair.append((pts @ R.T, nrm @ R.T))
+        ext = max(np.ptp(p[0][:, 1]) for p in pair)
+        yc = y + ext / 2 + 2 * h
+        y = yc + ext / 2 + 4 * h
+        gap = rng.uniform(0, 2 * h)
+        ca = np.array([-pair[0][0][:, 0].max() - gap / 2, yc, 0.0])
+        centres = [ca]
+        if len(pair) == 2:
+            centres.append(np.array([-pair[1][0][:, 0].min() + gap / 2, yc, 0.0]))
+        for (pts, nrm), c, side in zip(pair, centres, (1.0, -1.0)):
+            v0 = random_direction(rng) * rng.uniform(0, 2)
+            v0[0] = side * abs(v0[0])
+            w = random_direction(rng) * rng.uniform(0, 5)
+            x = pts + c
+            v = v0 + np.cross(w, pts)
+            Cm = np.broadcast_to(skew(w), (x.shape[0], 3, 3)).copy()
+            parts.append((x, nrm, v, Cm, np.full(x.shape[0], 1.0 / x.shape[0])))
+    return _assemble(parts, h, mu, n_iter, name)
+
+
+def batch_of_scenes(n_scenes: int = 64, seed: int = SEED_BASE + 4, min_nodes: float = 1e3, max_nodes: float = 2e5,
+                    bodies=(2, 6), hs=(1.0 / 64, 1.0 / 128, 1.0 / 256), mu: float = 0.3, n_iter: int = 8):
+    """Independent scenes of uneven size: ln P ~ U(ln min, ln max), bodies ~
+    U{bodies}, h uniform over `hs`, node spacing h/2."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_scenes):
+        P = int(np.exp(rng.uniform(np.log(min_nodes), np.log(max_nodes))))
+        nb = int(rng.integers(bodies[0], bodies[1] + 1))
+        h = float(hs[int(rng.integers(0, len(hs)))])
+        out.append(multi_body_scene(rng, P, nb, h, mu, n_iter, name=f"scene{i}_{P}_{nb}b_h1/{round(1 / h)}"))
+    return out

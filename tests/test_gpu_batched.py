@@ -1,0 +1,143 @@
+"""apic_contact_step_batched: several independent scenes in one call must give,
+scene by scene, what the oracle gives for each scene alone."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_02259_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+TOL_V, TOL_C, TOL_MOM = 1e-5, 1e-4, 1e-6
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2108_02259_gb300 import apic, build
+
+    build.build()
+    c = apic.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(s, dt):
+    import torch
+
+    f = s.astype(dt)
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    dev = torch.device("cuda:0")
+
+    def t(a, d):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=d).to(dev)
+
+    return t(f.x, torch.float64), t(f.v, tdt), t(f.C, tdt), t(f.m, tdt), t(f.nrm, tdt), t(f.body, torch.int32)
+
+
+def _check(s, v, Cm, st, mu_pair=None, tol_v=TOL_V, tol_c=TOL_C, label=""):
+    rv, rC, rst = oracle.contact_step(s.x, s.v, s.C, s.m, s.nrm, s.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
+                                      mu_pair=mu_pair)
+    vs = np.abs(s.v).max()
+    cs = max(np.linalg.norm(s.C.reshape(-1, 9), axis=1).max(), np.linalg.norm(rC.reshape(-1, 9), axis=1).max())
+    cs = cs if cs > 0 else 2 * vs / s.h
+    ev, ec = np.abs(v - rv).max() / vs, np.abs(Cm - rC).max() / cs
+    print(f"[batched] {label}: n={s.n} v err {ev:.2e} C err {ec:.2e}")
+    assert ev <= tol_v and ec <= tol_c, (label, ev, ec)
+    if st is not None:
+        sP = np.sum(s.m * np.linalg.norm(s.v, axis=1))
+        assert np.abs(st["P_out"] - st["P_in"]).max() <= TOL_MOM * sP
+        assert st["multibody_nodes"] == rst["multibody_nodes"]
+
+
+def _mixed_batch():
+    rng = np.random.default_rng(123)
+    sc = [scenes.multi_body_scene(rng, 1500, 2, 1 / 64, n_iter=3),
+          scenes.two_cubes(mu=0.0, n_iter=3),
+          scenes.multi_body_scene(rng, 4000, 5, 1 / 128, mu=0.5, n_iter=3),
+          scenes.random_cloud(800, n_bodies=3, seed=4, h=0.1, n_iter=3, origin=(-2.0, 1.0, 0.5)),
+          scenes.multi_body_scene(rng, 2500, 3, 1 / 256, mu=0.1, n_iter=3)]
+    # same location for two scenes: scenes are independent even when they overlap in space
+    sc.append(scenes.Scene(sc[0].x.copy(), -sc[0].v, -sc[0].C, sc[0].m, sc[0].nrm, sc[0].body, sc[0].n_bodies, sc[0].h,
+                           0.3, 3))
+    return sc
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+def test_batched_matches_oracle_per_scene(ctx, dt):
+    import torch
+
+    from paper_2108_02259_gb300 import apic
+
+    sc = _mixed_batch()
+    mp = np.array([[0.2, 0.4, 0.3], [0.4, 0.1, 0.25], [0.3, 0.25, 0.5]])
+    bs = []
+    for i, s in enumerate(sc):
+        X, V, C, M, N, B = _dev(s, dt)
+        bs.append(apic.BatchScene(X, V, C, M, N, B, s.h, s.mu, n_bodies=s.n_bodies,
+                                  mu_pair=mp if i == 4 else None))
+    stats = apic.contact_step_batched(ctx, bs, n_iter=3, stats=True)
+    torch.cuda.synchronize()
+    tol = (TOL_V, TOL_C) if dt == np.float32 else (1e-11, 1e-11)
+    for i, (s, b) in enumerate(zip(sc, bs)):
+        _check(s, b.v_out.cpu().double().numpy(), b.C_out.cpu().double().numpy(), stats[i],
+               mu_pair=mp if i == 4 else None, tol_v=3 * tol[0], tol_c=tol[1], label=f"scene {i} {dt.__name__}")
+
+
+def test_batched_equals_single_scene_calls(ctx):
+    import torch
+
+    from paper_2108_02259_gb300 import apic
+
+    sc = _mixed_batch()
+    bs, single = [], []
+    for s in sc:
+        X, V, C, M, N, B = _dev(s, np.float32)
+        bs.append(apic.BatchScene(X, V, C, M, N, B, s.h, s.mu, n_bodies=s.n_bodies))
+        r = apic.contact_step(ctx, X, V, C, M, N, B, s.h, s.mu, 3, n_bodies=s.n_bodies)
+        single.append((r.v, r.C))
+    apic.contact_step_batched(ctx, bs, n_iter=3)
+    torch.cuda.synchronize()
+    for s, b, (v1, C1) in zip(sc, bs, single):
+        vs = np.abs(s.v).max()
+        assert torch.abs(b.v_out - v1).max().item() <= 2e-6 * vs
+        assert torch.abs(b.C_out - C1).max().item() <= 2e-5 * max(np.abs(s.C).max(), 2 * vs / s.h)
+
+
+def test_batched_host_pointers_and_empty_scene(ctx):
+    from paper_2108_02259_gb300 import apic
+
+    sc = _mixed_batch()[:3]
+    empty = scenes.Scene(sc[0].x[:0], sc[0].v[:0], sc[0].C[:0], sc[0].m[:0], sc[0].nrm[:0], sc[0].body[:0], 1,
+                         0.05, 0.3, 3)
+    sc.insert(1, empty)
+    bs = []
+    for s in sc:
+        f = s.astype(np.float32)
+        bs.append(apic.BatchScene(f.x, f.v, f.C, f.m, f.nrm, f.body, s.h, s.mu, n_bodies=s.n_bodies))
+    stats = apic.contact_step_batched(ctx, bs, n_iter=3, stats=True)
+    assert stats[1]["work_items"] == 0
+    for i, (s, b) in enumerate(zip(sc, bs)):
+        if s.n:
+            _check(s, b.v_out.astype(np.float64), b.C_out.astype(np.float64), stats[i], tol_v=3 * TOL_V,
+                   label=f"host scene {i}")
+
+
+def test_batched_rejects_mixed_flags(ctx):
+    from paper_2108_02259_gb300 import apic
+
+    sc = _mixed_batch()[:2]
+    bs = []
+    for s in sc:
+        X, V, C, M, N, B = _dev(s, np.float32)
+        bs.append(apic.BatchScene(X, V, C, M, N, B, s.h, s.mu, n_bodies=s.n_bodies))
+    lib = apic.load()
+    import ctypes
+
+    arr = (apic.StepArgs * 2)()
+    for i, b in enumerate(bs):
+        arr[i] = apic.StepArgs(int(b.x.shape[0]), b.n_bodies, 3 + i, b.body.data_ptr(), b.x.data_ptr(),
+                               b.v.data_ptr(), b.C.data_ptr(), b.m.data_ptr(), b.nrm.data_ptr(), b.v_out.data_ptr(),
+                               b.C_out.data_ptr(), b.h, b.mu, None, 0)
+    rc = lib.apic_contact_step_batched(ctx.handle, arr, 2, None, None)
+    assert rc == apic.APIC_ERR_INVALID_ARG
+    assert b"n_iter" in lib.apic_last_error()
