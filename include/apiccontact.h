@@ -45,7 +45,9 @@ typedef int32_t apic_status;
 #define APIC_ERR_INVALID_ARG (-1)   /* bad size, pointer, flag or value   */
 #define APIC_ERR_OUT_OF_MEMORY (-2) /* device allocation or budget failed */
 #define APIC_ERR_CUDA (-3)          /* a CUDA runtime call failed         */
-#define APIC_ERR_TIMEOUT (-4)       /* a bounded device wait gave up      */
+#define APIC_ERR_TIMEOUT (-4)       /* a bounded wait gave up             */
+#define APIC_ERR_ADMISSION (-5)     /* the HBM budget cannot hold it now  */
+#define APIC_ERR_NOT_READY (-6)     /* a request has not completed yet    */
 
 /* Flags of apic_step_args.flags */
 #define APIC_FP64 (1u << 0)          /* v, C, m, nrm (in and out) are double; all arithmetic FP64.
@@ -179,6 +181,73 @@ apic_status apic_contact_step_batched(apic_ctx* ctx, const apic_step_args* scene
  *   - Synchronises the stream twice while sizing the grid, and at the end
  *     when stats is non-NULL.  Errors are reported by apic_last_error(). */
 apic_status apic_contact_step_static(const apic_step_args* args, void* stream, apic_stats* stats);
+
+/* ---------------------------------------------------------------------------
+ * Serving: many concurrent simulations, state resident on the device.
+ *
+ * A server owns worker threads, each with its own context and CUDA stream.
+ * A simulation (apic_sim) keeps its particles' x, v, C, m, normals and body
+ * ids on the device between steps.  apic_sim_submit queues one contact step
+ * of that simulation (the step writes V_hat back into v and C, then, when
+ * dt_advect > 0, moves x += dt_advect * v).  Workers take every ready request
+ * (at most one in flight per simulation, FIFO per simulation) and run them
+ * as one batched step; a request that arrives while a batch is on the GPU is
+ * picked up by the next free worker, so batches overlap on the device.
+ * Requests are batched only with requests of the same flags and n_iter.
+ * --------------------------------------------------------------------------*/
+typedef struct apic_server apic_server;
+typedef struct apic_sim apic_sim;
+
+typedef struct {
+  int64_t completed;        /* completed step requests                       */
+  int64_t failed;           /* requests that ended in an error               */
+  int64_t batches;          /* batched launches                              */
+  int64_t particle_iters;   /* sum of n * (n_iter + 1) over completed steps  */
+  double latency_p50_ms;    /* submit -> completion, over completed requests */
+  double latency_p99_ms;
+  double latency_mean_ms;
+  double mean_batch_scenes; /* requests per batched launch                   */
+  int64_t resident_bytes;   /* device bytes held by open simulations         */
+  int64_t open_sims;
+} apic_server_stats;
+
+/* Create a server on `device` with `n_workers` worker threads (>= 1).
+ * hbm_budget_bytes caps the resident state of open simulations plus the
+ * workers' scratch (0 = no cap); max_batch_scenes caps requests per batch. */
+apic_status apic_server_create(apic_server** out, int32_t device, size_t hbm_budget_bytes, int32_t n_workers,
+                               int32_t max_batch_scenes);
+
+/* Finish queued requests, stop the workers, free every simulation. */
+apic_status apic_server_destroy(apic_server* srv);
+
+/* Admit a simulation: copy its state (host or device pointers per
+ * APIC_HOST_PTRS) to resident device memory.  h, mu, mu_pair, n_iter and
+ * flags are kept for its steps; v_out / C_out are ignored.  Returns
+ * APIC_ERR_ADMISSION when the budget cannot hold it now (retry after other
+ * simulations close). */
+apic_status apic_sim_open(apic_server* srv, const apic_step_args* init, apic_sim** out);
+
+/* Queue one contact step of `sim`; *ticket identifies the request. */
+apic_status apic_sim_submit(apic_sim* sim, double dt_advect, uint64_t* ticket);
+
+/* Has the request finished?  done = 1 and its latency (submit -> completion)
+ * when it has; returns the request's own error status if it failed. */
+apic_status apic_ticket_poll(apic_server* srv, uint64_t ticket, int32_t* done, double* latency_ms);
+
+/* Wait at most timeout_s seconds for the request; APIC_ERR_TIMEOUT if it has
+ * not finished by then. */
+apic_status apic_ticket_wait(apic_server* srv, uint64_t ticket, double timeout_s, double* latency_ms);
+
+/* Copy the simulation's current state to HOST memory (each pointer may be
+ * NULL): x [n*3] doubles, v [n*3] and C [n*9] in the simulation's precision.
+ * Waits for its queued and running steps first. */
+apic_status apic_sim_read(apic_sim* sim, double* x_out, void* v_out, void* C_out);
+
+/* Wait for the simulation's steps, then free its resident state. */
+apic_status apic_sim_close(apic_sim* sim);
+
+/* Counters and latency percentiles since creation (or the last reset). */
+apic_status apic_server_get_stats(apic_server* srv, apic_server_stats* out, int32_t reset);
 
 /* Turn kernel timing on (1) or off (0) and reset the counters. */
 apic_status apic_set_profiling(apic_ctx* ctx, int32_t on);

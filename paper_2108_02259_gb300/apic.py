@@ -24,6 +24,8 @@ APIC_ERR_INVALID_ARG = -1
 APIC_ERR_OUT_OF_MEMORY = -2
 APIC_ERR_CUDA = -3
 APIC_ERR_TIMEOUT = -4
+APIC_ERR_ADMISSION = -5
+APIC_ERR_NOT_READY = -6
 
 APIC_FP64 = 1 << 0
 APIC_HOST_PTRS = 1 << 1
@@ -33,7 +35,8 @@ APIC_VARIANT_SEP23 = 1 << 3
 EXPORTED = [
     "apic_last_error", "apic_version", "apic_create", "apic_destroy", "apic_contact_step",
     "apic_set_profiling", "apic_get_profile", "apic_scratch_bytes", "apic_contact_step_static",
-    "apic_contact_step_batched",
+    "apic_contact_step_batched", "apic_server_create", "apic_server_destroy", "apic_sim_open", "apic_sim_submit",
+    "apic_ticket_poll", "apic_ticket_wait", "apic_sim_read", "apic_sim_close", "apic_server_get_stats",
 ]
 
 
@@ -57,6 +60,14 @@ class Stats(C.Structure):
         return dict(P_in=np.array(self.P_in[:]), P_out=np.array(self.P_out[:]), L_in=np.array(self.L_in[:]),
                     L_out=np.array(self.L_out[:]), multibody_nodes=int(self.multibody_nodes),
                     active_blocks=int(self.active_blocks), work_items=int(self.work_items))
+
+
+class ServerStats(C.Structure):
+    _fields_ = [
+        ("completed", C.c_int64), ("failed", C.c_int64), ("batches", C.c_int64), ("particle_iters", C.c_int64),
+        ("latency_p50_ms", C.c_double), ("latency_p99_ms", C.c_double), ("latency_mean_ms", C.c_double),
+        ("mean_batch_scenes", C.c_double), ("resident_bytes", C.c_int64), ("open_sims", C.c_int64),
+    ]
 
 
 class Profile(C.Structure):
@@ -90,6 +101,18 @@ def load(path: str = LIB_PATH):
     lib.apic_create.argtypes = [C.POINTER(P), C.c_int32, C.c_size_t]
     lib.apic_destroy.argtypes = [P]
     lib.apic_contact_step.argtypes = [P, C.POINTER(StepArgs), P, C.POINTER(Stats)]
+    lib.apic_server_create.argtypes = [C.POINTER(P), C.c_int32, C.c_size_t, C.c_int32, C.c_int32]
+    lib.apic_server_destroy.argtypes = [P]
+    lib.apic_sim_open.argtypes = [P, C.POINTER(StepArgs), C.POINTER(P)]
+    lib.apic_sim_submit.argtypes = [P, C.c_double, C.POINTER(C.c_uint64)]
+    lib.apic_ticket_poll.argtypes = [P, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+    lib.apic_ticket_wait.argtypes = [P, C.c_uint64, C.c_double, C.POINTER(C.c_double)]
+    lib.apic_sim_read.argtypes = [P, P, P, P]
+    lib.apic_sim_close.argtypes = [P]
+    lib.apic_server_get_stats.argtypes = [P, C.POINTER(ServerStats), C.c_int32]
+    for f in ("apic_server_create", "apic_server_destroy", "apic_sim_open", "apic_sim_submit", "apic_ticket_poll",
+              "apic_ticket_wait", "apic_sim_read", "apic_sim_close", "apic_server_get_stats"):
+        getattr(lib, f).restype = C.c_int32
     lib.apic_contact_step_batched.argtypes = [P, C.POINTER(StepArgs), C.c_int32, P, C.POINTER(Stats)]
     lib.apic_contact_step_batched.restype = C.c_int32
     lib.apic_contact_step_static.argtypes = [C.POINTER(StepArgs), P, C.POINTER(Stats)]
@@ -312,3 +335,103 @@ def contact_step_batched(ctx: Context, scenes, n_iter: int, flags: int = 0, stre
     st = (Stats * ns)() if stats else None
     _check(lib.apic_contact_step_batched(ctx.handle, arr, ns, sptr, st if stats else None))
     return [st[i].as_dict() for i in range(ns)] if stats else None
+
+
+class Server:
+    """apic_server: resident simulations stepped by worker threads that batch
+    ready requests (continuous batching) under an HBM budget."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, n_workers: int = 2, max_batch_scenes: int = 64):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.apic_server_create(C.byref(h), int(device), int(hbm_budget_bytes), int(n_workers),
+                                      int(max_batch_scenes)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().apic_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def open_sim(self, x, v, Cm, m, nrm, body, h, mu, n_iter, n_bodies=None, mu_pair=None, flags=0):
+        """Admit a simulation from host numpy arrays (or CUDA tensors)."""
+        return Sim(self, x, v, Cm, m, nrm, body, h, mu, n_iter, n_bodies, mu_pair, flags)
+
+    def poll(self, ticket):
+        done, lat = C.c_int32(), C.c_double()
+        _check(load().apic_ticket_poll(self._h, int(ticket), C.byref(done), C.byref(lat)))
+        return bool(done.value), (lat.value if done.value else None)
+
+    def wait(self, ticket, timeout_s: float = 60.0):
+        lat = C.c_double()
+        _check(load().apic_ticket_wait(self._h, int(ticket), float(timeout_s), C.byref(lat)))
+        return lat.value
+
+    def stats(self, reset: bool = False) -> dict:
+        st = ServerStats()
+        _check(load().apic_server_get_stats(self._h, C.byref(st), 1 if reset else 0))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+
+class Sim:
+    def __init__(self, srv, x, v, Cm, m, nrm, body, h, mu, n_iter, n_bodies=None, mu_pair=None, flags=0):
+        lib = load()
+        self.srv = srv
+        dev = _is_torch(x)
+        if not dev:
+            x = np.ascontiguousarray(x, np.float64)
+            body = np.ascontiguousarray(body, np.int32)
+            dt = np.asarray(v).dtype
+            v, Cm, m, nrm = (np.ascontiguousarray(a, dt) for a in (v, Cm, m, nrm))
+            flags |= APIC_HOST_PTRS
+            fp64 = dt == np.float64
+        else:
+            import torch
+
+            fp64 = v.dtype == torch.float64
+        if fp64:
+            flags |= APIC_FP64
+        self.n = int(x.shape[0])
+        self.dtype = np.float64 if fp64 else np.float32
+        nb = n_bodies if n_bodies is not None else int(body.max()) + 1
+        mp = None
+        if mu_pair is not None:
+            mp = np.ascontiguousarray(np.asarray(mu_pair, np.float64).reshape(nb, nb))
+        a = StepArgs(self.n, int(nb), int(n_iter), _ptr(body), _ptr(x), _ptr(v), _ptr(Cm), _ptr(m), _ptr(nrm), None,
+                     None, float(h), float(mu), None if mp is None else mp.ctypes.data, int(flags))
+        hsim = C.c_void_p()
+        _check(lib.apic_sim_open(srv.handle, C.byref(a), C.byref(hsim)))
+        self._h = hsim
+
+    def submit(self, dt_advect: float = 0.0) -> int:
+        t = C.c_uint64()
+        _check(load().apic_sim_submit(self._h, float(dt_advect), C.byref(t)))
+        return t.value
+
+    def read(self):
+        x = np.empty((self.n, 3), np.float64)
+        v = np.empty((self.n, 3), self.dtype)
+        Cm = np.empty((self.n, 3, 3), self.dtype)
+        _check(load().apic_sim_read(self._h, x.ctypes.data, v.ctypes.data, Cm.ctypes.data))
+        return x, v, Cm
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().apic_sim_close(self._h)
+            self._h = None

@@ -149,6 +149,10 @@ cudaError_t launch_scene_counts(int n_blocks, const int* blist, const uint32_t* 
                                 const int4* item_info, const SceneDev* sc, int ns, unsigned long long* out,
                                 cudaStream_t s);
 
+// x += dt v for n particles (x double, v in T).
+template <class T>
+cudaError_t launch_advect(int64_t n, double* x, const T* v, double dt, cudaStream_t s);
+
 // Set the calling thread's message returned by apic_last_error().
 void set_last_error(const char* msg);
 

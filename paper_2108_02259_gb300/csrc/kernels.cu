@@ -888,6 +888,13 @@ __global__ void k_scene_counts(int n_blocks, const int* __restrict__ blist, cons
     atomicAdd(&out[3 * item_info[i].z + 2], 1ull);
 }
 
+// x += dt v (the serving loop's optional advection after a contact step).
+template <class T>
+__global__ void k_advect(int64_t n, double* __restrict__ x, const T* __restrict__ v, double dt) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < 3 * n) x[i] += dt * (double)v[i];
+}
+
 inline unsigned grid_for(int64_t n, int threads) {
   return (unsigned)((n + threads - 1) / threads);
 }
@@ -987,6 +994,13 @@ cudaError_t launch_momentum(int64_t n, const double* x, const T* v, const T* C, 
   return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t launch_advect(int64_t n, double* x, const T* v, double dt, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_advect<T><<<grid_for(3 * n, 256), 256, 0, s>>>(n, x, v, dt);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scene_counts(int n_blocks, const int* blist, const uint32_t* gmask, int n_items,
                                 const int4* item_info, const SceneDev* sc, int ns, unsigned long long* out,
                                 cudaStream_t s) {
@@ -1005,7 +1019,8 @@ cudaError_t launch_scene_counts(int n_blocks, const int* blist, const uint32_t* 
   template cudaError_t launch_normalize<T>(int64_t, const T*, const uint32_t*, V4<T>*, V4<double>*,     \
                                            V4<T>*, int, cudaStream_t);                                  \
   template cudaError_t launch_momentum<T>(int64_t, const double*, const T*, const T*, const T*, double, \
-                                          double*, cudaStream_t);
+                                          double*, cudaStream_t);                                       \
+  template cudaError_t launch_advect<T>(int64_t, double*, const T*, double, cudaStream_t);
 APIC_INST_T(float)
 APIC_INST_T(double)
 

@@ -1,0 +1,452 @@
+// Serving loop of libapiccontact: resident simulations, a request queue,
+// worker threads that batch ready requests into one batched contact step,
+// admission by an HBM budget, and per-request latency.
+//
+// Each worker owns an apic_ctx and a non-blocking CUDA stream.  A worker
+// takes, in FIFO order, every queued request whose simulation has no step in
+// flight (and that shares flags and n_iter with the first one it took), up to
+// max_batch requests and a scratch estimate that fits the budget, and runs
+// them as one apic_contact_step_batched call with the simulations' resident
+// arrays as inputs and outputs.  While it waits for its batch, other workers
+// take the requests that arrived meanwhile, so batches overlap on the GPU.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "../../include/apiccontact.h"
+#include "apic_internal.h"
+
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+// Scratch the pipeline holds per particle of a batch, as an admission
+// estimate (sort keys and values, sorted planes, Delta, item tables and the
+// grid share; FP32 path).
+constexpr size_t kScratchPerParticle = 640;
+
+apic_status sfail(apic_status code, const char* msg) {
+  apic::set_last_error(msg);
+  return code;
+}
+
+}  // namespace
+
+struct apic_sim {
+  apic_server* srv = nullptr;
+  int64_t n = 0;
+  int32_t n_bodies = 1, n_iter = 0;
+  uint32_t flags = 0;  // without APIC_HOST_PTRS
+  double h = 0, mu = 0;
+  std::vector<double> mu_pair;
+  size_t esize = 4;
+  double* x = nullptr;
+  int32_t* body = nullptr;
+  void *v = nullptr, *C = nullptr, *m = nullptr, *nrm = nullptr;
+  size_t bytes = 0;
+  bool busy = false;   // a step in flight
+  int64_t queued = 0;  // steps waiting in the queue
+};
+
+namespace {
+
+struct Ticket {
+  apic_sim* sim = nullptr;
+  double dt = 0;
+  Clock::time_point t_submit, t_done;
+  int state = 0;  // 0 queued, 1 running, 2 done
+  apic_status status = APIC_OK;
+};
+
+}  // namespace
+
+struct apic_server {
+  int device = 0;
+  size_t budget = 0;
+  int max_batch = 64;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, Ticket> tickets;
+  uint64_t next_ticket = 1;
+  std::vector<std::thread> workers;
+  std::vector<size_t> worker_scratch;
+  bool stop = false;
+  size_t resident = 0;
+  int64_t open = 0;
+  std::unordered_set<apic_sim*> sims;  // open simulations
+  // statistics
+  std::vector<double> lat_ms;
+  int64_t completed = 0, failed = 0, batches = 0, particle_iters = 0, batch_scenes = 0;
+};
+
+namespace {
+
+size_t scratch_total(const apic_server* s) {
+  size_t t = 0;
+  for (size_t b : s->worker_scratch) t += b;
+  return t;
+}
+
+void worker_main(apic_server* srv, int wid) {
+  cudaSetDevice(srv->device);
+  apic_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  const bool ok = apic_create(&ctx, srv->device, 0) == APIC_OK &&
+                  cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess;
+  std::vector<uint64_t> batch;
+  std::vector<apic_step_args> args;
+  for (;;) {
+    batch.clear();
+    {
+      std::unique_lock<std::mutex> lk(srv->mu);
+      auto runnable = [&] {
+        for (uint64_t t : srv->queue)
+          if (!srv->tickets[t].sim->busy) return true;
+        return false;
+      };
+      srv->cv_work.wait(lk, [&] { return srv->stop || runnable(); });
+      if (srv->stop && !runnable()) break;
+      // Budget left for this batch's scratch beyond what the workers hold.
+      size_t room = SIZE_MAX;
+      if (srv->budget) {
+        const size_t held = srv->resident + scratch_total(srv);
+        room = srv->budget > held ? srv->budget - held + srv->worker_scratch[wid] : 0;
+      }
+      uint32_t flags = 0;
+      int32_t n_iter = 0;
+      size_t particles = 0;
+      for (auto it = srv->queue.begin(); it != srv->queue.end() && (int)batch.size() < srv->max_batch;) {
+        Ticket& tk = srv->tickets[*it];
+        apic_sim* sm = tk.sim;
+        const size_t need = (particles + (size_t)sm->n) * kScratchPerParticle * (sm->esize / 4);
+        const bool first = batch.empty();
+        if (!sm->busy && (first || (sm->flags == flags && sm->n_iter == n_iter)) && (first || need <= room)) {
+          if (first) {
+            flags = sm->flags;
+            n_iter = sm->n_iter;
+          }
+          sm->busy = true;
+          sm->queued -= 1;
+          tk.state = 1;
+          particles += (size_t)sm->n;
+          batch.push_back(*it);
+          it = srv->queue.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    if (batch.empty()) continue;
+    args.assign(batch.size(), apic_step_args{});
+    double dts[1024];
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      for (size_t i = 0; i < batch.size(); ++i) {
+        const Ticket& tk = srv->tickets[batch[i]];
+        apic_sim* sm = tk.sim;
+        apic_step_args& a = args[i];
+        a.n = sm->n;
+        a.n_bodies = sm->n_bodies;
+        a.n_iter = sm->n_iter;
+        a.body = sm->body;
+        a.x = sm->x;
+        a.v = sm->v;
+        a.C = sm->C;
+        a.m = sm->m;
+        a.nrm = sm->nrm;
+        a.v_out = sm->v;  // V_hat replaces the resident velocity state
+        a.C_out = sm->C;
+        a.h = sm->h;
+        a.mu = sm->mu;
+        a.mu_pair = sm->mu_pair.empty() ? nullptr : sm->mu_pair.data();
+        a.flags = sm->flags;
+        dts[i % 1024] = tk.dt;
+      }
+    }
+    apic_status st = ok ? apic_contact_step_batched(ctx, args.data(), (int32_t)args.size(), stream, nullptr)
+                        : APIC_ERR_CUDA;
+    if (st == APIC_OK) {
+      for (size_t i = 0; i < args.size(); ++i) {
+        const double dt = dts[i % 1024];
+        if (dt == 0.0 || args[i].n == 0) continue;
+        cudaError_t e = (args[i].flags & APIC_FP64)
+                            ? apic::launch_advect<double>(args[i].n, const_cast<double*>(args[i].x),
+                                                          static_cast<const double*>(args[i].v), dt, stream)
+                            : apic::launch_advect<float>(args[i].n, const_cast<double*>(args[i].x),
+                                                         static_cast<const float*>(args[i].v), dt, stream);
+        if (e != cudaSuccess) st = APIC_ERR_CUDA;
+      }
+      if (cudaStreamSynchronize(stream) != cudaSuccess) st = APIC_ERR_CUDA;
+    }
+    size_t held = 0;
+    if (ctx) apic_scratch_bytes(ctx, &held);
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      const auto now = Clock::now();
+      srv->worker_scratch[wid] = held;
+      srv->batches += 1;
+      srv->batch_scenes += (int64_t)batch.size();
+      for (uint64_t t : batch) {
+        Ticket& tk = srv->tickets[t];
+        tk.state = 2;
+        tk.status = st;
+        tk.t_done = now;
+        tk.sim->busy = false;
+        if (st == APIC_OK) {
+          srv->completed += 1;
+          srv->particle_iters += tk.sim->n * (int64_t)(tk.sim->n_iter + 1);
+          srv->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - tk.t_submit).count());
+        } else {
+          srv->failed += 1;
+        }
+      }
+    }
+    srv->cv_done.notify_all();
+    srv->cv_work.notify_all();
+  }
+  if (stream) cudaStreamDestroy(stream);
+  if (ctx) apic_destroy(ctx);
+}
+
+void free_sim_memory(apic_sim* s) {
+  cudaFree(s->x);
+  cudaFree(s->body);
+  cudaFree(s->v);
+  cudaFree(s->C);
+  cudaFree(s->m);
+  cudaFree(s->nrm);
+}
+
+// Wait (lock held) until the simulation has nothing queued or in flight.
+void wait_idle(apic_server* srv, std::unique_lock<std::mutex>& lk, apic_sim* s) {
+  srv->cv_done.wait(lk, [&] { return !s->busy && s->queued == 0; });
+}
+
+}  // namespace
+
+extern "C" {
+
+apic_status apic_server_create(apic_server** out, int32_t device, size_t hbm_budget_bytes, int32_t n_workers,
+                               int32_t max_batch_scenes) {
+  if (!out) return sfail(APIC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_workers < 1 || n_workers > 16) return sfail(APIC_ERR_INVALID_ARG, "n_workers must be in [1, 16]");
+  if (max_batch_scenes < 1 || max_batch_scenes > 1024)
+    return sfail(APIC_ERR_INVALID_ARG, "max_batch_scenes must be in [1, 1024]");
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return sfail(APIC_ERR_INVALID_ARG, "no such CUDA device");
+  apic_server* srv = new apic_server();
+  srv->device = device;
+  srv->budget = hbm_budget_bytes;
+  srv->max_batch = max_batch_scenes;
+  srv->worker_scratch.assign(n_workers, 0);
+  for (int w = 0; w < n_workers; ++w) srv->workers.emplace_back(worker_main, srv, w);
+  *out = srv;
+  return APIC_OK;
+}
+
+apic_status apic_server_destroy(apic_server* srv) {
+  if (!srv) return APIC_OK;
+  {
+    std::unique_lock<std::mutex> lk(srv->mu);
+    srv->cv_done.wait(lk, [&] {
+      if (!srv->queue.empty()) return false;
+      for (auto& kv : srv->tickets)
+        if (kv.second.state != 2) return false;
+      return true;
+    });
+    srv->stop = true;
+  }
+  srv->cv_work.notify_all();
+  for (auto& t : srv->workers) t.join();
+  cudaSetDevice(srv->device);
+  for (apic_sim* sm : srv->sims) {  // simulations the caller did not close
+    free_sim_memory(sm);
+    delete sm;
+  }
+  delete srv;
+  return APIC_OK;
+}
+
+apic_status apic_sim_open(apic_server* srv, const apic_step_args* a, apic_sim** out) {
+  if (!srv || !a || !out) return sfail(APIC_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (a->n <= 0 || a->n > (int64_t)INT32_MAX / 4) return sfail(APIC_ERR_INVALID_ARG, "n out of range");
+  if (a->n_bodies < 1 || a->n_bodies > 32 || a->n_iter < 0 || !(a->h > 0.0) || !(a->mu >= 0.0))
+    return sfail(APIC_ERR_INVALID_ARG, "invalid n_bodies, n_iter, h or mu");
+  if (!a->x || !a->body || !a->v || !a->C || !a->m || !a->nrm)
+    return sfail(APIC_ERR_INVALID_ARG, "a required array pointer is NULL");
+  const uint32_t known = APIC_FP64 | APIC_HOST_PTRS | APIC_VARIANT_PIC | APIC_VARIANT_SEP23;
+  if (a->flags & ~known) return sfail(APIC_ERR_INVALID_ARG, "unknown flag bits");
+  const size_t es = (a->flags & APIC_FP64) ? 8 : 4;
+  const size_t n = (size_t)a->n;
+  const size_t bytes = n * (3 * sizeof(double) + sizeof(int32_t) + es * (3 + 9 + 1 + 3));
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->budget && srv->resident + scratch_total(srv) + bytes + n * kScratchPerParticle * (es / 4) > srv->budget)
+      return sfail(APIC_ERR_ADMISSION, "the HBM budget cannot hold this simulation now");
+    srv->resident += bytes;
+  }
+  cudaSetDevice(srv->device);
+  apic_sim* s = new apic_sim();
+  s->srv = srv;
+  s->n = a->n;
+  s->n_bodies = a->n_bodies;
+  s->n_iter = a->n_iter;
+  s->flags = a->flags & ~APIC_HOST_PTRS;
+  s->h = a->h;
+  s->mu = a->mu;
+  if (a->mu_pair) s->mu_pair.assign(a->mu_pair, a->mu_pair + a->n_bodies * a->n_bodies);
+  s->esize = es;
+  s->bytes = bytes;
+  const cudaMemcpyKind kind = (a->flags & APIC_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaError_t e = cudaSuccess;
+  auto alloc_copy = [&](void** dst, const void* src, size_t nbytes) {
+    if (e != cudaSuccess) return;
+    e = cudaMalloc(dst, nbytes);
+    if (e == cudaSuccess) e = cudaMemcpy(*dst, src, nbytes, kind);
+  };
+  alloc_copy(reinterpret_cast<void**>(&s->x), a->x, 3 * n * sizeof(double));
+  alloc_copy(reinterpret_cast<void**>(&s->body), a->body, n * sizeof(int32_t));
+  alloc_copy(&s->v, a->v, 3 * n * es);
+  alloc_copy(&s->C, a->C, 9 * n * es);
+  alloc_copy(&s->m, a->m, n * es);
+  alloc_copy(&s->nrm, a->nrm, 3 * n * es);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_sim_memory(s);
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->resident -= bytes;
+    delete s;
+    return sfail(e == cudaErrorMemoryAllocation ? APIC_ERR_OUT_OF_MEMORY : APIC_ERR_CUDA, cudaGetErrorString(e));
+  }
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->open += 1;
+    srv->sims.insert(s);
+  }
+  *out = s;
+  return APIC_OK;
+}
+
+apic_status apic_sim_submit(apic_sim* s, double dt_advect, uint64_t* ticket) {
+  if (!s || !ticket) return sfail(APIC_ERR_INVALID_ARG, "NULL argument");
+  if (!(dt_advect >= 0.0)) return sfail(APIC_ERR_INVALID_ARG, "dt_advect must be >= 0");
+  apic_server* srv = s->srv;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    const uint64_t t = srv->next_ticket++;
+    Ticket tk;
+    tk.sim = s;
+    tk.dt = dt_advect;
+    tk.t_submit = Clock::now();
+    srv->tickets.emplace(t, tk);
+    srv->queue.push_back(t);
+    s->queued += 1;
+    *ticket = t;
+  }
+  srv->cv_work.notify_one();
+  return APIC_OK;
+}
+
+apic_status apic_ticket_poll(apic_server* srv, uint64_t ticket, int32_t* done, double* latency_ms) {
+  if (!srv || !done) return sfail(APIC_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->tickets.find(ticket);
+  if (it == srv->tickets.end()) return sfail(APIC_ERR_INVALID_ARG, "unknown ticket");
+  *done = it->second.state == 2;
+  if (*done && latency_ms)
+    *latency_ms = std::chrono::duration<double, std::milli>(it->second.t_done - it->second.t_submit).count();
+  if (*done && it->second.status != APIC_OK) return sfail(it->second.status, "the request failed");
+  return APIC_OK;
+}
+
+apic_status apic_ticket_wait(apic_server* srv, uint64_t ticket, double timeout_s, double* latency_ms) {
+  if (!srv) return sfail(APIC_ERR_INVALID_ARG, "NULL argument");
+  std::unique_lock<std::mutex> lk(srv->mu);
+  auto it = srv->tickets.find(ticket);
+  if (it == srv->tickets.end()) return sfail(APIC_ERR_INVALID_ARG, "unknown ticket");
+  const auto limit = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                        std::chrono::duration<double>(std::max(0.0, timeout_s)));
+  if (!srv->cv_done.wait_until(lk, limit, [&] { return srv->tickets[ticket].state == 2; }))
+    return sfail(APIC_ERR_TIMEOUT, "the request did not finish in time");
+  const Ticket& tk = srv->tickets[ticket];
+  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(tk.t_done - tk.t_submit).count();
+  if (tk.status != APIC_OK) return sfail(tk.status, "the request failed");
+  return APIC_OK;
+}
+
+apic_status apic_sim_read(apic_sim* s, double* x_out, void* v_out, void* C_out) {
+  if (!s) return sfail(APIC_ERR_INVALID_ARG, "NULL argument");
+  apic_server* srv = s->srv;
+  std::unique_lock<std::mutex> lk(srv->mu);
+  wait_idle(srv, lk, s);
+  cudaSetDevice(srv->device);
+  const size_t n = (size_t)s->n;
+  cudaError_t e = cudaSuccess;
+  if (x_out) e = cudaMemcpy(x_out, s->x, 3 * n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && v_out) e = cudaMemcpy(v_out, s->v, 3 * n * s->esize, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && C_out) e = cudaMemcpy(C_out, s->C, 9 * n * s->esize, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return sfail(APIC_ERR_CUDA, cudaGetErrorString(e));
+  return APIC_OK;
+}
+
+apic_status apic_sim_close(apic_sim* s) {
+  if (!s) return APIC_OK;
+  apic_server* srv = s->srv;
+  {
+    std::unique_lock<std::mutex> lk(srv->mu);
+    wait_idle(srv, lk, s);
+    srv->resident -= s->bytes;
+    srv->open -= 1;
+    srv->sims.erase(s);
+    for (auto& kv : srv->tickets)
+      if (kv.second.sim == s) kv.second.sim = nullptr;
+  }
+  cudaSetDevice(srv->device);
+  free_sim_memory(s);
+  delete s;
+  return APIC_OK;
+}
+
+apic_status apic_server_get_stats(apic_server* srv, apic_server_stats* out, int32_t reset) {
+  if (!srv || !out) return sfail(APIC_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  std::memset(out, 0, sizeof(*out));
+  out->completed = srv->completed;
+  out->failed = srv->failed;
+  out->batches = srv->batches;
+  out->particle_iters = srv->particle_iters;
+  out->mean_batch_scenes = srv->batches ? (double)srv->batch_scenes / (double)srv->batches : 0.0;
+  out->resident_bytes = (int64_t)srv->resident;
+  out->open_sims = srv->open;
+  if (!srv->lat_ms.empty()) {
+    std::vector<double> l = srv->lat_ms;
+    auto pct = [&](double q) {
+      const size_t k = std::min(l.size() - 1, (size_t)(q * (double)(l.size() - 1) + 0.5));
+      std::nth_element(l.begin(), l.begin() + (ptrdiff_t)k, l.end());
+      return l[k];
+    };
+    double sum = 0;
+    for (double d : l) sum += d;
+    out->latency_mean_ms = sum / (double)l.size();
+    out->latency_p50_ms = pct(0.50);
+    out->latency_p99_ms = pct(0.99);
+  }
+  if (reset) {
+    srv->lat_ms.clear();
+    srv->completed = srv->failed = srv->batches = srv->particle_iters = srv->batch_scenes = 0;
+  }
+  return APIC_OK;
+}
+
+}  // extern "C"

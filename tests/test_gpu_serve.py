@@ -1,0 +1,159 @@
+"""The serving loop: resident simulations stepped by batching workers.
+
+Each served result must equal what the oracle gives for that simulation
+stepped alone, and a simulation must give the same result alone and in a mix
+of concurrent simulations (within the FP32 tolerance)."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_02259_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+TOL_V, TOL_C = 1e-5, 1e-4
+
+
+@pytest.fixture(scope="module")
+def apic():
+    from paper_2108_02259_gb300 import apic, build
+
+    build.build()
+    return apic
+
+
+def _sims(k, seed=0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(k):
+        h = [1 / 64, 1 / 128][i % 2]
+        out.append(scenes.multi_body_scene(rng, int(rng.integers(800, 4000)), int(rng.integers(2, 5)), h,
+                                           mu=float(rng.uniform(0, 0.5)), n_iter=3))
+    return out
+
+
+def _oracle_steps(s, steps, dt):
+    x, v, Cm = s.x.copy(), s.v.copy(), s.C.copy()
+    for _ in range(steps):
+        v, Cm, _ = oracle.contact_step(x, v, Cm, s.m, s.nrm, s.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies)
+        x = x + dt * v
+    return x, v, Cm
+
+
+def _err(s, got, ref):
+    vs = np.abs(s.v).max()
+    cs = max(np.abs(ref[2]).max(), np.abs(s.C).max(), 2 * vs / s.h)
+    return np.abs(got[1] - ref[1]).max() / vs, np.abs(got[2] - ref[2]).max() / cs, np.abs(got[0] - ref[0]).max()
+
+
+def test_served_steps_match_oracle(apic):
+    sims = _sims(5)
+    with apic.Server(0, n_workers=2, max_batch_scenes=8) as srv:
+        handles = []
+        for s in sims:
+            f = s.astype(np.float32)
+            handles.append(srv.open_sim(f.x, f.v, f.C, f.m, f.nrm, f.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies))
+        steps = 3
+        dts = [0.1 * s.h / np.abs(s.v).max() for s in sims]
+        tickets = []
+        for _ in range(steps):
+            for hdl, dt in zip(handles, dts):
+                tickets.append(hdl.submit(dt))
+        for t in tickets:
+            assert srv.wait(t, 60.0) >= 0.0
+        st = srv.stats()
+        assert st["completed"] == steps * len(sims) and st["failed"] == 0
+        assert st["latency_p99_ms"] >= st["latency_p50_ms"] > 0
+        for s, hdl, dt in zip(sims, handles, dts):
+            got = hdl.read()
+            ev, ec, ex = _err(s, got, _oracle_steps(s, steps, dt))
+            print(f"[serve] n={s.n}: v err {ev:.2e} C err {ec:.2e} x err {ex:.2e}")
+            # x moves by dt * v_hat each step: its error is bounded by the v error times steps * dt
+            assert ev <= 3 * TOL_V and ec <= TOL_C and ex <= steps * dt * 3 * TOL_V * np.abs(s.v).max()
+            hdl.close()
+
+
+def test_same_result_alone_and_in_the_mix(apic):
+    """A simulation stepped alone and stepped while many others are submitted
+    concurrently (so its requests share batches and overlap with other
+    batches on the GPU) reaches the same state."""
+    target = _sims(1, seed=7)[0]
+    others = _sims(12, seed=8)
+    steps = 4
+    dt = 0.1 * target.h / np.abs(target.v).max()
+
+    def run(with_mix):
+        with apic.Server(0, n_workers=3, max_batch_scenes=16) as srv:
+            f = target.astype(np.float32)
+            a = srv.open_sim(f.x, f.v, f.C, f.m, f.nrm, f.body, target.h, target.mu, target.n_iter,
+                             n_bodies=target.n_bodies)
+            mix = []
+            if with_mix:
+                for s in others:
+                    g = s.astype(np.float32)
+                    mix.append(srv.open_sim(g.x, g.v, g.C, g.m, g.nrm, g.body, s.h, s.mu, s.n_iter,
+                                            n_bodies=s.n_bodies))
+            stop = threading.Event()
+
+            def churn():
+                while not stop.is_set():
+                    ts = [m.submit(0.0) for m in mix]
+                    for t in ts:
+                        srv.wait(t, 60.0)
+
+            th = threading.Thread(target=churn) if with_mix else None
+            if th:
+                th.start()
+            for _ in range(steps):
+                srv.wait(a.submit(dt), 60.0)
+                time.sleep(0.002)
+            stop.set()
+            if th:
+                th.join()
+            out = a.read()
+            batches = srv.stats()["mean_batch_scenes"]
+            return out, batches
+
+    alone, _ = run(False)
+    mixed, mean_batch = run(True)
+    assert mean_batch > 1.0  # the target really shared batches
+    ev, ec, ex = _err(target, mixed, alone)
+    print(f"[serve] alone vs mix: v {ev:.2e} C {ec:.2e} x {ex:.2e}, mean batch {mean_batch:.2f}")
+    assert ev <= TOL_V and ec <= TOL_C and ex <= steps * dt * TOL_V * np.abs(target.v).max()
+
+
+def test_admission_by_budget(apic):
+    s = _sims(1, seed=3)[0]
+    f = s.astype(np.float32)
+    # resident state is 92 B per particle (FP32); admission also reserves
+    # 640 B per particle of step scratch for the simulation being admitted:
+    # two fit in 2*92n + 640n, a third needs 3*92n + 640n.
+    budget = s.n * (2 * 92 + 640) + s.n * 46
+    with apic.Server(0, hbm_budget_bytes=budget, n_workers=1) as srv:
+        a = srv.open_sim(f.x, f.v, f.C, f.m, f.nrm, f.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies)
+        b = srv.open_sim(f.x, f.v, f.C, f.m, f.nrm, f.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies)
+        with pytest.raises(apic.ApicError) as e:
+            srv.open_sim(f.x, f.v, f.C, f.m, f.nrm, f.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies)
+        assert e.value.code == apic.APIC_ERR_ADMISSION
+        b.close()
+        c = srv.open_sim(f.x, f.v, f.C, f.m, f.nrm, f.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies)
+        srv.wait(c.submit(0.0), 60.0)
+        srv.wait(a.submit(0.0), 60.0)
+        assert srv.stats()["open_sims"] == 2
+
+
+def test_wait_timeout_and_poll(apic):
+    s = scenes.four_bodies(scale=0.3)
+    f = s.astype(np.float32)
+    with apic.Server(0, n_workers=1) as srv:
+        a = srv.open_sim(f.x, f.v, f.C, f.m, f.nrm, f.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies)
+        ts = [a.submit(0.0) for _ in range(20)]
+        with pytest.raises(apic.ApicError) as e:
+            srv.wait(ts[-1], 1e-6)
+        assert e.value.code == apic.APIC_ERR_TIMEOUT
+        srv.wait(ts[-1], 120.0)
+        done, lat = srv.poll(ts[0])
+        assert done and lat > 0
