@@ -20,13 +20,11 @@ constexpr int kBlk = 4;
 constexpr int kTile = 7;
 constexpr int kTile3 = kTile * kTile * kTile;
 constexpr int kNodesPerBlock = kBlk * kBlk * kBlk;
-// A work item holds at most kItemSlots padded particle slots and runs on a
-// CTA of kChunk threads.
+// A work item holds at most kChunk particles (one per thread of its CTA).
 #ifndef APIC_CHUNK
 #define APIC_CHUNK 128
 #endif
 constexpr int kChunk = APIC_CHUNK;
-constexpr int kItemSlots = kChunk;
 
 // Error bits raised by the validation pass.
 constexpr int kErrBody = 1;
@@ -39,9 +37,7 @@ struct DevScalars {
   int err;       // kErr* bits
   int n_items;   // work items
   int n_blocks;  // active grid blocks
-  int n_runs;    // cell runs of the sorted particles
-  int n_pad;     // particle slots after padding every odd run with a ghost
-  int pad[3];
+  int pad;
 };
 
 // Dense page table over a box of grid blocks (block coordinates relative to
@@ -92,8 +88,7 @@ enum Mode : int {
 template <class T>
 struct IterParams {
   int n_items;
-  int n_particles;         // padded particle slots
-  int64_t plane;           // stride of the V / Delta planes (slot capacity)
+  int n_particles;
   int max_bodies;          // key multiplier: bodies of the largest scene
   int n_scenes;
   const SceneDev* sc;      // [n_scenes]
@@ -114,7 +109,7 @@ struct IterParams {
   T* gm;                   // grid mass, [nodes]
   uint32_t* gmask;         // body bits, [nodes]
   V4<double>* gp64;        // FP64 momentum at multi-body nodes (FP32 path), [nodes]
-  const int* perm;         // padded slot -> batch particle index, -1 for a ghost
+  const int* perm;         // sorted -> batch particle index
   int pic;                 // PIC transfers
   int sep23;               // Sec. 2.3 rule
 };
@@ -127,22 +122,10 @@ template <class K>
 cudaError_t launch_keys(int64_t n, const SceneDev* sc, int ns, const int4* cellb, int max_bodies, K* keys,
                         int* vals, int* err, cudaStream_t s);
 template <class T>
-cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm, const int* pidx, int64_t plane,
-                          const int4* cellb, V4<T>* pt, V4<T>* pn, V4<T>* V, cudaStream_t s);
+cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm, const int4* cellb, V4<T>* pt,
+                          V4<T>* pn, V4<T>* V, cudaStream_t s);
 template <class K>
-cudaError_t launch_run_heads(int64_t n, const K* keys, int* rh, cudaStream_t s);
-cudaError_t launch_run_pad(int64_t n, const int* n_runs, const int* rstart, int* plen, cudaStream_t s);
-cudaError_t launch_padded_pos(int64_t n, const int* rh, const int* re, const int* rstart, const int* pstart,
-                              const int* plen, const int* n_runs, int* pidx, int* n_pad, cudaStream_t s);
-template <class K>
-cudaError_t launch_pad_index(int64_t n, const int* pidx, const K* keys, const int* perm, K* keys_pad, int* perm_pad,
-                             cudaStream_t s);
-template <class T, class K>
-cudaError_t launch_ghosts(int64_t n, const int* n_runs, const int* rstart, const int* pstart, V4<T>* pt, V4<T>* pn,
-                          V4<T>* V, int64_t plane, K* keys_pad, int* perm_pad, cudaStream_t s);
-template <class K>
-cudaError_t launch_heads(int64_t cap, const int* n_pad, const K* keys, const int* perm_pad, int* flags,
-                         cudaStream_t s);
+cudaError_t launch_heads(int64_t n, const K* keys, int* flags, cudaStream_t s);
 template <class K>
 cudaError_t launch_item_info(const int* item_start, const int* n_items, const K* keys, int max_bodies,
                              const SceneDev* sc, int ns, int4* item_info, int max_items, cudaStream_t s);
@@ -150,7 +133,7 @@ cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* li
                            int* count, cudaStream_t s);
 template <class K>
 cudaError_t launch_mark_items(const int* item_start, const int4* item_info, const int* n_items, const K* keys,
-                              const int* n_pad, int max_items, const SceneDev* sc, int* flags, cudaStream_t s);
+                              int64_t n, int max_items, const SceneDev* sc, int* flags, cudaStream_t s);
 template <class T>
 cudaError_t launch_items(const IterParams<T>& p, int mode, cudaStream_t s);
 // all64: take every node's momentum from the FP64 accumulators (after kModeMassV).

@@ -84,7 +84,7 @@ __device__ __forceinline__ void undesirable(const T dv[3], const T dC[9], const 
 }
 
 template <class T>
-__device__ __forceinline__ void load12(const V4<T>* planes, int64_t n, int64_t s, T v[3], T C[9]) {
+__device__ __forceinline__ void load12(const V4<T>* planes, int n, int s, T v[3], T C[9]) {
   const V4<T> a = planes[s], b = planes[n + s], c = planes[2 * n + s];
   v[0] = a.x; v[1] = a.y; v[2] = a.z;
   C[0] = a.w; C[1] = b.x; C[2] = b.y;
@@ -93,7 +93,7 @@ __device__ __forceinline__ void load12(const V4<T>* planes, int64_t n, int64_t s
 }
 
 template <class T>
-__device__ __forceinline__ void store12(V4<T>* planes, int64_t n, int64_t s, const T v[3], const T C[9]) {
+__device__ __forceinline__ void store12(V4<T>* planes, int n, int s, const T v[3], const T C[9]) {
   planes[s] = V4<T>{v[0], v[1], v[2], C[0]};
   planes[n + s] = V4<T>{C[1], C[2], C[3], C[4]};
   planes[2 * n + s] = V4<T>{C[5], C[6], C[7], C[8]};
@@ -288,7 +288,6 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
   __shared__ int snb[27];
   const int tid = threadIdx.x;
   const int n = p.n_particles;
-  const int64_t plane = p.plane;
   const int item = blockIdx.x;
   if (item >= p.n_items) return;
   const int4 info = p.item_info[item];
@@ -320,8 +319,8 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
     if (kReadD || kReadV) {
       const V4<T>* planes = kReadD ? p.D : p.V;
       q0 = planes[s];
-      q1 = planes[plane + s];
-      q2 = planes[2 * plane + s];
+      q1 = planes[n + s];
+      q2 = planes[2 * n + s];
     }
   }
   if (tid < 27) {
@@ -434,10 +433,8 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
       if (out) {
         // V_hat = V + Delta_N, back in caller order, C = Ch / h
         T v[3], C[9];
-        load12(p.V, plane, s, v, C);
-        const int pg = p.perm[s];
-        if (pg < 0) return;  // a ghost slot has no caller particle
-        const int64_t idx = pg - S.part_off;
+        load12(p.V, n, s, v, C);
+        const int64_t idx = p.perm[s] - S.part_off;
         T* vo = static_cast<T*>(S.v_out);
         T* Co = static_cast<T*>(S.C_out);
         const T inv_h = (T)S.inv_h;
@@ -446,7 +443,7 @@ __global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const I
 #pragma unroll
         for (int a = 0; a < 9; ++a) Co[9 * idx + a] = (C[a] + dC[a]) * inv_h;
       } else {
-        store12(p.D, plane, s, dv, dC);
+        store12(p.D, n, s, dv, dC);
         T u[3], uC[9];
         undesirable(dv, dC, nrm, mu, p.sep23, u, uC);
         stash[0][sidx(tid)] = pt;
@@ -735,12 +732,10 @@ __global__ void k_keys(int64_t n, const SceneDev* __restrict__ sc, int ns, const
 // and V = (v, h C) in three float4 planes.
 template <class T>
 __global__ void k_gather(int64_t n, const SceneDev* __restrict__ sc, int ns, const int* __restrict__ perm,
-                         const int* __restrict__ pidx, int64_t plane, const int4* __restrict__ cellb, V4<T>* pt,
-                         V4<T>* pn, V4<T>* V) {
-  const int64_t s0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s0 >= n) return;
-  const int64_t g = perm[s0];
-  const int64_t s = pidx[s0];
+                         const int4* __restrict__ cellb, V4<T>* pt, V4<T>* pn, V4<T>* V) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int64_t g = perm[s];
   const SceneDev& S = sc[scene_of_particle(sc, ns, g)];
   const int64_t i = g - S.part_off;
   const int4 c = cellb[g];
@@ -760,90 +755,15 @@ __global__ void k_gather(int64_t n, const SceneDev* __restrict__ sc, int ns, con
   for (int a = 0; a < 3; ++a) vv[a] = v[3 * i + a];
 #pragma unroll
   for (int a = 0; a < 9; ++a) Ch[a] = C[9 * i + a] * hh;
-  store12(V, plane, s, vv, Ch);
+  store12(V, (int)n, (int)s, vv, Ch);
 }
 
-// Cell runs of the sorted particles (equal full keys) are padded to even
-// length: an odd run ends with a massless ghost slot.  Slots (2q, 2q+1) then
-// always hold two particles of one cell.  The steps: run heads, run starts
-// (compaction), padded run lengths, their offsets (scan), padded positions.
 template <class K>
-__global__ void k_run_heads(int64_t n, const K* __restrict__ keys, int* rh) {
+__global__ void k_heads(int64_t n, const K* __restrict__ keys, int* flags) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
-  rh[s] = (s == 0 || keys[s] != keys[s - 1]) ? 1 : 0;
-}
-
-__global__ void k_run_pad(int64_t n, const int* __restrict__ n_runs, const int* __restrict__ rstart, int* plen) {
-  const int R = *n_runs;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    if (r < R) {
-      const int len = (r + 1 < R ? rstart[r + 1] : (int)n) - rstart[r];
-      plen[r] = len + (len & 1);
-    } else {
-      plen[r] = 0;
-    }
-  }
-}
-
-__global__ void k_padded_pos(int64_t n, const int* __restrict__ rh, const int* __restrict__ re,
-                             const int* __restrict__ rstart, const int* __restrict__ pstart,
-                             const int* __restrict__ plen, const int* __restrict__ n_runs, int* pidx, int* n_pad) {
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const int r = re[s] + rh[s] - 1;
-  pidx[s] = pstart[r] + (int)(s - rstart[r]);
-  if (s == 0) {
-    const int R = *n_runs;
-    *n_pad = pstart[R - 1] + plen[R - 1];
-  }
-}
-
-// Keys and caller indices in padded order.
-template <class K>
-__global__ void k_pad_index(int64_t n, const int* __restrict__ pidx, const K* __restrict__ keys,
-                            const int* __restrict__ perm, K* keys_pad, int* perm_pad) {
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const int q = pidx[s];
-  keys_pad[q] = keys[s];
-  perm_pad[q] = perm[s];
-}
-
-// Fill the ghost slot of every odd run: the partner's offset and cell with
-// zero mass, zero normal and zero V; no caller index.
-template <class T, class K>
-__global__ void k_ghosts(int64_t n, const int* __restrict__ n_runs, const int* __restrict__ rstart,
-                         const int* __restrict__ pstart, V4<T>* pt, V4<T>* pn, V4<T>* V, int64_t plane, K* keys_pad,
-                         int* perm_pad) {
-  const int R = *n_runs;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
-    const int len = (r + 1 < R ? rstart[r + 1] : (int)n) - rstart[r];
-    if (!(len & 1)) continue;
-    const int64_t g = (int64_t)pstart[r] + len;
-    const V4<T> a = pt[g - 1];
-    pt[g] = V4<T>{a.x, a.y, a.z, T(0)};
-    pn[g] = V4<T>{T(0), T(0), T(0), pn[g - 1].w};
-    const V4<T> z{T(0), T(0), T(0), T(0)};
-    V[g] = z;
-    V[plane + g] = z;
-    V[2 * plane + g] = z;
-    keys_pad[g] = keys_pad[g - 1];
-    perm_pad[g] = -1;
-  }
-}
-
-// Item heads over the padded slots [0, cap): a new item at every (grid block,
-// body) change and every kItemSlots slots; ghost slots and slots beyond the
-// padded count are never heads.
-template <class K>
-__global__ void k_heads(int64_t cap, const int* __restrict__ n_pad, const K* __restrict__ keys,
-                        const int* __restrict__ perm_pad, int* flags) {
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= cap) return;
-  const int np = *n_pad;
-  flags[q] = (q < np && perm_pad[q] >= 0 &&
-              (q % kItemSlots == 0 || (keys[q] >> 6) != (keys[q - 1] >> 6))) ? 1 : 0;
+  // a new item at every (grid block, body) change and every kChunk particles
+  flags[s] = (s % kChunk == 0 || (keys[s] >> 6) != (keys[s - 1] >> 6)) ? 1 : 0;
 }
 
 template <class K>
@@ -865,11 +785,10 @@ __global__ void k_item_info(const int* __restrict__ item_start, const int* __res
 // subset of the 3x3x3 blocks around B (once per item, not per particle).
 template <class K>
 __global__ void k_mark_items(const int* __restrict__ item_start, const int4* __restrict__ item_info,
-                             const int* __restrict__ n_items_p, const K* __restrict__ keys,
-                             const int* __restrict__ n_pad, const SceneDev* __restrict__ sc, int* flags) {
+                             const int* __restrict__ n_items_p, const K* __restrict__ keys, int64_t n,
+                             const SceneDev* __restrict__ sc, int* flags) {
   const int lane = threadIdx.x & 31;
   const int n_items = *n_items_p;
-  const int64_t n = *n_pad;
   const int warps = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
   for (int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); i < n_items; i += warps) {
     const int s0 = item_start[i];
@@ -999,56 +918,17 @@ cudaError_t launch_keys(int64_t n, const SceneDev* sc, int ns, const int4* cellb
 }
 
 template <class T>
-cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm, const int* pidx, int64_t plane,
-                          const int4* cellb, V4<T>* pt, V4<T>* pn, V4<T>* V, cudaStream_t s) {
+cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm, const int4* cellb, V4<T>* pt,
+                          V4<T>* pn, V4<T>* V, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_gather<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, perm, pidx, plane, cellb, pt, pn, V);
+  k_gather<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, perm, cellb, pt, pn, V);
   return cudaGetLastError();
 }
 
 template <class K>
-cudaError_t launch_run_heads(int64_t n, const K* keys, int* rh, cudaStream_t s) {
+cudaError_t launch_heads(int64_t n, const K* keys, int* flags, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_run_heads<K><<<grid_for(n, 256), 256, 0, s>>>(n, keys, rh);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_run_pad(int64_t n, const int* n_runs, const int* rstart, int* plen, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const unsigned g = (unsigned)std::min<int64_t>(grid_for(n, 256), 152 * 16);
-  k_run_pad<<<g, 256, 0, s>>>(n, n_runs, rstart, plen);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_padded_pos(int64_t n, const int* rh, const int* re, const int* rstart, const int* pstart,
-                              const int* plen, const int* n_runs, int* pidx, int* n_pad, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  k_padded_pos<<<grid_for(n, 256), 256, 0, s>>>(n, rh, re, rstart, pstart, plen, n_runs, pidx, n_pad);
-  return cudaGetLastError();
-}
-
-template <class K>
-cudaError_t launch_pad_index(int64_t n, const int* pidx, const K* keys, const int* perm, K* keys_pad, int* perm_pad,
-                             cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  k_pad_index<K><<<grid_for(n, 256), 256, 0, s>>>(n, pidx, keys, perm, keys_pad, perm_pad);
-  return cudaGetLastError();
-}
-
-template <class T, class K>
-cudaError_t launch_ghosts(int64_t n, const int* n_runs, const int* rstart, const int* pstart, V4<T>* pt, V4<T>* pn,
-                          V4<T>* V, int64_t plane, K* keys_pad, int* perm_pad, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const unsigned g = (unsigned)std::min<int64_t>(grid_for(n, 256), 152 * 16);
-  k_ghosts<T, K><<<g, 256, 0, s>>>(n, n_runs, rstart, pstart, pt, pn, V, plane, keys_pad, perm_pad);
-  return cudaGetLastError();
-}
-
-template <class K>
-cudaError_t launch_heads(int64_t cap, const int* n_pad, const K* keys, const int* perm_pad, int* flags,
-                         cudaStream_t s) {
-  if (cap <= 0) return cudaSuccess;
-  k_heads<K><<<grid_for(cap, 256), 256, 0, s>>>(cap, n_pad, keys, perm_pad, flags);
+  k_heads<K><<<grid_for(n, 256), 256, 0, s>>>(n, keys, flags);
   return cudaGetLastError();
 }
 
@@ -1063,10 +943,10 @@ cudaError_t launch_item_info(const int* item_start, const int* n_items, const K*
 
 template <class K>
 cudaError_t launch_mark_items(const int* item_start, const int4* item_info, const int* n_items, const K* keys,
-                              const int* n_pad, int max_items, const SceneDev* sc, int* flags, cudaStream_t s) {
+                              int64_t n, int max_items, const SceneDev* sc, int* flags, cudaStream_t s) {
   if (max_items <= 0) return cudaSuccess;
   const int64_t warps = std::min<int64_t>(max_items, 152 * 64);
-  k_mark_items<K><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(item_start, item_info, n_items, keys, n_pad,
+  k_mark_items<K><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(item_start, item_info, n_items, keys, n,
                                                                        sc, flags);
   return cudaGetLastError();
 }
@@ -1133,8 +1013,8 @@ cudaError_t launch_scene_counts(int n_blocks, const int* blist, const uint32_t* 
 
 #define APIC_INST_T(T)                                                                                  \
   template cudaError_t launch_cells<T>(int64_t, const SceneDev*, int, int4*, int*, int*, cudaStream_t); \
-  template cudaError_t launch_gather<T>(int64_t, const SceneDev*, int, const int*, const int*, int64_t,  \
-                                        const int4*, V4<T>*, V4<T>*, V4<T>*, cudaStream_t);             \
+  template cudaError_t launch_gather<T>(int64_t, const SceneDev*, int, const int*, const int4*, V4<T>*,  \
+                                        V4<T>*, V4<T>*, cudaStream_t);                                  \
   template cudaError_t launch_items<T>(const IterParams<T>&, int, cudaStream_t);                        \
   template cudaError_t launch_normalize<T>(int64_t, const T*, const uint32_t*, V4<T>*, V4<double>*,     \
                                            V4<T>*, int, cudaStream_t);                                  \
@@ -1147,16 +1027,10 @@ APIC_INST_T(double)
 #define APIC_INST_K(K)                                                                                     \
   template cudaError_t launch_keys<K>(int64_t, const SceneDev*, int, const int4*, int, K*, int*, int*,     \
                                       cudaStream_t);                                                       \
-  template cudaError_t launch_heads<K>(int64_t, const int*, const K*, const int*, int*, cudaStream_t);    \
-  template cudaError_t launch_run_heads<K>(int64_t, const K*, int*, cudaStream_t);                         \
-  template cudaError_t launch_pad_index<K>(int64_t, const int*, const K*, const int*, K*, int*, cudaStream_t); \
-  template cudaError_t launch_ghosts<float, K>(int64_t, const int*, const int*, const int*, V4<float>*,     \
-                                               V4<float>*, V4<float>*, int64_t, K*, int*, cudaStream_t);   \
-  template cudaError_t launch_ghosts<double, K>(int64_t, const int*, const int*, const int*, V4<double>*,  \
-                                                V4<double>*, V4<double>*, int64_t, K*, int*, cudaStream_t); \
+  template cudaError_t launch_heads<K>(int64_t, const K*, int*, cudaStream_t);                             \
   template cudaError_t launch_item_info<K>(const int*, const int*, const K*, int, const SceneDev*, int,    \
                                            int4*, int, cudaStream_t);                                      \
-  template cudaError_t launch_mark_items<K>(const int*, const int4*, const int*, const K*, const int*, int, \
+  template cudaError_t launch_mark_items<K>(const int*, const int4*, const int*, const K*, int64_t, int,   \
                                             const SceneDev*, int*, cudaStream_t);
 APIC_INST_K(uint32_t)
 APIC_INST_K(uint64_t)

@@ -35,8 +35,7 @@ enum Slot : int {
   kSlotHeads, kSlotOffs, kSlotItemStart, kSlotItemInfo, kSlotBFlags, kSlotBOffs, kSlotBList, kSlotPage,
   kSlotGm, kSlotGmask, kSlotGp, kSlotGp64, kSlotGv, kSlotGmb, kSlotMuTable, kSlotCubTmp, kSlotScenes,
   kSlotSBbox, kSlotSMom, kSlotSCount, kSlotHX, kSlotHBody, kSlotHV, kSlotHC, kSlotHM, kSlotHN, kSlotHVo,
-  kSlotHCo, kSlotDS, kSlotRunHeads, kSlotRunIdx, kSlotRunStart, kSlotRunPlen, kSlotRunPstart, kSlotPidx,
-  kSlotPermPad, kSlotKeysPad, kSlotCount
+  kSlotHCo, kSlotDS, kSlotCount
 };
 
 constexpr int kMaxBodies = 32;
@@ -246,8 +245,6 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   int4* item_info;
   int* page = nullptr;
   int* blist = nullptr;
-  int* perm_pad = nullptr;
-  int64_t cap = 0;
   for (int attempt = 0;; ++attempt) {
     // 1. cells, validation, bounding boxes of particle blocks.
     const bool fresh = !env.have_box() || attempt > 0;
@@ -317,63 +314,30 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     else
       P_TRY((sort_keys<Env, uint32_t>(env, n, sc, ns, cellb, max_bodies, end_bit, &ds->err, &perm, &keys, s)));
 
-    // 4. cell runs padded to even length (a massless ghost ends each odd
-    //    run), and the sorted SoA planes in that padded order.
-    cap = 2 * n;
-    int *rh, *re, *rstart, *plen, *pstart, *pidx;
-    P_TRY(env.take(kSlotRunHeads, n, &rh, "run heads"));
-    P_TRY(env.take(kSlotRunIdx, n, &re, "run index"));
-    P_TRY(env.take(kSlotRunStart, n, &rstart, "run starts"));
-    P_TRY(env.take(kSlotRunPlen, n, &plen, "padded run lengths"));
-    P_TRY(env.take(kSlotRunPstart, n, &pstart, "padded run offsets"));
-    P_TRY(env.take(kSlotPidx, n, &pidx, "padded positions"));
-    P_TRY(env.take(kSlotPermPad, cap, &perm_pad, "padded permutation"));
-    if (k64)
-      P_LAUNCH(env, launch_run_heads<uint64_t>(n, static_cast<const uint64_t*>(keys), rh, s));
-    else
-      P_LAUNCH(env, launch_run_heads<uint32_t>(n, static_cast<const uint32_t*>(keys), rh, s));
-    P_TRY(exclusive_sum(env, rh, re, n, s));
-    P_LAUNCH(env, launch_compact(n, rh, re, rstart, nullptr, &ds->n_runs, s));
-    P_LAUNCH(env, launch_run_pad(n, &ds->n_runs, rstart, plen, s));
-    P_TRY(exclusive_sum(env, plen, pstart, n, s));
-    P_LAUNCH(env, launch_padded_pos(n, rh, re, rstart, pstart, plen, &ds->n_runs, pidx, &ds->n_pad, s));
-    P_TRY(env.take(kSlotPt, cap, &pt, "particle offsets"));
-    P_TRY(env.take(kSlotPn, cap, &pn, "particle normals"));
-    P_TRY(env.take(kSlotV, 3 * cap, &V, "sorted V"));
-    P_TRY(env.take(kSlotD, 3 * cap, &D, "Delta"));
-    P_LAUNCH(env, launch_gather<T>(n, sc, ns, perm, pidx, cap, cellb, pt, pn, V, s));
-    if (k64) {
-      uint64_t* kp;
-      P_TRY(env.take(kSlotKeysPad, cap, &kp, "padded keys"));
-      P_LAUNCH(env, launch_pad_index<uint64_t>(n, pidx, static_cast<const uint64_t*>(keys), perm, kp, perm_pad, s));
-      P_LAUNCH(env, (launch_ghosts<T, uint64_t>(n, &ds->n_runs, rstart, pstart, pt, pn, V, cap, kp, perm_pad, s)));
-      keys = kp;
-    } else {
-      uint32_t* kp;
-      P_TRY(env.take(kSlotKeysPad, cap, &kp, "padded keys"));
-      P_LAUNCH(env, launch_pad_index<uint32_t>(n, pidx, static_cast<const uint32_t*>(keys), perm, kp, perm_pad, s));
-      P_LAUNCH(env, (launch_ghosts<T, uint32_t>(n, &ds->n_runs, rstart, pstart, pt, pn, V, cap, kp, perm_pad, s)));
-      keys = kp;
-    }
+    // 4. sorted SoA.
+    P_TRY(env.take(kSlotPt, n, &pt, "particle offsets"));
+    P_TRY(env.take(kSlotPn, n, &pn, "particle normals"));
+    P_TRY(env.take(kSlotV, 3 * n, &V, "sorted V"));
+    P_TRY(env.take(kSlotD, 3 * n, &D, "Delta"));
+    P_LAUNCH(env, launch_gather<T>(n, sc, ns, perm, cellb, pt, pn, V, s));
 
-    // 5. work items over the padded slots: runs of equal (grid block, body),
-    //    at most kItemSlots long.
-    P_TRY(env.take(kSlotHeads, cap, &heads, "item heads"));
-    P_TRY(env.take(kSlotOffs, cap, &offs, "item offsets"));
-    P_TRY(env.take(kSlotItemStart, cap, &item_start, "item starts"));
-    P_TRY(env.take(kSlotItemInfo, cap, &item_info, "item info"));
+    // 5. work items: runs of equal (grid block, body), at most kChunk long.
+    P_TRY(env.take(kSlotHeads, n, &heads, "item heads"));
+    P_TRY(env.take(kSlotOffs, n, &offs, "item offsets"));
+    P_TRY(env.take(kSlotItemStart, n, &item_start, "item starts"));
+    P_TRY(env.take(kSlotItemInfo, n, &item_info, "item info"));
     if (k64)
-      P_LAUNCH(env, launch_heads<uint64_t>(cap, &ds->n_pad, static_cast<const uint64_t*>(keys), perm_pad, heads, s));
+      P_LAUNCH(env, launch_heads<uint64_t>(n, static_cast<const uint64_t*>(keys), heads, s));
     else
-      P_LAUNCH(env, launch_heads<uint32_t>(cap, &ds->n_pad, static_cast<const uint32_t*>(keys), perm_pad, heads, s));
-    P_TRY(exclusive_sum(env, heads, offs, cap, s));
-    P_LAUNCH(env, launch_compact(cap, heads, offs, item_start, nullptr, &ds->n_items, s));
+      P_LAUNCH(env, launch_heads<uint32_t>(n, static_cast<const uint32_t*>(keys), heads, s));
+    P_TRY(exclusive_sum(env, heads, offs, n, s));
+    P_LAUNCH(env, launch_compact(n, heads, offs, item_start, nullptr, &ds->n_items, s));
     if (k64)
       P_LAUNCH(env, launch_item_info<uint64_t>(item_start, &ds->n_items, static_cast<const uint64_t*>(keys),
-                                               max_bodies, sc, ns, item_info, (int)cap, s));
+                                               max_bodies, sc, ns, item_info, (int)n, s));
     else
       P_LAUNCH(env, launch_item_info<uint32_t>(item_start, &ds->n_items, static_cast<const uint32_t*>(keys),
-                                               max_bodies, sc, ns, item_info, (int)cap, s));
+                                               max_bodies, sc, ns, item_info, (int)n, s));
 
     // 6. active grid blocks: every block some stencil reaches; page table.
     int *bflags, *boffs;
@@ -384,12 +348,10 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     P_CUDA(cudaMemsetAsync(bflags, 0, NB * sizeof(int), s));
     if (k64)
       P_LAUNCH(env, launch_mark_items<uint64_t>(item_start, item_info, &ds->n_items,
-                                                static_cast<const uint64_t*>(keys), &ds->n_pad, (int)cap, sc,
-                                                bflags, s));
+                                                static_cast<const uint64_t*>(keys), n, (int)n, sc, bflags, s));
     else
       P_LAUNCH(env, launch_mark_items<uint32_t>(item_start, item_info, &ds->n_items,
-                                                static_cast<const uint32_t*>(keys), &ds->n_pad, (int)cap, sc,
-                                                bflags, s));
+                                                static_cast<const uint32_t*>(keys), n, (int)n, sc, bflags, s));
     P_TRY(exclusive_sum(env, bflags, boffs, NB, s));
     P_LAUNCH(env, launch_compact(NB, bflags, boffs, blist, page, &ds->n_blocks, s));
     P_CUDA(cudaMemcpyAsync(hs, ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
@@ -410,7 +372,6 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   }
   const int n_items = hs->n_items;
   const int n_blocks = hs->n_blocks;
-  const int n_pad = hs->n_pad;
   const int64_t n_nodes = (int64_t)n_blocks * kNodesPerBlock;
 
   // 7. node arrays; mass, body mask and P2G(V); friction blend; normalise.
@@ -436,7 +397,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     P_TRY(env.take(kSlotGmb, (size_t)max_bodies * n_nodes, &gmb, "per-body grid mass"));
     P_CUDA(cudaMemsetAsync(gmb, 0, (size_t)max_bodies * n_nodes * sizeof(T), s));
     P_TRY(env.take(kSlotMuTable, (size_t)n_mu, &mu_table, "friction tables"));
-    P_TRY(env.take(kSlotMup, cap, &mup, "particle friction"));
+    P_TRY(env.take(kSlotMup, n, &mup, "particle friction"));
     T* hmu = static_cast<T*>(env.host_buf((size_t)n_mu * sizeof(T)));
     if (!hmu) return pfail(APIC_ERR_INVALID_ARG, "friction tables too large for this entry point");
     for (int i = 0; i < ns; ++i)
@@ -448,8 +409,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
 
   IterParams<T> p{};
   p.n_items = n_items;
-  p.n_particles = n_pad;
-  p.plane = cap;
+  p.n_particles = (int)n;
   p.max_bodies = max_bodies;
   p.n_scenes = ns;
   p.sc = sc;
@@ -470,7 +430,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   p.gm = gm;
   p.gmask = gmask;
   p.gp64 = gp64;
-  p.perm = perm_pad;
+  p.perm = perm;
   p.pic = (flags & APIC_VARIANT_PIC) ? 1 : 0;
   p.sep23 = (flags & APIC_VARIANT_SEP23) ? 1 : 0;
 
