@@ -260,6 +260,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="fix the transfer-kernel variant (default: autotune for the workload)")
+    ap.add_argument("--no-graphs", action="store_true", help="launch the transfer passes one by one")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -308,7 +311,14 @@ def main():
         else:
             step_one(bs[0])
 
+    # pick the transfer-kernel variant for this size class (untimed), then
     # one checked step: the device's own momentum balance
+    if args.variant >= 0:
+        ctx.set_variant(args.variant)
+        variant = args.variant
+    else:
+        variant = ctx.autotune(bs, N, stream=stream)
+    ctx.set_graphs(not args.no_graphs)
     st = apic.contact_step_batched(ctx, bs, N, stream=stream, stats=True)
     for _ in range(args.warmup):
         step()
@@ -329,7 +339,7 @@ def main():
         clocks = Clocks("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
     except Exception:
         clocks = Clocks(dev.index)
-    ctx.set_profiling(True)
+    ctx.set_profiling(False)  # resets the launch counter; passes replay as a graph
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
@@ -338,6 +348,11 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     ck = clocks.stop()
+    launches = ctx.profile()["kernel_launches"]
+    # per-pass kernel times for the roofline: a separate, untimed run with
+    # an event pair around every pass (launched one by one)
+    ctx.set_profiling(True)
+    timed(step, max(2, min(args.steps, 5)))
     prof = ctx.profile()
     ctx.set_profiling(False)
     if ws > 1:
@@ -425,8 +440,10 @@ def main():
         "dtype": "f64" if dt == np.float64 else "f32", "data": "synthetic",
         "config": workload_config(args.workload, sc, dt),
         "e2e": e2e,
-        "gpu_launches": int(prof["kernel_launches"]),
-        "sort_primitive_calls": int(prof["sort_launches"]),
+        "gpu_launches": int(launches),
+        "kernel_variant": apic.variants()[variant],
+        "cuda_graph": not args.no_graphs,
+        "sort_primitive_calls_per_step": prof["sort_launches"] / max(prof["steps"], 1),
         "roofline": {"bound": "hbm", "kernel": "k_items (fused G2P + projection + P2G pass)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,

@@ -258,6 +258,51 @@ apic_status apic_get_profile(apic_ctx* ctx, apic_profile* out);
 /* Bytes of device scratch the context currently holds. */
 apic_status apic_scratch_bytes(apic_ctx* ctx, size_t* out);
 
+/* ---------------------------------------------------------------------------
+ * Kernel variants, autotuning and CUDA graphs (no counterpart in the paper:
+ * they change how the transfer passes are launched, never what they compute).
+ *
+ * The fused transfer kernel is built in apic_variant_count() variants that
+ * differ in how many 128-thread CTAs each SM holds (register cap versus
+ * occupancy); which is fastest depends on the scene.  By default a context
+ * tunes per size class (FP32 path; classes = bit length of the call's total
+ * particle count): the first calls of a class run each variant twice, timed
+ * with CUDA events on the caller's stream, and the fastest is used from then
+ * on.  The FP64 path has one variant.
+ *
+ * The launch sequence from the mass pass to the last transfer pass is
+ * captured as a CUDA graph on the second consecutive call whose sizes and
+ * buffers match the previous call's, and replayed while they keep matching.
+ * --------------------------------------------------------------------------*/
+
+/* Number of variants, and a one-line description of variant v ("" if out of
+ * range; the string is static). */
+int32_t apic_variant_count(void);
+const char* apic_variant_name(int32_t v);
+
+/* Fix the variant for every later call on ctx (0 .. count-1), or -1 to tune
+ * per size class (the default).  APIC_ERR_INVALID_ARG if out of range. */
+apic_status apic_set_variant(apic_ctx* ctx, int32_t v);
+
+/* The variant used for a call of n_particles FP32 particles: *decided = 1 and
+ * the tuned (or fixed) variant, or *decided = 0 and variant 0 while the size
+ * class is still being tuned. */
+apic_status apic_get_variant(apic_ctx* ctx, int64_t n_particles, int32_t* variant, int32_t* decided);
+
+/* Tune the size class of these scenes now: runs apic_contact_step_batched on
+ * them until the class is decided (at most 2 * count + 1 calls, synchronising
+ * `stream` after each) and returns the choice in *variant (nullable).  The
+ * outputs are overwritten by every call; with in-place arrays (v_out == v)
+ * the state advances, so tune on a copy.  APIC_ERR_INVALID_ARG when a variant
+ * is fixed. */
+apic_status apic_autotune(apic_ctx* ctx, const apic_step_args* scenes, int32_t n_scenes, void* stream,
+                          int32_t* variant);
+
+/* Capture and replay the transfer passes as a CUDA graph (1, the default) or
+ * launch them one by one (0).  Profiling (apic_set_profiling) launches them
+ * one by one regardless, to time each pass. */
+apic_status apic_set_graphs(apic_ctx* ctx, int32_t on);
+
 #ifdef __cplusplus
 }
 #endif

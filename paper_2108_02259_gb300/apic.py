@@ -37,6 +37,8 @@ EXPORTED = [
     "apic_set_profiling", "apic_get_profile", "apic_scratch_bytes", "apic_contact_step_static",
     "apic_contact_step_batched", "apic_server_create", "apic_server_destroy", "apic_sim_open", "apic_sim_submit",
     "apic_ticket_poll", "apic_ticket_wait", "apic_sim_read", "apic_sim_close", "apic_server_get_stats",
+    "apic_variant_count", "apic_variant_name", "apic_set_variant", "apic_get_variant", "apic_autotune",
+    "apic_set_graphs",
 ]
 
 
@@ -120,8 +122,16 @@ def load(path: str = LIB_PATH):
     lib.apic_set_profiling.argtypes = [P, C.c_int32]
     lib.apic_get_profile.argtypes = [P, C.POINTER(Profile)]
     lib.apic_scratch_bytes.argtypes = [P, C.POINTER(C.c_size_t)]
+    lib.apic_variant_count.argtypes = []
+    lib.apic_variant_count.restype = C.c_int32
+    lib.apic_variant_name.argtypes = [C.c_int32]
+    lib.apic_variant_name.restype = C.c_char_p
+    lib.apic_set_variant.argtypes = [P, C.c_int32]
+    lib.apic_get_variant.argtypes = [P, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.apic_autotune.argtypes = [P, C.POINTER(StepArgs), C.c_int32, P, C.POINTER(C.c_int32)]
+    lib.apic_set_graphs.argtypes = [P, C.c_int32]
     for f in ("apic_create", "apic_destroy", "apic_contact_step", "apic_set_profiling", "apic_get_profile",
-              "apic_scratch_bytes"):
+              "apic_scratch_bytes", "apic_set_variant", "apic_get_variant", "apic_autotune", "apic_set_graphs"):
         getattr(lib, f).restype = C.c_int32
     _lib = lib
     return lib
@@ -175,6 +185,34 @@ class Context:
         v = C.c_size_t()
         _check(load().apic_scratch_bytes(self._h, C.byref(v)))
         return int(v.value)
+
+    def set_variant(self, v: int):
+        """Fix the transfer-kernel variant (-1: tune per size class)."""
+        _check(load().apic_set_variant(self._h, int(v)))
+
+    def variant(self, n_particles: int) -> tuple[int, bool]:
+        """(variant, decided) for a call of n_particles FP32 particles."""
+        v, d = C.c_int32(), C.c_int32()
+        _check(load().apic_get_variant(self._h, int(n_particles), C.byref(v), C.byref(d)))
+        return int(v.value), bool(d.value)
+
+    def autotune(self, scenes, n_iter: int, flags: int = 0, stream=None) -> int:
+        """Tune the size class of these BatchScene now (their outputs are
+        overwritten); returns the chosen variant."""
+        arr, ns, sptr, _keep = _batch_args(scenes, n_iter, flags, stream)
+        v = C.c_int32()
+        _check(load().apic_autotune(self._h, arr, ns, sptr, C.byref(v)))
+        return int(v.value)
+
+    def set_graphs(self, on: bool):
+        """Replay the transfer passes as a CUDA graph (default) or not."""
+        _check(load().apic_set_graphs(self._h, 1 if on else 0))
+
+
+def variants() -> list[str]:
+    """Descriptions of the transfer-kernel variants, by index."""
+    lib = load()
+    return [lib.apic_variant_name(i).decode() for i in range(lib.apic_variant_count())]
 
 
 def _is_torch(a):
@@ -302,11 +340,7 @@ class BatchScene:
         self.v_out, self.C_out = v_out, C_out
 
 
-def contact_step_batched(ctx: Context, scenes, n_iter: int, flags: int = 0, stream=None, stats: bool = False):
-    """apic_contact_step_batched over a list of BatchScene (all device or all
-    host arrays, one precision).  Returns the per-scene stats (or None); the
-    results are in each scene's v_out / C_out."""
-    lib = load()
+def _batch_args(scenes, n_iter, flags, stream):
     ns = len(scenes)
     dev = _is_torch(scenes[0].x)
     if dev:
@@ -332,8 +366,16 @@ def contact_step_batched(ctx: Context, scenes, n_iter: int, flags: int = 0, stre
         arr[i] = StepArgs(int(sc.x.shape[0]), int(sc.n_bodies), int(n_iter), _ptr(sc.body), _ptr(sc.x), _ptr(sc.v),
                           _ptr(sc.C), _ptr(sc.m), _ptr(sc.nrm), _ptr(sc.v_out), _ptr(sc.C_out), sc.h, sc.mu,
                           None if mp is None else mp.ctypes.data, int(flags))
+    return arr, ns, sptr, keep
+
+
+def contact_step_batched(ctx: Context, scenes, n_iter: int, flags: int = 0, stream=None, stats: bool = False):
+    """apic_contact_step_batched over a list of BatchScene (all device or all
+    host arrays, one precision).  Returns the per-scene stats (or None); the
+    results are in each scene's v_out / C_out."""
+    arr, ns, sptr, _keep = _batch_args(scenes, n_iter, flags, stream)
     st = (Stats * ns)() if stats else None
-    _check(lib.apic_contact_step_batched(ctx.handle, arr, ns, sptr, st if stats else None))
+    _check(load().apic_contact_step_batched(ctx.handle, arr, ns, sptr, st if stats else None))
     return [st[i].as_dict() for i in range(ns)] if stats else None
 
 

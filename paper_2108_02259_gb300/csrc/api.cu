@@ -1,7 +1,9 @@
 // C ABI of libapiccontact: contexts, validation, grow-only scratch,
 // profiling, and the single-scene and batched contact steps (both run the
 // pipeline of pipeline.cuh).
+#include <algorithm>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -48,6 +50,31 @@ struct apic_ctx {
   };
   std::vector<SpanRec> spans;
   apic_profile prof{};
+  // autotuner: per size class (FP32, bit length of the particle count), the
+  // best time of the series region seen for each kernel variant
+  struct TuneClass {
+    float best_ms[kNumVariants];
+    int samples[kNumVariants] = {};
+    int chosen = -1;
+    TuneClass() {
+      for (float& b : best_ms) b = 1e30f;
+    }
+  };
+  std::map<int, TuneClass> tune;
+  int forced_variant = -1;  // >= 0: fixed by the caller
+  int tune_reps = 2;        // timed runs of each variant before choosing
+  cudaEvent_t tune_a = nullptr, tune_b = nullptr;
+  int pending_class = -1, pending_variant = -1;  // a timed run not yet read back
+  int cur_class = -1, cur_variant = 0;
+  bool cur_measure = false;
+  // CUDA graph of the series region (memsets, mass pass, N + 1 passes)
+  bool graphs_on = true;
+  std::vector<char> gkey;  // the region's key at the last call
+  bool gkey_captured = false;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int64_t graph_kernels = 0;
+  int64_t graph_replays = 0;
 };
 
 namespace {
@@ -115,6 +142,37 @@ apic_status harvest(apic_ctx* c) {
   return APIC_OK;
 }
 
+int tune_class(int64_t n) {
+  int b = 0;
+  while (b < 62 && (int64_t(1) << b) <= n) ++b;
+  return b;  // bit length of n
+}
+
+// Read back the last timed run (if it has finished) into its size class.
+void collect_tuning(apic_ctx* c) {
+  if (c->pending_class < 0) return;
+  const cudaError_t q = cudaEventQuery(c->tune_b);
+  if (q == cudaSuccess) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->tune_a, c->tune_b) == cudaSuccess) {
+      apic_ctx::TuneClass& tc = c->tune[c->pending_class];
+      const int v = c->pending_variant;
+      tc.best_ms[v] = std::min(tc.best_ms[v], ms);
+      tc.samples[v] += 1;
+      bool all = true;
+      for (int i = 0; i < kNumVariants; ++i) all = all && tc.samples[i] >= c->tune_reps;
+      if (all && tc.chosen < 0) {
+        int best = 0;
+        for (int i = 1; i < kNumVariants; ++i)
+          if (tc.best_ms[i] < tc.best_ms[best]) best = i;
+        tc.chosen = best;
+      }
+    }
+  }
+  cudaGetLastError();  // a run still in flight is dropped, not an error
+  c->pending_class = -1;
+}
+
 // The pipeline's environment backed by a context: grow-only scratch per
 // slot, a page-table box cache across steps, CUDA-event spans.
 struct CtxEnv {
@@ -156,6 +214,96 @@ struct CtxEnv {
   void done(int64_t n, int64_t nodes) {
     c->prof.particles = n;
     c->prof.active_nodes = nodes;
+  }
+
+  // Kernel variant for this call: the caller's fixed choice, the size
+  // class's tuned choice, or (while the class is being tuned) the variant
+  // with the fewest timed runs, whose series region is then timed.
+  int variant(size_t tsize, int64_t n) {
+    collect_tuning(c);
+    c->cur_measure = false;
+    if (c->forced_variant >= 0) return c->forced_variant;
+    if (tsize != 4) return 0;  // one FP64 variant
+    const int k = tune_class(n);
+    apic_ctx::TuneClass& tc = c->tune[k];
+    if (tc.chosen >= 0) return tc.chosen;
+    int v = 0;
+    for (int i = 1; i < kNumVariants; ++i)
+      if (tc.samples[i] < tc.samples[v]) v = i;
+    c->cur_class = k;
+    c->cur_variant = v;
+    c->cur_measure = c->tune_a != nullptr;
+    return v;
+  }
+
+  // Run the series region: directly the first time a key is seen (and
+  // whenever graphs are off or profiling needs per-pass events), captured
+  // as a CUDA graph the second consecutive time, replayed after that.
+  template <class F>
+  apic_status run_series(const void* key, size_t kb, cudaStream_t s, F& body) {
+    const bool measure = c->cur_measure;
+    if (measure) P_CUDA(cudaEventRecord(c->tune_a, s));
+    P_TRY(series(key, kb, s, body));
+    if (measure) {
+      P_CUDA(cudaEventRecord(c->tune_b, s));
+      c->pending_class = c->cur_class;
+      c->pending_variant = c->cur_variant;
+    }
+    return APIC_OK;
+  }
+
+  template <class F>
+  apic_status series(const void* key, size_t kb, cudaStream_t s, F& body) {
+    if (!c->graphs_on || c->prof_on) return body(s);
+    const char* kp = static_cast<const char*>(key);
+    const bool same = c->gkey.size() == kb && std::memcmp(c->gkey.data(), kp, kb) == 0;
+    if (same && c->gkey_captured) {
+      P_CUDA(cudaGraphLaunch(c->gexec, s));
+      c->prof.kernel_launches += c->graph_kernels;
+      c->graph_replays += 1;
+      return APIC_OK;
+    }
+    if (!same) {
+      c->gkey.assign(kp, kp + kb);
+      c->gkey_captured = false;
+      return body(s);
+    }
+    if (!c->cap_stream) P_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    const int64_t k0 = c->prof.kernel_launches;
+    P_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const apic_status st = body(c->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    c->graph_kernels = c->prof.kernel_launches - k0;
+    c->prof.kernel_launches = k0;
+    if (st != APIC_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      c->gkey.clear();
+      if (st != APIC_OK) return st;
+      return pfail(APIC_ERR_CUDA, "graph capture of the transfer passes: %s", cudaGetErrorString(e));
+    }
+    if (c->gexec) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(c->gexec, g, &info) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+      }
+    }
+    if (!c->gexec) {
+      const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+      if (ei != cudaSuccess) {
+        cudaGraphDestroy(g);
+        c->gexec = nullptr;
+        c->gkey.clear();
+        return pfail(APIC_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+      }
+    }
+    cudaGraphDestroy(g);
+    c->gkey_captured = true;
+    P_CUDA(cudaGraphLaunch(c->gexec, s));
+    c->prof.kernel_launches += c->graph_kernels;
+    return APIC_OK;
   }
 
   struct Span {
@@ -219,6 +367,8 @@ apic_status apic_create(apic_ctx** out, int32_t device, size_t hbm_budget_bytes)
   cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMalloc(&c->ds, sizeof(DevScalars));
   if (e == cudaSuccess) e = cudaMallocHost(&c->hs, sizeof(DevScalars));
+  if (e == cudaSuccess) e = cudaEventCreate(&c->tune_a);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->tune_b);
   if (e != cudaSuccess) {
     apic_destroy(c);
     return pfail(APIC_ERR_CUDA, "apic_create: %s", cudaGetErrorString(e));
@@ -234,6 +384,10 @@ apic_status apic_destroy(apic_ctx* c) {
   if (c->ds) cudaFree(c->ds);
   if (c->hs) cudaFreeHost(c->hs);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
+  if (c->tune_a) cudaEventDestroy(c->tune_a);
+  if (c->tune_b) cudaEventDestroy(c->tune_b);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return APIC_OK;
 }
@@ -275,6 +429,68 @@ apic_status apic_get_profile(apic_ctx* c, apic_profile* out) {
   if (!c || !out) return pfail(APIC_ERR_INVALID_ARG, "NULL argument");
   P_TRY(harvest(c));
   *out = c->prof;
+  return APIC_OK;
+}
+
+int32_t apic_variant_count(void) { return kNumVariants; }
+
+const char* apic_variant_name(int32_t v) {
+  static const char* names[kNumVariants] = {
+      "128 threads/CTA, 8 CTAs/SM (64 registers)",
+      "128 threads/CTA, 9 CTAs/SM (56 registers)",
+      "128 threads/CTA, 7 CTAs/SM (72 registers)",
+  };
+  return v >= 0 && v < kNumVariants ? names[v] : "";
+}
+
+apic_status apic_set_variant(apic_ctx* c, int32_t v) {
+  if (!c) return pfail(APIC_ERR_INVALID_ARG, "ctx is NULL");
+  if (v < -1 || v >= kNumVariants) return pfail(APIC_ERR_INVALID_ARG, "variant %d not in [-1, %d)", v, kNumVariants);
+  c->forced_variant = v;
+  return APIC_OK;
+}
+
+apic_status apic_get_variant(apic_ctx* c, int64_t n_particles, int32_t* variant, int32_t* decided) {
+  if (!c || !variant || !decided) return pfail(APIC_ERR_INVALID_ARG, "NULL argument");
+  collect_tuning(c);
+  if (c->forced_variant >= 0) {
+    *variant = c->forced_variant;
+    *decided = 1;
+    return APIC_OK;
+  }
+  auto it = c->tune.find(tune_class(n_particles));
+  const bool ok = it != c->tune.end() && it->second.chosen >= 0;
+  *variant = ok ? it->second.chosen : 0;
+  *decided = ok ? 1 : 0;
+  return APIC_OK;
+}
+
+apic_status apic_autotune(apic_ctx* c, const apic_step_args* scenes, int32_t n_scenes, void* stream,
+                          int32_t* variant) {
+  if (!c) return pfail(APIC_ERR_INVALID_ARG, "ctx is NULL");
+  if (c->forced_variant >= 0)
+    return pfail(APIC_ERR_INVALID_ARG, "the variant is fixed (apic_set_variant); set -1 to tune");
+  int64_t n = 0;
+  for (int i = 0; scenes && i < n_scenes; ++i) n += scenes[i].n;
+  const int rounds = kNumVariants * c->tune_reps + 1;
+  int32_t v = 0, decided = 0;
+  for (int r = 0; r < rounds; ++r) {
+    P_TRY(apic_get_variant(c, n, &v, &decided));
+    if (decided) break;
+    P_TRY(apic_contact_step_batched(c, scenes, n_scenes, stream, nullptr));
+    P_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  }
+  P_TRY(apic_get_variant(c, n, &v, &decided));
+  if (!decided) return pfail(APIC_ERR_CUDA, "autotuning did not finish (timings unavailable)");
+  if (variant) *variant = v;
+  return APIC_OK;
+}
+
+apic_status apic_set_graphs(apic_ctx* c, int32_t on) {
+  if (!c) return pfail(APIC_ERR_INVALID_ARG, "ctx is NULL");
+  c->graphs_on = on != 0;
+  c->gkey.clear();
+  c->gkey_captured = false;
   return APIC_OK;
 }
 

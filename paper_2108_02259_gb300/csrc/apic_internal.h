@@ -134,8 +134,14 @@ cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* li
 template <class K>
 cudaError_t launch_mark_items(const int* item_start, const int4* item_info, const int* n_items, const K* keys,
                               int64_t n, int max_items, const SceneDev* sc, int* flags, cudaStream_t s);
+// Variants of the fused transfer kernel: resident CTAs per SM it is
+// compiled for (its register cap: 8 -> 64, 9 -> 56, 7 -> 72 registers).
+// Variant 0 is the default; the FP32 path exists in all of them, the FP64
+// path in variant 0 only (other variants fall back to it).
+constexpr int kNumVariants = 3;
+constexpr int kVariantMinBlocks[kNumVariants] = {8, 9, 7};
 template <class T>
-cudaError_t launch_items(const IterParams<T>& p, int mode, cudaStream_t s);
+cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, cudaStream_t s);
 // all64: take every node's momentum from the FP64 accumulators (after kModeMassV).
 template <class T>
 cudaError_t launch_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask, V4<T>* gp,

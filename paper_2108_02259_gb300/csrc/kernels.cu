@@ -18,11 +18,6 @@
 
 #include "apic_internal.h"
 
-// Resident CTAs per SM the fused kernel is compiled for (register cap).
-#ifndef APIC_ITEMS_MIN_BLOCKS
-#define APIC_ITEMS_MIN_BLOCKS 8
-#endif
-
 namespace apic {
 namespace {
 
@@ -272,8 +267,11 @@ struct RowAcc<float, K> {
 //
 // The shared P2G tile is then added to the global grid (FP64 at nodes that
 // two or more bodies touch, on the FP32 path).
-template <class T, int MODE>
-__global__ void __launch_bounds__(kChunk, APIC_ITEMS_MIN_BLOCKS) k_items(const IterParams<T> p) {
+//
+// MINB is the number of resident CTAs per SM the kernel is compiled for
+// (its register cap); the autotuner picks among kVariantMinBlocks.
+template <class T, int MODE, int MINB>
+__global__ void __launch_bounds__(kChunk, MINB) k_items(const IterParams<T> p) {
   constexpr bool kG2P = MODE == kModeFirst || MODE == kModeMid || MODE == kModeLast || MODE == kModeOnly;
   constexpr bool kP2G = MODE == kModeMass || MODE == kModeP2GV || MODE == kModeMassV || MODE == kModeFirst ||
                         MODE == kModeMid;
@@ -958,22 +956,34 @@ cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* li
   return cudaGetLastError();
 }
 
-template <class T>
-cudaError_t launch_items(const IterParams<T>& p, int mode, cudaStream_t s) {
-  if (p.n_items <= 0) return cudaSuccess;
+template <class T, int MINB>
+cudaError_t launch_items_minb(const IterParams<T>& p, int mode, cudaStream_t s) {
   const unsigned grid = (unsigned)p.n_items;
   switch (mode) {
-    case kModeMass: k_items<T, kModeMass><<<grid, kChunk, 0, s>>>(p); break;
-    case kModeP2GV: k_items<T, kModeP2GV><<<grid, kChunk, 0, s>>>(p); break;
-    case kModeFirst: k_items<T, kModeFirst><<<grid, kChunk, 0, s>>>(p); break;
-    case kModeMid: k_items<T, kModeMid><<<grid, kChunk, 0, s>>>(p); break;
-    case kModeLast: k_items<T, kModeLast><<<grid, kChunk, 0, s>>>(p); break;
-    case kModeOnly: k_items<T, kModeOnly><<<grid, kChunk, 0, s>>>(p); break;
-    case kModeMu: k_items<T, kModeMu><<<grid, kChunk, 0, s>>>(p); break;
-    case kModeMassV: k_items<T, kModeMassV><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeMass: k_items<T, kModeMass, MINB><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeP2GV: k_items<T, kModeP2GV, MINB><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeFirst: k_items<T, kModeFirst, MINB><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeMid: k_items<T, kModeMid, MINB><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeLast: k_items<T, kModeLast, MINB><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeOnly: k_items<T, kModeOnly, MINB><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeMu: k_items<T, kModeMu, MINB><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeMassV: k_items<T, kModeMassV, MINB><<<grid, kChunk, 0, s>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, cudaStream_t s) {
+  if (p.n_items <= 0) return cudaSuccess;
+  if (variant < 0 || variant >= kNumVariants) return cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == 4) {
+    // the FP32 path is built in every variant
+    if (variant == 1) return launch_items_minb<T, kVariantMinBlocks[1]>(p, mode, s);
+    if (variant == 2) return launch_items_minb<T, kVariantMinBlocks[2]>(p, mode, s);
+  }
+  // the FP64 path (parity and small scenes) only in variant 0
+  return launch_items_minb<T, kVariantMinBlocks[0]>(p, mode, s);
 }
 
 template <class T>
@@ -1015,7 +1025,7 @@ cudaError_t launch_scene_counts(int n_blocks, const int* blist, const uint32_t* 
   template cudaError_t launch_cells<T>(int64_t, const SceneDev*, int, int4*, int*, int*, cudaStream_t); \
   template cudaError_t launch_gather<T>(int64_t, const SceneDev*, int, const int*, const int4*, V4<T>*,  \
                                         V4<T>*, V4<T>*, cudaStream_t);                                  \
-  template cudaError_t launch_items<T>(const IterParams<T>&, int, cudaStream_t);                        \
+  template cudaError_t launch_items<T>(const IterParams<T>&, int, int, cudaStream_t);                   \
   template cudaError_t launch_normalize<T>(int64_t, const T*, const uint32_t*, V4<T>*, V4<double>*,     \
                                            V4<T>*, int, cudaStream_t);                                  \
   template cudaError_t launch_momentum<T>(int64_t, const double*, const T*, const T*, const T*, double, \

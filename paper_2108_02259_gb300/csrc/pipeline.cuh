@@ -386,16 +386,9 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   P_TRY(env.take(kSlotGmask, n_nodes, &gmask, "grid body mask"));
   P_TRY(env.take(kSlotGp, n_nodes, &gp, "grid momentum"));
   P_TRY(env.take(kSlotGv, n_nodes, &gv, "grid velocity"));
-  P_CUDA(cudaMemsetAsync(gm, 0, n_nodes * sizeof(T), s));
-  P_CUDA(cudaMemsetAsync(gmask, 0, n_nodes * sizeof(uint32_t), s));
-  P_CUDA(cudaMemsetAsync(gp, 0, n_nodes * sizeof(V4<T>), s));
-  if (sizeof(T) == 4) {
-    P_TRY(env.take(kSlotGp64, n_nodes, &gp64, "FP64 node momentum"));
-    P_CUDA(cudaMemsetAsync(gp64, 0, n_nodes * sizeof(V4<double>), s));
-  }
+  if (sizeof(T) == 4) P_TRY(env.take(kSlotGp64, n_nodes, &gp64, "FP64 node momentum"));
   if (any_mu) {
     P_TRY(env.take(kSlotGmb, (size_t)max_bodies * n_nodes, &gmb, "per-body grid mass"));
-    P_CUDA(cudaMemsetAsync(gmb, 0, (size_t)max_bodies * n_nodes * sizeof(T), s));
     P_TRY(env.take(kSlotMuTable, (size_t)n_mu, &mu_table, "friction tables"));
     P_TRY(env.take(kSlotMup, n, &mup, "particle friction"));
     T* hmu = static_cast<T*>(env.host_buf((size_t)n_mu * sizeof(T)));
@@ -407,7 +400,17 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     P_CUDA(cudaMemcpyAsync(mu_table, hmu, (size_t)n_mu * sizeof(T), cudaMemcpyHostToDevice, s));
   }
 
-  IterParams<T> p{};
+  // The launch sequence from here to the end of the series depends only on
+  // these values, so an environment may capture it once as a CUDA graph and
+  // replay it while they stay the same.
+  struct PassKey {
+    IterParams<T> p;
+    T* mup;
+    int n_iter, any_mu, variant, pad;
+  };
+  PassKey key;
+  std::memset(&key, 0, sizeof(key));  // padding bytes take part in the comparison
+  IterParams<T>& p = key.p;
   p.n_items = n_items;
   p.n_particles = (int)n;
   p.max_bodies = max_bodies;
@@ -433,24 +436,40 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   p.perm = perm;
   p.pic = (flags & APIC_VARIANT_PIC) ? 1 : 0;
   p.sep23 = (flags & APIC_VARIANT_SEP23) ? 1 : 0;
+  key.mup = mup;
+  key.n_iter = N;
+  key.any_mu = any_mu ? 1 : 0;
+  key.variant = env.variant(sizeof(T), n);
 
-  P_LAUNCH(env, launch_items<T>(p, kModeMassV, s));
-  if (any_mu) {
-    P_LAUNCH(env, launch_items<T>(p, kModeMu, s));
-    p.mup = mup;
-  }
-  P_LAUNCH(env, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 1, s));
-  span_prep.stop();
-
-  // 8. the N + 1 transfer passes.
-  for (int pass = 0; pass <= N; ++pass) {
-    const int mode = N == 0 ? kModeOnly : pass == 0 ? kModeFirst : pass == N ? kModeLast : kModeMid;
-    {
-      typename Env::Span span_pass(env, s, 2);
-      P_LAUNCH(env, launch_items<T>(p, mode, s));
+  auto series = [&](cudaStream_t q) -> apic_status {
+    IterParams<T> pp = key.p;
+    const int var = key.variant;
+    P_CUDA(cudaMemsetAsync(gm, 0, n_nodes * sizeof(T), q));
+    P_CUDA(cudaMemsetAsync(gmask, 0, n_nodes * sizeof(uint32_t), q));
+    P_CUDA(cudaMemsetAsync(gp, 0, n_nodes * sizeof(V4<T>), q));
+    if (gp64) P_CUDA(cudaMemsetAsync(gp64, 0, n_nodes * sizeof(V4<double>), q));
+    if (gmb) P_CUDA(cudaMemsetAsync(gmb, 0, (size_t)max_bodies * n_nodes * sizeof(T), q));
+    P_LAUNCH(env, launch_items<T>(pp, kModeMassV, var, q));
+    if (any_mu) {
+      P_LAUNCH(env, launch_items<T>(pp, kModeMu, var, q));
+      pp.mup = mup;
     }
-    if (pass < N) P_LAUNCH(env, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 0, s));
-  }
+    P_LAUNCH(env, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 1, q));
+    span_prep.stop();
+
+    // 8. the N + 1 transfer passes.
+    for (int pass = 0; pass <= N; ++pass) {
+      const int mode = N == 0 ? kModeOnly : pass == 0 ? kModeFirst : pass == N ? kModeLast : kModeMid;
+      {
+        typename Env::Span span_pass(env, q, 2);
+        P_LAUNCH(env, launch_items<T>(pp, mode, var, q));
+      }
+      if (pass < N) P_LAUNCH(env, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 0, q));
+    }
+    return APIC_OK;
+  };
+  P_TRY(env.run_series(&key, sizeof(key), s, series));
+  span_prep.stop();
   span_step.stop();
 
   if (stats) {

@@ -94,6 +94,12 @@ struct StaticEnv {
   void launched() {}
   void sorted() {}
   void done(int64_t, int64_t) {}
+  // default kernel variant, launched directly (no graph, no tuning state)
+  int variant(size_t, int64_t) { return 0; }
+  template <class F>
+  apic_status run_series(const void*, size_t, cudaStream_t s, F& body) {
+    return body(s);
+  }
   struct Span {
     Span(StaticEnv&, cudaStream_t, int) {}
     void stop() {}
