@@ -21,9 +21,10 @@ Workloads (seeded, synthetic, shaped like the paper's bodies):
                 requests at 0.5 / 0.8 / 0.95 of the measured batched capacity;
                 reports throughput and p50/p99 request latency (value: load 0.8)
 
-Multi-GPU (torchrun): every rank steps its own copy of the scene (the scenes
-are independent; no collective on the data path); value = all ranks'
-particle-iterations / the slowest rank's time.
+Multi-GPU (torchrun): every rank steps its own scene(s) of the workload's shape
+and size, drawn from seed + 1000 * rank (independent problems: no collective
+on the data path, only a barrier and a max-reduction of the time); value =
+all ranks' particle-iterations / the slowest rank's time (weak scaling).
 """
 from __future__ import annotations
 
@@ -45,26 +46,46 @@ UNIT = "particle-iters/s"
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 
-def make_scene(name):
+RANK_SEED_STRIDE = 1000  # rank r draws its scenes from the workload's seed + 1000 r
+
+
+def make_scene(name, rank=0):
     from paper_2108_02259_gb300 import scenes
 
+    off = RANK_SEED_STRIDE * rank
     if name == "four_bodies":
-        return scenes.four_bodies(), np.float32
-    if name == "two_cubes":
+        return scenes.four_bodies(seed=scenes.SEED_BASE + 2 + off), np.float32
+    if name == "two_cubes":  # no random draw: every rank steps the same two cubes
         return scenes.two_cubes(mu=0.3, n_iter=10), np.float64
     if name == "eight_bodies":
-        return scenes.eight_bodies(), np.float32
+        return scenes.eight_bodies(seed=scenes.SEED_BASE + 3 + off), np.float32
     raise SystemExit(f"unknown workload {name}")
 
 
-def make_workload(name):
-    """(list of scenes, dtype, batched)."""
+def make_workload(name, rank=0):
+    """(list of scenes, dtype, batched) of one rank.  Ranks step independent
+    scenes of the same shape and size (seeds differ), so per-rank work is
+    fixed as ranks are added (weak scaling) and no data crosses ranks."""
     from paper_2108_02259_gb300 import scenes
 
     if name == "batched64":
-        return scenes.batch_of_scenes(64), np.float32, True
-    s, dt = make_scene(name)
+        return scenes.batch_of_scenes(64, seed=scenes.SEED_BASE + 4 + RANK_SEED_STRIDE * rank), np.float32, True
+    s, dt = make_scene(name, rank)
     return [s], dt, False
+
+
+def max_over_ranks(x: float, ws: int, device="cpu") -> float:
+    """The largest x over all ranks (the slowest rank's time); x itself at
+    one rank.  `device` is where the process group's backend reduces (a
+    CUDA device for NCCL, the CPU for gloo)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def workload_config(name, sc, dt):
@@ -284,7 +305,7 @@ def main():
     from paper_2108_02259_gb300 import apic, build
 
     build.build()
-    sc, dt, batched = make_workload(args.workload)
+    sc, dt, batched = make_workload(args.workload, rank)
     tdt = torch.float32 if dt == np.float32 else torch.float64
     N = sc[0].n_iter
     P = sum(s.n for s in sc)
@@ -355,10 +376,7 @@ def main():
     timed(step, max(2, min(args.steps, 5)))
     prof = ctx.profile()
     ctx.set_profiling(False)
-    if ws > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(t_ms, ws, dev)
     units = P * (N + 1) * args.steps * ws
     value = units / (t_ms / 1e3)
 
@@ -419,10 +437,7 @@ def main():
             host_step()
         torch.cuda.synchronize(dev)
         el = time.perf_counter() - t0
-        if ws > 1:
-            tt = torch.tensor([el], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            el = float(tt.item())
+        el = max_over_ranks(el, ws, dev)
         isz = np.dtype(dt).itemsize
         e2e = {"value": units / el, "unit": UNIT,
                "h2d_bytes_per_step": int(P * (24 + 4 + isz * (3 + 9 + 1 + 3))),
