@@ -117,12 +117,15 @@ typedef struct {
   int64_t steps;
   int64_t iter_launches;   /* launches of the fused transfer kernel           */
   double iter_ms;          /* their summed durations                           */
-  double prep_ms;          /* keys, sort, gather, grid activation              */
+  double prep_ms;          /* keys, sort, gather, grid activation, up to the
+                              host's read of the grid size                     */
   double step_ms;          /* whole steps                                      */
   int64_t particles;       /* particles of the last step                      */
   int64_t active_nodes;    /* grid nodes of the last step                     */
   int64_t kernel_launches; /* launches of this library's own kernels          */
   int64_t sort_launches;   /* device sort / scan primitive calls (CUB)        */
+  double mass_ms;          /* mass + P2G(V) pass, friction blend, normalise    */
+  int64_t graph_launches;  /* CUDA graph launches (sizing and series regions) */
 } apic_profile;
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -76,7 +76,8 @@ class Profile(C.Structure):
     _fields_ = [
         ("steps", C.c_int64), ("iter_launches", C.c_int64), ("iter_ms", C.c_double), ("prep_ms", C.c_double),
         ("step_ms", C.c_double), ("particles", C.c_int64), ("active_nodes", C.c_int64),
-        ("kernel_launches", C.c_int64), ("sort_launches", C.c_int64),
+        ("kernel_launches", C.c_int64), ("sort_launches", C.c_int64), ("mass_ms", C.c_double),
+        ("graph_launches", C.c_int64),
     ]
 
 

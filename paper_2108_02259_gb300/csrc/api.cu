@@ -37,7 +37,8 @@ struct apic_ctx {
   std::vector<Box> boxes;
   int box_ns = -1;
   bool have_box = false;
-  std::vector<SceneDev> h_scenes;
+  SceneDev* h_scenes = nullptr;  // pinned (a graph's copy node reads it)
+  int h_scenes_cap = 0;
   std::vector<int> h_bbox;
   std::vector<char> h_buf;
   // profiling
@@ -46,7 +47,7 @@ struct apic_ctx {
   size_t ev_used = 0;
   struct SpanRec {
     cudaEvent_t a, b;
-    int kind;  // 0 step, 1 prep, 2 transfer pass
+    int kind;  // 0 step, 1 prep, 2 transfer pass, 3 mass pass
   };
   std::vector<SpanRec> spans;
   apic_profile prof{};
@@ -67,14 +68,19 @@ struct apic_ctx {
   int pending_class = -1, pending_variant = -1;  // a timed run not yet read back
   int cur_class = -1, cur_variant = 0;
   bool cur_measure = false;
-  // CUDA graph of the series region (memsets, mass pass, N + 1 passes)
+  // CUDA graphs of the grid-sizing sequence and of the series region
+  // (memsets, mass pass, N + 1 passes)
+  struct GraphSlot {
+    std::vector<char> key;  // the region's key at the last call (+ alloc_gen)
+    bool captured = false;
+    bool failed = false;  // capture failed once: launch directly from then on
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0, sorts = 0;  // launches inside the graph
+  };
   bool graphs_on = true;
-  std::vector<char> gkey;  // the region's key at the last call
-  bool gkey_captured = false;
-  cudaGraphExec_t gexec = nullptr;
+  GraphSlot gsizing, gseries;
   cudaStream_t cap_stream = nullptr;
-  int64_t graph_kernels = 0;
-  int64_t graph_replays = 0;
+  uint64_t alloc_gen = 0;  // bumped whenever a scratch buffer moves
 };
 
 namespace {
@@ -95,6 +101,7 @@ apic_status grow(apic_ctx* c, Buf& b, size_t bytes) {
     b.ptr = nullptr;
     b.bytes = 0;
   }
+  c->alloc_gen += 1;
   cudaError_t e = cudaMalloc(&b.ptr, want);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -132,6 +139,8 @@ apic_status harvest(apic_ctx* c) {
       c->prof.steps += 1;
     } else if (sp.kind == 1) {
       c->prof.prep_ms += ms;
+    } else if (sp.kind == 3) {
+      c->prof.mass_ms += ms;
     } else {
       c->prof.iter_ms += ms;
       c->prof.iter_launches += 1;
@@ -187,8 +196,19 @@ struct CtxEnv {
   DevScalars* ds() { return c->ds; }
   DevScalars* hs() { return c->hs; }
   SceneDev* host_scenes(int ns) {
-    c->h_scenes.assign(ns, SceneDev{});
-    return c->h_scenes.data();
+    if (ns > c->h_scenes_cap) {
+      if (c->h_scenes) cudaFreeHost(c->h_scenes);
+      c->h_scenes = nullptr;
+      c->h_scenes_cap = 0;
+      if (cudaMallocHost(&c->h_scenes, ns * sizeof(SceneDev)) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_scenes = nullptr;
+        return nullptr;
+      }
+      c->h_scenes_cap = ns;
+    }
+    for (int i = 0; i < ns; ++i) c->h_scenes[i] = SceneDev{};
+    return c->h_scenes;
   }
   int* host_bbox(int ns) {
     c->h_bbox.resize(6 * (size_t)ns);
@@ -236,14 +256,20 @@ struct CtxEnv {
     return v;
   }
 
-  // Run the series region: directly the first time a key is seen (and
-  // whenever graphs are off or profiling needs per-pass events), captured
-  // as a CUDA graph the second consecutive time, replayed after that.
+  // The sizing sequence, as a graph when `allowed` (device pointers) and the
+  // same sizes and buffers come back.
+  template <class F>
+  apic_status run_sizing(const void* key, size_t kb, bool allowed, cudaStream_t s, F& body) {
+    if (!allowed) return body(s);
+    return graph_run(c->gsizing, key, kb, s, body);
+  }
+
+  // The series region (timed for the autotuner while its class is tuned).
   template <class F>
   apic_status run_series(const void* key, size_t kb, cudaStream_t s, F& body) {
     const bool measure = c->cur_measure;
     if (measure) P_CUDA(cudaEventRecord(c->tune_a, s));
-    P_TRY(series(key, kb, s, body));
+    P_TRY(graph_run(c->gseries, key, kb, s, body));
     if (measure) {
       P_CUDA(cudaEventRecord(c->tune_b, s));
       c->pending_class = c->cur_class;
@@ -252,57 +278,74 @@ struct CtxEnv {
     return APIC_OK;
   }
 
+  // Run a launch sequence: directly the first time its key is seen (and
+  // whenever graphs are off, or profiling needs per-pass events), captured
+  // as a CUDA graph the second consecutive time, replayed after that.  The
+  // key is the caller's bytes plus the context's allocation generation, so
+  // a buffer that moved forces a fresh capture.
   template <class F>
-  apic_status series(const void* key, size_t kb, cudaStream_t s, F& body) {
-    if (!c->graphs_on || c->prof_on) return body(s);
-    const char* kp = static_cast<const char*>(key);
-    const bool same = c->gkey.size() == kb && std::memcmp(c->gkey.data(), kp, kb) == 0;
-    if (same && c->gkey_captured) {
-      P_CUDA(cudaGraphLaunch(c->gexec, s));
-      c->prof.kernel_launches += c->graph_kernels;
-      c->graph_replays += 1;
+  apic_status graph_run(apic_ctx::GraphSlot& g, const void* key, size_t kb, cudaStream_t s, F& body) {
+    if (!c->graphs_on || c->prof_on || g.failed) return body(s);
+    std::vector<char> k(static_cast<const char*>(key), static_cast<const char*>(key) + kb);
+    const char* gp = reinterpret_cast<const char*>(&c->alloc_gen);
+    k.insert(k.end(), gp, gp + sizeof(c->alloc_gen));
+    const bool same = g.key == k;
+    if (same && g.captured) {
+      P_CUDA(cudaGraphLaunch(g.exec, s));
+      c->prof.kernel_launches += g.kernels;
+      c->prof.sort_launches += g.sorts;
+      c->prof.graph_launches += 1;
       return APIC_OK;
     }
     if (!same) {
-      c->gkey.assign(kp, kp + kb);
-      c->gkey_captured = false;
+      g.key = std::move(k);
+      g.captured = false;
       return body(s);
     }
     if (!c->cap_stream) P_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-    const int64_t k0 = c->prof.kernel_launches;
+    const int64_t k0 = c->prof.kernel_launches, s0 = c->prof.sort_launches;
+    const uint64_t gen0 = c->alloc_gen;
     P_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     const apic_status st = body(c->cap_stream);
-    cudaGraph_t g = nullptr;
-    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
-    c->graph_kernels = c->prof.kernel_launches - k0;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    g.kernels = c->prof.kernel_launches - k0;
+    g.sorts = c->prof.sort_launches - s0;
     c->prof.kernel_launches = k0;
-    if (st != APIC_OK || e != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      c->gkey.clear();
-      if (st != APIC_OK) return st;
-      return pfail(APIC_ERR_CUDA, "graph capture of the transfer passes: %s", cudaGetErrorString(e));
+    c->prof.sort_launches = s0;
+    if (st != APIC_OK || e != cudaSuccess || c->alloc_gen != gen0) {
+      // Nothing ran while capturing.  Whatever went wrong (a buffer that had
+      // to grow, a call capture does not allow), run the sequence directly:
+      // a real error shows up there and is returned.
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      g.key.clear();
+      g.failed = st != APIC_OK || e != cudaSuccess;
+      return body(s);
     }
-    if (c->gexec) {
+    if (g.exec) {
       cudaGraphExecUpdateResultInfo info;
-      if (cudaGraphExecUpdate(c->gexec, g, &info) != cudaSuccess) {
+      if (cudaGraphExecUpdate(g.exec, graph, &info) != cudaSuccess) {
         cudaGetLastError();
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
       }
     }
-    if (!c->gexec) {
-      const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+    if (!g.exec) {
+      const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
       if (ei != cudaSuccess) {
-        cudaGraphDestroy(g);
-        c->gexec = nullptr;
-        c->gkey.clear();
+        cudaGraphDestroy(graph);
+        g.exec = nullptr;
+        g.key.clear();
         return pfail(APIC_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
       }
     }
-    cudaGraphDestroy(g);
-    c->gkey_captured = true;
-    P_CUDA(cudaGraphLaunch(c->gexec, s));
-    c->prof.kernel_launches += c->graph_kernels;
+    cudaGraphDestroy(graph);
+    g.captured = true;
+    P_CUDA(cudaGraphLaunch(g.exec, s));
+    c->prof.graph_launches += 1;
+    c->prof.kernel_launches += g.kernels;
+    c->prof.sort_launches += g.sorts;
     return APIC_OK;
   }
 
@@ -386,7 +429,9 @@ apic_status apic_destroy(apic_ctx* c) {
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   if (c->tune_a) cudaEventDestroy(c->tune_a);
   if (c->tune_b) cudaEventDestroy(c->tune_b);
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->gsizing.exec) cudaGraphExecDestroy(c->gsizing.exec);
+  if (c->gseries.exec) cudaGraphExecDestroy(c->gseries.exec);
+  if (c->h_scenes) cudaFreeHost(c->h_scenes);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return APIC_OK;
@@ -489,8 +534,11 @@ apic_status apic_autotune(apic_ctx* c, const apic_step_args* scenes, int32_t n_s
 apic_status apic_set_graphs(apic_ctx* c, int32_t on) {
   if (!c) return pfail(APIC_ERR_INVALID_ARG, "ctx is NULL");
   c->graphs_on = on != 0;
-  c->gkey.clear();
-  c->gkey_captured = false;
+  for (apic_ctx::GraphSlot* g : {&c->gsizing, &c->gseries}) {
+    g->key.clear();
+    g->captured = false;
+    g->failed = false;
+  }
   return APIC_OK;
 }
 

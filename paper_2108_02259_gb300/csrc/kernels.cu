@@ -170,6 +170,62 @@ __device__ __forceinline__ void g2p_tile(const V4<T>* sv, int base, const T wx[4
   }
 }
 
+// The FP32 form of g2p_tile with paired FMAs: per node, (ax_x, ax_y) and
+// (adx_x, adx_y) take (v_x, v_y) times (N, N) and (N d, N d), and
+// (ax_z, adx_z) takes (v_z, v_z) times (N, N d) -- three paired FMAs where
+// g2p_tile issues six.  Needs node velocities stored as (v_x, v_y, v_z, v_z).
+__device__ __forceinline__ void g2p_tile_f32(const V4<float>* sv, int base, const float wx[4], const float dx[4],
+                                             const float wy[4], const float dy[4], const float wz[4],
+                                             const float dz[4], float hv[3], float hC[9]) {
+  float2 wxx[4], wdd[4], wxd[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float wd = wx[k] * dx[k];
+    wxx[k] = make_float2(wx[k], wx[k]);
+    wdd[k] = make_float2(wd, wd);
+    wxd[k] = make_float2(wx[k], wd);
+  }
+  float2 s0 = make_float2(0.f, 0.f), sx = s0, sy = s0, sz = s0;
+  float s0z = 0.f, sxz = 0.f, syz = 0.f, szz = 0.f;
+#pragma unroll
+  for (int kz = 0; kz < 4; ++kz) {
+#pragma unroll
+    for (int ky = 0; ky < 4; ++ky) {
+      float2 a01 = make_float2(0.f, 0.f), d01 = a01, az = a01;
+#pragma unroll
+      for (int kx = 0; kx < 4; ++kx) {
+        const V4<float> g = sv[base + kz * (kTile * kTile) + ky * kTile + kx];
+        const float2 gxy = make_float2(g.x, g.y), gzz = make_float2(g.z, g.w);
+        a01 = __ffma2_rn(gxy, wxx[kx], a01);
+        d01 = __ffma2_rn(gxy, wdd[kx], d01);
+        az = __ffma2_rn(gzz, wxd[kx], az);
+      }
+      const float wyz = wy[ky] * wz[kz];
+      const float wyzdy = wyz * dy[ky], wyzdz = wyz * dz[kz];
+      s0 = __ffma2_rn(a01, make_float2(wyz, wyz), s0);
+      sx = __ffma2_rn(d01, make_float2(wyz, wyz), sx);
+      sy = __ffma2_rn(a01, make_float2(wyzdy, wyzdy), sy);
+      sz = __ffma2_rn(a01, make_float2(wyzdz, wyzdz), sz);
+      s0z += wyz * az.x;
+      sxz += wyz * az.y;
+      syz += wyzdy * az.x;
+      szz += wyzdz * az.x;
+    }
+  }
+  hv[0] = s0.x;
+  hv[1] = s0.y;
+  hv[2] = s0z;
+  hC[0] = 2.f * sx.x;
+  hC[1] = 2.f * sy.x;
+  hC[2] = 2.f * sz.x;
+  hC[3] = 2.f * sx.y;
+  hC[4] = 2.f * sy.y;
+  hC[5] = 2.f * sz.y;
+  hC[6] = 2.f * sxz;
+  hC[7] = 2.f * syz;
+  hC[8] = 2.f * szz;
+}
+
 // Quadratic B-spline weight of one node row k (0..3, i.e. node i-1+k) as a
 // polynomial in t, N_k(t) = c0 + c1 t + c2 t^2 (the App. B functions expanded).
 template <class T>
@@ -401,6 +457,8 @@ __global__ void __launch_bounds__(kChunk, MINB) k_items(const IterParams<T> p) {
       T hv[3], hC[9];
       if (p.pic)
         g2p_tile<T, false>(sv, base, wx, dx, wy, dy, wz, dz, hv, hC);
+      else if constexpr (sizeof(T) == 4)
+        g2p_tile_f32(sv, base, wx, dx, wy, dy, wz, dz, hv, hC);
       else
         g2p_tile<T, true>(sv, base, wx, dx, wy, dy, wz, dz, hv, hC);
       const T nrm[3] = {pn.x, pn.y, pn.z};
@@ -554,6 +612,8 @@ __global__ void __launch_bounds__(kChunk, MINB) k_items(const IterParams<T> p) {
 }
 
 // v_i = p_i / m_i (0 where m_i = 0), then clear p_i for the next pass.
+// The node velocity is stored as (v_x, v_y, v_z, v_z): the repeated v_z lets
+// G2P pair it with (N, N d) in one paired FMA.
 // Nodes that two or more bodies touch take their momentum from the FP64
 // accumulators (FP32 path).
 template <class T>
@@ -567,12 +627,13 @@ __global__ void k_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask,
     const V4<double> q = gp64[i];
     if (m > T(0)) {
       const double md = (double)m;
-      v = V4<T>{(T)(q.x / md), (T)(q.y / md), (T)(q.z / md), T(0)};
+      const T vz = (T)(q.z / md);
+      v = V4<T>{(T)(q.x / md), (T)(q.y / md), vz, vz};
     }
     gp64[i] = V4<double>{0.0, 0.0, 0.0, 0.0};
   } else {
     const V4<T> q = gp[i];
-    if (m > T(0)) v = V4<T>{q.x / m, q.y / m, q.z / m, T(0)};
+    if (m > T(0)) v = V4<T>{q.x / m, q.y / m, q.z / m, q.z / m};
   }
   gp[i] = V4<T>{T(0), T(0), T(0), T(0)};
   gv[i] = v;

@@ -20,6 +20,7 @@
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -112,34 +113,74 @@ inline apic_status validate_scene(const apic_step_args* a, int idx, uint32_t all
   return APIC_OK;
 }
 
-template <class Env, class K>
-apic_status sort_keys(Env& env, int64_t n, const SceneDev* sc, int ns, const int4* cellb, int max_bodies,
-                      int end_bit, int* err, int** perm_out, const void** keys_out, cudaStream_t s) {
+// Scratch of steps 3-6 for n particles and NB page-table entries.  Every
+// buffer and every CUB temporary size is fixed here, before any of those
+// steps is enqueued, so that the enqueue sequence itself allocates nothing
+// and assigns nothing (it may be captured once and replayed as a graph).
+struct SizingBufs {
+  int end_bit = 0;
+  bool k64 = false;
+  void *ka = nullptr, *kb = nullptr;  // keys, sorted keys (uint32_t or uint64_t)
+  int *va = nullptr, *perm = nullptr; // sort values, sorted permutation
+  char* tmp = nullptr;                 // CUB temporaries (max of the three uses)
+  size_t tmp_sort = 0, tmp_scan_n = 0, tmp_scan_nb = 0;
+  int *heads = nullptr, *offs = nullptr, *item_start = nullptr;
+  int4* item_info = nullptr;
+  int *bflags = nullptr, *boffs = nullptr, *blist = nullptr, *page = nullptr;
+};
+
+template <class K, class Env>
+apic_status plan_keys(Env& env, int64_t n, SizingBufs& b) {
   K *ka, *kb;
-  int *va, *vb;
   P_TRY(env.take(kSlotKeysA, n, &ka, "sort keys"));
   P_TRY(env.take(kSlotKeysB, n, &kb, "sorted keys"));
-  P_TRY(env.take(kSlotVals, n, &va, "sort values"));
-  P_TRY(env.take(kSlotPerm, n, &vb, "permutation"));
-  P_LAUNCH(env, launch_keys<K>(n, sc, ns, cellb, max_bodies, ka, va, err, s));
-  size_t tmp = 0;
-  P_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, ka, kb, va, vb, (int)n, 0, end_bit, s));
-  char* t = nullptr;
-  P_TRY(env.take(kSlotCubTmp, tmp, &t, "sort temporaries"));
-  P_CUDA(cub::DeviceRadixSort::SortPairs(t, tmp, ka, kb, va, vb, (int)n, 0, end_bit, s));
-  env.sorted();
-  *perm_out = vb;
-  *keys_out = kb;
+  P_TRY(env.take(kSlotVals, n, &b.va, "sort values"));
+  P_TRY(env.take(kSlotPerm, n, &b.perm, "permutation"));
+  P_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, b.tmp_sort, ka, kb, b.va, b.perm, (int)n, 0, b.end_bit));
+  b.ka = ka;
+  b.kb = kb;
   return APIC_OK;
 }
 
 template <class Env>
-apic_status exclusive_sum(Env& env, const int* in, int* out, int64_t n, cudaStream_t s) {
-  size_t tmp = 0;
-  P_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, in, out, n, s));
-  char* t = nullptr;
-  P_TRY(env.take(kSlotCubTmp, tmp, &t, "scan temporaries"));
-  P_CUDA(cub::DeviceScan::ExclusiveSum(t, tmp, in, out, n, s));
+apic_status plan_sizing(Env& env, int64_t n, int64_t NB, int max_bodies, SizingBufs& b) {
+  b.end_bit = bits_for((uint64_t)NB * (uint64_t)max_bodies - 1) + 6;
+  b.k64 = b.end_bit > 32;
+  if (b.k64)
+    P_TRY(plan_keys<uint64_t>(env, n, b));
+  else
+    P_TRY(plan_keys<uint32_t>(env, n, b));
+  P_TRY(env.take(kSlotHeads, n, &b.heads, "item heads"));
+  P_TRY(env.take(kSlotOffs, n, &b.offs, "item offsets"));
+  P_TRY(env.take(kSlotItemStart, n, &b.item_start, "item starts"));
+  P_TRY(env.take(kSlotItemInfo, n, &b.item_info, "item info"));
+  P_TRY(env.take(kSlotBFlags, NB, &b.bflags, "block flags"));
+  P_TRY(env.take(kSlotBOffs, NB, &b.boffs, "block offsets"));
+  P_TRY(env.take(kSlotBList, NB, &b.blist, "block list"));
+  P_TRY(env.take(kSlotPage, NB, &b.page, "page table"));
+  P_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, b.tmp_scan_n, b.heads, b.offs, n));
+  P_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, b.tmp_scan_nb, b.bflags, b.boffs, NB));
+  const size_t t = std::max(b.tmp_sort, std::max(b.tmp_scan_n, b.tmp_scan_nb));
+  P_TRY(env.take(kSlotCubTmp, t, &b.tmp, "sort and scan temporaries"));
+  return APIC_OK;
+}
+
+template <class K, class Env>
+apic_status sort_keys(Env& env, int64_t n, const SceneDev* sc, int ns, const int4* cellb, int max_bodies,
+                      int* err, const SizingBufs& b, cudaStream_t s) {
+  K* ka = static_cast<K*>(b.ka);
+  K* kb = static_cast<K*>(b.kb);
+  P_LAUNCH(env, launch_keys<K>(n, sc, ns, cellb, max_bodies, ka, b.va, err, s));
+  size_t tmp = b.tmp_sort;
+  P_CUDA(cub::DeviceRadixSort::SortPairs(b.tmp, tmp, ka, kb, b.va, b.perm, (int)n, 0, b.end_bit, s));
+  env.sorted();
+  return APIC_OK;
+}
+
+template <class Env>
+apic_status exclusive_sum(Env& env, const SizingBufs& b, size_t tmp, const int* in, int* out, int64_t n,
+                          cudaStream_t s) {
+  P_CUDA(cub::DeviceScan::ExclusiveSum(b.tmp, tmp, in, out, n, s));
   env.sorted();
   return APIC_OK;
 }
@@ -237,42 +278,93 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   Box* boxes = env.box_cache(ns);  // persistent per-scene boxes (or scratch)
 
   int64_t NB = 0;
-  int* perm = nullptr;
-  const void* keys = nullptr;
-  bool k64 = false;
   V4<T> *pt, *pn, *V, *D;
-  int *heads, *offs, *item_start;
-  int4* item_info;
-  int* page = nullptr;
-  int* blist = nullptr;
+  // 3-6 as one launch sequence (cells first when the box is reused): keys,
+  // one radix sort over all scenes, sorted SoA, work items, active blocks
+  // and the page table, then the device counters back to the host.  Only
+  // enqueues work: every buffer comes from plan_sizing.
+  SizingBufs sb;
+  auto sizing = [&](cudaStream_t q, bool with_cells) -> apic_status {
+    if (with_cells) {
+      P_CUDA(cudaMemcpyAsync(ds, hs, sizeof(DevScalars), cudaMemcpyHostToDevice, q));
+      P_CUDA(cudaMemcpyAsync(sc, hsc, ns * sizeof(SceneDev), cudaMemcpyHostToDevice, q));
+      P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, sbbox, &ds->err, q));
+    }
+    // 3. keys and one radix sort over all scenes.
+    if (sb.k64)
+      P_TRY((sort_keys<uint64_t>(env, n, sc, ns, cellb, max_bodies, &ds->err, sb, q)));
+    else
+      P_TRY((sort_keys<uint32_t>(env, n, sc, ns, cellb, max_bodies, &ds->err, sb, q)));
+    // 4. sorted SoA.
+    P_LAUNCH(env, launch_gather<T>(n, sc, ns, sb.perm, cellb, pt, pn, V, q));
+    // 5. work items: runs of equal (grid block, body), at most kChunk long.
+    if (sb.k64)
+      P_LAUNCH(env, launch_heads<uint64_t>(n, static_cast<const uint64_t*>(sb.kb), sb.heads, q));
+    else
+      P_LAUNCH(env, launch_heads<uint32_t>(n, static_cast<const uint32_t*>(sb.kb), sb.heads, q));
+    P_TRY(exclusive_sum(env, sb, sb.tmp_scan_n, sb.heads, sb.offs, n, q));
+    P_LAUNCH(env, launch_compact(n, sb.heads, sb.offs, sb.item_start, nullptr, &ds->n_items, q));
+    if (sb.k64)
+      P_LAUNCH(env, launch_item_info<uint64_t>(sb.item_start, &ds->n_items, static_cast<const uint64_t*>(sb.kb),
+                                               max_bodies, sc, ns, sb.item_info, (int)n, q));
+    else
+      P_LAUNCH(env, launch_item_info<uint32_t>(sb.item_start, &ds->n_items, static_cast<const uint32_t*>(sb.kb),
+                                               max_bodies, sc, ns, sb.item_info, (int)n, q));
+    // 6. active grid blocks: every block some stencil reaches; page table.
+    P_CUDA(cudaMemsetAsync(sb.bflags, 0, NB * sizeof(int), q));
+    if (sb.k64)
+      P_LAUNCH(env, launch_mark_items<uint64_t>(sb.item_start, sb.item_info, &ds->n_items,
+                                                static_cast<const uint64_t*>(sb.kb), n, (int)n, sc, sb.bflags, q));
+    else
+      P_LAUNCH(env, launch_mark_items<uint32_t>(sb.item_start, sb.item_info, &ds->n_items,
+                                                static_cast<const uint32_t*>(sb.kb), n, (int)n, sc, sb.bflags, q));
+    P_TRY(exclusive_sum(env, sb, sb.tmp_scan_nb, sb.bflags, sb.boffs, NB, q));
+    P_LAUNCH(env, launch_compact(NB, sb.bflags, sb.boffs, sb.blist, sb.page, &ds->n_blocks, q));
+    P_CUDA(cudaMemcpyAsync(hs, ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, q));
+    return APIC_OK;
+  };
+  P_TRY(env.take(kSlotPt, n, &pt, "particle offsets"));
+  P_TRY(env.take(kSlotPn, n, &pn, "particle normals"));
+  P_TRY(env.take(kSlotV, 3 * n, &V, "sorted V"));
+  P_TRY(env.take(kSlotD, 3 * n, &D, "Delta"));
+
   for (int attempt = 0;; ++attempt) {
     // 1. cells, validation, bounding boxes of particle blocks.
     const bool fresh = !env.have_box() || attempt > 0;
-    if (fresh) {
+    *hs = DevScalars{};
+    if (!fresh) {
+      // boxes reused from the previous step: the whole sequence depends only
+      // on the sizes below (and the buffers), so it may run as a graph
+      NB = 0;
+      for (int i = 0; i < ns; ++i) {
+        hsc[i].box = boxes[i];
+        hsc[i].page_off = NB;
+        NB += (int64_t)hsc[i].box.nx * hsc[i].box.ny * hsc[i].box.nz;
+      }
+      struct SizingKey {
+        int64_t n, NB;
+        int ns, max_bodies, tsize, host;
+      } key;
+      std::memset(&key, 0, sizeof(key));
+      key.n = n;
+      key.NB = NB;
+      key.ns = ns;
+      key.max_bodies = max_bodies;
+      key.tsize = (int)sizeof(T);
+      key.host = host ? 1 : 0;
+      P_TRY(plan_sizing(env, n, NB, max_bodies, sb));
+      auto body = [&](cudaStream_t q) -> apic_status { return sizing(q, true); };
+      P_TRY(env.run_sizing(&key, sizeof(key), !host, s, body));
+    } else {
       for (int i = 0; i < ns; ++i) {
         int* b = hbbox + 6 * i;
         b[0] = b[1] = b[2] = INT32_MAX;
         b[3] = b[4] = b[5] = INT32_MIN;
       }
       P_CUDA(cudaMemcpyAsync(sbbox, hbbox, 6 * ns * sizeof(int), cudaMemcpyHostToDevice, s));
-    } else {
-      // boxes reused from the previous step: the table already holds them
-      for (int i = 0; i < ns; ++i) {
-        hsc[i].box = boxes[i];
-      }
-    }
-    *hs = DevScalars{};
-    P_CUDA(cudaMemcpyAsync(ds, hs, sizeof(DevScalars), cudaMemcpyHostToDevice, s));
-    if (!fresh) {
-      NB = 0;
-      for (int i = 0; i < ns; ++i) {
-        hsc[i].page_off = NB;
-        NB += (int64_t)hsc[i].box.nx * hsc[i].box.ny * hsc[i].box.nz;
-      }
-    }
-    P_CUDA(cudaMemcpyAsync(sc, hsc, ns * sizeof(SceneDev), cudaMemcpyHostToDevice, s));
-    P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, sbbox, &ds->err, s));
-    if (fresh) {
+      P_CUDA(cudaMemcpyAsync(ds, hs, sizeof(DevScalars), cudaMemcpyHostToDevice, s));
+      P_CUDA(cudaMemcpyAsync(sc, hsc, ns * sizeof(SceneDev), cudaMemcpyHostToDevice, s));
+      P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, sbbox, &ds->err, s));
       // 2. page-table boxes: one block of stencil margin plus kBoxSlack
       //    blocks of room for motion in later steps; laid end to end.
       P_CUDA(cudaMemcpyAsync(hbbox, sbbox, 6 * ns * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -305,56 +397,10 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       }
       env.keep_box();
       P_CUDA(cudaMemcpyAsync(sc, hsc, ns * sizeof(SceneDev), cudaMemcpyHostToDevice, s));
+      P_TRY(plan_sizing(env, n, NB, max_bodies, sb));
+      P_TRY(sizing(s, false));
     }
-    // 3. keys and one radix sort over all scenes.
-    const int end_bit = bits_for((uint64_t)NB * (uint64_t)max_bodies - 1) + 6;
-    k64 = end_bit > 32;
-    if (k64)
-      P_TRY((sort_keys<Env, uint64_t>(env, n, sc, ns, cellb, max_bodies, end_bit, &ds->err, &perm, &keys, s)));
-    else
-      P_TRY((sort_keys<Env, uint32_t>(env, n, sc, ns, cellb, max_bodies, end_bit, &ds->err, &perm, &keys, s)));
-
-    // 4. sorted SoA.
-    P_TRY(env.take(kSlotPt, n, &pt, "particle offsets"));
-    P_TRY(env.take(kSlotPn, n, &pn, "particle normals"));
-    P_TRY(env.take(kSlotV, 3 * n, &V, "sorted V"));
-    P_TRY(env.take(kSlotD, 3 * n, &D, "Delta"));
-    P_LAUNCH(env, launch_gather<T>(n, sc, ns, perm, cellb, pt, pn, V, s));
-
-    // 5. work items: runs of equal (grid block, body), at most kChunk long.
-    P_TRY(env.take(kSlotHeads, n, &heads, "item heads"));
-    P_TRY(env.take(kSlotOffs, n, &offs, "item offsets"));
-    P_TRY(env.take(kSlotItemStart, n, &item_start, "item starts"));
-    P_TRY(env.take(kSlotItemInfo, n, &item_info, "item info"));
-    if (k64)
-      P_LAUNCH(env, launch_heads<uint64_t>(n, static_cast<const uint64_t*>(keys), heads, s));
-    else
-      P_LAUNCH(env, launch_heads<uint32_t>(n, static_cast<const uint32_t*>(keys), heads, s));
-    P_TRY(exclusive_sum(env, heads, offs, n, s));
-    P_LAUNCH(env, launch_compact(n, heads, offs, item_start, nullptr, &ds->n_items, s));
-    if (k64)
-      P_LAUNCH(env, launch_item_info<uint64_t>(item_start, &ds->n_items, static_cast<const uint64_t*>(keys),
-                                               max_bodies, sc, ns, item_info, (int)n, s));
-    else
-      P_LAUNCH(env, launch_item_info<uint32_t>(item_start, &ds->n_items, static_cast<const uint32_t*>(keys),
-                                               max_bodies, sc, ns, item_info, (int)n, s));
-
-    // 6. active grid blocks: every block some stencil reaches; page table.
-    int *bflags, *boffs;
-    P_TRY(env.take(kSlotBFlags, NB, &bflags, "block flags"));
-    P_TRY(env.take(kSlotBOffs, NB, &boffs, "block offsets"));
-    P_TRY(env.take(kSlotBList, NB, &blist, "block list"));
-    P_TRY(env.take(kSlotPage, NB, &page, "page table"));
-    P_CUDA(cudaMemsetAsync(bflags, 0, NB * sizeof(int), s));
-    if (k64)
-      P_LAUNCH(env, launch_mark_items<uint64_t>(item_start, item_info, &ds->n_items,
-                                                static_cast<const uint64_t*>(keys), n, (int)n, sc, bflags, s));
-    else
-      P_LAUNCH(env, launch_mark_items<uint32_t>(item_start, item_info, &ds->n_items,
-                                                static_cast<const uint32_t*>(keys), n, (int)n, sc, bflags, s));
-    P_TRY(exclusive_sum(env, bflags, boffs, NB, s));
-    P_LAUNCH(env, launch_compact(NB, bflags, boffs, blist, page, &ds->n_blocks, s));
-    P_CUDA(cudaMemcpyAsync(hs, ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    span_prep.stop();
     P_CUDA(cudaStreamSynchronize(s));
     if ((hs->err & kErrBox) && !(hs->err & ~kErrBox) && attempt == 0) {
       env.forget_box();  // a particle left a reused box: size fresh ones
@@ -362,6 +408,11 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     }
     break;
   }
+  const int* perm = sb.perm;
+  const int* item_start = sb.item_start;
+  const int4* item_info = sb.item_info;
+  const int* page = sb.page;
+  const int* blist = sb.blist;
   if (hs->err) {
     const int e = hs->err;
     env.forget_box();
@@ -444,6 +495,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   auto series = [&](cudaStream_t q) -> apic_status {
     IterParams<T> pp = key.p;
     const int var = key.variant;
+    typename Env::Span span_mass(env, q, 3);
     P_CUDA(cudaMemsetAsync(gm, 0, n_nodes * sizeof(T), q));
     P_CUDA(cudaMemsetAsync(gmask, 0, n_nodes * sizeof(uint32_t), q));
     P_CUDA(cudaMemsetAsync(gp, 0, n_nodes * sizeof(V4<T>), q));
@@ -455,7 +507,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       pp.mup = mup;
     }
     P_LAUNCH(env, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 1, q));
-    span_prep.stop();
+    span_mass.stop();
 
     // 8. the N + 1 transfer passes.
     for (int pass = 0; pass <= N; ++pass) {
@@ -469,7 +521,6 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     return APIC_OK;
   };
   P_TRY(env.run_series(&key, sizeof(key), s, series));
-  span_prep.stop();
   span_step.stop();
 
   if (stats) {

@@ -114,6 +114,13 @@ def test_graph_replay_matches_direct_launches(apic):
             _close(sk, rg.v.cpu().double().numpy(), rg.C.cpu().double().numpy(), rd.v.cpu().double().numpy(),
                    rd.C.cpu().double().numpy(), f"call {k}")
         assert float(rg.v.abs().max()) > 0
+        # graphs ran on g (sizing and series, replayed), none on d; both
+        # contexts count the same kernel launches
+        pg, pd = g.profile(), d.profile()
+        assert pg["graph_launches"] >= 4
+        assert pd["graph_launches"] == 0
+        assert pg["kernel_launches"] == pd["kernel_launches"]
+        assert pg["sort_launches"] == pd["sort_launches"]
 
 
 def test_autotune_settles_and_keeps_parity(apic):
