@@ -220,6 +220,11 @@ typedef struct {
 apic_status apic_server_create(apic_server** out, int32_t device, size_t hbm_budget_bytes, int32_t n_workers,
                                int32_t max_batch_scenes);
 
+/* Launch policy of the workers' contexts for the batches they start from now
+ * on: `variant` as apic_set_variant (-1: tune per size class, the default),
+ * `graphs` as apic_set_graphs (1, the default).  Not in the paper. */
+apic_status apic_server_set_policy(apic_server* srv, int32_t variant, int32_t graphs);
+
 /* Finish queued requests, stop the workers, free every simulation. */
 apic_status apic_server_destroy(apic_server* srv);
 

@@ -38,7 +38,7 @@ EXPORTED = [
     "apic_contact_step_batched", "apic_server_create", "apic_server_destroy", "apic_sim_open", "apic_sim_submit",
     "apic_ticket_poll", "apic_ticket_wait", "apic_sim_read", "apic_sim_close", "apic_server_get_stats",
     "apic_variant_count", "apic_variant_name", "apic_set_variant", "apic_get_variant", "apic_autotune",
-    "apic_set_graphs",
+    "apic_set_graphs", "apic_server_set_policy",
 ]
 
 
@@ -131,6 +131,8 @@ def load(path: str = LIB_PATH):
     lib.apic_get_variant.argtypes = [P, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.apic_autotune.argtypes = [P, C.POINTER(StepArgs), C.c_int32, P, C.POINTER(C.c_int32)]
     lib.apic_set_graphs.argtypes = [P, C.c_int32]
+    lib.apic_server_set_policy.argtypes = [P, C.c_int32, C.c_int32]
+    lib.apic_server_set_policy.restype = C.c_int32
     for f in ("apic_create", "apic_destroy", "apic_contact_step", "apic_set_profiling", "apic_get_profile",
               "apic_scratch_bytes", "apic_set_variant", "apic_get_variant", "apic_autotune", "apic_set_graphs"):
         getattr(lib, f).restype = C.c_int32
@@ -425,6 +427,10 @@ class Server:
         lat = C.c_double()
         _check(load().apic_ticket_wait(self._h, int(ticket), float(timeout_s), C.byref(lat)))
         return lat.value
+
+    def set_policy(self, variant: int = -1, graphs: bool = True):
+        """Launch policy of the worker contexts (see apic_server_set_policy)."""
+        _check(load().apic_server_set_policy(self._h, int(variant), 1 if graphs else 0))
 
     def stats(self, reset: bool = False) -> dict:
         st = ServerStats()

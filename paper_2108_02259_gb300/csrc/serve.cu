@@ -79,6 +79,8 @@ struct apic_server {
   std::vector<std::thread> workers;
   std::vector<size_t> worker_scratch;
   bool stop = false;
+  int variant = -1;  // launch policy of the workers' contexts
+  int graphs = 1;
   size_t resident = 0;
   int64_t open = 0;
   std::unordered_set<apic_sim*> sims;  // open simulations
@@ -103,8 +105,10 @@ void worker_main(apic_server* srv, int wid) {
                   cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess;
   std::vector<uint64_t> batch;
   std::vector<apic_step_args> args;
+  int variant = -1, graphs = 1;  // the context's current policy
   for (;;) {
     batch.clear();
+    int want_variant, want_graphs;
     {
       std::unique_lock<std::mutex> lk(srv->mu);
       auto runnable = [&] {
@@ -114,6 +118,8 @@ void worker_main(apic_server* srv, int wid) {
       };
       srv->cv_work.wait(lk, [&] { return srv->stop || runnable(); });
       if (srv->stop && !runnable()) break;
+      want_variant = srv->variant;
+      want_graphs = srv->graphs;
       // Budget left for this batch's scratch beyond what the workers hold.
       size_t room = SIZE_MAX;
       if (srv->budget) {
@@ -145,6 +151,14 @@ void worker_main(apic_server* srv, int wid) {
       }
     }
     if (batch.empty()) continue;
+    if (ctx && want_variant != variant) {
+      apic_set_variant(ctx, want_variant);
+      variant = want_variant;
+    }
+    if (ctx && want_graphs != graphs) {
+      apic_set_graphs(ctx, want_graphs);
+      graphs = want_graphs;
+    }
     args.assign(batch.size(), apic_step_args{});
     double dts[1024];
     {
@@ -251,6 +265,16 @@ apic_status apic_server_create(apic_server** out, int32_t device, size_t hbm_bud
   srv->worker_scratch.assign(n_workers, 0);
   for (int w = 0; w < n_workers; ++w) srv->workers.emplace_back(worker_main, srv, w);
   *out = srv;
+  return APIC_OK;
+}
+
+apic_status apic_server_set_policy(apic_server* srv, int32_t variant, int32_t graphs) {
+  if (!srv) return sfail(APIC_ERR_INVALID_ARG, "server is NULL");
+  if (variant < -1 || variant >= apic_variant_count())
+    return sfail(APIC_ERR_INVALID_ARG, "variant out of range (-1 tunes per size class)");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  srv->variant = variant;
+  srv->graphs = graphs != 0;
   return APIC_OK;
 }
 
