@@ -16,4 +16,5 @@ from .oracle import (  # noqa: F401
     momentum,
     contact_step,
     apic1d_linear,
+    node_normals,
 )

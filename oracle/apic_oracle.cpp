@@ -20,6 +20,7 @@
 //   * undesirable part (Coulomb friction) ..... Sec. 2.4 (default) or the
 //                                              Sec. 2.3 separation rule (flag)
 //   * 1-D two-particle linear-hat transfers ... Sec. 3.1
+//   * node normals from boundary faces ....... Sec. 2.3 (area-weighted)
 //
 // The public C ABI takes C_p = B_p D_p^{-1} (the APIC affine matrix) because
 // that is what callers carry; internally B_p = C_p D_p with D_p computed from
@@ -33,6 +34,9 @@
 //   oracle_undesirable ............ pinned (closed-form cone cases)
 //   oracle_contact_step ........... pinned (momentum, affine, symmetry)
 //   oracle_apic1d_linear .......... pinned (closed-form matrix of Sec. 3.1)
+//   oracle_node_normals ........... pinned (closed-form cube, roof and
+//                                    plane cases, icosahedron symmetry,
+//                                    winding and rotation)
 //   per-body-pair friction (mu_pair) ... parity unpinned (a reading; the paper
 //                                    has a single scalar mu)
 #include <algorithm>
@@ -498,6 +502,38 @@ int oracle_apic1d_linear(int64_t n, const double* x, const double* v, const doub
     }
     vout[p] = vh;
     Bout[p] = bh;
+  }
+  return 0;
+}
+
+// Node normals (Sec. 2.3, where the normal n_p of each particle is built):
+// the outward normals of the boundary faces adjacent to a node, weighted by
+// face area, summed and normalised.  Faces are triangles (a, b, c) wound
+// counter-clockwise seen from outside, so that (b - a) x (c - a) points
+// outward with length twice the area.  Nodes on no face, or whose weighted
+// sum vanishes, get n = 0.  Returns -1 for an index outside [0, n).
+int oracle_node_normals(int64_t n, const double* x, int64_t n_tri, const int32_t* tri, double* nrm) {
+  if (n < 0 || n_tri < 0) return -1;
+  std::vector<double> acc((size_t)(3 * n), 0.0);
+  for (int64_t f = 0; f < n_tri; ++f) {
+    const int32_t a = tri[3 * f], b = tri[3 * f + 1], c = tri[3 * f + 2];
+    if (a < 0 || b < 0 || c < 0 || a >= n || b >= n || c >= n) return -1;
+    double e1[3], e2[3], an[3];
+    for (int k = 0; k < 3; ++k) {
+      e1[k] = x[3 * b + k] - x[3 * a + k];
+      e2[k] = x[3 * c + k] - x[3 * a + k];
+    }
+    // area times unit outward normal = half the cross product
+    an[0] = 0.5 * (e1[1] * e2[2] - e1[2] * e2[1]);
+    an[1] = 0.5 * (e1[2] * e2[0] - e1[0] * e2[2]);
+    an[2] = 0.5 * (e1[0] * e2[1] - e1[1] * e2[0]);
+    for (int32_t v : {a, b, c})
+      for (int k = 0; k < 3; ++k) acc[(size_t)(3 * v + k)] += an[k];
+  }
+  for (int64_t p = 0; p < n; ++p) {
+    const double* s = &acc[(size_t)(3 * p)];
+    const double len = std::sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    for (int k = 0; k < 3; ++k) nrm[3 * p + k] = len > 0.0 ? s[k] / len : 0.0;
   }
   return 0;
 }

@@ -59,6 +59,8 @@ def _load():
             lib.oracle_contact_step.restype = C.c_int
             lib.oracle_apic1d_linear.argtypes = [i64, P, P, P, P, d, d, P, P]
             lib.oracle_apic1d_linear.restype = C.c_int
+            lib.oracle_node_normals.argtypes = [i64, P, i64, P, P]
+            lib.oracle_node_normals.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -177,3 +179,15 @@ def apic1d_linear(x, v, B, m, h, x0=0.0):
     if lib.oracle_apic1d_linear(x.shape[0], _ptr(x), _ptr(v), _ptr(B), _ptr(m), float(h), float(x0), _ptr(vout), _ptr(Bout)) != 0:
         raise ValueError("oracle_apic1d_linear: invalid arguments")
     return vout, Bout
+
+
+def node_normals(x, tri):
+    """Area-weighted, normalised node normals from boundary triangles
+    (Sec. 2.3); 0 for nodes on no face."""
+    lib = _load()
+    x = _f64(x, (-1, 3))
+    tri = np.ascontiguousarray(np.asarray(tri, np.int32).reshape(-1, 3))
+    out = np.zeros_like(x)
+    if lib.oracle_node_normals(x.shape[0], _ptr(x), tri.shape[0], tri.ctypes.data, _ptr(out)) != 0:
+        raise ValueError("oracle_node_normals: a triangle index is outside [0, n)")
+    return out

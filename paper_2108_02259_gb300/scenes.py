@@ -342,3 +342,90 @@ def served_simulations(n_sims: int = 256, n_shapes: int = 32, seed: int = SEED_B
         sims.append(Scene(s.x + shift, s.v, s.C, s.m, s.nrm, s.body, s.n_bodies, s.h, float(rng.uniform(0, 0.5)),
                           n_iter, None, f"sim{k}_{s.name}"))
     return sims
+
+
+# ----------------------------------------------------------- surface meshes
+# Boundary triangulations for the node-normal construction of Sec. 2.3.
+# Triangles are wound counter-clockwise seen from outside.
+
+def cube_surface_mesh(side: float = 1.0):
+    """Cube [0, side]^3: 8 corners then 6 face centres; each face is four
+    triangles around its centre (so every corner sees each of its three faces
+    through two triangles of equal area)."""
+    c = np.array([[i, j, k] for k in (0, 1) for j in (0, 1) for i in (0, 1)], np.float64) * side
+    faces = [  # corner ids counter-clockwise seen from outside, and the outward axis
+        ([0, 2, 3, 1], (0, 0, -1)), ([4, 5, 7, 6], (0, 0, 1)),
+        ([0, 1, 5, 4], (0, -1, 0)), ([2, 6, 7, 3], (0, 1, 0)),
+        ([0, 4, 6, 2], (-1, 0, 0)), ([1, 3, 7, 5], (1, 0, 0)),
+    ]
+    x = [*c]
+    tri = []
+    for ids, _ in faces:
+        centre = len(x)
+        x.append(c[ids].mean(axis=0))
+        for a in range(4):
+            tri.append([centre, ids[a], ids[(a + 1) % 4]])
+    return np.array(x), np.array(tri, np.int32)
+
+
+def icosphere(level: int = 0, radius: float = 1.0):
+    """Unit icosahedron subdivided `level` times, vertices projected to the
+    sphere; outward winding."""
+    t = (1.0 + 5.0 ** 0.5) / 2.0
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+         (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11),
+         (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    x = [np.array(p, np.float64) / np.linalg.norm(p) for p in v]
+    for _ in range(level):
+        mid = {}
+
+        def midpoint(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in mid:
+                p = x[a] + x[b]
+                x.append(p / np.linalg.norm(p))
+                mid[key] = len(x) - 1
+            return mid[key]
+
+        nf = []
+        for a, b, c in f:
+            ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        f = nf
+    return np.array(x) * radius, np.array(f, np.int32)
+
+
+def box_lattice_surface(nx: int, ny: int, nz: int, spacing: float = 1.0, origin=(0.0, 0.0, 0.0)):
+    """All nodes of an nx x ny x nz lattice (x fastest) and the triangles of
+    its boundary (each boundary quad split in two).  Interior nodes are on
+    no triangle."""
+    ii, jj, kk = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    x = np.stack([ii.T.ravel(), jj.T.ravel(), kk.T.ravel()], 1).astype(np.float64) * spacing + np.asarray(origin)
+
+    def nid(i, j, k):
+        return (k * ny + j) * nx + i
+
+    tri = []
+
+    def quad(a, b, c, d):  # counter-clockwise seen from outside
+        tri.append([a, b, c])
+        tri.append([a, c, d])
+
+    for j in range(ny - 1):
+        for k in range(nz - 1):
+            quad(nid(0, j, k), nid(0, j, k + 1), nid(0, j + 1, k + 1), nid(0, j + 1, k))  # -x
+            i = nx - 1
+            quad(nid(i, j, k), nid(i, j + 1, k), nid(i, j + 1, k + 1), nid(i, j, k + 1))  # +x
+    for i in range(nx - 1):
+        for k in range(nz - 1):
+            quad(nid(i, 0, k), nid(i + 1, 0, k), nid(i + 1, 0, k + 1), nid(i, 0, k + 1))  # -y
+            j = ny - 1
+            quad(nid(i, j, k), nid(i, j, k + 1), nid(i + 1, j, k + 1), nid(i + 1, j, k))  # +y
+    for i in range(nx - 1):
+        for j in range(ny - 1):
+            quad(nid(i, j, 0), nid(i, j + 1, 0), nid(i + 1, j + 1, 0), nid(i + 1, j, 0))  # -z
+            k = nz - 1
+            quad(nid(i, j, k), nid(i + 1, j, k), nid(i + 1, j + 1, k), nid(i, j + 1, k))  # +z
+    return x, np.array(tri, np.int32)
