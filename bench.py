@@ -471,6 +471,7 @@ def main():
                            "work_items": int(sum(x["work_items"] for x in st))},
         "clocks": ck,
     }
+    line["node_normals"] = bench_node_normals(apic, ctx, dev, stream, flush)
     if plain is not None:
         line["plain_single_scene"] = {"value": plain, "unit": UNIT,
                                       "what": "the same scenes, one apic_contact_step call each",
@@ -578,6 +579,39 @@ def run_served(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def bench_node_normals(apic, ctx, dev, stream, flush, reps=10):
+    """apic_node_normals (Sec. 2.3 node normals) on the boundary of a
+    100^3-node lattice block: 1,000,000 nodes, 117,612 triangles.  Device
+    time per call (CUDA events, L2 flushed before each), against the bytes
+    the operation must move: 12 B of ids per triangle; per node 24 B of x,
+    24 B of FP64 sums written and read back, 12 B of normals."""
+    import torch
+
+    from paper_2108_02259_gb300 import scenes
+
+    x, tri = scenes.box_lattice_surface(100, 100, 100, spacing=1 / 512)
+    X = torch.as_tensor(x, device=dev)
+    Tr = torch.as_tensor(tri, device=dev)
+    out = torch.empty((len(x), 3), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        apic.node_normals(ctx, X, Tr, out=out, stream=stream)
+    ms = []
+    for i in range(reps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        apic.node_normals(ctx, X, Tr, out=out, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(a.elapsed_time(b))
+    t = statistics.median(ms)
+    alg = 12 * len(tri) + (24 + 48 + 12) * len(x)
+    peak, kind = measured_peak_hbm()
+    return {"mesh": "boundary of a 100^3-node lattice block", "nodes": len(x), "triangles": len(tri),
+            "ms": t, "triangles_per_s": len(tri) / (t / 1e3), "nodes_per_s": len(x) / (t / 1e3),
+            "algorithmic_bytes": alg, "achieved_gbs": alg / (t / 1e3) / 1e9, "frac_of_hbm_peak": alg / (t / 1e3) / 1e9 / peak}
 
 
 def step_breakdown(prof):

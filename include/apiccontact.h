@@ -266,6 +266,25 @@ apic_status apic_get_profile(apic_ctx* ctx, apic_profile* out);
 /* Bytes of device scratch the context currently holds. */
 apic_status apic_scratch_bytes(apic_ctx* ctx, size_t* out);
 
+/* Node normals n_p for apic_step_args.nrm, built as Sec. 2.3 builds them:
+ * the outward normals of the boundary faces adjacent to each node, weighted
+ * by face area, summed and normalised.
+ *   x    [n*3] node positions (doubles, AoS xyz), the configuration the
+ *        normals are wanted in;
+ *   tri  [n_tri*3] int32 node ids of the boundary triangles, each wound
+ *        counter-clockwise seen from outside (split quads into two); NULL
+ *        when n_tri = 0;
+ *   nrm_out [n*3] unit normals, float (or double with APIC_FP64); 0 for a
+ *        node on no triangle (interior nodes) or on zero-area ones only.
+ * Flags: APIC_FP64, APIC_HOST_PTRS (all three arrays in host memory).  The
+ * sums are FP64 (atomic, so their rounding order varies between calls, far
+ * below FP32 resolution).  Scratch (24 bytes per node, plus staging for host
+ * arrays) comes from the context.  Synchronises `stream` before returning;
+ * APIC_ERR_INVALID_ARG if a triangle index is outside [0, n) (nrm_out is then
+ * unspecified). */
+apic_status apic_node_normals(apic_ctx* ctx, int64_t n, const double* x, int64_t n_tri, const int32_t* tri,
+                              void* nrm_out, uint32_t flags, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Kernel variants, autotuning and CUDA graphs (no counterpart in the paper:
  * they change how the transfer passes are launched, never what they compute).

@@ -38,7 +38,7 @@ EXPORTED = [
     "apic_contact_step_batched", "apic_server_create", "apic_server_destroy", "apic_sim_open", "apic_sim_submit",
     "apic_ticket_poll", "apic_ticket_wait", "apic_sim_read", "apic_sim_close", "apic_server_get_stats",
     "apic_variant_count", "apic_variant_name", "apic_set_variant", "apic_get_variant", "apic_autotune",
-    "apic_set_graphs", "apic_server_set_policy",
+    "apic_set_graphs", "apic_server_set_policy", "apic_node_normals",
 ]
 
 
@@ -132,6 +132,8 @@ def load(path: str = LIB_PATH):
     lib.apic_autotune.argtypes = [P, C.POINTER(StepArgs), C.c_int32, P, C.POINTER(C.c_int32)]
     lib.apic_set_graphs.argtypes = [P, C.c_int32]
     lib.apic_server_set_policy.argtypes = [P, C.c_int32, C.c_int32]
+    lib.apic_node_normals.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_uint32, P]
+    lib.apic_node_normals.restype = C.c_int32
     lib.apic_server_set_policy.restype = C.c_int32
     for f in ("apic_create", "apic_destroy", "apic_contact_step", "apic_set_profiling", "apic_get_profile",
               "apic_scratch_bytes", "apic_set_variant", "apic_get_variant", "apic_autotune", "apic_set_graphs"):
@@ -325,6 +327,35 @@ def contact_step_static(x, v, Cm, m, nrm, body, h: float, mu: float, n_iter: int
     st = Stats() if stats else None
     _check(lib.apic_contact_step_static(C.byref(a), stream.cuda_stream, C.byref(st) if stats else None))
     return StepResult(v_out, C_out, st.as_dict() if stats else None)
+
+
+def node_normals(ctx: Context, x, tri, fp64: bool = False, out=None, stream=None):
+    """apic_node_normals: area-weighted unit normals of the boundary faces
+    around each node (Sec. 2.3).  x [n, 3] float64 and tri [n_tri, 3] int32,
+    both torch CUDA tensors (device path) or both numpy arrays (host path).
+    Returns out [n, 3] (float32, or float64 with fp64)."""
+    lib = load()
+    n = int(x.shape[0])
+    n_tri = int(tri.shape[0])
+    flags = APIC_FP64 if fp64 else 0
+    if _is_torch(x):
+        import torch
+
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float64 if fp64 else torch.float32, device=x.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        sptr = stream.cuda_stream
+    else:
+        flags |= APIC_HOST_PTRS
+        x = np.ascontiguousarray(x, np.float64)
+        tri = np.ascontiguousarray(tri, np.int32)
+        if out is None:
+            out = np.empty((n, 3), np.float64 if fp64 else np.float32)
+        sptr = None if stream is None else stream.cuda_stream
+    _check(lib.apic_node_normals(ctx.handle, n, _ptr(x), n_tri, _ptr(tri) if n_tri else None, _ptr(out), flags,
+                                 sptr))
+    return out
 
 
 class BatchScene:

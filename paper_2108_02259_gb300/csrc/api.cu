@@ -477,6 +477,56 @@ apic_status apic_get_profile(apic_ctx* c, apic_profile* out) {
   return APIC_OK;
 }
 
+apic_status apic_node_normals(apic_ctx* c, int64_t n, const double* x, int64_t n_tri, const int32_t* tri,
+                              void* nrm_out, uint32_t flags, void* stream) {
+  if (!c) return pfail(APIC_ERR_INVALID_ARG, "ctx is NULL");
+  if (n < 0 || n_tri < 0) return pfail(APIC_ERR_INVALID_ARG, "n = %lld, n_tri = %lld must be >= 0", (long long)n,
+                                       (long long)n_tri);
+  if (n > (int64_t)INT32_MAX) return pfail(APIC_ERR_INVALID_ARG, "n = %lld exceeds int32 node ids", (long long)n);
+  if (flags & ~(uint32_t)(APIC_FP64 | APIC_HOST_PTRS))
+    return pfail(APIC_ERR_INVALID_ARG, "flag bits 0x%x not accepted here", flags & ~(uint32_t)(APIC_FP64 | APIC_HOST_PTRS));
+  if (n == 0) {
+    if (n_tri > 0) return pfail(APIC_ERR_INVALID_ARG, "triangles given for n = 0 nodes");
+    return APIC_OK;
+  }
+  if (!x || !nrm_out || (n_tri > 0 && !tri)) return pfail(APIC_ERR_INVALID_ARG, "a required array pointer is NULL");
+  P_CUDA(cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CtxEnv env{c};
+  const bool host = (flags & APIC_HOST_PTRS) != 0;
+  const size_t es = (flags & APIC_FP64) ? sizeof(double) : sizeof(float);
+  double* acc;
+  P_TRY(env.take(kSlotNrmAcc, 3 * n, &acc, "normal sums"));
+  const double* dx = x;
+  const int32_t* dtri = tri;
+  void* dout = nrm_out;
+  if (host) {
+    double* sx;
+    int32_t* st = nullptr;
+    char* so;
+    P_TRY(env.take(kSlotNrmX, 3 * n, &sx, "staged x"));
+    if (n_tri > 0) P_TRY(env.take(kSlotNrmTri, 3 * n_tri, &st, "staged triangles"));
+    P_TRY(env.take(kSlotNrmOut, 3 * n * es, &so, "staged normals"));
+    P_CUDA(cudaMemcpyAsync(sx, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (n_tri > 0) P_CUDA(cudaMemcpyAsync(st, tri, 3 * n_tri * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    dx = sx;
+    dtri = st;
+    dout = so;
+  }
+  P_CUDA(cudaMemsetAsync(c->ds, 0, sizeof(DevScalars), s));
+  P_CUDA(cudaMemsetAsync(acc, 0, 3 * n * sizeof(double), s));
+  P_LAUNCH(env, launch_face_normals(n_tri, dtri, dx, n, acc, &c->ds->err, s));
+  if (flags & APIC_FP64)
+    P_LAUNCH(env, launch_unit_normals<double>(n, acc, static_cast<double*>(dout), s));
+  else
+    P_LAUNCH(env, launch_unit_normals<float>(n, acc, static_cast<float*>(dout), s));
+  if (host) P_CUDA(cudaMemcpyAsync(nrm_out, dout, 3 * n * es, cudaMemcpyDeviceToHost, s));
+  P_CUDA(cudaMemcpyAsync(c->hs, c->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+  P_CUDA(cudaStreamSynchronize(s));
+  if (c->hs->err) return pfail(APIC_ERR_INVALID_ARG, "a triangle index is outside [0, %lld)", (long long)n);
+  return APIC_OK;
+}
+
 int32_t apic_variant_count(void) { return kNumVariants; }
 
 const char* apic_variant_name(int32_t v) {

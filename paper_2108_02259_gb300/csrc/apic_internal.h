@@ -159,6 +159,13 @@ cudaError_t launch_scene_counts(int n_blocks, const int* blist, const uint32_t* 
 template <class T>
 cudaError_t launch_advect(int64_t n, double* x, const T* v, double dt, cudaStream_t s);
 
+// Sec. 2.3 node normals: FP64 area-weighted face-normal sums (acc[3 n],
+// zeroed by the caller; err |= kErrBody for a bad index), then unit normals.
+cudaError_t launch_face_normals(int64_t n_tri, const int32_t* tri, const double* x, int64_t n, double* acc,
+                                int* err, cudaStream_t s);
+template <class T>
+cudaError_t launch_unit_normals(int64_t n, const double* acc, T* out, cudaStream_t s);
+
 // Set the calling thread's message returned by apic_last_error().
 void set_last_error(const char* msg);
 

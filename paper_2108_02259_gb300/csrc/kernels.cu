@@ -1082,6 +1082,64 @@ cudaError_t launch_scene_counts(int n_blocks, const int* blist, const uint32_t* 
   return cudaGetLastError();
 }
 
+// Sec. 2.3 node normals, step 1: per boundary triangle (a, b, c), half the
+// cross product (b - a) x (c - a) -- the face's area times its outward unit
+// normal -- added to each of its nodes in FP64.  A triangle with an index
+// outside [0, n) is skipped and flagged.
+__global__ void k_face_normals(int64_t n_tri, const int32_t* tri, const double* x, int64_t n, double* acc,
+                               int* err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n_tri; f += stride) {
+    const int32_t v[3] = {tri[3 * f], tri[3 * f + 1], tri[3 * f + 2]};
+    if (v[0] < 0 || v[1] < 0 || v[2] < 0 || v[0] >= n || v[1] >= n || v[2] >= n) {
+      atomicOr(err, kErrBody);
+      continue;
+    }
+    double e1[3], e2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double xa = x[3 * (int64_t)v[0] + k];
+      e1[k] = x[3 * (int64_t)v[1] + k] - xa;
+      e2[k] = x[3 * (int64_t)v[2] + k] - xa;
+    }
+    const double an[3] = {0.5 * (e1[1] * e2[2] - e1[2] * e2[1]), 0.5 * (e1[2] * e2[0] - e1[0] * e2[2]),
+                          0.5 * (e1[0] * e2[1] - e1[1] * e2[0])};
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) atomicAdd(&acc[3 * (int64_t)v[c] + k], an[k]);
+  }
+}
+
+// Step 2: n_p = s_p / |s_p|, 0 where the weighted sum vanishes (nodes on no
+// face, or on zero-area faces only).
+template <class T>
+__global__ void k_unit_normals(int64_t n, const double* acc, T* out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double s0 = acc[3 * i], s1 = acc[3 * i + 1], s2 = acc[3 * i + 2];
+  const double len = sqrt(s0 * s0 + s1 * s1 + s2 * s2);
+  const double r = len > 0.0 ? 1.0 / len : 0.0;
+  out[3 * i] = (T)(s0 * r);
+  out[3 * i + 1] = (T)(s1 * r);
+  out[3 * i + 2] = (T)(s2 * r);
+}
+
+cudaError_t launch_face_normals(int64_t n_tri, const int32_t* tri, const double* x, int64_t n, double* acc,
+                                int* err, cudaStream_t s) {
+  if (n_tri <= 0) return cudaSuccess;
+  const unsigned g = (unsigned)std::min<int64_t>(grid_for(n_tri, 256), 152 * 16);
+  k_face_normals<<<g, 256, 0, s>>>(n_tri, tri, x, n, acc, err);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_unit_normals(int64_t n, const double* acc, T* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_unit_normals<T><<<grid_for(n, 256), 256, 0, s>>>(n, acc, out);
+  return cudaGetLastError();
+}
+
 #define APIC_INST_T(T)                                                                                  \
   template cudaError_t launch_cells<T>(int64_t, const SceneDev*, int, int4*, int*, int*, cudaStream_t); \
   template cudaError_t launch_gather<T>(int64_t, const SceneDev*, int, const int*, const int4*, V4<T>*,  \
@@ -1091,7 +1149,8 @@ cudaError_t launch_scene_counts(int n_blocks, const int* blist, const uint32_t* 
                                            V4<T>*, int, cudaStream_t);                                  \
   template cudaError_t launch_momentum<T>(int64_t, const double*, const T*, const T*, const T*, double, \
                                           double*, cudaStream_t);                                       \
-  template cudaError_t launch_advect<T>(int64_t, double*, const T*, double, cudaStream_t);
+  template cudaError_t launch_advect<T>(int64_t, double*, const T*, double, cudaStream_t);                \
+  template cudaError_t launch_unit_normals<T>(int64_t, const double*, T*, cudaStream_t);
 APIC_INST_T(float)
 APIC_INST_T(double)
 
