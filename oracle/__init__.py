@@ -17,4 +17,5 @@ from .oracle import (  # noqa: F401
     contact_step,
     apic1d_linear,
     node_normals,
+    augury_steps,
 )

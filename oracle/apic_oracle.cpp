@@ -21,6 +21,8 @@
 //                                              Sec. 2.3 separation rule (flag)
 //   * 1-D two-particle linear-hat transfers ... Sec. 3.1
 //   * node normals from boundary faces ....... Sec. 2.3 (area-weighted)
+//   * augury dynamics, springs + gravity ...... Sec. 2.2 eq. apic_accel,
+//                                              eq. Newmark (velocity Verlet)
 //
 // The public C ABI takes C_p = B_p D_p^{-1} (the APIC affine matrix) because
 // that is what callers carry; internally B_p = C_p D_p with D_p computed from
@@ -37,6 +39,10 @@
 //   oracle_node_normals ........... pinned (closed-form cube, roof and
 //                                    plane cases, icosahedron symmetry,
 //                                    winding and rotation)
+//   oracle_augury_steps ........... pinned (discrete Verlet closed forms for
+//                                    an isolated spring pair and free fall,
+//                                    rigid translation, momentum, mirror
+//                                    symmetry); rebound threshold unpinned
 //   per-body-pair friction (mu_pair) ... parity unpinned (a reading; the paper
 //                                    has a single scalar mu)
 #include <algorithm>
@@ -534,6 +540,116 @@ int oracle_node_normals(int64_t n, const double* x, int64_t n_tri, const int32_t
     const double* s = &acc[(size_t)(3 * p)];
     const double len = std::sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
     for (int k = 0; k < 3; ++k) nrm[3 * p + k] = len > 0.0 ? s[k] / len : 0.0;
+  }
+  return 0;
+}
+
+// Augury dynamics (Sec. 2.2): eq. apic_augury integrated with eq. Newmark,
+// here with a linear-spring foreground (a stand-in for the paper's finite
+// elements) plus uniform gravity.  The printed eq. Newmark has its half-step
+// indices garbled; it is read as velocity Verlet (explicit Newmark,
+// gamma = 1/2):
+//   V^{n+1/2} = V^n + dt/2 A^n
+//   x^{n+1}   = x^n + dt v^{n+1/2}
+//   A^{n+1}   = {a(x^{n+1}), 0} + A_hat^{n+1}
+//   V^{n+1}   = V^{n+1/2} + dt/2 A^{n+1}
+// with eq. apic_accel A_hat = (H - I) V_bar / tau, V_bar = V_t + tau {a, 0},
+// where V_t, the velocity at t^{n+1} before contact, is V^{n+1/2} + dt/2 {a, 0}
+// (the mechanical part of the last half kick), and H is the contact step
+// (the Sec. 2.3 series with the Sec. 2.4 projection) on normals built from
+// the boundary triangles at x^{n+1}.  Fixed nodes (fixed[p] != 0) keep
+// v = 0, C = 0, A = 0.  `init` first computes A^0 at x^0 with V_t = V^0.
+// av[n*3], aC[n*9] carry A between calls.  energy (may be NULL) receives
+// [kinetic 1/2 m |v|^2, spring energy, gravity energy -m g.x] after the run.
+int oracle_augury_steps(int64_t n, int32_t n_bodies, const int32_t* body, double* x, double* v, double* C,
+                        double* av, double* aC, const double* m, const uint8_t* fixed, int64_t n_springs,
+                        const int32_t* springs, const double* rest, const double* k, const double* g,
+                        int64_t n_tri, const int32_t* tri, double h, double mu, const double* mu_pair,
+                        int32_t n_iter, uint32_t flags, double dt, double tau, int32_t n_steps, int32_t init,
+                        double* energy) {
+  if (n <= 0 || !(dt > 0.0) || !(tau > 0.0) || n_steps < 0) return -1;
+  for (int64_t s = 0; s < n_springs; ++s)
+    if (springs[2 * s] < 0 || springs[2 * s] >= n || springs[2 * s + 1] < 0 || springs[2 * s + 1] >= n) return -1;
+  std::vector<double> am((size_t)(3 * n)), nrm((size_t)(3 * n), 0.0), vbar((size_t)(3 * n)),
+      vhat((size_t)(3 * n)), Chat((size_t)(9 * n));
+  auto is_fixed = [&](int64_t p) { return fixed && fixed[p]; };
+  // a(x): spring forces / m + g
+  auto mechanical = [&]() {
+    for (int64_t p = 0; p < n; ++p)
+      for (int c = 0; c < 3; ++c) am[(size_t)(3 * p + c)] = 0.0;
+    for (int64_t s = 0; s < n_springs; ++s) {
+      const int32_t i = springs[2 * s], j = springs[2 * s + 1];
+      double d[3], len2 = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        d[c] = x[3 * j + c] - x[3 * i + c];
+        len2 += d[c] * d[c];
+      }
+      const double len = std::sqrt(len2);
+      if (!(len > 0.0)) continue;
+      const double f = k[s] * (len - rest[s]) / len;  // pulls i toward j when stretched
+      for (int c = 0; c < 3; ++c) {
+        am[(size_t)(3 * i + c)] += f * d[c];
+        am[(size_t)(3 * j + c)] -= f * d[c];
+      }
+    }
+    for (int64_t p = 0; p < n; ++p)
+      for (int c = 0; c < 3; ++c) am[(size_t)(3 * p + c)] = am[(size_t)(3 * p + c)] / m[p] + (g ? g[c] : 0.0);
+  };
+  // A = {a, 0} + (H - I) V_bar / tau with V_bar = (v_t + tau a, C)
+  auto accelerate = [&](const double* vt) -> int {
+    if (n_tri > 0 && oracle_node_normals(n, x, n_tri, tri, nrm.data()) != 0) return -1;
+    for (int64_t i = 0; i < 3 * n; ++i) vbar[(size_t)i] = vt[i] + tau * am[(size_t)i];
+    if (oracle_contact_step(n, n_bodies, body, x, vbar.data(), C, m, nrm.data(), h, mu, mu_pair, n_iter, flags,
+                            vhat.data(), Chat.data(), nullptr) != 0)
+      return -1;
+    for (int64_t p = 0; p < n; ++p) {
+      for (int c = 0; c < 3; ++c) {
+        const size_t i = (size_t)(3 * p + c);
+        av[i] = is_fixed(p) ? 0.0 : am[i] + (vhat[i] - vbar[i]) / tau;
+      }
+      for (int c = 0; c < 9; ++c) {
+        const size_t i = (size_t)(9 * p + c);
+        aC[i] = is_fixed(p) ? 0.0 : (Chat[i] - C[i]) / tau;
+      }
+    }
+    return 0;
+  };
+  std::vector<double> vt((size_t)(3 * n));
+  if (init) {
+    mechanical();
+    if (accelerate(v) != 0) return -1;
+  }
+  for (int32_t step = 0; step < n_steps; ++step) {
+    for (int64_t p = 0; p < n; ++p) {  // V^{n+1/2}, x^{n+1}
+      for (int c = 0; c < 3; ++c) v[3 * p + c] = is_fixed(p) ? 0.0 : v[3 * p + c] + 0.5 * dt * av[3 * p + c];
+      for (int c = 0; c < 9; ++c) C[9 * p + c] = is_fixed(p) ? 0.0 : C[9 * p + c] + 0.5 * dt * aC[9 * p + c];
+      for (int c = 0; c < 3; ++c) x[3 * p + c] += dt * v[3 * p + c];
+    }
+    mechanical();  // a(x^{n+1})
+    for (int64_t i = 0; i < 3 * n; ++i) vt[(size_t)i] = v[i] + 0.5 * dt * am[(size_t)i];
+    if (accelerate(vt.data()) != 0) return -1;
+    for (int64_t p = 0; p < n; ++p) {  // V^{n+1}
+      for (int c = 0; c < 3; ++c) v[3 * p + c] += 0.5 * dt * av[3 * p + c];
+      for (int c = 0; c < 9; ++c) C[9 * p + c] += 0.5 * dt * aC[9 * p + c];
+    }
+  }
+  if (energy) {
+    double kin = 0.0, spr = 0.0, grav = 0.0;
+    for (int64_t p = 0; p < n; ++p)
+      for (int c = 0; c < 3; ++c) {
+        kin += 0.5 * m[p] * v[3 * p + c] * v[3 * p + c];
+        grav -= m[p] * (g ? g[c] : 0.0) * x[3 * p + c];
+      }
+    for (int64_t s = 0; s < n_springs; ++s) {
+      const int32_t i = springs[2 * s], j = springs[2 * s + 1];
+      double len2 = 0.0;
+      for (int c = 0; c < 3; ++c) len2 += (x[3 * j + c] - x[3 * i + c]) * (x[3 * j + c] - x[3 * i + c]);
+      const double e = std::sqrt(len2) - rest[s];
+      spr += 0.5 * k[s] * e * e;
+    }
+    energy[0] = kin;
+    energy[1] = spr;
+    energy[2] = grav;
   }
   return 0;
 }

@@ -61,6 +61,9 @@ def _load():
             lib.oracle_apic1d_linear.restype = C.c_int
             lib.oracle_node_normals.argtypes = [i64, P, i64, P, P]
             lib.oracle_node_normals.restype = C.c_int
+            lib.oracle_augury_steps.argtypes = [i64, i32, P, P, P, P, P, P, P, P, i64, P, P, P, P, i64, P, d, d, P,
+                                                i32, u32, d, d, i32, i32, P]
+            lib.oracle_augury_steps.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -191,3 +194,33 @@ def node_normals(x, tri):
     if lib.oracle_node_normals(x.shape[0], _ptr(x), tri.shape[0], tri.ctypes.data, _ptr(out)) != 0:
         raise ValueError("oracle_node_normals: a triangle index is outside [0, n)")
     return out
+
+
+def augury_steps(x, v, Cm, m, body, springs, rest, stiffness, tri, h, mu, n_iter, dt, tau, n_steps, av=None,
+                 aC=None, gravity=None, fixed=None, n_bodies=None, mu_pair=None, flags=0, init=True):
+    """Augury dynamics (Sec. 2.2, eq. Newmark read as velocity Verlet) with a
+    linear-spring foreground.  Returns (x, v, C[n,3,3], av, aC[n,3,3],
+    energy dict) after n_steps; inputs are not modified."""
+    lib = _load()
+    x, v, Cm, m = _f64(x, (-1, 3)).copy(), _f64(v, (-1, 3)).copy(), _f64(Cm, (-1, 3, 3)).copy(), _f64(m, -1)
+    n = x.shape[0]
+    av = np.zeros((n, 3)) if av is None else _f64(av, (-1, 3)).copy()
+    aC = np.zeros((n, 3, 3)) if aC is None else _f64(aC, (-1, 3, 3)).copy()
+    body = np.ascontiguousarray(np.asarray(body, np.int32).reshape(-1))
+    if n_bodies is None:
+        n_bodies = int(body.max()) + 1
+    sp = np.ascontiguousarray(np.asarray(springs, np.int32).reshape(-1, 2))
+    rest, stiffness = _f64(rest, -1), _f64(stiffness, -1)
+    tri = np.ascontiguousarray(np.asarray(tri, np.int32).reshape(-1, 3))
+    g = None if gravity is None else _f64(gravity, 3)
+    fx = None if fixed is None else np.ascontiguousarray(np.asarray(fixed, np.uint8).reshape(-1))
+    mp = None if mu_pair is None else _f64(mu_pair, (n_bodies, n_bodies))
+    en = np.zeros(3)
+    rc = lib.oracle_augury_steps(n, int(n_bodies), _ptr(body), _ptr(x), _ptr(v), _ptr(Cm), _ptr(av), _ptr(aC),
+                                 _ptr(m), None if fx is None else fx.ctypes.data, sp.shape[0], sp.ctypes.data,
+                                 _ptr(rest), _ptr(stiffness), _ptr(g), tri.shape[0], tri.ctypes.data if len(tri) else None,
+                                 float(h), float(mu), _ptr(mp), int(n_iter), int(flags), float(dt), float(tau),
+                                 int(n_steps), 1 if init else 0, _ptr(en))
+    if rc != 0:
+        raise ValueError("oracle_augury_steps: invalid arguments")
+    return x, v, Cm, av, aC, dict(kinetic=en[0], springs=en[1], gravity=en[2])

@@ -429,3 +429,84 @@ def box_lattice_surface(nx: int, ny: int, nz: int, spacing: float = 1.0, origin=
             k = nz - 1
             quad(nid(i, j, k), nid(i + 1, j, k), nid(i + 1, j + 1, k), nid(i, j + 1, k))  # +z
     return x, np.array(tri, np.int32)
+
+
+# ----------------------------------------------------- elastic foreground
+# Inputs of the augury dynamics driver (Sec. 2.2): lattice bodies held
+# together by linear springs (a stand-in for the paper's finite elements),
+# with boundary triangles for the Sec. 2.3 normals.
+
+@dataclass
+class ElasticScene:
+    scene: Scene               # x, v, C, m, body, h, mu, n_iter (nrm unused: built from tri)
+    springs: np.ndarray        # [S, 2] int32 node pairs
+    rest: np.ndarray           # [S] rest lengths
+    stiffness: np.ndarray      # [S] spring constants
+    tri: np.ndarray            # [T, 3] int32 boundary triangles, outward winding
+    gravity: np.ndarray        # [3]
+    dt: float
+    tau: float
+
+
+def lattice_springs(nx: int, ny: int, nz: int, spacing: float, k_axis: float, k_diag: float, offset: int = 0):
+    """Springs of an nx x ny x nz lattice (x fastest): the 3 axis neighbours
+    and the 2 diagonals of every lattice-cell face.  Returns (pairs, rest, k)."""
+    idx = np.arange(nx * ny * nz).reshape(nz, ny, nx) + offset
+    pairs, rest, ks = [], [], []
+
+    def add(a, b, L, k):
+        p = np.stack([a.ravel(), b.ravel()], 1)
+        pairs.append(p)
+        rest.append(np.full(len(p), L))
+        ks.append(np.full(len(p), k))
+
+    add(idx[:, :, :-1], idx[:, :, 1:], spacing, k_axis)
+    add(idx[:, :-1, :], idx[:, 1:, :], spacing, k_axis)
+    add(idx[:-1, :, :], idx[1:, :, :], spacing, k_axis)
+    d = spacing * np.sqrt(2.0)
+    add(idx[:, :-1, :-1], idx[:, 1:, 1:], d, k_diag)   # xy faces
+    add(idx[:, :-1, 1:], idx[:, 1:, :-1], d, k_diag)
+    add(idx[:-1, :, :-1], idx[1:, :, 1:], d, k_diag)   # xz faces
+    add(idx[:-1, :, 1:], idx[1:, :, :-1], d, k_diag)
+    add(idx[:-1, :-1, :], idx[1:, 1:, :], d, k_diag)   # yz faces
+    add(idx[:-1, 1:, :], idx[1:, :-1, :], d, k_diag)
+    return (np.concatenate(pairs).astype(np.int32), np.concatenate(rest), np.concatenate(ks))
+
+
+def elastic_pair(n_side: int = 6, spacing: float = 1 / 32, v0: float = 1.0, wave_speed: float = 12.0,
+                 gap_cells: float = 1.0, mu: float = 0.0, n_iter: int = 4, tilt: float = 0.0,
+                 courant: float = 0.1) -> ElasticScene:
+    """Two identical elastic lattice cubes (n_side^3 nodes, unit mass each)
+    approaching head on along x at +-v0, mirror images of each other about
+    the plane x = 0.5, which is a grid-node plane (h = 2 * spacing, the paper's
+    background grid of twice the element size).  `tilt` rotates the second
+    cube about the x axis (radians), breaking the symmetry.  Springs give a
+    long-wave sound speed of about `wave_speed`; dt = courant * spacing / wave_speed."""
+    h = 2.0 * spacing
+    side = (n_side - 1) * spacing
+    x0, t0 = box_lattice_surface(n_side, n_side, n_side, spacing)
+    x0 = x0 - x0.mean(axis=0)
+    gap = gap_cells * h
+    c0 = np.array([0.5 - gap / 2 - side / 2, 0.5, 0.5])
+    c1 = np.array([0.5 + gap / 2 + side / 2, 0.5, 0.5])
+    xa = x0 + c0
+    ca, sa = np.cos(tilt), np.sin(tilt)
+    R = np.array([[1, 0, 0], [0, ca, -sa], [0, sa, ca]])
+    xb = (x0 * np.array([-1.0, 1.0, 1.0])) @ R.T + c1  # mirrored lattice (then tilted)
+    nb = len(x0)
+    x = np.vstack([xa, xb])
+    tri = np.vstack([t0, t0[:, ::-1] + nb]).astype(np.int32)  # mirroring flips the winding
+    m = np.full(2 * nb, 1.0 / nb)
+    rho = (1.0 / nb) / spacing ** 3
+    k_axis = rho * wave_speed ** 2 * spacing  # E ~ k / spacing for a cubic lattice, c = sqrt(E / rho)
+    pa, ra, kk = lattice_springs(n_side, n_side, n_side, spacing, k_axis, 0.5 * k_axis)
+    springs = np.vstack([pa, pa + nb]).astype(np.int32)
+    rest = np.concatenate([ra, ra])
+    stiff = np.concatenate([kk, kk])
+    v = np.zeros_like(x)
+    v[:nb, 0], v[nb:, 0] = v0, -v0
+    body = np.repeat(np.arange(2), nb).astype(np.int32)
+    sc = Scene(x, v, np.zeros((2 * nb, 9)), m, np.zeros_like(x), body, 2, h, mu, n_iter, None,
+               f"elastic_pair_{n_side}", dict(spacing=spacing, wave_speed=wave_speed, tilt=tilt))
+    dt = courant * spacing / wave_speed
+    return ElasticScene(sc, springs, rest, stiff, tri, np.zeros(3), dt, dt)
