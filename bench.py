@@ -472,6 +472,7 @@ def main():
         "clocks": ck,
     }
     line["node_normals"] = bench_node_normals(apic, ctx, dev, stream, flush)
+    line["augury_dynamics"] = bench_augury(apic, ctx, dev, stream)
     if plain is not None:
         line["plain_single_scene"] = {"value": plain, "unit": UNIT,
                                       "what": "the same scenes, one apic_contact_step call each",
@@ -612,6 +613,42 @@ def bench_node_normals(apic, ctx, dev, stream, flush, reps=10):
     return {"mesh": "boundary of a 100^3-node lattice block", "nodes": len(x), "triangles": len(tri),
             "ms": t, "triangles_per_s": len(tri) / (t / 1e3), "nodes_per_s": len(x) / (t / 1e3),
             "algorithmic_bytes": alg, "achieved_gbs": alg / (t / 1e3) / 1e9, "frac_of_hbm_peak": alg / (t / 1e3) / 1e9 / peak}
+
+
+def bench_augury(apic, ctx, dev, stream, steps=20):
+    """apic_augury_steps (Sec. 2.2 augury dynamics, springs + contact) on two
+    elastic lattice cubes of 40^3 nodes (128,000 nodes, 1,104,480 springs,
+    N = 4), already in contact: device time per time step (CUDA events)."""
+    import torch
+
+    from paper_2108_02259_gb300 import scenes
+
+    e = scenes.elastic_pair(n_side=40, spacing=1 / 256, gap_cells=0.5)
+    s = e.scene
+
+    def d(a, ty):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=ty, device=dev)
+
+    st = [d(s.x, torch.float64), d(s.v, torch.float32), d(np.zeros((s.n, 9)), torch.float32),
+          d(np.zeros((s.n, 3)), torch.float32), d(np.zeros((s.n, 9)), torch.float32), d(s.m, torch.float32),
+          d(s.body, torch.int32), d(e.springs, torch.int32), d(e.rest, torch.float64), d(e.stiffness, torch.float64),
+          d(e.tri, torch.int32)]
+
+    def run(k, init=False):
+        apic.augury_steps(ctx, *st, s.h, s.mu, s.n_iter, e.dt, e.tau, k, n_bodies=2, init=init, stream=stream)
+
+    run(3, init=True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    a.record(stream)
+    run(steps)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    return {"scene": "two elastic lattice cubes, 40^3 nodes each, in contact", "nodes": s.n,
+            "springs": int(len(e.springs)), "n_iter": s.n_iter, "ms_per_time_step": ms,
+            "node_steps_per_s": s.n / (ms / 1e3),
+            "note": "each time step: normals from boundary triangles, spring forces, one contact step, two half kicks"}
 
 
 def step_breakdown(prof):

@@ -286,6 +286,65 @@ apic_status apic_node_normals(apic_ctx* ctx, int64_t n, const double* x, int64_t
                               void* nrm_out, uint32_t flags, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Augury dynamics (Sec. 2.2): the contact step inside a time integrator.
+ *
+ * eq. apic_accel gives the contact acceleration A_hat = (H - I) V_bar / tau of
+ * the predicted generalized velocity V_bar = V_t + tau A_t; eq. apic_Augury
+ * adds it to the mechanical acceleration; eq. Newmark integrates.  The printed
+ * eq. Newmark has garbled half-step indices; it is read as velocity Verlet:
+ *   V^{n+1/2} = V^n + dt/2 A^n;  x^{n+1} = x^n + dt v^{n+1/2};
+ *   A^{n+1} = {a(x^{n+1}), 0} + A_hat^{n+1};  V^{n+1} = V^{n+1/2} + dt/2 A^{n+1},
+ * with V_t = V^{n+1/2} + dt/2 {a(x^{n+1}), 0} (the velocity at t^{n+1} before
+ * contact).  H is apic_contact_step on normals rebuilt every step from the
+ * boundary triangles (apic_node_normals).  The mechanical acceleration comes
+ * from linear springs (a stand-in for the paper's finite elements, which are
+ * out of scope) plus uniform gravity.  Not a paper listing: the paper gives
+ * the equations, not this API.
+ * --------------------------------------------------------------------------*/
+#define APIC_AUGURY_INIT (1u << 4) /* first compute A^0 at x^0 (V_t = V^0) */
+
+typedef struct {
+  int64_t n;                 /* nodes (particles), > 0                               */
+  int32_t n_bodies;          /* as apic_step_args                                    */
+  int32_t n_iter;            /* N of the contact step                                */
+  const int32_t* body;       /* [n]                                                  */
+  double* x;                 /* [n*3] positions, advanced in place                   */
+  void* v;                   /* [n*3] velocity, advanced in place (float; double with APIC_FP64) */
+  void* C;                   /* [n*9] affine velocity C = B D^-1, advanced in place   */
+  void* av;                  /* [n*3] acceleration A^n (v part), carried between calls */
+  void* aC;                  /* [n*9] acceleration A^n (C part)                      */
+  const void* m;             /* [n] masses > 0                                       */
+  const uint8_t* fixed;      /* [n] nonzero: node held (v = C = A = 0), or NULL       */
+  int64_t n_springs;         /* linear springs between node pairs                    */
+  const int32_t* springs;    /* [n_springs*2] node ids                               */
+  const double* rest;        /* [n_springs] rest lengths                             */
+  const double* stiffness;   /* [n_springs] spring constants (force per length)      */
+  double gravity[3];         /* uniform acceleration                                 */
+  int64_t n_tri;             /* boundary triangles for the normals (0: all normals 0) */
+  const int32_t* tri;        /* [n_tri*3], outward winding                           */
+  double h, mu;              /* grid spacing, friction (as apic_step_args)           */
+  const double* mu_pair;     /* host, n_bodies^2, or NULL                            */
+  double dt, tau;            /* time step and augury time (the paper uses tau = dt)  */
+  uint32_t flags;            /* APIC_FP64, APIC_VARIANT_PIC, APIC_VARIANT_SEP23, APIC_AUGURY_INIT */
+} apic_augury_args;
+
+typedef struct {
+  double P[3], L[3];         /* linear and angular momentum (L with the affine spin term) */
+  double kinetic;            /* sum 1/2 m |v|^2                                      */
+  double springs;            /* sum 1/2 k (|d| - L0)^2                               */
+  double gravity;            /* -sum m g.x                                           */
+} apic_augury_stats;
+
+/* Advance the state n_steps time steps on `stream` (device pointers only).
+ * Scratch comes from the context.  Synchronises before returning.  Errors:
+ * APIC_ERR_INVALID_ARG for bad sizes, NULL arrays, disallowed flags, or a
+ * spring or triangle index outside [0, n) (the state is then unspecified);
+ * the contact step's own errors pass through.  stats (nullable) describe the
+ * final state. */
+apic_status apic_augury_steps(apic_ctx* ctx, const apic_augury_args* args, int32_t n_steps, void* stream,
+                              apic_augury_stats* stats);
+
+/* ---------------------------------------------------------------------------
  * Kernel variants, autotuning and CUDA graphs (no counterpart in the paper:
  * they change how the transfer passes are launched, never what they compute).
  *

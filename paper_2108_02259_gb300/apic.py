@@ -31,6 +31,7 @@ APIC_FP64 = 1 << 0
 APIC_HOST_PTRS = 1 << 1
 APIC_VARIANT_PIC = 1 << 2
 APIC_VARIANT_SEP23 = 1 << 3
+APIC_AUGURY_INIT = 1 << 4
 
 EXPORTED = [
     "apic_last_error", "apic_version", "apic_create", "apic_destroy", "apic_contact_step",
@@ -38,7 +39,7 @@ EXPORTED = [
     "apic_contact_step_batched", "apic_server_create", "apic_server_destroy", "apic_sim_open", "apic_sim_submit",
     "apic_ticket_poll", "apic_ticket_wait", "apic_sim_read", "apic_sim_close", "apic_server_get_stats",
     "apic_variant_count", "apic_variant_name", "apic_set_variant", "apic_get_variant", "apic_autotune",
-    "apic_set_graphs", "apic_server_set_policy", "apic_node_normals",
+    "apic_set_graphs", "apic_server_set_policy", "apic_node_normals", "apic_augury_steps",
 ]
 
 
@@ -82,6 +83,26 @@ class Profile(C.Structure):
 
 
 _lib = None
+
+
+class AuguryArgs(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64), ("n_bodies", C.c_int32), ("n_iter", C.c_int32), ("body", C.c_void_p),
+        ("x", C.c_void_p), ("v", C.c_void_p), ("C", C.c_void_p), ("av", C.c_void_p), ("aC", C.c_void_p),
+        ("m", C.c_void_p), ("fixed", C.c_void_p), ("n_springs", C.c_int64), ("springs", C.c_void_p),
+        ("rest", C.c_void_p), ("stiffness", C.c_void_p), ("gravity", C.c_double * 3), ("n_tri", C.c_int64),
+        ("tri", C.c_void_p), ("h", C.c_double), ("mu", C.c_double), ("mu_pair", C.c_void_p), ("dt", C.c_double),
+        ("tau", C.c_double), ("flags", C.c_uint32),
+    ]
+
+
+class AuguryStats(C.Structure):
+    _fields_ = [("P", C.c_double * 3), ("L", C.c_double * 3), ("kinetic", C.c_double), ("springs", C.c_double),
+                ("gravity", C.c_double)]
+
+    def as_dict(self):
+        return {"P": np.array(self.P[:]), "L": np.array(self.L[:]), "kinetic": self.kinetic,
+                "springs": self.springs, "gravity": self.gravity}
 
 
 class ApicError(RuntimeError):
@@ -134,6 +155,8 @@ def load(path: str = LIB_PATH):
     lib.apic_server_set_policy.argtypes = [P, C.c_int32, C.c_int32]
     lib.apic_node_normals.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_uint32, P]
     lib.apic_node_normals.restype = C.c_int32
+    lib.apic_augury_steps.argtypes = [P, C.POINTER(AuguryArgs), C.c_int32, P, C.POINTER(AuguryStats)]
+    lib.apic_augury_steps.restype = C.c_int32
     lib.apic_server_set_policy.restype = C.c_int32
     for f in ("apic_create", "apic_destroy", "apic_contact_step", "apic_set_profiling", "apic_get_profile",
               "apic_scratch_bytes", "apic_set_variant", "apic_get_variant", "apic_autotune", "apic_set_graphs"):
@@ -356,6 +379,42 @@ def node_normals(ctx: Context, x, tri, fp64: bool = False, out=None, stream=None
     _check(lib.apic_node_normals(ctx.handle, n, _ptr(x), n_tri, _ptr(tri) if n_tri else None, _ptr(out), flags,
                                  sptr))
     return out
+
+
+def augury_steps(ctx: Context, x, v, Cm, av, aC, m, body, springs, rest, stiffness, tri, h: float, mu: float,
+                 n_iter: int, dt: float, tau: float, n_steps: int, gravity=(0.0, 0.0, 0.0), fixed=None,
+                 n_bodies: int | None = None, mu_pair=None, flags: int = 0, init: bool = False, stream=None,
+                 stats: bool = False):
+    """apic_augury_steps on torch CUDA tensors, advanced in place: x [n,3]
+    float64; v [n,3], Cm [n,9], av [n,3], aC [n,9], m [n] float32 (or all
+    float64 for the FP64 path); body int32; springs [S,2] int32; rest and
+    stiffness float64; tri [T,3] int32; fixed uint8 or None.  Returns the
+    final-state stats dict (or None)."""
+    import torch
+
+    lib = load()
+    if v.dtype == torch.float64:
+        flags |= APIC_FP64
+    if init:
+        flags |= APIC_AUGURY_INIT
+    n = int(x.shape[0])
+    if n_bodies is None:
+        n_bodies = int(body.max().item()) + 1
+    mp = None
+    if mu_pair is not None:
+        mp = np.ascontiguousarray(np.asarray(mu_pair, np.float64).reshape(n_bodies, n_bodies))
+    a = AuguryArgs(n, int(n_bodies), int(n_iter), _ptr(body), _ptr(x), _ptr(v), _ptr(Cm), _ptr(av), _ptr(aC), _ptr(m),
+                   _ptr(fixed), int(springs.shape[0]), _ptr(springs) if springs.shape[0] else None,
+                   _ptr(rest) if springs.shape[0] else None, _ptr(stiffness) if springs.shape[0] else None,
+                   (C.c_double * 3)(*[float(g) for g in gravity]), int(tri.shape[0]),
+                   _ptr(tri) if tri.shape[0] else None, float(h), float(mu), None if mp is None else mp.ctypes.data,
+                   float(dt), float(tau), int(flags))
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    st = AuguryStats()
+    _check(lib.apic_augury_steps(ctx.handle, C.byref(a), int(n_steps), stream.cuda_stream,
+                                 C.byref(st) if stats else None))
+    return st.as_dict() if stats else None
 
 
 class BatchScene:

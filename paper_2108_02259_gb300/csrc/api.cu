@@ -391,6 +391,13 @@ apic_status run(apic_ctx* c, const apic_step_args* scenes, int ns, void* stream,
 
 }  // namespace
 
+apic_status apic::ctx_take(apic_ctx* c, int slot, size_t bytes, void** out) {
+  if (slot < 0 || slot >= kSlotCount) return pfail(APIC_ERR_INVALID_ARG, "internal: scratch slot %d", slot);
+  P_TRY(grow(c, c->bufs[slot], bytes + 64));
+  *out = c->bufs[slot].ptr;
+  return APIC_OK;
+}
+
 extern "C" {
 
 const char* apic_last_error(void) { return g_last_error.c_str(); }

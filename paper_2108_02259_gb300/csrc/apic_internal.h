@@ -166,6 +166,25 @@ cudaError_t launch_face_normals(int64_t n_tri, const int32_t* tri, const double*
 template <class T>
 cudaError_t launch_unit_normals(int64_t n, const double* acc, T* out, cudaStream_t s);
 
+// Augury dynamics kernels (see kernels.cu): kick + drift, FP64 spring
+// forces (err |= kErrBody for a bad index), prediction, finish, energies.
+template <class T>
+cudaError_t launch_aug_kick_drift(int64_t n, double* x, T* v, T* C, const T* av, const T* aC, const uint8_t* fixed,
+                                  T half_dt, double dt, cudaStream_t s);
+cudaError_t launch_aug_springs(int64_t n_springs, const int32_t* springs, const double* rest, const double* k,
+                               const double* x, int64_t n, double* f, int* err, cudaStream_t s);
+template <class T>
+cudaError_t launch_aug_predict(int64_t n, const double* f, const T* m, const double* g, const T* v, T* am, T* vbar,
+                               T c_bar, cudaStream_t s);
+template <class T>
+cudaError_t launch_aug_finish(int64_t n, const T* am, const T* vbar, const T* vhat, const T* Chat,
+                              const uint8_t* fixed, T inv_tau, T half_dt, T* v, T* C, T* av, T* aC,
+                              cudaStream_t s);
+template <class T>
+cudaError_t launch_aug_energy(int64_t n, const double* x, const T* v, const T* m, const double* g, int64_t n_springs,
+                              const int32_t* springs, const double* rest, const double* k, double* out,
+                              cudaStream_t s);
+
 // Set the calling thread's message returned by apic_last_error().
 void set_last_error(const char* msg);
 

@@ -1140,6 +1140,171 @@ cudaError_t launch_unit_normals(int64_t n, const double* acc, T* out, cudaStream
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Augury dynamics (Sec. 2.2, eq. apic_accel, eq. Newmark read as velocity
+// Verlet) with a linear-spring foreground.  One step:
+//   kick+drift:  V += dt/2 A; x += dt v            (fixed nodes: V = 0)
+//   springs:     f = sum k (|d| - L0) d / |d|      (FP64 sums)
+//   predict:     a = f / m + g; V_bar = V + c {a, 0}, c = dt/2 + tau
+//   contact:     V_hat = contact step of V_bar      (the library's step)
+//   finish:      A = {a, 0} + (V_hat - V_bar) / tau; V += dt/2 A
+// (with c = tau and no kicks for the initial acceleration).
+
+template <class T>
+__global__ void k_aug_kick_drift(int64_t n, double* x, T* v, T* C, const T* av, const T* aC, const uint8_t* fixed,
+                                 T half_dt, double dt) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const bool held = fixed != nullptr && fixed[p] != 0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T vn = held ? T(0) : v[3 * p + c] + half_dt * av[3 * p + c];
+    v[3 * p + c] = vn;
+    x[3 * p + c] += dt * (double)vn;
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c) C[9 * p + c] = held ? T(0) : C[9 * p + c] + half_dt * aC[9 * p + c];
+}
+
+__global__ void k_aug_springs(int64_t n_springs, const int32_t* springs, const double* rest, const double* k,
+                              const double* x, int64_t n, double* f, int* err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_springs; s += stride) {
+    const int32_t i = springs[2 * s], j = springs[2 * s + 1];
+    if (i < 0 || j < 0 || i >= n || j >= n) {
+      atomicOr(err, kErrBody);
+      continue;
+    }
+    double d[3], len2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      d[c] = x[3 * (int64_t)j + c] - x[3 * (int64_t)i + c];
+      len2 += d[c] * d[c];
+    }
+    const double len = sqrt(len2);
+    if (!(len > 0.0)) continue;
+    const double fs = k[s] * (len - rest[s]) / len;  // pulls i toward j when stretched
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      atomicAdd(&f[3 * (int64_t)i + c], fs * d[c]);
+      atomicAdd(&f[3 * (int64_t)j + c], -fs * d[c]);
+    }
+  }
+}
+
+template <class T>
+__global__ void k_aug_predict(int64_t n, const double* f, const T* m, double gx, double gy, double gz, const T* v,
+                              T* am, T* vbar, T c_bar) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const double g[3] = {gx, gy, gz};
+  const double mp = (double)m[p];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T a = (T)(f[3 * p + c] / mp + g[c]);
+    am[3 * p + c] = a;
+    vbar[3 * p + c] = v[3 * p + c] + c_bar * a;
+  }
+}
+
+template <class T>
+__global__ void k_aug_finish(int64_t n, const T* am, const T* vbar, const T* vhat, const T* Chat, const uint8_t* fixed,
+                             T inv_tau, T half_dt, T* v, T* C, T* av, T* aC) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const bool held = fixed != nullptr && fixed[p] != 0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T a = held ? T(0) : am[3 * p + c] + (vhat[3 * p + c] - vbar[3 * p + c]) * inv_tau;
+    av[3 * p + c] = a;
+    v[3 * p + c] += half_dt * a;
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    const T a = held ? T(0) : (Chat[9 * p + c] - C[9 * p + c]) * inv_tau;
+    aC[9 * p + c] = a;
+    C[9 * p + c] += half_dt * a;
+  }
+}
+
+// out[0] += sum 1/2 m |v|^2, out[1] += sum 1/2 k (|d| - L0)^2, out[2] += -sum m g.x
+template <class T>
+__global__ void k_aug_energy(int64_t n, const double* x, const T* v, const T* m, double gx, double gy, double gz,
+                             int64_t n_springs, const int32_t* springs, const double* rest, const double* k,
+                             double* out) {
+  double e[3] = {0.0, 0.0, 0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t p = t0; p < n; p += stride) {
+    const double mp = (double)m[p];
+    double v2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v2 += (double)v[3 * p + c] * (double)v[3 * p + c];
+    e[0] += 0.5 * mp * v2;
+    e[2] -= mp * (gx * x[3 * p] + gy * x[3 * p + 1] + gz * x[3 * p + 2]);
+  }
+  for (int64_t s = t0; s < n_springs; s += stride) {
+    const int32_t i = springs[2 * s], j = springs[2 * s + 1];
+    if (i < 0 || j < 0 || i >= n || j >= n) continue;
+    double len2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double d = x[3 * (int64_t)j + c] - x[3 * (int64_t)i + c];
+      len2 += d * d;
+    }
+    const double ex = sqrt(len2) - rest[s];
+    e[1] += 0.5 * k[s] * ex * ex;
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    double val = e[q];
+    for (int o = 16; o > 0; o >>= 1) val += __shfl_down_sync(0xffffffffu, val, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&out[q], val);
+  }
+}
+
+template <class T>
+cudaError_t launch_aug_kick_drift(int64_t n, double* x, T* v, T* C, const T* av, const T* aC, const uint8_t* fixed,
+                                  T half_dt, double dt, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_aug_kick_drift<T><<<grid_for(n, 256), 256, 0, s>>>(n, x, v, C, av, aC, fixed, half_dt, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aug_springs(int64_t n_springs, const int32_t* springs, const double* rest, const double* k,
+                               const double* x, int64_t n, double* f, int* err, cudaStream_t s) {
+  if (n_springs <= 0) return cudaSuccess;
+  const unsigned g = (unsigned)std::min<int64_t>(grid_for(n_springs, 256), 152 * 16);
+  k_aug_springs<<<g, 256, 0, s>>>(n_springs, springs, rest, k, x, n, f, err);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_aug_predict(int64_t n, const double* f, const T* m, const double* g, const T* v, T* am, T* vbar,
+                               T c_bar, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_aug_predict<T><<<grid_for(n, 256), 256, 0, s>>>(n, f, m, g[0], g[1], g[2], v, am, vbar, c_bar);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_aug_finish(int64_t n, const T* am, const T* vbar, const T* vhat, const T* Chat,
+                              const uint8_t* fixed, T inv_tau, T half_dt, T* v, T* C, T* av, T* aC,
+                              cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_aug_finish<T><<<grid_for(n, 256), 256, 0, s>>>(n, am, vbar, vhat, Chat, fixed, inv_tau, half_dt, v, C, av, aC);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_aug_energy(int64_t n, const double* x, const T* v, const T* m, const double* g, int64_t n_springs,
+                              const int32_t* springs, const double* rest, const double* k, double* out,
+                              cudaStream_t s) {
+  const unsigned gr = (unsigned)std::min<int64_t>(grid_for(std::max<int64_t>(std::max<int64_t>(n, n_springs), 1), 256), 608);
+  k_aug_energy<T><<<gr, 256, 0, s>>>(n, x, v, m, g[0], g[1], g[2], n_springs, springs, rest, k, out);
+  return cudaGetLastError();
+}
+
 #define APIC_INST_T(T)                                                                                  \
   template cudaError_t launch_cells<T>(int64_t, const SceneDev*, int, int4*, int*, int*, cudaStream_t); \
   template cudaError_t launch_gather<T>(int64_t, const SceneDev*, int, const int*, const int4*, V4<T>*,  \
@@ -1150,7 +1315,15 @@ cudaError_t launch_unit_normals(int64_t n, const double* acc, T* out, cudaStream
   template cudaError_t launch_momentum<T>(int64_t, const double*, const T*, const T*, const T*, double, \
                                           double*, cudaStream_t);                                       \
   template cudaError_t launch_advect<T>(int64_t, double*, const T*, double, cudaStream_t);                \
-  template cudaError_t launch_unit_normals<T>(int64_t, const double*, T*, cudaStream_t);
+  template cudaError_t launch_unit_normals<T>(int64_t, const double*, T*, cudaStream_t);                 \
+  template cudaError_t launch_aug_kick_drift<T>(int64_t, double*, T*, T*, const T*, const T*, const uint8_t*, T,  \
+                                                double, cudaStream_t);                                    \
+  template cudaError_t launch_aug_predict<T>(int64_t, const double*, const T*, const double*, const T*, T*, T*, \
+                                             T, cudaStream_t);                                            \
+  template cudaError_t launch_aug_finish<T>(int64_t, const T*, const T*, const T*, const T*, const uint8_t*, T, \
+                                            T, T*, T*, T*, T*, cudaStream_t);                              \
+  template cudaError_t launch_aug_energy<T>(int64_t, const double*, const T*, const T*, const double*, int64_t, \
+                                            const int32_t*, const double*, const double*, double*, cudaStream_t);
 APIC_INST_T(float)
 APIC_INST_T(double)
 

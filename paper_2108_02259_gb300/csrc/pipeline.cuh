@@ -36,7 +36,8 @@ enum Slot : int {
   kSlotHeads, kSlotOffs, kSlotItemStart, kSlotItemInfo, kSlotBFlags, kSlotBOffs, kSlotBList, kSlotPage,
   kSlotGm, kSlotGmask, kSlotGp, kSlotGp64, kSlotGv, kSlotGmb, kSlotMuTable, kSlotCubTmp, kSlotScenes,
   kSlotSBbox, kSlotSMom, kSlotSCount, kSlotHX, kSlotHBody, kSlotHV, kSlotHC, kSlotHM, kSlotHN, kSlotHVo,
-  kSlotHCo, kSlotDS, kSlotNrmAcc, kSlotNrmX, kSlotNrmTri, kSlotNrmOut, kSlotCount
+  kSlotHCo, kSlotDS, kSlotNrmAcc, kSlotNrmX, kSlotNrmTri, kSlotNrmOut, kSlotAugF, kSlotAugAm, kSlotAugVbar,
+  kSlotAugVhat, kSlotAugChat, kSlotAugNrm, kSlotAugOut, kSlotCount
 };
 
 constexpr int kMaxBodies = 32;
@@ -44,6 +45,9 @@ constexpr int64_t kMaxPageEntries = int64_t(1) << 28;  // dense page table limit
 constexpr int kBoxSlack = 2;  // blocks of room for motion when a page-table box is reused
 
 apic_status pfail(apic_status code, const char* fmt, ...);
+
+// Grow-only scratch of a context, by slot (defined with the context).
+apic_status ctx_take(apic_ctx* c, int slot, size_t bytes, void** out);
 
 #define P_CUDA(expr)                                                                              \
   do {                                                                                            \
