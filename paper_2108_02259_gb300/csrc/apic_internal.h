@@ -37,7 +37,7 @@ struct DevScalars {
   int err;       // kErr* bits
   int n_items;   // work items
   int n_blocks;  // active grid blocks
-  int pad;
+  int n_runs;    // runs of equal (grid block, body)
 };
 
 // Dense page table over a box of grid blocks (block coordinates relative to
@@ -124,8 +124,14 @@ cudaError_t launch_keys(int64_t n, const SceneDev* sc, int ns, const int4* cellb
 template <class T>
 cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm, const int4* cellb, V4<T>* pt,
                           V4<T>* pn, V4<T>* V, cudaStream_t s);
+// Run heads: flags[s] = 1 where the (grid block, body) of sorted particle s
+// differs from s - 1.
 template <class K>
 cudaError_t launch_heads(int64_t n, const K* keys, int* flags, cudaStream_t s);
+// Item heads: runs (from their flags, exclusive offsets and compacted starts)
+// split into ceil(len / kChunk) equal items.
+cudaError_t launch_item_heads(int64_t n, const int* run_flags, const int* run_offs, const int* run_start,
+                              const int* n_runs, int* flags, cudaStream_t s);
 template <class K>
 cudaError_t launch_item_info(const int* item_start, const int* n_items, const K* keys, int max_bodies,
                              const SceneDev* sc, int ns, int4* item_info, int max_items, cudaStream_t s);

@@ -512,7 +512,9 @@ __global__ void __launch_bounds__(kChunk, MINB) k_items(const IterParams<T> p) {
     }
   }
   if (!kP2G) return;
-  __syncthreads();
+  // Half-warp h of phase 2 walks particles 16h .. 16h+15, which lanes of its
+  // own warp stashed in phase 1: ordering within the warp is enough.
+  __syncwarp();
 
   // ---------------- phase 2: cell-centric P2G ----------------
   {
@@ -821,8 +823,21 @@ template <class K>
 __global__ void k_heads(int64_t n, const K* __restrict__ keys, int* flags) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
-  // a new item at every (grid block, body) change and every kChunk particles
-  flags[s] = (s % kChunk == 0 || (keys[s] >> 6) != (keys[s - 1] >> 6)) ? 1 : 0;
+  // a new run at every (grid block, body) change
+  flags[s] = (s == 0 || (keys[s] >> 6) != (keys[s - 1] >> 6)) ? 1 : 0;
+}
+
+// Work items: each run of len particles splits into ceil(len / kChunk)
+// items of equal size (within one), so no item is a short tail.
+__global__ void k_item_heads(int64_t n, const int* __restrict__ run_flags, const int* __restrict__ run_offs,
+                             const int* __restrict__ run_start, const int* __restrict__ n_runs, int* flags) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int r = run_offs[s] + run_flags[s] - 1;  // the run holding s
+  const int64_t a = run_start[r];
+  const int64_t b = r + 1 < *n_runs ? run_start[r + 1] : n;
+  const int64_t len = b - a, items = (len + kChunk - 1) / kChunk, off = s - a;
+  flags[s] = (off == 0 || (off * items) / len != ((off - 1) * items) / len) ? 1 : 0;
 }
 
 template <class K>
@@ -988,6 +1003,13 @@ template <class K>
 cudaError_t launch_heads(int64_t n, const K* keys, int* flags, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_heads<K><<<grid_for(n, 256), 256, 0, s>>>(n, keys, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_item_heads(int64_t n, const int* run_flags, const int* run_offs, const int* run_start,
+                              const int* n_runs, int* flags, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_item_heads<<<grid_for(n, 256), 256, 0, s>>>(n, run_flags, run_offs, run_start, n_runs, flags);
   return cudaGetLastError();
 }
 

@@ -37,7 +37,7 @@ enum Slot : int {
   kSlotGm, kSlotGmask, kSlotGp, kSlotGp64, kSlotGv, kSlotGmb, kSlotMuTable, kSlotCubTmp, kSlotScenes,
   kSlotSBbox, kSlotSMom, kSlotSCount, kSlotHX, kSlotHBody, kSlotHV, kSlotHC, kSlotHM, kSlotHN, kSlotHVo,
   kSlotHCo, kSlotDS, kSlotNrmAcc, kSlotNrmX, kSlotNrmTri, kSlotNrmOut, kSlotAugF, kSlotAugAm, kSlotAugVbar,
-  kSlotAugVhat, kSlotAugChat, kSlotAugNrm, kSlotAugOut, kSlotCount
+  kSlotAugVhat, kSlotAugChat, kSlotAugNrm, kSlotAugOut, kSlotRunFlags, kSlotRunOffs, kSlotRunStart, kSlotCount
 };
 
 constexpr int kMaxBodies = 32;
@@ -128,6 +128,7 @@ struct SizingBufs {
   int *va = nullptr, *perm = nullptr; // sort values, sorted permutation
   char* tmp = nullptr;                 // CUB temporaries (max of the three uses)
   size_t tmp_sort = 0, tmp_scan_n = 0, tmp_scan_nb = 0;
+  int *run_flags = nullptr, *run_offs = nullptr, *run_start = nullptr;
   int *heads = nullptr, *offs = nullptr, *item_start = nullptr;
   int4* item_info = nullptr;
   int *bflags = nullptr, *boffs = nullptr, *blist = nullptr, *page = nullptr;
@@ -154,6 +155,9 @@ apic_status plan_sizing(Env& env, int64_t n, int64_t NB, int max_bodies, SizingB
     P_TRY(plan_keys<uint64_t>(env, n, b));
   else
     P_TRY(plan_keys<uint32_t>(env, n, b));
+  P_TRY(env.take(kSlotRunFlags, n, &b.run_flags, "run heads"));
+  P_TRY(env.take(kSlotRunOffs, n, &b.run_offs, "run offsets"));
+  P_TRY(env.take(kSlotRunStart, n, &b.run_start, "run starts"));
   P_TRY(env.take(kSlotHeads, n, &b.heads, "item heads"));
   P_TRY(env.take(kSlotOffs, n, &b.offs, "item offsets"));
   P_TRY(env.take(kSlotItemStart, n, &b.item_start, "item starts"));
@@ -301,11 +305,15 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       P_TRY((sort_keys<uint32_t>(env, n, sc, ns, cellb, max_bodies, &ds->err, sb, q)));
     // 4. sorted SoA.
     P_LAUNCH(env, launch_gather<T>(n, sc, ns, sb.perm, cellb, pt, pn, V, q));
-    // 5. work items: runs of equal (grid block, body), at most kChunk long.
+    // 5. work items: runs of equal (grid block, body), each split into
+    //    equal items of at most kChunk particles.
     if (sb.k64)
-      P_LAUNCH(env, launch_heads<uint64_t>(n, static_cast<const uint64_t*>(sb.kb), sb.heads, q));
+      P_LAUNCH(env, launch_heads<uint64_t>(n, static_cast<const uint64_t*>(sb.kb), sb.run_flags, q));
     else
-      P_LAUNCH(env, launch_heads<uint32_t>(n, static_cast<const uint32_t*>(sb.kb), sb.heads, q));
+      P_LAUNCH(env, launch_heads<uint32_t>(n, static_cast<const uint32_t*>(sb.kb), sb.run_flags, q));
+    P_TRY(exclusive_sum(env, sb, sb.tmp_scan_n, sb.run_flags, sb.run_offs, n, q));
+    P_LAUNCH(env, launch_compact(n, sb.run_flags, sb.run_offs, sb.run_start, nullptr, &ds->n_runs, q));
+    P_LAUNCH(env, launch_item_heads(n, sb.run_flags, sb.run_offs, sb.run_start, &ds->n_runs, sb.heads, q));
     P_TRY(exclusive_sum(env, sb, sb.tmp_scan_n, sb.heads, sb.offs, n, q));
     P_LAUNCH(env, launch_compact(n, sb.heads, sb.offs, sb.item_start, nullptr, &ds->n_items, q));
     if (sb.k64)
