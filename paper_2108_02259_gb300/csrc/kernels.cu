@@ -387,9 +387,25 @@ __global__ void __launch_bounds__(kChunk, MINB) k_items(const IterParams<T> p) {
       for (int a = 0; a < kComp; ++a) sacc[a][t] = T(0);
   __syncthreads();
   if (kG2P) {
-    for (int t = t_lo + tid; t < t_hi; t += kChunk) {
-      const int node = tile_node(snb, t);
-      sv[t] = node >= 0 ? p.gv[node] : V4<T>{T(0), T(0), T(0), T(0)};
+    if constexpr (sizeof(T) == 4) {
+      // global -> shared without staging in registers (cp.async, 16 bytes:
+      // V4<float> is 16-byte aligned in both spaces); all of this thread's
+      // copies are in flight together
+      for (int t = t_lo + tid; t < t_hi; t += kChunk) {
+        const int node = tile_node(snb, t);
+        if (node >= 0) {
+          const unsigned dst = (unsigned)__cvta_generic_to_shared(&sv[t]);
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(&p.gv[node]) : "memory");
+        } else {
+          sv[t] = V4<T>{T(0), T(0), T(0), T(0)};
+        }
+      }
+      asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+    } else {
+      for (int t = t_lo + tid; t < t_hi; t += kChunk) {
+        const int node = tile_node(snb, t);
+        sv[t] = node >= 0 ? p.gv[node] : V4<T>{T(0), T(0), T(0), T(0)};
+      }
     }
     __syncthreads();
   }
