@@ -187,6 +187,15 @@ def algorithmic_bytes_per_pass(P, G):
     return 128.0 * P + 24.0 * G
 
 
+# Essential FP32 work of one fused pass per particle, an FMA counted as 2:
+# G2P sum-factorised (x stage 64 nodes x 6 FMA, y-z stage 16 x 12) 1,152;
+# P2G (64 nodes x 3 components x 2 FMA, plus 16 row factors) 1,104; weights,
+# Delta update and two projections ~140.
+FLOP_PER_PARTICLE_PASS = 2400.0
+# GB300 FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (maximum SM clock).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
 def bounded_sample(s, max_particles=1_100_000):
     """The oracle's bounded sample of a scene: the whole scene when small,
     else its first approaching pair of bodies (bodies 0 and 1)."""
@@ -284,6 +293,8 @@ def main():
     ap.add_argument("--variant", type=int, default=-1,
                     help="fix the transfer-kernel variant (default: autotune for the workload)")
     ap.add_argument("--no-graphs", action="store_true", help="launch the transfer passes one by one")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the node-normal and augury-driver measurements (contact step only)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -464,6 +475,12 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg, "avg_launch_ms": iter_avg_ms,
                      "launches": int(prof["iter_launches"]), "active_nodes": int(G)},
+        "roofline_fp32": {"bound": "alu", "kernel": "k_items (fused G2P + projection + P2G pass)",
+                          "achieved": FLOP_PER_PARTICLE_PASS * P / (iter_avg_ms / 1e3) / 1e12,
+                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                          "frac": FLOP_PER_PARTICLE_PASS * P / (iter_avg_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                          "flop_per_particle_pass": FLOP_PER_PARTICLE_PASS,
+                          "peak_from": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"},
         "step_breakdown_ms": step_breakdown(prof),
         "momentum_check": {"P_drift_rel": drift,
                            "multibody_nodes": int(sum(x["multibody_nodes"] for x in st)),
@@ -471,8 +488,9 @@ def main():
                            "work_items": int(sum(x["work_items"] for x in st))},
         "clocks": ck,
     }
-    line["node_normals"] = bench_node_normals(apic, ctx, dev, stream, flush)
-    line["augury_dynamics"] = bench_augury(apic, ctx, dev, stream)
+    if not args.no_extras:
+        line["node_normals"] = bench_node_normals(apic, ctx, dev, stream, flush)
+        line["augury_dynamics"] = bench_augury(apic, ctx, dev, stream)
     if plain is not None:
         line["plain_single_scene"] = {"value": plain, "unit": UNIT,
                                       "what": "the same scenes, one apic_contact_step call each",
