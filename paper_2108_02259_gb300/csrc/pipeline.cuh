@@ -205,6 +205,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
 
   // Scene table: particle offsets, caller pointers (staged for host arrays).
   SceneDev* hsc = env.host_scenes(ns);
+  if (!hsc) return pfail(APIC_ERR_OUT_OF_MEMORY, "no host staging for a table of %d scenes", ns);
   int64_t n = 0;
   int max_bodies = 1, n_mu = 0;
   bool any_mu = false;
