@@ -141,3 +141,31 @@ def test_batched_rejects_mixed_flags(ctx):
     rc = lib.apic_contact_step_batched(ctx.handle, arr, 2, None, None)
     assert rc == apic.APIC_ERR_INVALID_ARG
     assert b"n_iter" in lib.apic_last_error()
+
+
+def test_batched_calls_with_changing_membership_and_inputs(ctx):
+    """Consecutive batched calls whose membership changes (all scenes, a
+    subset, all again ...) and whose velocities change every call: each
+    scene's result matches the oracle for that call's inputs, through graph
+    captures, replays and re-captures."""
+    import torch
+
+    from paper_2108_02259_gb300 import apic
+
+    sc = _mixed_batch()
+    dev = [_dev(s, np.float32) for s in sc]
+    plan = [range(6), range(6), [0, 2, 4], [0, 2, 4], [0, 2, 4], range(6), range(6), range(6)]
+    for k, members in enumerate(plan):
+        scale = 1.0 + 0.1 * k
+        bs, used = [], []
+        for i in members:
+            X, V, Cc, M, NR, B = dev[i]
+            s = sc[i]
+            bs.append(apic.BatchScene(X, V * scale, Cc * scale, M, NR, B, s.h, s.mu, n_bodies=s.n_bodies))
+            used.append(scenes.Scene(**{**s.__dict__, "v": s.v * scale, "C": s.C * scale}))
+        apic.contact_step_batched(ctx, bs, 3)
+        torch.cuda.synchronize()
+        for s, b in zip(used, bs):
+            _check(s, b.v_out.cpu().double().numpy(), b.C_out.cpu().double().numpy().reshape(-1, 3, 3), None,
+                   label=f"call {k}")
+    assert ctx.profile()["graph_launches"] > 0

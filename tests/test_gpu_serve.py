@@ -157,3 +157,44 @@ def test_wait_timeout_and_poll(apic):
         srv.wait(ts[-1], 120.0)
         done, lat = srv.poll(ts[0])
         assert done and lat > 0
+
+
+def test_mixed_precisions_variants_and_iterations(apic):
+    """One server, simulations that must never share a batch (FP64 and FP32,
+    PIC, the Sec. 2.3 rule, different N) and one with a body-pair friction
+    table, submitted interleaved: each matches the oracle stepped alone."""
+    rng = np.random.default_rng(7)
+    PIC, SEP23 = apic.APIC_VARIANT_PIC, apic.APIC_VARIANT_SEP23
+    cases = []
+    for k, (dt, flags, n_iter) in enumerate([(np.float64, 0, 3), (np.float32, 0, 3), (np.float32, PIC, 3),
+                                             (np.float32, SEP23, 2), (np.float32, 0, 5), (np.float64, PIC, 1)]):
+        s = scenes.multi_body_scene(rng, int(rng.integers(800, 2500)), 3, 1 / 64, mu=0.3, n_iter=n_iter)
+        mp = None
+        if k == 4:
+            a = rng.uniform(0.1, 0.5, (3, 3))
+            mp = (a + a.T) / 2
+        cases.append((s, dt, flags, mp))
+    with apic.Server(0, n_workers=2, max_batch_scenes=8) as srv:
+        hs = []
+        for s, dt, flags, mp in cases:
+            f = s.astype(dt)
+            hs.append(srv.open_sim(f.x, f.v, f.C, f.m, f.nrm, f.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
+                                   mu_pair=mp, flags=flags))
+        tickets = [h.submit(0.0) for _ in range(2) for h in hs]
+        for t in tickets:
+            srv.wait(t, 60.0)
+        assert srv.stats()["failed"] == 0
+        oflag = {0: 0, PIC: oracle.FLAG_PIC, SEP23: oracle.FLAG_SEP23}
+        for (s, dt, flags, mp), h in zip(cases, hs):
+            v, Cm = s.v.copy(), s.C.copy()
+            for _ in range(2):
+                v, Cm, _ = oracle.contact_step(s.x, v, Cm, s.m, s.nrm, s.body, s.h, s.mu, s.n_iter,
+                                               n_bodies=s.n_bodies, mu_pair=mp, flags=oflag[flags])
+            x, gv, gC = h.read()
+            vs = np.abs(s.v).max()
+            cs = max(np.abs(Cm).max(), np.abs(s.C).max(), 2 * vs / s.h)
+            tol = (1e-11, 1e-11) if dt == np.float64 else (3 * TOL_V, TOL_C)
+            assert np.abs(gv - v).max() <= tol[0] * vs, (dt, flags, s.n_iter)
+            assert np.abs(gC.reshape(-1, 9) - Cm.reshape(-1, 9)).max() <= tol[1] * cs, (dt, flags, s.n_iter)
+            assert np.all(x == s.x)  # dt_advect = 0
+            h.close()
