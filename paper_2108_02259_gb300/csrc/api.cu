@@ -538,9 +538,11 @@ int32_t apic_variant_count(void) { return kNumVariants; }
 
 const char* apic_variant_name(int32_t v) {
   static const char* names[kNumVariants] = {
-      "128 threads/CTA, 8 CTAs/SM (64 registers)",
-      "128 threads/CTA, 9 CTAs/SM (56 registers)",
-      "128 threads/CTA, 7 CTAs/SM (72 registers)",
+      "128 threads/CTA, items <= 128, 8 CTAs/SM (64 registers)",
+      "128 threads/CTA, items <= 128, 9 CTAs/SM (56 registers)",
+      "128 threads/CTA, items <= 128, 7 CTAs/SM (72 registers)",
+      "64 threads/CTA, items <= 64, 13 CTAs/SM (72 registers)",
+      "64 threads/CTA, items <= 64, 16 CTAs/SM (64 registers, 13 resident by shared memory)",
   };
   return v >= 0 && v < kNumVariants ? names[v] : "";
 }

@@ -20,7 +20,8 @@ constexpr int kBlk = 4;
 constexpr int kTile = 7;
 constexpr int kTile3 = kTile * kTile * kTile;
 constexpr int kNodesPerBlock = kBlk * kBlk * kBlk;
-// A work item holds at most kChunk particles (one per thread of its CTA).
+// A work item holds at most kChunk particles (one per thread of its CTA);
+// kernel variants may use smaller CTAs and items (kVariantChunk).
 #ifndef APIC_CHUNK
 #define APIC_CHUNK 128
 #endif
@@ -129,9 +130,9 @@ cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm
 template <class K>
 cudaError_t launch_heads(int64_t n, const K* keys, int* flags, cudaStream_t s);
 // Item heads: runs (from their flags, exclusive offsets and compacted starts)
-// split into ceil(len / kChunk) equal items.
+// split into ceil(len / chunk) equal items (16 <= chunk <= kChunk).
 cudaError_t launch_item_heads(int64_t n, const int* run_flags, const int* run_offs, const int* run_start,
-                              const int* n_runs, int* flags, cudaStream_t s);
+                              const int* n_runs, int chunk, int* flags, cudaStream_t s);
 template <class K>
 cudaError_t launch_item_info(const int* item_start, const int* n_items, const K* keys, int max_bodies,
                              const SceneDev* sc, int ns, int4* item_info, int max_items, cudaStream_t s);
@@ -140,12 +141,13 @@ cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* li
 template <class K>
 cudaError_t launch_mark_items(const int* item_start, const int4* item_info, const int* n_items, const K* keys,
                               int64_t n, int max_items, const SceneDev* sc, int* flags, cudaStream_t s);
-// Variants of the fused transfer kernel: resident CTAs per SM it is
-// compiled for (its register cap: 8 -> 64, 9 -> 56, 7 -> 72 registers).
-// Variant 0 is the default; the FP32 path exists in all of them, the FP64
-// path in variant 0 only (other variants fall back to it).
-constexpr int kNumVariants = 3;
-constexpr int kVariantMinBlocks[kNumVariants] = {8, 9, 7};
+// Variants of the fused transfer kernel: CTA size (= the largest work item)
+// and resident CTAs per SM it is compiled for (its register cap).  Variant 0
+// is the default; the FP32 path exists in all of them, the FP64 path in
+// variant 0 only (which it always uses).
+constexpr int kNumVariants = 5;
+constexpr int kVariantChunk[kNumVariants] = {128, 128, 128, 64, 64};
+constexpr int kVariantMinBlocks[kNumVariants] = {8, 9, 7, 13, 16};
 template <class T>
 cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, cudaStream_t s);
 // all64: take every node's momentum from the FP64 accumulators (after kModeMassV).

@@ -255,7 +255,6 @@ __device__ __forceinline__ void flush_mom(double*, V4<double>* gp, V4<double>*, 
 
 // Stash rows of particle j are padded by one slot every 16 particles, so the
 // two half-warps of a warp (16 particles apart) read different banks.
-constexpr int kStashN = kChunk + kChunk / 16;
 __device__ __forceinline__ int sidx(int j) { return j + (j >> 4); }
 
 // Phase-2 register accumulators of one lane: nodes kx = 0..3 of its stencil
@@ -308,8 +307,8 @@ struct RowAcc<float, K> {
   }
 };
 
-// One work item = up to kChunk sorted particles of one body whose cells lie
-// in one grid block.  A CTA of kChunk threads runs it in two phases:
+// One work item = up to CHUNK sorted particles of one body whose cells lie
+// in one grid block.  A CTA of CHUNK threads runs it in two phases:
 //
 //  phase 1, one thread per particle (lanes sorted by cell, so neighbouring
 //    lanes read the same tile nodes): G2P from the 7^3-node shared tile of
@@ -324,10 +323,12 @@ struct RowAcc<float, K> {
 // The shared P2G tile is then added to the global grid (FP64 at nodes that
 // two or more bodies touch, on the FP32 path).
 //
-// MINB is the number of resident CTAs per SM the kernel is compiled for
-// (its register cap); the autotuner picks among kVariantMinBlocks.
-template <class T, int MODE, int MINB>
-__global__ void __launch_bounds__(kChunk, MINB) k_items(const IterParams<T> p) {
+// CHUNK is the CTA size (and the largest item), MINB the number of resident
+// CTAs per SM the kernel is compiled for (its register cap); the autotuner
+// picks among the (kVariantChunk, kVariantMinBlocks) pairs.
+template <class T, int MODE, int MINB, int CHUNK>
+__global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
+  constexpr int kStashN = CHUNK + CHUNK / 16;
   constexpr bool kG2P = MODE == kModeFirst || MODE == kModeMid || MODE == kModeLast || MODE == kModeOnly;
   constexpr bool kP2G = MODE == kModeMass || MODE == kModeP2GV || MODE == kModeMassV || MODE == kModeFirst ||
                         MODE == kModeMid;
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(kChunk, MINB) k_items(const IterParams<T> p) {
   __shared__ uint32_t smask[MODE == kModeMu ? kTile3 : 1];
   __shared__ T sacc[kP2G ? kComp : 1][kTile3];
   __shared__ V4<T> stash[kP2G ? 6 : 1][kP2G ? kStashN : 1];
-  __shared__ int sloc[kChunk];
+  __shared__ int sloc[CHUNK];
   __shared__ int snb[27];
   const int tid = threadIdx.x;
   const int n = p.n_particles;
@@ -355,7 +356,7 @@ __global__ void __launch_bounds__(kChunk, MINB) k_items(const IterParams<T> p) {
   const int body = info.y;
   const int s0 = p.item_start[item];
   const int s1 = item + 1 < p.n_items ? p.item_start[item + 1] : n;
-  const int count = s1 - s0;  // <= kChunk
+  const int count = s1 - s0;  // <= CHUNK
   // Particles are sorted by cell (z-major) inside an item, so its stencils
   // reach only tile layers c in [lz(first), lz(last) + 3]: fetch, clear and
   // flush just those.
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(kChunk, MINB) k_items(const IterParams<T> p) {
     snb[tid] = p.page[page_off + ((bz + oz) * box.ny + (by + oy)) * box.nx + (bx + ox)];
   }
   if (kP2G)
-    for (int t = t_lo + tid; t < t_hi; t += kChunk)
+    for (int t = t_lo + tid; t < t_hi; t += CHUNK)
 #pragma unroll
       for (int a = 0; a < kComp; ++a) sacc[a][t] = T(0);
   __syncthreads();
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(kChunk, MINB) k_items(const IterParams<T> p) {
       // global -> shared without staging in registers (cp.async, 16 bytes:
       // V4<float> is 16-byte aligned in both spaces); all of this thread's
       // copies are in flight together
-      for (int t = t_lo + tid; t < t_hi; t += kChunk) {
+      for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
         const int node = tile_node(snb, t);
         if (node >= 0) {
           const unsigned dst = (unsigned)__cvta_generic_to_shared(&sv[t]);
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(kChunk, MINB) k_items(const IterParams<T> p) {
       }
       asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
     } else {
-      for (int t = t_lo + tid; t < t_hi; t += kChunk) {
+      for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
         const int node = tile_node(snb, t);
         sv[t] = node >= 0 ? p.gv[node] : V4<T>{T(0), T(0), T(0), T(0)};
       }
@@ -410,7 +411,7 @@ __global__ void __launch_bounds__(kChunk, MINB) k_items(const IterParams<T> p) {
     __syncthreads();
   }
   if (MODE == kModeMu) {
-    for (int t = t_lo + tid; t < t_hi; t += kChunk) {
+    for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
       const int node = tile_node(snb, t);
       smask[t] = node >= 0 ? p.gmask[node] : 0u;
     }
@@ -602,7 +603,7 @@ __global__ void __launch_bounds__(kChunk, MINB) k_items(const IterParams<T> p) {
   __syncthreads();
 
   // ---------------- add the tile to the global grid ----------------
-  for (int t = t_lo + tid; t < t_hi; t += kChunk) {
+  for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
     const int node = tile_node(snb, t);
     if (node < 0) continue;
     if constexpr (kMass) {
@@ -843,16 +844,17 @@ __global__ void k_heads(int64_t n, const K* __restrict__ keys, int* flags) {
   flags[s] = (s == 0 || (keys[s] >> 6) != (keys[s - 1] >> 6)) ? 1 : 0;
 }
 
-// Work items: each run of len particles splits into ceil(len / kChunk)
+// Work items: each run of len particles splits into ceil(len / chunk)
 // items of equal size (within one), so no item is a short tail.
 __global__ void k_item_heads(int64_t n, const int* __restrict__ run_flags, const int* __restrict__ run_offs,
-                             const int* __restrict__ run_start, const int* __restrict__ n_runs, int* flags) {
+                             const int* __restrict__ run_start, const int* __restrict__ n_runs, int chunk,
+                             int* flags) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int r = run_offs[s] + run_flags[s] - 1;  // the run holding s
   const int64_t a = run_start[r];
   const int64_t b = r + 1 < *n_runs ? run_start[r + 1] : n;
-  const int64_t len = b - a, items = (len + kChunk - 1) / kChunk, off = s - a;
+  const int64_t len = b - a, items = (len + chunk - 1) / chunk, off = s - a;
   flags[s] = (off == 0 || (off * items) / len != ((off - 1) * items) / len) ? 1 : 0;
 }
 
@@ -1023,9 +1025,10 @@ cudaError_t launch_heads(int64_t n, const K* keys, int* flags, cudaStream_t s) {
 }
 
 cudaError_t launch_item_heads(int64_t n, const int* run_flags, const int* run_offs, const int* run_start,
-                              const int* n_runs, int* flags, cudaStream_t s) {
+                              const int* n_runs, int chunk, int* flags, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_item_heads<<<grid_for(n, 256), 256, 0, s>>>(n, run_flags, run_offs, run_start, n_runs, flags);
+  if (chunk < 16 || chunk > kChunk) return cudaErrorInvalidValue;
+  k_item_heads<<<grid_for(n, 256), 256, 0, s>>>(n, run_flags, run_offs, run_start, n_runs, chunk, flags);
   return cudaGetLastError();
 }
 
@@ -1055,18 +1058,18 @@ cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* li
   return cudaGetLastError();
 }
 
-template <class T, int MINB>
-cudaError_t launch_items_minb(const IterParams<T>& p, int mode, cudaStream_t s) {
+template <class T, int MINB, int CHUNK>
+cudaError_t launch_items_cfg(const IterParams<T>& p, int mode, cudaStream_t s) {
   const unsigned grid = (unsigned)p.n_items;
   switch (mode) {
-    case kModeMass: k_items<T, kModeMass, MINB><<<grid, kChunk, 0, s>>>(p); break;
-    case kModeP2GV: k_items<T, kModeP2GV, MINB><<<grid, kChunk, 0, s>>>(p); break;
-    case kModeFirst: k_items<T, kModeFirst, MINB><<<grid, kChunk, 0, s>>>(p); break;
-    case kModeMid: k_items<T, kModeMid, MINB><<<grid, kChunk, 0, s>>>(p); break;
-    case kModeLast: k_items<T, kModeLast, MINB><<<grid, kChunk, 0, s>>>(p); break;
-    case kModeOnly: k_items<T, kModeOnly, MINB><<<grid, kChunk, 0, s>>>(p); break;
-    case kModeMu: k_items<T, kModeMu, MINB><<<grid, kChunk, 0, s>>>(p); break;
-    case kModeMassV: k_items<T, kModeMassV, MINB><<<grid, kChunk, 0, s>>>(p); break;
+    case kModeMass: k_items<T, kModeMass, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
+    case kModeP2GV: k_items<T, kModeP2GV, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
+    case kModeFirst: k_items<T, kModeFirst, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
+    case kModeMid: k_items<T, kModeMid, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
+    case kModeLast: k_items<T, kModeLast, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
+    case kModeOnly: k_items<T, kModeOnly, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
+    case kModeMu: k_items<T, kModeMu, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
+    case kModeMassV: k_items<T, kModeMassV, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1078,11 +1081,16 @@ cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, cudaStre
   if (variant < 0 || variant >= kNumVariants) return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 4) {
     // the FP32 path is built in every variant
-    if (variant == 1) return launch_items_minb<T, kVariantMinBlocks[1]>(p, mode, s);
-    if (variant == 2) return launch_items_minb<T, kVariantMinBlocks[2]>(p, mode, s);
+    switch (variant) {
+      case 1: return launch_items_cfg<T, kVariantMinBlocks[1], kVariantChunk[1]>(p, mode, s);
+      case 2: return launch_items_cfg<T, kVariantMinBlocks[2], kVariantChunk[2]>(p, mode, s);
+      case 3: return launch_items_cfg<T, kVariantMinBlocks[3], kVariantChunk[3]>(p, mode, s);
+      case 4: return launch_items_cfg<T, kVariantMinBlocks[4], kVariantChunk[4]>(p, mode, s);
+      default: break;
+    }
   }
   // the FP64 path (parity and small scenes) only in variant 0
-  return launch_items_minb<T, kVariantMinBlocks[0]>(p, mode, s);
+  return launch_items_cfg<T, kVariantMinBlocks[0], kVariantChunk[0]>(p, mode, s);
 }
 
 template <class T>

@@ -6,7 +6,7 @@
 //   2. per-scene page-table boxes laid end to end          (host, or reused)
 //   3. keys and one radix sort over all scenes              (k_keys, CUB)
 //   4. sorted SoA planes                                    (k_gather)
-//   5. work items of <= kChunk particles of one (block, body)
+//   5. work items of <= chunk particles of one (block, body)
 //   6. active blocks and the page table                     (k_mark_items, scan, k_compact)
 //   7. mass, body mask and P2G(V); optional friction blend; normalise
 //   8. N + 1 fused transfer passes (Sec. 2.3 series, Sec. 2.4 projection)
@@ -275,6 +275,11 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     }
   }
 
+  // Kernel variant of this call (the autotuner's choice, or a variant it is
+  // timing): its CTA size is also the largest work item the sizing makes.
+  const int variant = env.variant(sizeof(T), n);
+  const int chunk = kVariantChunk[sizeof(T) == 4 ? variant : 0];
+
   DevScalars* ds = env.ds();
   DevScalars* hs = env.hs();
   SceneDev* sc;
@@ -307,14 +312,14 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     // 4. sorted SoA.
     P_LAUNCH(env, launch_gather<T>(n, sc, ns, sb.perm, cellb, pt, pn, V, q));
     // 5. work items: runs of equal (grid block, body), each split into
-    //    equal items of at most kChunk particles.
+    //    equal items of at most `chunk` particles (the variant's CTA size).
     if (sb.k64)
       P_LAUNCH(env, launch_heads<uint64_t>(n, static_cast<const uint64_t*>(sb.kb), sb.run_flags, q));
     else
       P_LAUNCH(env, launch_heads<uint32_t>(n, static_cast<const uint32_t*>(sb.kb), sb.run_flags, q));
     P_TRY(exclusive_sum(env, sb, sb.tmp_scan_n, sb.run_flags, sb.run_offs, n, q));
     P_LAUNCH(env, launch_compact(n, sb.run_flags, sb.run_offs, sb.run_start, nullptr, &ds->n_runs, q));
-    P_LAUNCH(env, launch_item_heads(n, sb.run_flags, sb.run_offs, sb.run_start, &ds->n_runs, sb.heads, q));
+    P_LAUNCH(env, launch_item_heads(n, sb.run_flags, sb.run_offs, sb.run_start, &ds->n_runs, chunk, sb.heads, q));
     P_TRY(exclusive_sum(env, sb, sb.tmp_scan_n, sb.heads, sb.offs, n, q));
     P_LAUNCH(env, launch_compact(n, sb.heads, sb.offs, sb.item_start, nullptr, &ds->n_items, q));
     if (sb.k64)
@@ -356,9 +361,10 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       }
       struct SizingKey {
         int64_t n, NB;
-        int ns, max_bodies, tsize, host;
+        int ns, max_bodies, tsize, host, chunk, pad;
       } key;
       std::memset(&key, 0, sizeof(key));
+      key.chunk = chunk;
       key.n = n;
       key.NB = NB;
       key.ns = ns;
@@ -503,7 +509,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   key.mup = mup;
   key.n_iter = N;
   key.any_mu = any_mu ? 1 : 0;
-  key.variant = env.variant(sizeof(T), n);
+  key.variant = variant;
 
   auto series = [&](cudaStream_t q) -> apic_status {
     IterParams<T> pp = key.p;
