@@ -373,7 +373,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       key.host = host ? 1 : 0;
       P_TRY(plan_sizing(env, n, NB, max_bodies, sb));
       auto body = [&](cudaStream_t q) -> apic_status { return sizing(q, true); };
-      P_TRY(env.run_sizing(&key, sizeof(key), !host, s, body));
+      P_TRY(env.run_sizing(&key, sizeof(key), true, s, body));
     } else {
       for (int i = 0; i < ns; ++i) {
         int* b = hbbox + 6 * i;
