@@ -239,11 +239,15 @@ apic_status apic_sim_open(apic_server* srv, const apic_step_args* init, apic_sim
 apic_status apic_sim_submit(apic_sim* sim, double dt_advect, uint64_t* ticket);
 
 /* Has the request finished?  done = 1 and its latency (submit -> completion)
- * when it has; returns the request's own error status if it failed. */
+ * when it has; returns the request's own error status if it failed.  A
+ * finished request is forgotten once reported (here or by apic_ticket_wait),
+ * and when its simulation closes: later queries of it return
+ * APIC_ERR_INVALID_ARG ("unknown ticket"). */
 apic_status apic_ticket_poll(apic_server* srv, uint64_t ticket, int32_t* done, double* latency_ms);
 
 /* Wait at most timeout_s seconds for the request; APIC_ERR_TIMEOUT if it has
- * not finished by then. */
+ * not finished by then (the request stays known).  Once it returns after the
+ * request finished, the ticket is forgotten, as for apic_ticket_poll. */
 apic_status apic_ticket_wait(apic_server* srv, uint64_t ticket, double timeout_s, double* latency_ms);
 
 /* Copy the simulation's current state to HOST memory (each pointer may be
@@ -254,7 +258,8 @@ apic_status apic_sim_read(apic_sim* sim, double* x_out, void* v_out, void* C_out
 /* Wait for the simulation's steps, then free its resident state. */
 apic_status apic_sim_close(apic_sim* sim);
 
-/* Counters and latency percentiles since creation (or the last reset). */
+/* Counters and latency percentiles since creation (or the last reset); the
+ * percentiles cover at most the last 2^20 completed requests. */
 apic_status apic_server_get_stats(apic_server* srv, apic_server_stats* out, int32_t reset);
 
 /* Turn kernel timing on (1) or off (0) and reset the counters. */

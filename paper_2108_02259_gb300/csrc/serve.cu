@@ -14,6 +14,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <iterator>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -31,6 +32,9 @@ namespace {
 // estimate (sort keys and values, sorted planes, Delta, item tables and the
 // grid share; FP32 path).
 constexpr size_t kScratchPerParticle = 640;
+
+// Latency samples kept for the percentiles (the most recent ones).
+constexpr size_t kMaxLatencySamples = size_t(1) << 20;
 
 apic_status sfail(apic_status code, const char* msg) {
   apic::set_last_error(msg);
@@ -217,6 +221,8 @@ void worker_main(apic_server* srv, int wid) {
         if (st == APIC_OK) {
           srv->completed += 1;
           srv->particle_iters += tk.sim->n * (int64_t)(tk.sim->n_iter + 1);
+          if (srv->lat_ms.size() >= kMaxLatencySamples)  // keep the most recent half
+            srv->lat_ms.erase(srv->lat_ms.begin(), srv->lat_ms.begin() + kMaxLatencySamples / 2);
           srv->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - tk.t_submit).count());
         } else {
           srv->failed += 1;
@@ -388,9 +394,12 @@ apic_status apic_ticket_poll(apic_server* srv, uint64_t ticket, int32_t* done, d
   auto it = srv->tickets.find(ticket);
   if (it == srv->tickets.end()) return sfail(APIC_ERR_INVALID_ARG, "unknown ticket");
   *done = it->second.state == 2;
-  if (*done && latency_ms)
+  if (!*done) return APIC_OK;
+  if (latency_ms)
     *latency_ms = std::chrono::duration<double, std::milli>(it->second.t_done - it->second.t_submit).count();
-  if (*done && it->second.status != APIC_OK) return sfail(it->second.status, "the request failed");
+  const apic_status st = it->second.status;
+  srv->tickets.erase(it);  // reported: forgotten
+  if (st != APIC_OK) return sfail(st, "the request failed");
   return APIC_OK;
 }
 
@@ -403,9 +412,12 @@ apic_status apic_ticket_wait(apic_server* srv, uint64_t ticket, double timeout_s
                                         std::chrono::duration<double>(std::max(0.0, timeout_s)));
   if (!srv->cv_done.wait_until(lk, limit, [&] { return srv->tickets[ticket].state == 2; }))
     return sfail(APIC_ERR_TIMEOUT, "the request did not finish in time");
-  const Ticket& tk = srv->tickets[ticket];
-  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(tk.t_done - tk.t_submit).count();
-  if (tk.status != APIC_OK) return sfail(tk.status, "the request failed");
+  auto done = srv->tickets.find(ticket);
+  if (latency_ms)
+    *latency_ms = std::chrono::duration<double, std::milli>(done->second.t_done - done->second.t_submit).count();
+  const apic_status st = done->second.status;
+  srv->tickets.erase(done);  // reported: forgotten
+  if (st != APIC_OK) return sfail(st, "the request failed");
   return APIC_OK;
 }
 
@@ -433,8 +445,8 @@ apic_status apic_sim_close(apic_sim* s) {
     srv->resident -= s->bytes;
     srv->open -= 1;
     srv->sims.erase(s);
-    for (auto& kv : srv->tickets)
-      if (kv.second.sim == s) kv.second.sim = nullptr;
+    for (auto it = srv->tickets.begin(); it != srv->tickets.end();)  // its requests are all done
+      it = it->second.sim == s ? srv->tickets.erase(it) : std::next(it);
   }
   cudaSetDevice(srv->device);
   free_sim_memory(s);

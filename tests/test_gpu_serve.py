@@ -157,6 +157,17 @@ def test_wait_timeout_and_poll(apic):
         srv.wait(ts[-1], 120.0)
         done, lat = srv.poll(ts[0])
         assert done and lat > 0
+        # a reported ticket is forgotten
+        for t in (ts[0], ts[-1]):
+            with pytest.raises(apic.ApicError) as e:
+                srv.poll(t)
+            assert e.value.code == apic.APIC_ERR_INVALID_ARG
+        # the others are still known until their simulation closes
+        assert srv.poll(ts[5])[0]
+        assert srv.wait(ts[6], 1.0) > 0
+        a.close()
+        with pytest.raises(apic.ApicError):
+            srv.poll(ts[7])
 
 
 def test_mixed_precisions_variants_and_iterations(apic):
