@@ -255,6 +255,19 @@ apic_status apic_ticket_wait(apic_server* srv, uint64_t ticket, double timeout_s
  * Waits for its queued and running steps first. */
 apic_status apic_sim_read(apic_sim* sim, double* x_out, void* v_out, void* C_out);
 
+/* Checkpoint: the simulation's whole state (positions, body ids, v, C, masses,
+ * normals, h, mu, mu_pair, n_iter, flags) into a HOST buffer, after its queued
+ * and running steps.  With host_buf NULL, *bytes receives the size needed;
+ * otherwise *bytes is the buffer's size on entry (APIC_ERR_INVALID_ARG if too
+ * small) and the size written on return.  The format is this library's own,
+ * in host byte order. */
+apic_status apic_sim_export(apic_sim* sim, void* host_buf, size_t* bytes);
+
+/* Resume: open a new simulation on srv from a checkpoint written by
+ * apic_sim_export (admission as apic_sim_open).  APIC_ERR_INVALID_ARG for a
+ * buffer that is not a complete checkpoint of this library. */
+apic_status apic_sim_import(apic_server* srv, const void* host_buf, size_t bytes, apic_sim** out);
+
 /* Wait for the simulation's steps, then free its resident state. */
 apic_status apic_sim_close(apic_sim* sim);
 

@@ -39,7 +39,8 @@ EXPORTED = [
     "apic_contact_step_batched", "apic_server_create", "apic_server_destroy", "apic_sim_open", "apic_sim_submit",
     "apic_ticket_poll", "apic_ticket_wait", "apic_sim_read", "apic_sim_close", "apic_server_get_stats",
     "apic_variant_count", "apic_variant_name", "apic_set_variant", "apic_get_variant", "apic_autotune",
-    "apic_set_graphs", "apic_server_set_policy", "apic_node_normals", "apic_augury_steps",
+    "apic_set_graphs", "apic_server_set_policy", "apic_node_normals", "apic_augury_steps", "apic_sim_export",
+    "apic_sim_import",
 ]
 
 
@@ -157,6 +158,10 @@ def load(path: str = LIB_PATH):
     lib.apic_node_normals.restype = C.c_int32
     lib.apic_augury_steps.argtypes = [P, C.POINTER(AuguryArgs), C.c_int32, P, C.POINTER(AuguryStats)]
     lib.apic_augury_steps.restype = C.c_int32
+    lib.apic_sim_export.argtypes = [P, P, C.POINTER(C.c_size_t)]
+    lib.apic_sim_export.restype = C.c_int32
+    lib.apic_sim_import.argtypes = [P, P, C.c_size_t, C.POINTER(P)]
+    lib.apic_sim_import.restype = C.c_int32
     lib.apic_server_set_policy.restype = C.c_int32
     for f in ("apic_create", "apic_destroy", "apic_contact_step", "apic_set_profiling", "apic_get_profile",
               "apic_scratch_bytes", "apic_set_variant", "apic_get_variant", "apic_autotune", "apic_set_graphs"):
@@ -518,6 +523,15 @@ class Server:
         _check(load().apic_ticket_wait(self._h, int(ticket), float(timeout_s), C.byref(lat)))
         return lat.value
 
+    def import_sim(self, checkpoint: bytes):
+        """apic_sim_import: a new simulation resumed from Sim.export()."""
+        import struct
+
+        h = C.c_void_p()
+        _check(load().apic_sim_import(self._h, checkpoint, len(checkpoint), C.byref(h)))
+        _magic, _version, flags, n = struct.unpack_from("<8sIIq", checkpoint, 0)  # validated by the library
+        return Sim._adopt(self, h, int(n), np.float64 if flags & APIC_FP64 else np.float32)
+
     def set_policy(self, variant: int = -1, graphs: bool = True):
         """Launch policy of the worker contexts (see apic_server_set_policy)."""
         _check(load().apic_server_set_policy(self._h, int(variant), 1 if graphs else 0))
@@ -557,6 +571,21 @@ class Sim:
         hsim = C.c_void_p()
         _check(lib.apic_sim_open(srv.handle, C.byref(a), C.byref(hsim)))
         self._h = hsim
+
+    @classmethod
+    def _adopt(cls, srv, handle, n, dtype):
+        self = cls.__new__(cls)
+        self.srv, self._h, self.n, self.dtype = srv, handle, n, dtype
+        return self
+
+    def export(self) -> bytes:
+        """apic_sim_export: a checkpoint of the whole state, as bytes."""
+        lib = load()
+        size = C.c_size_t()
+        _check(lib.apic_sim_export(self._h, None, C.byref(size)))
+        buf = C.create_string_buffer(size.value)
+        _check(lib.apic_sim_export(self._h, buf, C.byref(size)))
+        return buf.raw[: size.value]
 
     def submit(self, dt_advect: float = 0.0) -> int:
         t = C.c_uint64()

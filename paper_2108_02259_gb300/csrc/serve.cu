@@ -19,6 +19,7 @@
 #include <thread>
 #include <unordered_map>
 #include <unordered_set>
+#include <utility>
 #include <vector>
 
 #include "../../include/apiccontact.h"
@@ -434,6 +435,111 @@ apic_status apic_sim_read(apic_sim* s, double* x_out, void* v_out, void* C_out) 
   if (e == cudaSuccess && C_out) e = cudaMemcpy(C_out, s->C, 9 * n * s->esize, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return sfail(APIC_ERR_CUDA, cudaGetErrorString(e));
   return APIC_OK;
+}
+
+namespace {
+
+// Checkpoint layout (host byte order): this header, then mu_pair
+// (n_bodies^2 doubles, when present), x (3n doubles), body (n int32), and v,
+// C, m, normals (3n, 9n, n, 3n values of esize bytes).
+struct SimCheckpoint {
+  char magic[8];
+  uint32_t version, flags;
+  int64_t n;
+  int32_t n_bodies, n_iter;
+  double h, mu;
+  int32_t has_mu_pair, esize;
+};
+constexpr char kCheckpointMagic[8] = {'A', 'P', 'I', 'C', 'S', 'I', 'M', '1'};
+
+size_t checkpoint_bytes(int64_t n, int32_t n_bodies, bool mu_pair, size_t es) {
+  return sizeof(SimCheckpoint) + (mu_pair ? sizeof(double) * n_bodies * n_bodies : 0) +
+         (size_t)n * (3 * sizeof(double) + sizeof(int32_t) + es * (3 + 9 + 1 + 3));
+}
+
+}  // namespace
+
+apic_status apic_sim_export(apic_sim* s, void* host_buf, size_t* bytes) {
+  if (!s || !bytes) return sfail(APIC_ERR_INVALID_ARG, "NULL argument");
+  const size_t need = checkpoint_bytes(s->n, s->n_bodies, !s->mu_pair.empty(), s->esize);
+  if (!host_buf) {
+    *bytes = need;
+    return APIC_OK;
+  }
+  if (*bytes < need) return sfail(APIC_ERR_INVALID_ARG, "checkpoint buffer too small (query the size first)");
+  apic_server* srv = s->srv;
+  std::unique_lock<std::mutex> lk(srv->mu);
+  wait_idle(srv, lk, s);
+  SimCheckpoint hd{};
+  std::memcpy(hd.magic, kCheckpointMagic, 8);
+  hd.version = 1;
+  hd.flags = s->flags;
+  hd.n = s->n;
+  hd.n_bodies = s->n_bodies;
+  hd.n_iter = s->n_iter;
+  hd.h = s->h;
+  hd.mu = s->mu;
+  hd.has_mu_pair = s->mu_pair.empty() ? 0 : 1;
+  hd.esize = (int32_t)s->esize;
+  char* o = static_cast<char*>(host_buf);
+  std::memcpy(o, &hd, sizeof(hd));
+  o += sizeof(hd);
+  if (hd.has_mu_pair) {
+    std::memcpy(o, s->mu_pair.data(), s->mu_pair.size() * sizeof(double));
+    o += s->mu_pair.size() * sizeof(double);
+  }
+  const size_t n = (size_t)s->n, es = s->esize;
+  cudaSetDevice(srv->device);
+  const std::pair<const void*, size_t> parts[] = {{s->x, 3 * n * sizeof(double)}, {s->body, n * sizeof(int32_t)},
+                                                  {s->v, 3 * n * es}, {s->C, 9 * n * es}, {s->m, n * es},
+                                                  {s->nrm, 3 * n * es}};
+  for (const auto& pt : parts) {
+    const cudaError_t e = cudaMemcpy(o, pt.first, pt.second, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return sfail(APIC_ERR_CUDA, cudaGetErrorString(e));
+    o += pt.second;
+  }
+  *bytes = need;
+  return APIC_OK;
+}
+
+apic_status apic_sim_import(apic_server* srv, const void* host_buf, size_t bytes, apic_sim** out) {
+  if (!srv || !host_buf || !out) return sfail(APIC_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  SimCheckpoint hd{};
+  if (bytes < sizeof(hd)) return sfail(APIC_ERR_INVALID_ARG, "not a checkpoint (too short)");
+  std::memcpy(&hd, host_buf, sizeof(hd));
+  if (std::memcmp(hd.magic, kCheckpointMagic, 8) != 0 || hd.version != 1)
+    return sfail(APIC_ERR_INVALID_ARG, "not a checkpoint of this library (magic or version)");
+  if (hd.n <= 0 || hd.n > (int64_t)INT32_MAX / 4 || hd.n_bodies < 1 || hd.n_bodies > 32 ||
+      (hd.esize != 4 && hd.esize != 8) || (hd.esize == 8) != ((hd.flags & APIC_FP64) != 0))
+    return sfail(APIC_ERR_INVALID_ARG, "corrupt checkpoint header");
+  if (bytes < checkpoint_bytes(hd.n, hd.n_bodies, hd.has_mu_pair != 0, (size_t)hd.esize))
+    return sfail(APIC_ERR_INVALID_ARG, "checkpoint truncated");
+  const char* p = static_cast<const char*>(host_buf) + sizeof(hd);
+  apic_step_args a{};
+  a.n = hd.n;
+  a.n_bodies = hd.n_bodies;
+  a.n_iter = hd.n_iter;
+  a.h = hd.h;
+  a.mu = hd.mu;
+  a.flags = hd.flags | APIC_HOST_PTRS;
+  if (hd.has_mu_pair) {
+    a.mu_pair = reinterpret_cast<const double*>(p);
+    p += sizeof(double) * hd.n_bodies * hd.n_bodies;
+  }
+  const size_t n = (size_t)hd.n, es = (size_t)hd.esize;
+  a.x = reinterpret_cast<const double*>(p);
+  p += 3 * n * sizeof(double);
+  a.body = reinterpret_cast<const int32_t*>(p);
+  p += n * sizeof(int32_t);
+  a.v = const_cast<char*>(p);
+  p += 3 * n * es;
+  a.C = const_cast<char*>(p);
+  p += 9 * n * es;
+  a.m = p;
+  p += n * es;
+  a.nrm = p;
+  return apic_sim_open(srv, &a, out);
 }
 
 apic_status apic_sim_close(apic_sim* s) {

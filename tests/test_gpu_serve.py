@@ -209,3 +209,42 @@ def test_mixed_precisions_variants_and_iterations(apic):
             assert np.abs(gC.reshape(-1, 9) - Cm.reshape(-1, 9)).max() <= tol[1] * cs, (dt, flags, s.n_iter)
             assert np.all(x == s.x)  # dt_advect = 0
             h.close()
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+def test_checkpoint_and_resume(apic, dt):
+    """A simulation exported after two steps, closed, and imported again
+    continues like one that was never interrupted; broken checkpoints are
+    refused."""
+    rng = np.random.default_rng(11)
+    s = scenes.multi_body_scene(rng, 2000, 3, 1 / 64, mu=0.3, n_iter=3)
+    a = rng.uniform(0.1, 0.5, (3, 3))
+    mp = (a + a.T) / 2
+    f = s.astype(dt)
+    step_dt = 0.1 * s.h / np.abs(s.v).max()
+    with apic.Server(0, n_workers=1) as srv:
+        ref = srv.open_sim(f.x, f.v, f.C, f.m, f.nrm, f.body, s.h, s.mu, s.n_iter, n_bodies=3, mu_pair=mp)
+        sim = srv.open_sim(f.x, f.v, f.C, f.m, f.nrm, f.body, s.h, s.mu, s.n_iter, n_bodies=3, mu_pair=mp)
+        for t in [ref.submit(step_dt) for _ in range(4)] + [sim.submit(step_dt) for _ in range(2)]:
+            srv.wait(t, 60.0)
+        ck = sim.export()
+        x2, v2, C2 = sim.read()
+        sim.close()
+        back = srv.import_sim(ck)
+        assert back.n == s.n and back.dtype == dt
+        x3, v3, C3 = back.read()
+        assert np.array_equal(x2, x3) and np.array_equal(v2, v3) and np.array_equal(C2, C3)
+        for t in [back.submit(step_dt) for _ in range(2)]:
+            srv.wait(t, 60.0)
+        xr, vr, Cr = ref.read()
+        xb, vb, Cb = back.read()
+        vs = np.abs(s.v).max()
+        tol = 1e-12 if dt == np.float64 else 3 * TOL_V
+        assert np.abs(vb - vr).max() <= tol * vs
+        assert np.abs(xb - xr).max() <= 4 * step_dt * tol * vs + 1e-15
+        for bad in (ck[:-1], b"NOTACKPT" + ck[8:], ck[:20]):
+            with pytest.raises(apic.ApicError) as e:
+                srv.import_sim(bad)
+            assert e.value.code == apic.APIC_ERR_INVALID_ARG
+        ref.close()
+        back.close()
