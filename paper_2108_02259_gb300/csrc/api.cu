@@ -39,6 +39,8 @@ struct apic_ctx {
   bool have_box = false;
   SceneDev* h_scenes = nullptr;  // pinned (a graph's copy node reads it)
   int h_scenes_cap = 0;
+  CopyEntry* h_copies = nullptr;  // pinned copy table (the copy kernel reads it)
+  int h_copies_cap = 0;
   std::vector<int> h_bbox;
   std::vector<char> h_buf;
   // profiling
@@ -198,6 +200,7 @@ struct CtxEnv {
   SceneDev* host_scenes(int ns) {
     if (ns > c->h_scenes_cap) {
       if (c->h_scenes) cudaFreeHost(c->h_scenes);
+  if (c->h_copies) cudaFreeHost(c->h_copies);
       c->h_scenes = nullptr;
       c->h_scenes_cap = 0;
       if (cudaMallocHost(&c->h_scenes, ns * sizeof(SceneDev)) != cudaSuccess) {
@@ -228,6 +231,31 @@ struct CtxEnv {
   void* host_buf(size_t bytes) {
     if (c->h_buf.size() < bytes) c->h_buf.resize(bytes);
     return c->h_buf.data();
+  }
+  // Pinned, device-visible table of n copy entries (nullptr if unavailable).
+  CopyEntry* copy_table(int n) {
+    if (n > c->h_copies_cap) {
+      if (c->h_copies) cudaFreeHost(c->h_copies);
+      c->h_copies = nullptr;
+      c->h_copies_cap = 0;
+      if (cudaMallocHost(&c->h_copies, (size_t)n * sizeof(CopyEntry)) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_copies = nullptr;
+        return nullptr;
+      }
+      c->h_copies_cap = n;
+    }
+    return c->h_copies;
+  }
+  // The device's address of a page-locked host array, or nullptr (pageable
+  // memory, device memory, or no mapping).
+  static const void* device_view(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
   }
   void launched() { c->prof.kernel_launches++; }
   void sorted() { c->prof.sort_launches++; }
@@ -439,6 +467,7 @@ apic_status apic_destroy(apic_ctx* c) {
   if (c->gsizing.exec) cudaGraphExecDestroy(c->gsizing.exec);
   if (c->gseries.exec) cudaGraphExecDestroy(c->gseries.exec);
   if (c->h_scenes) cudaFreeHost(c->h_scenes);
+  if (c->h_copies) cudaFreeHost(c->h_copies);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return APIC_OK;

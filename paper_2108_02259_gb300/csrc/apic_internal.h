@@ -193,6 +193,16 @@ cudaError_t launch_aug_energy(int64_t n, const double* x, const T* v, const T* m
                               const int32_t* springs, const double* rest, const double* k, double* out,
                               cudaStream_t s);
 
+// One copy of `bytes` bytes between device-visible addresses (device memory
+// or page-locked host memory seen through its device pointer).
+struct CopyEntry {
+  const void* src;
+  void* dst;
+  long long bytes;
+};
+// All copies of a table (itself device-visible) in one launch.
+cudaError_t launch_copy_table(const CopyEntry* table, int n_entries, long long max_bytes, cudaStream_t s);
+
 // Set the calling thread's message returned by apic_last_error().
 void set_last_error(const char* msg);
 

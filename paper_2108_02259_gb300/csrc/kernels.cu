@@ -1351,6 +1351,60 @@ cudaError_t launch_aug_energy(int64_t n, const double* x, const T* v, const T* m
   return cudaGetLastError();
 }
 
+// Table-driven copies (host staging of caller arrays in page-locked memory):
+// blockIdx.y picks the entry, the x-blocks stride over its bytes.  With
+// 4-byte granularity the copy moves 16-byte words whenever either end is
+// 16-byte aligned (that end, usually the host side of the link, gets whole
+// 16-byte accesses; the other is split into 4-byte ones), then a 4-byte tail;
+// otherwise bytes.
+__global__ void k_copy_table(const CopyEntry* __restrict__ table, int n_entries) {
+  const int e = blockIdx.y;
+  if (e >= n_entries) return;
+  const CopyEntry c = table[e];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const uintptr_t sa = (uintptr_t)c.src, da = (uintptr_t)c.dst;
+  if (((sa | da | (uintptr_t)c.bytes) & 3) == 0) {
+    const bool s16 = (sa & 15) == 0, d16 = (da & 15) == 0;
+    const uint32_t* src = static_cast<const uint32_t*>(c.src);
+    uint32_t* dst = static_cast<uint32_t*>(c.dst);
+    int64_t done_words = 0;
+    if (s16 || d16) {
+      const int64_t n16 = c.bytes / 16;
+      for (int64_t i = t0; i < n16; i += stride) {
+        uint4 w;
+        if (s16) {
+          w = static_cast<const uint4*>(c.src)[i];
+        } else {
+          w = make_uint4(src[4 * i], src[4 * i + 1], src[4 * i + 2], src[4 * i + 3]);
+        }
+        if (d16) {
+          static_cast<uint4*>(c.dst)[i] = w;
+        } else {
+          dst[4 * i] = w.x;
+          dst[4 * i + 1] = w.y;
+          dst[4 * i + 2] = w.z;
+          dst[4 * i + 3] = w.w;
+        }
+      }
+      done_words = 4 * n16;
+    }
+    for (int64_t i = done_words + t0; i < c.bytes / 4; i += stride) dst[i] = src[i];
+  } else {
+    const unsigned char* src = static_cast<const unsigned char*>(c.src);
+    unsigned char* dst = static_cast<unsigned char*>(c.dst);
+    for (int64_t i = t0; i < c.bytes; i += stride) dst[i] = src[i];
+  }
+}
+
+cudaError_t launch_copy_table(const CopyEntry* table, int n_entries, long long max_bytes, cudaStream_t s) {
+  if (n_entries <= 0 || max_bytes <= 0) return cudaSuccess;
+  if (n_entries > 65535) return cudaErrorInvalidValue;
+  const unsigned gx = (unsigned)std::min<long long>(std::max<long long>((max_bytes + 16383) / 16384, 1), 304);
+  k_copy_table<<<dim3(gx, (unsigned)n_entries), 256, 0, s>>>(table, n_entries);
+  return cudaGetLastError();
+}
+
 #define APIC_INST_T(T)                                                                                  \
   template cudaError_t launch_cells<T>(int64_t, const SceneDev*, int, int4*, int*, int*, cudaStream_t); \
   template cudaError_t launch_gather<T>(int64_t, const SceneDev*, int, const int*, const int4*, V4<T>*,  \

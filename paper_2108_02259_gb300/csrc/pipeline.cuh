@@ -25,6 +25,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <utility>
 
 #include "../../include/apiccontact.h"
 #include "apic_internal.h"
@@ -254,16 +255,45 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     P_TRY(env.take(kSlotHN, 3 * n, &dn, "staged normals"));
     P_TRY(env.take(kSlotHVo, 3 * n, &dvo, "staged v_out"));
     P_TRY(env.take(kSlotHCo, 9 * n, &dCo, "staged C_out"));
+    // Page-locked caller arrays are staged by one table-driven copy kernel
+    // (the host link is the limit either way, but per-copy overheads add up
+    // over many scenes); otherwise, or when a table is not available, one
+    // copy per array.
+    CopyEntry* tab = env.copy_table(8 * ns);
+    bool direct = tab != nullptr;
+    int nt = 0;
+    long long max_bytes = 0;
+    for (int i = 0; i < ns && direct; ++i) {
+      const apic_step_args& a = scenes[i];
+      const int64_t o = hsc[i].part_off, m = a.n;
+      if (m == 0) continue;
+      const std::pair<const void*, std::pair<void*, long long>> parts[6] = {
+          {a.x, {dx + 3 * o, 3 * m * (long long)sizeof(double)}}, {a.body, {db + o, m * (long long)sizeof(int32_t)}},
+          {a.v, {dv + 3 * o, 3 * m * (long long)sizeof(T)}},      {a.C, {dC + 9 * o, 9 * m * (long long)sizeof(T)}},
+          {a.m, {dm + o, m * (long long)sizeof(T)}},               {a.nrm, {dn + 3 * o, 3 * m * (long long)sizeof(T)}}};
+      for (const auto& pt : parts) {
+        const void* src = env.device_view(pt.first);
+        if (!src) {
+          direct = false;
+          break;
+        }
+        tab[nt++] = CopyEntry{src, pt.second.first, pt.second.second};
+        max_bytes = std::max(max_bytes, pt.second.second);
+      }
+    }
+    if (direct) P_LAUNCH(env, launch_copy_table(tab, nt, max_bytes, s));
     for (int i = 0; i < ns; ++i) {
       const apic_step_args& a = scenes[i];
       const int64_t o = hsc[i].part_off, m = a.n;
       if (m == 0) continue;
-      P_CUDA(cudaMemcpyAsync(dx + 3 * o, a.x, 3 * m * sizeof(double), cudaMemcpyHostToDevice, s));
-      P_CUDA(cudaMemcpyAsync(db + o, a.body, m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-      P_CUDA(cudaMemcpyAsync(dv + 3 * o, a.v, 3 * m * sizeof(T), cudaMemcpyHostToDevice, s));
-      P_CUDA(cudaMemcpyAsync(dC + 9 * o, a.C, 9 * m * sizeof(T), cudaMemcpyHostToDevice, s));
-      P_CUDA(cudaMemcpyAsync(dm + o, a.m, m * sizeof(T), cudaMemcpyHostToDevice, s));
-      P_CUDA(cudaMemcpyAsync(dn + 3 * o, a.nrm, 3 * m * sizeof(T), cudaMemcpyHostToDevice, s));
+      if (!direct) {
+        P_CUDA(cudaMemcpyAsync(dx + 3 * o, a.x, 3 * m * sizeof(double), cudaMemcpyHostToDevice, s));
+        P_CUDA(cudaMemcpyAsync(db + o, a.body, m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        P_CUDA(cudaMemcpyAsync(dv + 3 * o, a.v, 3 * m * sizeof(T), cudaMemcpyHostToDevice, s));
+        P_CUDA(cudaMemcpyAsync(dC + 9 * o, a.C, 9 * m * sizeof(T), cudaMemcpyHostToDevice, s));
+        P_CUDA(cudaMemcpyAsync(dm + o, a.m, m * sizeof(T), cudaMemcpyHostToDevice, s));
+        P_CUDA(cudaMemcpyAsync(dn + 3 * o, a.nrm, 3 * m * sizeof(T), cudaMemcpyHostToDevice, s));
+      }
       hsc[i].x = dx + 3 * o;
       hsc[i].body = db + o;
       hsc[i].v = dv + 3 * o;
@@ -579,11 +609,36 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     }
   }
   if (host) {
-    for (int i = 0; i < ns; ++i) {
+    // results back: one table-driven kernel into page-locked outputs (the
+    // table's last 2 ns entries; the input copies used the first ones and
+    // finished before the mid-step synchronisation), else one copy each
+    CopyEntry* tab = env.copy_table(8 * ns);
+    bool direct = tab != nullptr;
+    int nt = 0;
+    long long max_bytes = 0;
+    CopyEntry* out = direct ? tab + 6 * ns : nullptr;
+    for (int i = 0; i < ns && direct; ++i) {
       const apic_step_args& a = scenes[i];
       if (a.n == 0) continue;
-      P_CUDA(cudaMemcpyAsync(a.v_out, hsc[i].v_out, 3 * a.n * sizeof(T), cudaMemcpyDeviceToHost, s));
-      P_CUDA(cudaMemcpyAsync(a.C_out, hsc[i].C_out, 9 * a.n * sizeof(T), cudaMemcpyDeviceToHost, s));
+      void* dvo = const_cast<void*>(env.device_view(a.v_out));
+      void* dCo = const_cast<void*>(env.device_view(a.C_out));
+      if (!dvo || !dCo) {
+        direct = false;
+        break;
+      }
+      out[nt++] = CopyEntry{hsc[i].v_out, dvo, 3 * a.n * (long long)sizeof(T)};
+      out[nt++] = CopyEntry{hsc[i].C_out, dCo, 9 * a.n * (long long)sizeof(T)};
+      max_bytes = std::max(max_bytes, 9 * a.n * (long long)sizeof(T));
+    }
+    if (direct) {
+      P_LAUNCH(env, launch_copy_table(out, nt, max_bytes, s));
+    } else {
+      for (int i = 0; i < ns; ++i) {
+        const apic_step_args& a = scenes[i];
+        if (a.n == 0) continue;
+        P_CUDA(cudaMemcpyAsync(a.v_out, hsc[i].v_out, 3 * a.n * sizeof(T), cudaMemcpyDeviceToHost, s));
+        P_CUDA(cudaMemcpyAsync(a.C_out, hsc[i].C_out, 9 * a.n * sizeof(T), cudaMemcpyDeviceToHost, s));
+      }
     }
     P_CUDA(cudaStreamSynchronize(s));
   }

@@ -94,6 +94,9 @@ struct StaticEnv {
   void launched() {}
   void sorted() {}
   void done(int64_t, int64_t) {}
+  // device pointers only: no host staging
+  CopyEntry* copy_table(int) { return nullptr; }
+  static const void* device_view(const void*) { return nullptr; }
   // default kernel variant, launched directly (no graph, no tuning state)
   int variant(size_t, int64_t) { return 0; }
   template <class F>

@@ -169,3 +169,46 @@ def test_batched_calls_with_changing_membership_and_inputs(ctx):
             _check(s, b.v_out.cpu().double().numpy(), b.C_out.cpu().double().numpy().reshape(-1, 3, 3), None,
                    label=f"call {k}")
     assert ctx.profile()["graph_launches"] > 0
+
+
+def test_page_locked_host_arrays(ctx):
+    """Host-pointer calls whose arrays are page-locked take the one-kernel
+    staging path (inputs and results); some views start off 16-byte
+    boundaries.  Results must match the oracle and the pageable path."""
+    import torch
+
+    from paper_2108_02259_gb300 import apic
+
+    def pinned(a, dt, offset_rows=0):
+        a = np.ascontiguousarray(a, dt)
+        t = torch.empty((a.shape[0] + offset_rows,) + a.shape[1:], dtype=getattr(torch, np.dtype(dt).name)).pin_memory()
+        v = t.numpy()[offset_rows:]  # a view starting offset_rows rows in
+        v[...] = a
+        return v
+
+    sc = _mixed_batch()
+    pin_scenes, page_scenes = [], []
+    for k, s in enumerate(sc):
+        f = s.astype(np.float32)
+        off = k % 2  # every other scene's arrays start one row in
+        pin_scenes.append(apic.BatchScene(pinned(f.x, np.float64, off), pinned(f.v, np.float32, off),
+                                          pinned(f.C, np.float32, off), pinned(f.m, np.float32, off),
+                                          pinned(f.nrm, np.float32, off), pinned(f.body, np.int32, off), s.h, s.mu,
+                                          n_bodies=s.n_bodies, v_out=pinned(np.zeros_like(f.v), np.float32, off),
+                                          C_out=pinned(np.zeros_like(f.C), np.float32, off)))
+        page_scenes.append(apic.BatchScene(f.x, f.v, f.C, f.m, f.nrm, f.body, s.h, s.mu, n_bodies=s.n_bodies))
+    for _ in range(2):  # direct launches, then graph replay of the sizing sequence
+        apic.contact_step_batched(ctx, pin_scenes, 3)
+        apic.contact_step_batched(ctx, page_scenes, 3)
+        for s, a, b in zip(sc, pin_scenes, page_scenes):
+            _check(s, a.v_out.astype(np.float64), a.C_out.astype(np.float64).reshape(-1, 3, 3), None, label="pinned")
+            vs = np.abs(s.v).max()
+            assert np.abs(a.v_out - b.v_out).max() <= 2 * TOL_V * vs
+    # single scene, pinned
+    s = sc[2]
+    f = s.astype(np.float32)
+    vo, Co = pinned(np.zeros_like(f.v), np.float32, 1), pinned(np.zeros_like(f.C), np.float32, 1)
+    r = apic.contact_step(ctx, pinned(f.x, np.float64), pinned(f.v, np.float32, 1), pinned(f.C, np.float32),
+                          pinned(f.m, np.float32, 1), pinned(f.nrm, np.float32), pinned(f.body, np.int32, 1), s.h, s.mu,
+                          3, n_bodies=s.n_bodies, v_out=vo, C_out=Co)
+    _check(s, r.v.astype(np.float64), r.C.astype(np.float64).reshape(-1, 3, 3), None, label="pinned single")
