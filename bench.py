@@ -315,7 +315,11 @@ def main():
 
     from paper_2108_02259_gb300 import apic, build
 
-    build.build()
+    # one rank compiles (if anything is stale); the others wait for it
+    if rank == 0:
+        build.build()
+    if ws > 1:
+        torch.distributed.barrier()
     sc, dt, batched = make_workload(args.workload, rank)
     tdt = torch.float32 if dt == np.float32 else torch.float64
     N = sc[0].n_iter
