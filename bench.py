@@ -19,7 +19,8 @@ Workloads (seeded, synthetic, shaped like the paper's bodies):
   served        256 resident simulations (2k-1M nodes, 2-8 bodies, mu in [0, 0.5],
                 N = 8, 43.8M nodes in total) behind the serving loop; Poisson step
                 requests at 0.5 / 0.8 / 0.95 of the measured batched capacity;
-                reports throughput and p50/p99 request latency (value: load 0.8)
+                reports throughput and p50/p99 request latency (value: load 0.8);
+                one GPU (under torchrun only rank 0 runs it)
 
 Multi-GPU (torchrun): every rank steps its own scene(s) of the workload's shape
 and size, drawn from seed + 1000 * rank (independent problems: no collective
@@ -516,8 +517,10 @@ def run_served(args):
 
     from paper_2108_02259_gb300 import apic, build, scenes
 
-    build.build()
     ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0  # one server on one GPU: under torchrun the other ranks have nothing to do
+    build.build()
     dev = torch.device("cuda:0")
     sims = scenes.served_simulations()
     srv = apic.Server(0, hbm_budget_bytes=80 << 30, n_workers=2, max_batch_scenes=64)
