@@ -572,6 +572,8 @@ const char* apic_variant_name(int32_t v) {
       "128 threads/CTA, items <= 128, 7 CTAs/SM (72 registers)",
       "64 threads/CTA, items <= 64, 13 CTAs/SM (72 registers)",
       "64 threads/CTA, items <= 64, 16 CTAs/SM (64 registers, 13 resident by shared memory)",
+      "128 threads/CTA, items <= 128, 8 CTAs/SM (64 registers), stashed row weights",
+      "128 threads/CTA, items <= 128, 7 CTAs/SM (72 registers), stashed row weights",
   };
   return v >= 0 && v < kNumVariants ? names[v] : "";
 }

@@ -141,13 +141,16 @@ cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* li
 template <class K>
 cudaError_t launch_mark_items(const int* item_start, const int4* item_info, const int* n_items, const K* keys,
                               int64_t n, int max_items, const SceneDev* sc, int* flags, cudaStream_t s);
-// Variants of the fused transfer kernel: CTA size (= the largest work item)
-// and resident CTAs per SM it is compiled for (its register cap).  Variant 0
-// is the default; the FP32 path exists in all of them, the FP64 path in
-// variant 0 only (which it always uses).
-constexpr int kNumVariants = 5;
-constexpr int kVariantChunk[kNumVariants] = {128, 128, 128, 64, 64};
-constexpr int kVariantMinBlocks[kNumVariants] = {8, 9, 7, 13, 16};
+// Variants of the fused transfer kernel: CTA size (= the largest work item),
+// resident CTAs per SM it is compiled for (its register cap), and how P2G
+// lanes get their row weights m N_y N_z (recomputed per lane from t, or read
+// from factors stashed per particle in phase 1: fewer instructions, one more
+// stash row).  Variant 0 is the default; the FP32 path exists in all of
+// them, the FP64 path in variant 0 only (which it always uses).
+constexpr int kNumVariants = 7;
+constexpr int kVariantChunk[kNumVariants] = {128, 128, 128, 64, 64, 128, 128};
+constexpr int kVariantMinBlocks[kNumVariants] = {8, 9, 7, 13, 16, 8, 7};
+constexpr bool kVariantRowTab[kNumVariants] = {false, false, false, false, false, true, true};
 template <class T>
 cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, cudaStream_t s);
 // all64: take every node's momentum from the FP64 accumulators (after kModeMassV).

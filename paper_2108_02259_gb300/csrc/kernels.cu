@@ -326,7 +326,7 @@ struct RowAcc<float, K> {
 // CHUNK is the CTA size (and the largest item), MINB the number of resident
 // CTAs per SM the kernel is compiled for (its register cap); the autotuner
 // picks among the (kVariantChunk, kVariantMinBlocks) pairs.
-template <class T, int MODE, int MINB, int CHUNK>
+template <class T, int MODE, int MINB, int CHUNK, bool ROWTAB>
 __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   constexpr int kStashN = CHUNK + CHUNK / 16;
   constexpr bool kG2P = MODE == kModeFirst || MODE == kModeMid || MODE == kModeLast || MODE == kModeOnly;
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   __shared__ V4<T> sv[kG2P ? kTile3 : 1];
   __shared__ uint32_t smask[MODE == kModeMu ? kTile3 : 1];
   __shared__ T sacc[kP2G ? kComp : 1][kTile3];
-  __shared__ V4<T> stash[kP2G ? 6 : 1][kP2G ? kStashN : 1];
+  __shared__ V4<T> stash[kP2G ? (ROWTAB ? 7 : 6) : 1][kP2G ? kStashN : 1];
   __shared__ int sloc[CHUNK];
   __shared__ int snb[27];
   const int tid = threadIdx.x;
@@ -458,7 +458,21 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
     } else if (MODE == kModeMass || MODE == kModeP2GV || MODE == kModeMassV) {
       T wx[4], dx[4];
       bspline(pt.x, wx, dx);
-      stash[0][sidx(tid)] = pt;
+      if constexpr (ROWTAB) {
+        T wy[4], dy[4], wz[4], dz[4];
+        bspline(pt.y, wy, dy);
+        bspline(pt.z, wz, dz);
+        stash[0][sidx(tid)] = V4<T>{pt.w * wy[0], pt.w * wy[1], pt.w * wy[2], pt.w * wy[3]};
+        stash[ROWTAB ? 6 : 0][sidx(tid)] = V4<T>{wz[0], wz[1], wz[2], wz[3]};
+        if (MODE != kModeMass && !p.pic) {
+          // fold the particle's own offset into v: v_c - Ch_c1 t_y - Ch_c2 t_z
+          q0.x -= q1.x * pt.y + q1.y * pt.z;
+          q0.y -= q1.w * pt.y + q2.x * pt.z;
+          q0.z -= q2.z * pt.y + q2.w * pt.z;
+        }
+      } else {
+        stash[0][sidx(tid)] = pt;
+      }
       stash[4][sidx(tid)] = V4<T>{wx[0], wx[1], wx[2], wx[3]};
       stash[5][sidx(tid)] = V4<T>{wx[0] * dx[0], wx[1] * dx[1], wx[2] * dx[2], wx[3] * dx[3]};
       if (MODE != kModeMass) {
@@ -519,7 +533,17 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         store12(p.D, n, s, dv, dC);
         T u[3], uC[9];
         undesirable(dv, dC, nrm, mu, p.sep23, u, uC);
-        stash[0][sidx(tid)] = pt;
+        if constexpr (ROWTAB) {
+          stash[0][sidx(tid)] = V4<T>{pt.w * wy[0], pt.w * wy[1], pt.w * wy[2], pt.w * wy[3]};
+          stash[ROWTAB ? 6 : 0][sidx(tid)] = V4<T>{wz[0], wz[1], wz[2], wz[3]};
+          if (!p.pic) {  // fold the particle's own offset into u: u_c - Ch_c1 t_y - Ch_c2 t_z
+            u[0] -= uC[1] * pt.y + uC[2] * pt.z;
+            u[1] -= uC[4] * pt.y + uC[5] * pt.z;
+            u[2] -= uC[7] * pt.y + uC[8] * pt.z;
+          }
+        } else {
+          stash[0][sidx(tid)] = pt;
+        }
         stash[1][sidx(tid)] = V4<T>{u[0], u[1], u[2], uC[0]};
         stash[2][sidx(tid)] = V4<T>{uC[1], uC[2], uC[3], uC[4]};
         stash[3][sidx(tid)] = V4<T>{uC[5], uC[6], uC[7], uC[8]};
@@ -565,9 +589,19 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         if (cur >= 0) flush(cur);
         cur = base;
       }
-      const V4<T> a = stash[0][sidx(j)];
       const V4<T> X = stash[4][sidx(j)], XD = stash[5][sidx(j)];
-      const T wyzm = a.w * (cy0 + a.y * (cy1 + a.y * cy2)) * (cz0 + a.z * (cz1 + a.z * cz2));
+      T wyzm, ty = T(0), tz = T(0);
+      if constexpr (ROWTAB) {
+        // this lane's row weight m N_y(ky) N_z(kz), from the stashed factors
+        // (the particle's own offset is already folded into u)
+        wyzm = reinterpret_cast<const T*>(&stash[0][sidx(j)])[ky] *
+               reinterpret_cast<const T*>(&stash[ROWTAB ? 6 : 0][sidx(j)])[kz];
+      } else {
+        const V4<T> a = stash[0][sidx(j)];
+        wyzm = a.w * (cy0 + a.y * (cy1 + a.y * cy2)) * (cz0 + a.z * (cz1 + a.z * cz2));
+        ty = a.y;
+        tz = a.z;
+      }
       if (kMass) {
         const T A[1] = {wyzm};
         if constexpr (MODE == kModeMass)
@@ -580,7 +614,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         // W = (u, Ch); Ch rows (w0.w w1.x w1.y) (w1.z w1.w w2.x) (w2.y w2.z w2.w).
         // Node k of this row gets wx_k A + wx_k dx_k B with
         //   A_c = m wy wz (u_c + Ch_c1 dy + Ch_c2 dz),  B_c = m wy wz Ch_c0.
-        const T dy = oy - a.y, dz = oz - a.z;
+        const T dy = oy - ty, dz = oz - tz;
         T A[3], B[3];
         if (aff) {
           A[0] = wyzm * (w0.x + w1.x * dy + w1.y * dz);
@@ -1058,18 +1092,18 @@ cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* li
   return cudaGetLastError();
 }
 
-template <class T, int MINB, int CHUNK>
+template <class T, int MINB, int CHUNK, bool ROWTAB>
 cudaError_t launch_items_cfg(const IterParams<T>& p, int mode, cudaStream_t s) {
   const unsigned grid = (unsigned)p.n_items;
   switch (mode) {
-    case kModeMass: k_items<T, kModeMass, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
-    case kModeP2GV: k_items<T, kModeP2GV, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
-    case kModeFirst: k_items<T, kModeFirst, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
-    case kModeMid: k_items<T, kModeMid, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
-    case kModeLast: k_items<T, kModeLast, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
-    case kModeOnly: k_items<T, kModeOnly, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
-    case kModeMu: k_items<T, kModeMu, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
-    case kModeMassV: k_items<T, kModeMassV, MINB, CHUNK><<<grid, CHUNK, 0, s>>>(p); break;
+    case kModeMass: k_items<T, kModeMass, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
+    case kModeP2GV: k_items<T, kModeP2GV, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
+    case kModeFirst: k_items<T, kModeFirst, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
+    case kModeMid: k_items<T, kModeMid, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
+    case kModeLast: k_items<T, kModeLast, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
+    case kModeOnly: k_items<T, kModeOnly, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
+    case kModeMu: k_items<T, kModeMu, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
+    case kModeMassV: k_items<T, kModeMassV, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1081,16 +1115,20 @@ cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, cudaStre
   if (variant < 0 || variant >= kNumVariants) return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 4) {
     // the FP32 path is built in every variant
+#define APIC_VARIANT(v) launch_items_cfg<T, kVariantMinBlocks[v], kVariantChunk[v], kVariantRowTab[v]>(p, mode, s)
     switch (variant) {
-      case 1: return launch_items_cfg<T, kVariantMinBlocks[1], kVariantChunk[1]>(p, mode, s);
-      case 2: return launch_items_cfg<T, kVariantMinBlocks[2], kVariantChunk[2]>(p, mode, s);
-      case 3: return launch_items_cfg<T, kVariantMinBlocks[3], kVariantChunk[3]>(p, mode, s);
-      case 4: return launch_items_cfg<T, kVariantMinBlocks[4], kVariantChunk[4]>(p, mode, s);
+      case 1: return APIC_VARIANT(1);
+      case 2: return APIC_VARIANT(2);
+      case 3: return APIC_VARIANT(3);
+      case 4: return APIC_VARIANT(4);
+      case 5: return APIC_VARIANT(5);
+      case 6: return APIC_VARIANT(6);
       default: break;
     }
   }
   // the FP64 path (parity and small scenes) only in variant 0
-  return launch_items_cfg<T, kVariantMinBlocks[0], kVariantChunk[0]>(p, mode, s);
+  return APIC_VARIANT(0);
+#undef APIC_VARIANT
 }
 
 template <class T>
