@@ -280,3 +280,37 @@ def test_eight_bodies_full_size(ctx):
     sub = _subset(s, keep, (0, 1))
     rv, rC, rst = run_oracle(sub, mu_pair=sub.mu_pair)
     check(sub, (v[keep], Cm[keep], None), (rv, rC, rst), TOL_V32, TOL_C32, None, "eight bodies, pair 0 of full scene")
+
+
+def test_limits_rejected_cleanly():
+    """The documented limits fail with their error codes and leave the
+    context usable: |x/h| >= 2^29, a page-table box beyond 2^28 blocks,
+    more than 32 bodies, and a scene whose scratch exceeds the context's HBM
+    budget."""
+    from paper_2108_02259_gb300 import apic
+
+    ok = scenes.random_cloud(200, n_bodies=2, seed=9, h=0.1, n_iter=2)
+    with apic.Context(0, hbm_budget_bytes=8 << 20) as c:
+        f = ok.astype(np.float32)
+        far = f.x.copy()
+        far[0] = [2.0 ** 29 * ok.h * 1.5, 0.0, 0.0]
+        with pytest.raises(apic.ApicError) as e:
+            apic.contact_step(c, far, f.v, f.C, f.m, f.nrm, f.body, ok.h, 0.3, 2, n_bodies=2)
+        assert e.value.code == apic.APIC_ERR_INVALID_ARG and "position" in str(e.value)
+        spread = f.x.copy()
+        spread[0] = [1e4, 1e4, 1e4]  # a bounding box of ~10^15 grid blocks
+        with pytest.raises(apic.ApicError) as e:
+            apic.contact_step(c, spread, f.v, f.C, f.m, f.nrm, f.body, ok.h, 0.3, 2, n_bodies=2)
+        assert e.value.code == apic.APIC_ERR_INVALID_ARG and "page-table" in str(e.value)
+        with pytest.raises(apic.ApicError) as e:
+            apic.contact_step(c, f.x, f.v, f.C, f.m, f.nrm, f.body, ok.h, 0.3, 2, n_bodies=33)
+        assert e.value.code == apic.APIC_ERR_INVALID_ARG
+        big = scenes.four_bodies(scale=0.2).astype(np.float32)  # 40,000 nodes: more scratch than 8 MiB
+        with pytest.raises(apic.ApicError) as e:
+            apic.contact_step(c, big.x, big.v, big.C, big.m, big.nrm, big.body, 1 / 256, 0.3, 2, n_bodies=4)
+        assert e.value.code == apic.APIC_ERR_OUT_OF_MEMORY
+        assert c.scratch_bytes() <= 8 << 20
+        r = apic.contact_step(c, f.x, f.v, f.C, f.m, f.nrm, f.body, ok.h, ok.mu, ok.n_iter, n_bodies=2)
+        ref = run_oracle(ok)
+        check(ok, (r.v.astype(np.float64), r.C.astype(np.float64).reshape(-1, 3, 3), None), ref, 3 * TOL_V32,
+              TOL_C32, None, "after limits", count_multibody=False)
