@@ -197,6 +197,9 @@ apic_status apic_contact_step_static(const apic_step_args* args, void* stream, a
  * as one batched step; a request that arrives while a batch is on the GPU is
  * picked up by the next free worker, so batches overlap on the device.
  * Requests are batched only with requests of the same flags and n_iter.
+ * Unlike a context, a server may be called from any host thread (every call
+ * takes the server's lock).  The paper steps one simulation at a time; this
+ * serving layer has no counterpart in it.
  * --------------------------------------------------------------------------*/
 typedef struct apic_server apic_server;
 typedef struct apic_sim apic_sim;
@@ -274,6 +277,8 @@ apic_status apic_sim_close(apic_sim* sim);
 /* Counters and latency percentiles since creation (or the last reset); the
  * percentiles cover at most the last 2^20 completed requests. */
 apic_status apic_server_get_stats(apic_server* srv, apic_server_stats* out, int32_t reset);
+
+/* Diagnostics (no counterpart in the paper). */
 
 /* Turn kernel timing on (1) or off (0) and reset the counters. */
 apic_status apic_set_profiling(apic_ctx* ctx, int32_t on);
