@@ -294,6 +294,8 @@ def main():
     ap.add_argument("--variant", type=int, default=-1,
                     help="fix the transfer-kernel variant (default: autotune for the workload)")
     ap.add_argument("--no-graphs", action="store_true", help="launch the transfer passes one by one")
+    ap.add_argument("--no-overlap", action="store_true",
+                    help="launch each pass strictly after the grid before it (no programmatic dependent launch)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the node-normal and augury-driver measurements (contact step only)")
     args = ap.parse_args()
@@ -350,6 +352,7 @@ def main():
 
     # pick the transfer-kernel variant for this size class (untimed), then
     # one checked step: the device's own momentum balance
+    ctx.set_overlap(not args.no_overlap)
     if args.variant >= 0:
         ctx.set_variant(args.variant)
         variant = args.variant
@@ -474,6 +477,7 @@ def main():
         "gpu_launches": int(launches),
         "kernel_variant": apic.variants()[variant],
         "cuda_graph": not args.no_graphs,
+        "dependent_launch": not args.no_overlap,
         "sort_primitive_calls_per_step": prof["sort_launches"] / max(prof["steps"], 1),
         "roofline": {"bound": "hbm", "kernel": "k_items (fused G2P + projection + P2G pass)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",

@@ -412,6 +412,12 @@ apic_status apic_autotune(apic_ctx* ctx, const apic_step_args* scenes, int32_t n
  * one by one regardless, to time each pass. */
 apic_status apic_set_graphs(apic_ctx* ctx, int32_t on);
 
+/* Launch each transfer pass and node normalisation with programmatic
+ * dependent launch (1, the default), so that a grid's prologue overlaps the
+ * end of the grid before it, or strictly one after another (0).  The results
+ * are the same either way.  Profiling launches them strictly in order. */
+apic_status apic_set_overlap(apic_ctx* ctx, int32_t on);
+
 #ifdef __cplusplus
 }
 #endif

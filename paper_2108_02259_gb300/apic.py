@@ -39,8 +39,8 @@ EXPORTED = [
     "apic_contact_step_batched", "apic_server_create", "apic_server_destroy", "apic_sim_open", "apic_sim_submit",
     "apic_ticket_poll", "apic_ticket_wait", "apic_sim_read", "apic_sim_close", "apic_server_get_stats",
     "apic_variant_count", "apic_variant_name", "apic_set_variant", "apic_get_variant", "apic_autotune",
-    "apic_set_graphs", "apic_server_set_policy", "apic_node_normals", "apic_augury_steps", "apic_sim_export",
-    "apic_sim_import",
+    "apic_set_graphs", "apic_set_overlap", "apic_server_set_policy", "apic_node_normals", "apic_augury_steps",
+    "apic_sim_export", "apic_sim_import",
 ]
 
 
@@ -153,6 +153,7 @@ def load(path: str = LIB_PATH):
     lib.apic_get_variant.argtypes = [P, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.apic_autotune.argtypes = [P, C.POINTER(StepArgs), C.c_int32, P, C.POINTER(C.c_int32)]
     lib.apic_set_graphs.argtypes = [P, C.c_int32]
+    lib.apic_set_overlap.argtypes = [P, C.c_int32]
     lib.apic_server_set_policy.argtypes = [P, C.c_int32, C.c_int32]
     lib.apic_node_normals.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_uint32, P]
     lib.apic_node_normals.restype = C.c_int32
@@ -164,7 +165,8 @@ def load(path: str = LIB_PATH):
     lib.apic_sim_import.restype = C.c_int32
     lib.apic_server_set_policy.restype = C.c_int32
     for f in ("apic_create", "apic_destroy", "apic_contact_step", "apic_set_profiling", "apic_get_profile",
-              "apic_scratch_bytes", "apic_set_variant", "apic_get_variant", "apic_autotune", "apic_set_graphs"):
+              "apic_scratch_bytes", "apic_set_variant", "apic_get_variant", "apic_autotune", "apic_set_graphs",
+              "apic_set_overlap"):
         getattr(lib, f).restype = C.c_int32
     _lib = lib
     return lib
@@ -240,6 +242,10 @@ class Context:
     def set_graphs(self, on: bool):
         """Replay the transfer passes as a CUDA graph (default) or not."""
         _check(load().apic_set_graphs(self._h, 1 if on else 0))
+
+    def set_overlap(self, on: bool):
+        """Let each pass start while the grid before it finishes (default) or not."""
+        _check(load().apic_set_overlap(self._h, 1 if on else 0))
 
 
 def variants() -> list[str]:

@@ -80,6 +80,7 @@ struct apic_ctx {
     int64_t kernels = 0, sorts = 0;  // launches inside the graph
   };
   bool graphs_on = true;
+  bool overlap_on = true;  // programmatic dependent launch between the passes
   GraphSlot gsizing, gseries;
   cudaStream_t cap_stream = nullptr;
   uint64_t alloc_gen = 0;  // bumped whenever a scratch buffer moves
@@ -257,6 +258,9 @@ struct CtxEnv {
     }
     return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
   }
+  // Overlap each pass with the tail of the grid before it, except while
+  // profiling times the passes one by one.
+  bool overlap() const { return c->overlap_on && !c->prof_on; }
   void launched() { c->prof.kernel_launches++; }
   void sorted() { c->prof.sort_launches++; }
   void done(int64_t n, int64_t nodes) {
@@ -624,6 +628,17 @@ apic_status apic_autotune(apic_ctx* c, const apic_step_args* scenes, int32_t n_s
 apic_status apic_set_graphs(apic_ctx* c, int32_t on) {
   if (!c) return pfail(APIC_ERR_INVALID_ARG, "ctx is NULL");
   c->graphs_on = on != 0;
+  for (apic_ctx::GraphSlot* g : {&c->gsizing, &c->gseries}) {
+    g->key.clear();
+    g->captured = false;
+    g->failed = false;
+  }
+  return APIC_OK;
+}
+
+apic_status apic_set_overlap(apic_ctx* c, int32_t on) {
+  if (!c) return pfail(APIC_ERR_INVALID_ARG, "ctx is NULL");
+  c->overlap_on = on != 0;
   for (apic_ctx::GraphSlot* g : {&c->gsizing, &c->gseries}) {
     g->key.clear();
     g->captured = false;

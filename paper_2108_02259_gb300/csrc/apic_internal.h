@@ -151,12 +151,16 @@ constexpr int kNumVariants = 7;
 constexpr int kVariantChunk[kNumVariants] = {128, 128, 128, 64, 64, 128, 128};
 constexpr int kVariantMinBlocks[kNumVariants] = {8, 9, 7, 13, 16, 8, 7};
 constexpr bool kVariantRowTab[kNumVariants] = {false, false, false, false, false, true, true};
+// overlap: launch with programmatic stream serialization, so that the grid's
+// prologue (item metadata, particle loads, page lookups) runs while the grid
+// before it finishes.  Only for a launch that directly follows another
+// k_items or k_normalize launch in the same stream.
 template <class T>
-cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, cudaStream_t s);
+cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, bool overlap, cudaStream_t s);
 // all64: take every node's momentum from the FP64 accumulators (after kModeMassV).
 template <class T>
 cudaError_t launch_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask, V4<T>* gp,
-                             V4<double>* gp64, V4<T>* gv, int all64, cudaStream_t s);
+                             V4<double>* gp64, V4<T>* gv, int all64, bool overlap, cudaStream_t s);
 // FP64 totals of one scene: out6 = (P, L).
 template <class T>
 cudaError_t launch_momentum(int64_t n, const double* x, const T* v, const T* C, const T* m, double h,

@@ -28,6 +28,17 @@ __device__ __forceinline__ double bits_to(double, uint32_t b) {
 __device__ __forceinline__ uint32_t to_bits(float v) { return __float_as_uint(v); }
 __device__ __forceinline__ uint32_t to_bits(double v) { return (uint32_t)__double_as_longlong(v); }
 
+// Programmatic dependent launch (sm_90 and later).  A grid launched with the
+// programmatic-serialization attribute may start while the grid before it in
+// the stream still runs; grid_dep_wait() returns once every grid it depends
+// on has completed with its memory visible, and grid_dep_launch() lets the
+// next grid start.  Both do nothing in a grid launched without the attribute.
+// Before grid_dep_wait() a kernel reads only what the grid-sizing sequence
+// wrote (which completed before the first grid of the chain started) and
+// writes nothing to global memory.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // App. B quadratic B-spline weights of the nodes i-1, i, i+1, i+2 for the
 // in-cell offset t = x/h - floor(x/h), written out (with the 1/4 factor on
 // the middle two, the reading under which they sum to one):
@@ -344,7 +355,11 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   const int tid = threadIdx.x;
   const int n = p.n_particles;
   const int item = blockIdx.x;
-  if (item >= p.n_items) return;
+  grid_dep_launch();
+  if (item >= p.n_items) {
+    grid_dep_wait();
+    return;
+  }
   const int4 info = p.item_info[item];
   const SceneDev& S = p.sc[info.z];
   const Box box = S.box;
@@ -371,11 +386,10 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
     const int s = s0 + tid;
     pt = p.pt[s];
     pn = p.pn[s];
-    if (kReadD || kReadV) {
-      const V4<T>* planes = kReadD ? p.D : p.V;
-      q0 = planes[s];
-      q1 = planes[n + s];
-      q2 = planes[2 * n + s];
+    if (kReadV) {
+      q0 = p.V[s];
+      q1 = p.V[n + s];
+      q2 = p.V[2 * n + s];
     }
   }
   if (tid < 27) {
@@ -386,6 +400,15 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
     for (int t = t_lo + tid; t < t_hi; t += CHUNK)
 #pragma unroll
       for (int a = 0; a < kComp; ++a) sacc[a][t] = T(0);
+  // D, the node velocities, the node masks and the grid sums come from the
+  // grids before this one
+  grid_dep_wait();
+  if (kReadD && tid < count) {
+    const int s = s0 + tid;
+    q0 = p.D[s];
+    q1 = p.D[n + s];
+    q2 = p.D[2 * n + s];
+  }
   __syncthreads();
   if (kG2P) {
     if constexpr (sizeof(T) == 4) {
@@ -673,6 +696,8 @@ template <class T>
 __global__ void k_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask, V4<T>* gp,
                             V4<double>* gp64, V4<T>* gv, int all64) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  grid_dep_launch();
+  grid_dep_wait();
   if (i >= n_nodes) return;
   const T m = gm[i];
   V4<T> v{T(0), T(0), T(0), T(0)};
@@ -1092,30 +1117,53 @@ cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* li
   return cudaGetLastError();
 }
 
+// One launch, with programmatic stream serialization when `overlap` (the
+// grid may start while the one before it in the stream still runs; see
+// grid_dep_wait).
+template <class... P, class... A>
+cudaError_t launch_ex(void (*kernel)(P...), unsigned grid, unsigned block, bool overlap, cudaStream_t s,
+                      A... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = overlap ? 1 : 0;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 template <class T, int MINB, int CHUNK, bool ROWTAB>
-cudaError_t launch_items_cfg(const IterParams<T>& p, int mode, cudaStream_t s) {
+cudaError_t launch_items_cfg(const IterParams<T>& p, int mode, bool overlap, cudaStream_t s) {
   const unsigned grid = (unsigned)p.n_items;
   switch (mode) {
-    case kModeMass: k_items<T, kModeMass, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
-    case kModeP2GV: k_items<T, kModeP2GV, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
-    case kModeFirst: k_items<T, kModeFirst, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
-    case kModeMid: k_items<T, kModeMid, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
-    case kModeLast: k_items<T, kModeLast, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
-    case kModeOnly: k_items<T, kModeOnly, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
-    case kModeMu: k_items<T, kModeMu, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
-    case kModeMassV: k_items<T, kModeMassV, MINB, CHUNK, ROWTAB><<<grid, CHUNK, 0, s>>>(p); break;
+#define APIC_MODE(m) \
+  case m: return launch_ex(k_items<T, m, MINB, CHUNK, ROWTAB>, grid, CHUNK, overlap, s, p);
+    APIC_MODE(kModeMass)
+    APIC_MODE(kModeP2GV)
+    APIC_MODE(kModeFirst)
+    APIC_MODE(kModeMid)
+    APIC_MODE(kModeLast)
+    APIC_MODE(kModeOnly)
+    APIC_MODE(kModeMu)
+    APIC_MODE(kModeMassV)
+#undef APIC_MODE
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, cudaStream_t s) {
+cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, bool overlap, cudaStream_t s) {
   if (p.n_items <= 0) return cudaSuccess;
   if (variant < 0 || variant >= kNumVariants) return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 4) {
     // the FP32 path is built in every variant
-#define APIC_VARIANT(v) launch_items_cfg<T, kVariantMinBlocks[v], kVariantChunk[v], kVariantRowTab[v]>(p, mode, s)
+#define APIC_VARIANT(v) \
+  launch_items_cfg<T, kVariantMinBlocks[v], kVariantChunk[v], kVariantRowTab[v]>(p, mode, overlap, s)
     switch (variant) {
       case 1: return APIC_VARIANT(1);
       case 2: return APIC_VARIANT(2);
@@ -1133,10 +1181,10 @@ cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, cudaStre
 
 template <class T>
 cudaError_t launch_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask, V4<T>* gp,
-                             V4<double>* gp64, V4<T>* gv, int all64, cudaStream_t s) {
+                             V4<double>* gp64, V4<T>* gv, int all64, bool overlap, cudaStream_t s) {
   if (n_nodes <= 0) return cudaSuccess;
-  k_normalize<T><<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, gm, gmask, gp, gp64, gv, all64);
-  return cudaGetLastError();
+  return launch_ex(k_normalize<T>, grid_for(n_nodes, 256), 256, overlap, s, n_nodes, gm, gmask, gp, gp64, gv,
+                   all64);
 }
 
 template <class T>
@@ -1447,9 +1495,9 @@ cudaError_t launch_copy_table(const CopyEntry* table, int n_entries, long long m
   template cudaError_t launch_cells<T>(int64_t, const SceneDev*, int, int4*, int*, int*, cudaStream_t); \
   template cudaError_t launch_gather<T>(int64_t, const SceneDev*, int, const int*, const int4*, V4<T>*,  \
                                         V4<T>*, V4<T>*, cudaStream_t);                                  \
-  template cudaError_t launch_items<T>(const IterParams<T>&, int, int, cudaStream_t);                   \
+  template cudaError_t launch_items<T>(const IterParams<T>&, int, int, bool, cudaStream_t);             \
   template cudaError_t launch_normalize<T>(int64_t, const T*, const uint32_t*, V4<T>*, V4<double>*,     \
-                                           V4<T>*, int, cudaStream_t);                                  \
+                                           V4<T>*, int, bool, cudaStream_t);                            \
   template cudaError_t launch_momentum<T>(int64_t, const double*, const T*, const T*, const T*, double, \
                                           double*, cudaStream_t);                                       \
   template cudaError_t launch_advect<T>(int64_t, double*, const T*, double, cudaStream_t);                \

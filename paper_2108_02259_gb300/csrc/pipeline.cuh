@@ -544,18 +544,20 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   auto series = [&](cudaStream_t q) -> apic_status {
     IterParams<T> pp = key.p;
     const int var = key.variant;
+    // every launch after the mass pass follows a k_items or k_normalize launch
+    const bool ov = env.overlap();
     typename Env::Span span_mass(env, q, 3);
     P_CUDA(cudaMemsetAsync(gm, 0, n_nodes * sizeof(T), q));
     P_CUDA(cudaMemsetAsync(gmask, 0, n_nodes * sizeof(uint32_t), q));
     P_CUDA(cudaMemsetAsync(gp, 0, n_nodes * sizeof(V4<T>), q));
     if (gp64) P_CUDA(cudaMemsetAsync(gp64, 0, n_nodes * sizeof(V4<double>), q));
     if (gmb) P_CUDA(cudaMemsetAsync(gmb, 0, (size_t)max_bodies * n_nodes * sizeof(T), q));
-    P_LAUNCH(env, launch_items<T>(pp, kModeMassV, var, q));
+    P_LAUNCH(env, launch_items<T>(pp, kModeMassV, var, false, q));
     if (any_mu) {
-      P_LAUNCH(env, launch_items<T>(pp, kModeMu, var, q));
+      P_LAUNCH(env, launch_items<T>(pp, kModeMu, var, ov, q));
       pp.mup = mup;
     }
-    P_LAUNCH(env, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 1, q));
+    P_LAUNCH(env, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 1, ov, q));
     span_mass.stop();
 
     // 8. the N + 1 transfer passes.
@@ -563,9 +565,9 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       const int mode = N == 0 ? kModeOnly : pass == 0 ? kModeFirst : pass == N ? kModeLast : kModeMid;
       {
         typename Env::Span span_pass(env, q, 2);
-        P_LAUNCH(env, launch_items<T>(pp, mode, var, q));
+        P_LAUNCH(env, launch_items<T>(pp, mode, var, ov, q));
       }
-      if (pass < N) P_LAUNCH(env, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 0, q));
+      if (pass < N) P_LAUNCH(env, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 0, ov, q));
     }
     return APIC_OK;
   };

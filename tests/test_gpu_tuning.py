@@ -145,3 +145,37 @@ def test_autotune_settles_and_keeps_parity(apic):
         ctx.set_variant(1)
         with pytest.raises(apic.ApicError):
             ctx.autotune(sc, s.n_iter)
+
+
+@pytest.mark.parametrize("case", ["four_bodies", "mu_pair", "single_pass"])
+def test_dependent_launch_keeps_parity(apic, case):
+    """Programmatic dependent launch lets each pass start its prologue while
+    the grid before it finishes; the passes must still see the finished node
+    velocities and D.  Direct launches and graph replays, overlap on and off,
+    all match the oracle (the mu pass and the single N = 0 pass included)."""
+    import torch
+
+    mu_pair = None
+    if case == "four_bodies":
+        s = scenes.four_bodies(scale=0.1)
+    elif case == "mu_pair":
+        s = scenes.random_cloud(6000, n_bodies=4, seed=23, h=0.05, n_iter=3)
+        rng = np.random.default_rng(5)
+        a = rng.uniform(0.1, 0.5, (4, 4))
+        mu_pair = (a + a.T) / 2
+    else:
+        s = scenes.random_cloud(5000, n_bodies=3, seed=29, h=0.05, n_iter=0)
+    ref = oracle.contact_step(s.x, s.v, s.C, s.m, s.nrm, s.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
+                              mu_pair=mu_pair)
+    X, V, Cc, M, NR, B = _dev(s)
+    for on in (True, False):
+        with apic.Context(0) as ctx:
+            ctx.set_variant(len(apic.variants()) - 1)
+            ctx.set_overlap(on)
+            for k in range(4):  # direct, direct, captured, replayed
+                r = apic.contact_step(ctx, X, V, Cc, M, NR, B, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
+                                      mu_pair=mu_pair)
+                torch.cuda.synchronize()
+                _close(s, r.v.cpu().double().numpy(), r.C.cpu().double().numpy(), ref[0], ref[1],
+                       f"overlap {on}, call {k}")
+            assert ctx.profile()["graph_launches"] >= 2
