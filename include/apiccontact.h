@@ -59,6 +59,19 @@ typedef int32_t apic_status;
 #define APIC_VARIANT_PIC (1u << 2)   /* PIC transfers (Sec. 2.1.1): no affine term, C unchanged.   */
 #define APIC_VARIANT_SEP23 (1u << 3) /* Sec. 2.3 separation rule instead of the Sec. 2.4 cone:
                                         W = Delta if Delta_v . n > 0, else 0.                      */
+#define APIC_DETERMINISTIC (1u << 5) /* Bitwise-reproducible results (FP32 path only; not in the
+                                        paper): node sums are added as 64-bit fixed-point integers,
+                                        exactly and in any order, with a power-of-two scale per
+                                        scene and pass; the transfer kernel runs its first variant
+                                        (no autotuning).  A scene's outputs then depend only on its
+                                        own inputs: the same bits alone, in any batch, with graphs
+                                        or dependent launch on or off, from run to run on one GPU
+                                        model.  Costs one host synchronisation at the end of the
+                                        step.  A scene whose terms grow past the scale's headroom
+                                        within one pass is repeated with a wider one; if that also
+                                        fails (or inputs are non-finite) the call returns
+                                        APIC_ERR_INVALID_ARG and leaves that scene's outputs
+                                        untouched.  Statistics (apic_stats) are still FP64 sums.  */
 
 typedef struct apic_ctx apic_ctx;
 

@@ -31,6 +31,7 @@ APIC_FP64 = 1 << 0
 APIC_HOST_PTRS = 1 << 1
 APIC_VARIANT_PIC = 1 << 2
 APIC_VARIANT_SEP23 = 1 << 3
+APIC_DETERMINISTIC = 1 << 5
 APIC_AUGURY_INIT = 1 << 4
 
 EXPORTED = [

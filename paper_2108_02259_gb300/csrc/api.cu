@@ -268,6 +268,12 @@ struct CtxEnv {
     c->prof.active_nodes = nodes;
   }
 
+  // Variant 0, untimed (deterministic mode).
+  int variant_fixed() {
+    collect_tuning(c);
+    c->cur_measure = false;
+    return 0;
+  }
   // Kernel variant for this call: the caller's fixed choice, the size
   // class's tuned choice, or (while the class is being tuned) the variant
   // with the fewest timed runs, whose series region is then timed.
@@ -406,7 +412,8 @@ struct CtxEnv {
   };
 };
 
-constexpr uint32_t kAllFlags = APIC_FP64 | APIC_HOST_PTRS | APIC_VARIANT_PIC | APIC_VARIANT_SEP23;
+constexpr uint32_t kAllFlags =
+    APIC_FP64 | APIC_HOST_PTRS | APIC_VARIANT_PIC | APIC_VARIANT_SEP23 | APIC_DETERMINISTIC;
 
 apic_status run(apic_ctx* c, const apic_step_args* scenes, int ns, void* stream, apic_stats* stats) {
   P_CUDA(cudaSetDevice(c->device));

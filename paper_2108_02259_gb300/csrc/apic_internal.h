@@ -113,7 +113,23 @@ struct IterParams {
   const int* perm;         // sorted -> batch particle index
   int pic;                 // PIC transfers
   int sep23;               // Sec. 2.3 rule
+  // Fixed-point node sums (deterministic mode): per scene, fx_max[scene *
+  // fx_stride + k] holds the float bits of a bound on the particle terms a
+  // pass scatters (k = 0: masses, 1: V, 2 + j: W of pass j); fx_err[attempt
+  // * n_scenes + scene] is set when a term exceeded the bound its scale
+  // allowed; gmb_fx replaces gmb.  The pass's own slot is fx_slot.
+  unsigned* fx_max;
+  int* fx_err;
+  long long* gmb_fx;
+  int fx_stride;
+  int fx_slot;
+  int fx_attempt;
 };
+
+// Deterministic mode: fixed-point headroom (log2) of a pass's scale over the
+// bound measured in the pass before, first try and retry.
+constexpr int kFxHeadLog2 = 12;
+constexpr int kFxRetryHeadLog2 = 24;
 
 // Cells, validation, per-scene bounding boxes of particle blocks (sbbox[6 s]).
 template <class T>
@@ -161,6 +177,16 @@ cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, bool ove
 template <class T>
 cudaError_t launch_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask, V4<T>* gp,
                              V4<double>* gp64, V4<T>* gv, int all64, bool overlap, cudaStream_t s);
+// Deterministic mode (FP32 path).  fx_prep: per scene, bounds of the mass and
+// V terms of the mass pass (fx_max slots 0 and 1, zeroed by the caller);
+// err_row[scene] is set where a bound is not finite.
+cudaError_t launch_fx_prep(int64_t n, const SceneDev* sc, int ns, const int* perm, const V4<float>* pt,
+                           const V4<float>* V, unsigned* fx_max, int fx_stride, int* err_row, cudaStream_t s);
+// v_i from the fixed-point sums of the pass that used scale slot `slot`
+// (all64: after the mass pass, which also gives m_i); clears the sums.
+cudaError_t launch_normalize_fx(int64_t n_nodes, const int* blist, const SceneDev* sc, int ns, float* gm,
+                                long long* gfx, V4<float>* gv, const unsigned* fx_max, const int* fx_err,
+                                int fx_stride, int slot, int attempt, int all64, bool overlap, cudaStream_t s);
 // FP64 totals of one scene: out6 = (P, L).
 template <class T>
 cudaError_t launch_momentum(int64_t n, const double* x, const T* v, const T* C, const T* m, double h,

@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "apic_internal.h"
 
@@ -318,6 +319,48 @@ struct RowAcc<float, K> {
   }
 };
 
+// ---- Fixed-point node sums (deterministic mode, FP32 path) ----
+// A pass scatters, per particle and node, N m (w_c + sum_k Ch_ck d_k) with
+// N <= 1 and |d_k| <= 2 (cell units), so every component is bounded by
+//   b_p = m_p max_c (|w_c| + 2 sum_k |Ch_ck|).
+// If every b_p of a scene is at most B, a node sum over the scene's n
+// particles stays below n B; the scale S = 2^e with S n B <= 2^62 then keeps
+// it inside int64, and integer atomics add the scaled terms exactly, in any
+// order.  B comes from the bound measured in the pass before (or, for the
+// mass pass, from the inputs themselves), times a headroom of 2^lg; a term
+// over B is recorded, the step is repeated with a larger headroom, and
+// outputs are written only by a pass in which nothing was recorded.
+__device__ __forceinline__ float fx_bound(float m, const float* w, const float* Ch) {
+  float b = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float t = fabsf(w[c]) + 2.f * (fabsf(Ch[3 * c]) + fabsf(Ch[3 * c + 1]) + fabsf(Ch[3 * c + 2]));
+    b = (t > b || t != t) ? t : b;  // a NaN term propagates (fmaxf would drop it)
+  }
+  return m * b * 1.0001f;  // margin over the rounding of the terms themselves
+}
+// Scale of slot `slot` of one scene's bounds (fxs), headroom 2^lg, n terms
+// per node at most; *allowed = the largest b_p it admits.
+__device__ __forceinline__ double fx_scale(const unsigned* fxs, int slot, int lg, int n, double* allowed) {
+  float B = __uint_as_float(fxs[slot]);
+  if (slot >= 2) B = fmaxf(B, __uint_as_float(fxs[1]) * 0x1p-30f);  // W negligible next to V
+  B = fmaxf(B, 1e-30f);
+  const double Bd = ldexp((double)B, lg);
+  *allowed = Bd;
+  const double lim = 4611686018427387904.0 / ((double)max(n, 1) * Bd);  // 2^62 / (n B)
+  int e;
+  frexp(lim, &e);  // lim in [2^(e-1), 2^e)
+  return ldexp(1.0, e - 1);
+}
+// Headroom of a pass scattering W: the retry widens it for the scenes whose
+// first attempt recorded an excess.
+__device__ __forceinline__ int fx_head(const int* fx_err, int attempt, int scene) {
+  return attempt > 0 && __ldcg(fx_err + scene) != 0 ? kFxRetryHeadLog2 : kFxHeadLog2;
+}
+__device__ __forceinline__ unsigned long long to_fx(float x, double S) {
+  return (unsigned long long)__double2ll_rn((double)x * S);
+}
+
 // One work item = up to CHUNK sorted particles of one body whose cells lie
 // in one grid block.  A CTA of CHUNK threads runs it in two phases:
 //
@@ -337,7 +380,10 @@ struct RowAcc<float, K> {
 // CHUNK is the CTA size (and the largest item), MINB the number of resident
 // CTAs per SM the kernel is compiled for (its register cap); the autotuner
 // picks among the (kVariantChunk, kVariantMinBlocks) pairs.
-template <class T, int MODE, int MINB, int CHUNK, bool ROWTAB>
+//
+// DET (deterministic mode, FP32): the shared tile and the global node sums
+// hold scaled int64 terms (fixed point) instead of floating-point sums.
+template <class T, int MODE, int MINB, int CHUNK, bool ROWTAB, bool DET = false>
 __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   constexpr int kStashN = CHUNK + CHUNK / 16;
   constexpr bool kG2P = MODE == kModeFirst || MODE == kModeMid || MODE == kModeLast || MODE == kModeOnly;
@@ -348,7 +394,9 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   constexpr int kComp = MODE == kModeMass ? 1 : MODE == kModeMassV ? 4 : 3;
   __shared__ V4<T> sv[kG2P ? kTile3 : 1];
   __shared__ uint32_t smask[MODE == kModeMu ? kTile3 : 1];
-  __shared__ T sacc[kP2G ? kComp : 1][kTile3];
+  using Acc = typename std::conditional<DET, long long, T>::type;
+  __shared__ Acc sacc[kP2G ? kComp : 1][kTile3];
+  __shared__ unsigned s_fxmax;
   __shared__ V4<T> stash[kP2G ? (ROWTAB ? 7 : 6) : 1][kP2G ? kStashN : 1];
   __shared__ int sloc[CHUNK];
   __shared__ int snb[27];
@@ -399,10 +447,23 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   if (kP2G)
     for (int t = t_lo + tid; t < t_hi; t += CHUNK)
 #pragma unroll
-      for (int a = 0; a < kComp; ++a) sacc[a][t] = T(0);
+      for (int a = 0; a < kComp; ++a) sacc[a][t] = Acc(0);
+  if (DET && tid == 0) s_fxmax = 0u;
   // D, the node velocities, the node masks and the grid sums come from the
   // grids before this one
   grid_dep_wait();
+  // Fixed-point scales of this CTA's scene: S for momentum terms, Sm for
+  // masses; fx_ok is the largest term bound S admits.
+  double fxS = 0.0, fxSm = 0.0, fx_ok = 0.0;
+  bool fx_bad = false;
+  if constexpr (DET) {
+    const unsigned* fxs = p.fx_max + (int64_t)info.z * p.fx_stride;
+    double unused;
+    if (MODE == kModeMassV || MODE == kModeMu) fxSm = fx_scale(fxs, 0, 0, S.n, &unused);
+    if (MODE == kModeMassV) fxS = fx_scale(fxs, 1, 0, S.n, &fx_ok);
+    if (MODE == kModeFirst || MODE == kModeMid)
+      fxS = fx_scale(fxs, p.fx_slot, fx_head(p.fx_err, p.fx_attempt, info.z), S.n, &fx_ok);
+  }
   if (kReadD && tid < count) {
     const int s = s0 + tid;
     q0 = p.D[s];
@@ -472,7 +533,8 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         while (other) {
           const int bo = __ffs(other) - 1;
           other &= other - 1;
-          const T M = p.gmb[(int64_t)bo * p.n_nodes + node];
+          const T M = DET ? (T)((double)p.gmb_fx[(int64_t)bo * p.n_nodes + node] / fxSm)
+                          : p.gmb[(int64_t)bo * p.n_nodes + node];
           num += w * p.mu_table[S.mu_off + body * S.n_bodies + bo] * M;
           den += w * M;
         }
@@ -540,7 +602,10 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         for (int a = 0; a < 9; ++a) dC[a] = p.pic ? T(0) : pC[a] + hC[a] - wC[a];
         out = MODE == kModeLast;
       }
-      if (out) {
+      if (DET && out && __ldcg(p.fx_err + p.fx_attempt * p.n_scenes + info.z) != 0) {
+        // an earlier pass of this attempt exceeded its fixed-point range: the
+        // step is repeated, and the caller's outputs stay untouched
+      } else if (out) {
         // V_hat = V + Delta_N, back in caller order, C = Ch / h
         T v[3], C[9];
         load12(p.V, n, s, v, C);
@@ -556,6 +621,11 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         store12(p.D, n, s, dv, dC);
         T u[3], uC[9];
         undesirable(dv, dC, nrm, mu, p.sep23, u, uC);
+        if constexpr (DET) {
+          const float b = fx_bound(pt.w, u, uC);
+          fx_bad = !(b <= fx_ok);
+          atomicMax(&s_fxmax, __float_as_uint(b));
+        }
         if constexpr (ROWTAB) {
           stash[0][sidx(tid)] = V4<T>{pt.w * wy[0], pt.w * wy[1], pt.w * wy[2], pt.w * wy[3]};
           stash[ROWTAB ? 6 : 0][sidx(tid)] = V4<T>{wz[0], wz[1], wz[2], wz[3]};
@@ -599,9 +669,17 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
       const int row = base + kz * (kTile * kTile) + ky * kTile;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
+        if constexpr (DET) {
 #pragma unroll
-        for (int c = 0; c < (kMom ? 3 : 1); ++c) atomicAdd(&sacc[c][row + k], acc.get(k, c));
-        if constexpr (MODE == kModeMassV) atomicAdd(&sacc[3][row + k], macc.get(k, 0));
+          for (int c = 0; c < (kMom ? 3 : 1); ++c)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&sacc[c][row + k]), to_fx(acc.get(k, c), fxS));
+          if constexpr (MODE == kModeMassV)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&sacc[3][row + k]), to_fx(macc.get(k, 0), fxSm));
+        } else {
+#pragma unroll
+          for (int c = 0; c < (kMom ? 3 : 1); ++c) atomicAdd(&sacc[c][row + k], acc.get(k, c));
+          if constexpr (MODE == kModeMassV) atomicAdd(&sacc[3][row + k], macc.get(k, 0));
+        }
       }
       acc.zero();
       macc.zero();
@@ -660,6 +738,29 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   __syncthreads();
 
   // ---------------- add the tile to the global grid ----------------
+  if constexpr (DET && kP2G && kMom) {
+    if (fx_bad) atomicOr(p.fx_err + p.fx_attempt * p.n_scenes + info.z, 1);
+    if (MODE != kModeMassV && tid == 0) atomicMax(p.fx_max + (int64_t)info.z * p.fx_stride + p.fx_slot + 1, s_fxmax);
+    for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
+      const int node = tile_node(snb, t);
+      if (node < 0) continue;
+      unsigned long long* g = reinterpret_cast<unsigned long long*>(p.gp64) + 4 * (int64_t)node;
+      if constexpr (MODE == kModeMassV) {
+        const long long mv = sacc[3][t];
+        if (mv != 0) {
+          atomicAdd(g + 3, (unsigned long long)mv);
+          atomicOr(&p.gmask[node], 1u << body);
+          if (p.gmb_fx)
+            atomicAdd(reinterpret_cast<unsigned long long*>(p.gmb_fx + (int64_t)body * p.n_nodes + node),
+                      (unsigned long long)mv);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (sacc[c][t] != 0) atomicAdd(g + c, (unsigned long long)sacc[c][t]);
+    }
+    return;
+  }
   for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
     const int node = tile_node(snb, t);
     if (node < 0) continue;
@@ -739,6 +840,80 @@ __device__ __forceinline__ int scene_of_page(const SceneDev* sc, int ns, long lo
     if (sc[mid].page_off <= g) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+// Deterministic mode: node velocities from the fixed-point sums of the pass
+// that used bound slot `slot` (all64: the mass pass, which also gives m_i),
+// with the scales that pass used; clears the sums for the next pass.
+__global__ void k_normalize_fx(int64_t n_nodes, const int* __restrict__ blist, const SceneDev* __restrict__ sc,
+                               int ns, float* gm, long long* gfx, V4<float>* gv, const unsigned* fx_max,
+                               const int* fx_err, int fx_stride, int slot, int attempt, int all64) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  grid_dep_launch();
+  grid_dep_wait();
+  if (i >= n_nodes) return;
+  const int scene = scene_of_page(sc, ns, blist[i / kNodesPerBlock]);
+  const unsigned* fxs = fx_max + (int64_t)scene * fx_stride;
+  const int n = sc[scene].n;
+  double unused;
+  long long* g = gfx + 4 * i;
+  float m;
+  if (all64) {
+    m = (float)((double)g[3] / fx_scale(fxs, 0, 0, n, &unused));
+    gm[i] = m;
+    g[3] = 0;
+  } else {
+    m = gm[i];
+  }
+  const double S = fx_scale(fxs, slot, all64 ? 0 : fx_head(fx_err, attempt, scene), n, &unused);
+  V4<float> v{0.f, 0.f, 0.f, 0.f};
+  if (m > 0.f) {
+    const double md = (double)m * S;
+    const float vz = (float)((double)g[2] / md);
+    v = V4<float>{(float)((double)g[0] / md), (float)((double)g[1] / md), vz, vz};
+  }
+  g[0] = g[1] = g[2] = 0;
+  gv[i] = v;
+}
+
+// Deterministic mode: per scene, the largest mass (slot 0) and the largest
+// term bound b_p of V (slot 1); a non-finite bound sets the scene's range
+// flag (err_row).  Each CTA covers a contiguous run of sorted particles and
+// keeps the maxima of its first scene in shared memory.
+__global__ void k_fx_prep(int64_t n, const SceneDev* __restrict__ sc, int ns, const int* __restrict__ perm,
+                          const V4<float>* __restrict__ pt, const V4<float>* __restrict__ V, unsigned* fx_max,
+                          int fx_stride, int* err_row, int per_cta) {
+  __shared__ unsigned smax[2];
+  __shared__ int first_scene;
+  const int64_t s0 = (int64_t)blockIdx.x * per_cta;
+  const int64_t s1 = min(s0 + per_cta, n);
+  if (threadIdx.x == 0) {
+    smax[0] = smax[1] = 0u;
+    first_scene = s0 < n ? scene_of_particle(sc, ns, perm[s0]) : -1;
+  }
+  __syncthreads();
+  for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+    const int scene = scene_of_particle(sc, ns, perm[s]);
+    const V4<float> q0 = V[s], q1 = V[n + s], q2 = V[2 * n + s];
+    const float w[3] = {q0.x, q0.y, q0.z};
+    const float Ch[9] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+    const float m = pt[s].w;
+    const float b = fx_bound(m, w, Ch);
+    if (!isfinite(b)) atomicOr(err_row + scene, 1);
+    const unsigned bm = __float_as_uint(m), bv = __float_as_uint(b);
+    if (scene == first_scene) {
+      atomicMax(&smax[0], bm);
+      atomicMax(&smax[1], bv);
+    } else {
+      atomicMax(fx_max + (int64_t)scene * fx_stride, bm);
+      atomicMax(fx_max + (int64_t)scene * fx_stride + 1, bv);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && first_scene >= 0) {
+    atomicMax(fx_max + (int64_t)first_scene * fx_stride, smax[0]);
+    atomicMax(fx_max + (int64_t)first_scene * fx_stride + 1, smax[1]);
+  }
 }
 
 // Cell of every particle (x/h in FP64, floor), validation, and the bounding
@@ -1156,10 +1331,32 @@ cudaError_t launch_items_cfg(const IterParams<T>& p, int mode, bool overlap, cud
   }
 }
 
+// Deterministic mode: the modes of the FP32 step, variant 0's CTA shape.
+template <class T>
+cudaError_t launch_items_fx(const IterParams<T>& p, int mode, bool overlap, cudaStream_t s) {
+  constexpr int B = kVariantMinBlocks[0], C = kVariantChunk[0];
+  const unsigned grid = (unsigned)p.n_items;
+  switch (mode) {
+#define APIC_MODE(m) \
+  case m: return launch_ex(k_items<T, m, B, C, false, true>, grid, C, overlap, s, p);
+    APIC_MODE(kModeFirst)
+    APIC_MODE(kModeMid)
+    APIC_MODE(kModeLast)
+    APIC_MODE(kModeOnly)
+    APIC_MODE(kModeMu)
+    APIC_MODE(kModeMassV)
+#undef APIC_MODE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <class T>
 cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, bool overlap, cudaStream_t s) {
   if (p.n_items <= 0) return cudaSuccess;
   if (variant < 0 || variant >= kNumVariants) return cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == 4) {
+    if (p.fx_max != nullptr) return variant == 0 ? launch_items_fx<T>(p, mode, overlap, s) : cudaErrorInvalidValue;
+  }
   if constexpr (sizeof(T) == 4) {
     // the FP32 path is built in every variant
 #define APIC_VARIANT(v) \
@@ -1185,6 +1382,22 @@ cudaError_t launch_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask
   if (n_nodes <= 0) return cudaSuccess;
   return launch_ex(k_normalize<T>, grid_for(n_nodes, 256), 256, overlap, s, n_nodes, gm, gmask, gp, gp64, gv,
                    all64);
+}
+
+cudaError_t launch_fx_prep(int64_t n, const SceneDev* sc, int ns, const int* perm, const V4<float>* pt,
+                           const V4<float>* V, unsigned* fx_max, int fx_stride, int* err_row, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int per_cta = 4096;
+  k_fx_prep<<<grid_for(n, per_cta), 256, 0, s>>>(n, sc, ns, perm, pt, V, fx_max, fx_stride, err_row, per_cta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normalize_fx(int64_t n_nodes, const int* blist, const SceneDev* sc, int ns, float* gm,
+                                long long* gfx, V4<float>* gv, const unsigned* fx_max, const int* fx_err,
+                                int fx_stride, int slot, int attempt, int all64, bool overlap, cudaStream_t s) {
+  if (n_nodes <= 0) return cudaSuccess;
+  return launch_ex(k_normalize_fx, grid_for(n_nodes, 256), 256, overlap, s, n_nodes, blist, sc, ns, gm, gfx, gv,
+                   fx_max, fx_err, fx_stride, slot, attempt, all64);
 }
 
 template <class T>

@@ -26,6 +26,7 @@
 #include <cstdio>
 #include <cstring>
 #include <utility>
+#include <vector>
 
 #include "../../include/apiccontact.h"
 #include "apic_internal.h"
@@ -38,7 +39,8 @@ enum Slot : int {
   kSlotGm, kSlotGmask, kSlotGp, kSlotGp64, kSlotGv, kSlotGmb, kSlotMuTable, kSlotCubTmp, kSlotScenes,
   kSlotSBbox, kSlotSMom, kSlotSCount, kSlotHX, kSlotHBody, kSlotHV, kSlotHC, kSlotHM, kSlotHN, kSlotHVo,
   kSlotHCo, kSlotDS, kSlotNrmAcc, kSlotNrmX, kSlotNrmTri, kSlotNrmOut, kSlotAugF, kSlotAugAm, kSlotAugVbar,
-  kSlotAugVhat, kSlotAugChat, kSlotAugNrm, kSlotAugOut, kSlotRunFlags, kSlotRunOffs, kSlotRunStart, kSlotCount
+  kSlotAugVhat, kSlotAugChat, kSlotAugNrm, kSlotAugOut, kSlotRunFlags, kSlotRunOffs, kSlotRunStart, kSlotFxMax,
+  kSlotFxErr, kSlotGmbFx, kSlotCount
 };
 
 constexpr int kMaxBodies = 32;
@@ -200,7 +202,10 @@ template <class T, class Env>
 apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream_t s, apic_stats* stats) {
   const uint32_t flags = scenes[0].flags;
   const bool host = (flags & APIC_HOST_PTRS) != 0;
+  const bool det = (flags & APIC_DETERMINISTIC) != 0;
   const int N = scenes[0].n_iter;
+  if (det && sizeof(T) != 4)
+    return pfail(APIC_ERR_INVALID_ARG, "APIC_DETERMINISTIC applies to the FP32 path (not with APIC_FP64)");
   typename Env::Span span_step(env, s, 0);
   typename Env::Span span_prep(env, s, 1);
 
@@ -307,7 +312,9 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
 
   // Kernel variant of this call (the autotuner's choice, or a variant it is
   // timing): its CTA size is also the largest work item the sizing makes.
-  const int variant = env.variant(sizeof(T), n);
+  // (deterministic mode: variant 0, whose item split fixes the order of
+  // every floating-point sum)
+  const int variant = det ? env.variant_fixed() : env.variant(sizeof(T), n);
   const int chunk = kVariantChunk[sizeof(T) == 4 ? variant : 0];
 
   DevScalars* ds = env.ds();
@@ -487,8 +494,17 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   P_TRY(env.take(kSlotGp, n_nodes, &gp, "grid momentum"));
   P_TRY(env.take(kSlotGv, n_nodes, &gv, "grid velocity"));
   if (sizeof(T) == 4) P_TRY(env.take(kSlotGp64, n_nodes, &gp64, "FP64 node momentum"));
+  unsigned* fx_max = nullptr;
+  int* fx_err = nullptr;
+  long long* gmb_fx = nullptr;
+  const int fx_stride = N + 2;
+  if (det) {
+    P_TRY(env.take(kSlotFxMax, (size_t)ns * fx_stride, &fx_max, "fixed-point bounds"));
+    P_TRY(env.take(kSlotFxErr, (size_t)2 * ns, &fx_err, "fixed-point range flags"));
+    if (any_mu) P_TRY(env.take(kSlotGmbFx, (size_t)max_bodies * n_nodes, &gmb_fx, "per-body grid mass (fixed)"));
+  }
   if (any_mu) {
-    P_TRY(env.take(kSlotGmb, (size_t)max_bodies * n_nodes, &gmb, "per-body grid mass"));
+    if (!det) P_TRY(env.take(kSlotGmb, (size_t)max_bodies * n_nodes, &gmb, "per-body grid mass"));
     P_TRY(env.take(kSlotMuTable, (size_t)n_mu, &mu_table, "friction tables"));
     P_TRY(env.take(kSlotMup, n, &mup, "particle friction"));
     T* hmu = static_cast<T*>(env.host_buf((size_t)n_mu * sizeof(T)));
@@ -536,6 +552,10 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   p.perm = perm;
   p.pic = (flags & APIC_VARIANT_PIC) ? 1 : 0;
   p.sep23 = (flags & APIC_VARIANT_SEP23) ? 1 : 0;
+  p.fx_max = fx_max;
+  p.fx_err = fx_err;
+  p.gmb_fx = gmb_fx;
+  p.fx_stride = fx_stride;
   key.mup = mup;
   key.n_iter = N;
   key.any_mu = any_mu ? 1 : 0;
@@ -552,26 +572,66 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     P_CUDA(cudaMemsetAsync(gp, 0, n_nodes * sizeof(V4<T>), q));
     if (gp64) P_CUDA(cudaMemsetAsync(gp64, 0, n_nodes * sizeof(V4<double>), q));
     if (gmb) P_CUDA(cudaMemsetAsync(gmb, 0, (size_t)max_bodies * n_nodes * sizeof(T), q));
+    // deterministic mode: the fixed-point sums live in gp64's storage as
+    // int64 (x, y, z, mass); bounds and this attempt's range flags start at 0
+    long long* gfx = reinterpret_cast<long long*>(gp64);
+    if (det) {
+      if (gmb_fx) P_CUDA(cudaMemsetAsync(gmb_fx, 0, (size_t)max_bodies * n_nodes * sizeof(long long), q));
+      P_CUDA(cudaMemsetAsync(fx_max, 0, (size_t)ns * fx_stride * sizeof(unsigned), q));
+      P_CUDA(cudaMemsetAsync(fx_err + pp.fx_attempt * ns, 0, ns * sizeof(int), q));
+      P_LAUNCH(env, launch_fx_prep(n, sc, ns, perm, reinterpret_cast<const V4<float>*>(pt),
+                                   reinterpret_cast<const V4<float>*>(V), fx_max, fx_stride,
+                                   fx_err + pp.fx_attempt * ns, q));
+    }
+    auto normalize = [&](int slot, int all64) -> cudaError_t {
+      if (det)
+        return launch_normalize_fx(n_nodes, blist, sc, ns, reinterpret_cast<float*>(gm), gfx,
+                                   reinterpret_cast<V4<float>*>(gv), fx_max, fx_err, fx_stride, slot,
+                                   pp.fx_attempt, all64, ov, q);
+      return launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, all64, ov, q);
+    };
     P_LAUNCH(env, launch_items<T>(pp, kModeMassV, var, false, q));
     if (any_mu) {
       P_LAUNCH(env, launch_items<T>(pp, kModeMu, var, ov, q));
       pp.mup = mup;
     }
-    P_LAUNCH(env, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 1, ov, q));
+    P_LAUNCH(env, normalize(1, 1));
     span_mass.stop();
 
     // 8. the N + 1 transfer passes.
     for (int pass = 0; pass <= N; ++pass) {
       const int mode = N == 0 ? kModeOnly : pass == 0 ? kModeFirst : pass == N ? kModeLast : kModeMid;
+      pp.fx_slot = 1 + pass;  // bound of the W this pass scatters, measured by the pass before
       {
         typename Env::Span span_pass(env, q, 2);
         P_LAUNCH(env, launch_items<T>(pp, mode, var, ov, q));
       }
-      if (pass < N) P_LAUNCH(env, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 0, ov, q));
+      if (pass < N) P_LAUNCH(env, normalize(1 + pass, 0));
     }
     return APIC_OK;
   };
   P_TRY(env.run_series(&key, sizeof(key), s, series));
+  if (det) {
+    // A pass whose terms outgrew the headroom of its fixed-point scale left
+    // the outputs of its scene untouched: repeat the series once with a wider
+    // headroom for those scenes (the sorted inputs are unchanged).
+    std::vector<int> bad(ns);
+    for (int attempt = 0;; ++attempt) {
+      P_CUDA(cudaMemcpyAsync(bad.data(), fx_err + attempt * ns, ns * sizeof(int), cudaMemcpyDeviceToHost, s));
+      P_CUDA(cudaStreamSynchronize(s));
+      int first_bad = -1;
+      for (int i = 0; i < ns && first_bad < 0; ++i)
+        if (bad[i]) first_bad = i;
+      if (first_bad < 0) break;
+      if (attempt == 1)
+        return pfail(APIC_ERR_INVALID_ARG,
+                     "scene %d: deterministic mode: node sums outgrew their fixed-point range "
+                     "(non-finite inputs, or terms growing by more than 2^%d within one pass)",
+                     first_bad, kFxRetryHeadLog2);
+      key.p.fx_attempt = 1;
+      P_TRY(env.run_series(&key, sizeof(key), s, series));
+    }
+  }
   span_step.stop();
 
   if (stats) {

@@ -99,6 +99,7 @@ struct StaticEnv {
   static const void* device_view(const void*) { return nullptr; }
   // default kernel variant, launched directly (no graph, no tuning state)
   int variant(size_t, int64_t) { return 0; }
+  int variant_fixed() { return 0; }
   template <class F>
   apic_status run_series(const void*, size_t, cudaStream_t s, F& body) {
     return body(s);
@@ -119,7 +120,7 @@ struct StaticEnv {
 extern "C" {
 
 apic_status apic_contact_step_static(const apic_step_args* a, void* stream, apic_stats* stats) {
-  P_TRY(validate_scene(a, 0, APIC_FP64 | APIC_VARIANT_PIC | APIC_VARIANT_SEP23));
+  P_TRY(validate_scene(a, 0, APIC_FP64 | APIC_VARIANT_PIC | APIC_VARIANT_SEP23 | APIC_DETERMINISTIC));
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (a->n == 0) return APIC_OK;
   StaticEnv env;
