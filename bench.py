@@ -294,6 +294,8 @@ def main():
     ap.add_argument("--variant", type=int, default=-1,
                     help="fix the transfer-kernel variant (default: autotune for the workload)")
     ap.add_argument("--no-graphs", action="store_true", help="launch the transfer passes one by one")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="APIC_DETERMINISTIC: bitwise-reproducible steps (fixed-point node sums, variant 0)")
     ap.add_argument("--no-overlap", action="store_true",
                     help="launch each pass strictly after the grid before it (no programmatic dependent launch)")
     ap.add_argument("--no-extras", action="store_true",
@@ -339,27 +341,30 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     ctx = apic.Context(dev.index)
+    FL = apic.APIC_DETERMINISTIC if args.deterministic else 0
 
     def step_one(b):
         apic.contact_step(ctx, b.x, b.v, b.C, b.m, b.nrm, b.body, b.h, b.mu, N, n_bodies=b.n_bodies,
-                          mu_pair=b.mu_pair, v_out=b.v_out, C_out=b.C_out, stream=stream)
+                          mu_pair=b.mu_pair, v_out=b.v_out, C_out=b.C_out, stream=stream, flags=FL)
 
     def step():
         if batched:
-            apic.contact_step_batched(ctx, bs, N, stream=stream)
+            apic.contact_step_batched(ctx, bs, N, stream=stream, flags=FL)
         else:
             step_one(bs[0])
 
     # pick the transfer-kernel variant for this size class (untimed), then
     # one checked step: the device's own momentum balance
     ctx.set_overlap(not args.no_overlap)
-    if args.variant >= 0:
+    if args.deterministic:
+        variant = 0  # the mode runs the first variant, untuned
+    elif args.variant >= 0:
         ctx.set_variant(args.variant)
         variant = args.variant
     else:
         variant = ctx.autotune(bs, N, stream=stream)
     ctx.set_graphs(not args.no_graphs)
-    st = apic.contact_step_batched(ctx, bs, N, stream=stream, stats=True)
+    st = apic.contact_step_batched(ctx, bs, N, stream=stream, stats=True, flags=FL)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
@@ -419,7 +424,7 @@ def main():
     if os.path.exists(tfile):
         try:
             tj = json.load(open(tfile))
-            if tj.get("kernel_source_hash") == kernel_source_hash():
+            if tj.get("kernel_source_hash") == kernel_source_hash() and not args.deterministic:
                 traffic = tj.get("dram_bytes_per_launch")
         except Exception:
             traffic = None
@@ -440,11 +445,11 @@ def main():
 
         def host_step():
             if batched:
-                apic.contact_step_batched(ctx, hs, N, stream=stream)
+                apic.contact_step_batched(ctx, hs, N, stream=stream, flags=FL)
             else:
                 h = hs[0]
                 apic.contact_step(ctx, h.x, h.v, h.C, h.m, h.nrm, h.body, h.h, h.mu, N, n_bodies=h.n_bodies,
-                                  mu_pair=h.mu_pair, v_out=h.v_out, C_out=h.C_out, stream=stream)
+                                  mu_pair=h.mu_pair, v_out=h.v_out, C_out=h.C_out, stream=stream, flags=FL)
 
         for _ in range(2):
             host_step()
@@ -478,6 +483,7 @@ def main():
         "kernel_variant": apic.variants()[variant],
         "cuda_graph": not args.no_graphs,
         "dependent_launch": not args.no_overlap,
+        "deterministic": bool(args.deterministic),
         "sort_primitive_calls_per_step": prof["sort_launches"] / max(prof["steps"], 1),
         "roofline": {"bound": "hbm", "kernel": "k_items (fused G2P + projection + P2G pass)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",

@@ -340,25 +340,42 @@ __device__ __forceinline__ float fx_bound(float m, const float* w, const float* 
   return m * b * 1.0001f;  // margin over the rounding of the terms themselves
 }
 // Scale of slot `slot` of one scene's bounds (fxs), headroom 2^lg, n terms
-// per node at most; *allowed = the largest b_p it admits.
-__device__ __forceinline__ double fx_scale(const unsigned* fxs, int slot, int lg, int n, double* allowed) {
+// per node at most: S = 2^e, the largest power of two with S n B <= 2^62
+// (e at most 100, B at most 2^90); *allowed = the largest b_p it admits.
+// FP32 and integer arithmetic only (every CTA and the normalisation compute
+// the same S).
+__device__ __forceinline__ float fx_scale(const unsigned* fxs, int slot, int lg, int n, float* allowed) {
   float B = __uint_as_float(fxs[slot]);
   if (slot >= 2) B = fmaxf(B, __uint_as_float(fxs[1]) * 0x1p-30f);  // W negligible next to V
-  B = fmaxf(B, 1e-30f);
-  const double Bd = ldexp((double)B, lg);
-  *allowed = Bd;
-  const double lim = 4611686018427387904.0 / ((double)max(n, 1) * Bd);  // 2^62 / (n B)
-  int e;
-  frexp(lim, &e);  // lim in [2^(e-1), 2^e)
-  return ldexp(1.0, e - 1);
+  B = fminf(ldexpf(fmaxf(B, 1e-30f), lg), 0x1p90f);  // n B stays finite in FP32
+  *allowed = B;
+  int k;
+  const float f = frexpf((float)max(n, 1) * B, &k);  // n B = f 2^k, f in [0.5, 1)
+  (void)f;
+  // n B <= 2^k, so S = 2^(62 - k) gives S n B <= 2^62 (up to the rounding of
+  // n B, well inside int64's 2^63)
+  return ldexpf(1.f, min(62 - k, 100));
 }
 // Headroom of a pass scattering W: the retry widens it for the scenes whose
 // first attempt recorded an excess.
 __device__ __forceinline__ int fx_head(const int* fx_err, int attempt, int scene) {
   return attempt > 0 && __ldcg(fx_err + scene) != 0 ? kFxRetryHeadLog2 : kFxHeadLog2;
 }
-__device__ __forceinline__ unsigned long long to_fx(float x, double S) {
-  return (unsigned long long)__double2ll_rn((double)x * S);
+// x S rounded to the nearest integer (ties to even).  x S is exact in FP32 (S
+// is a power of two) and holds 24 significant bits, so above 2^24 it already
+// is an integer m 2^e that shifts into place.
+__device__ __forceinline__ unsigned long long to_fx(float x, float S) {
+  const float r = rintf(x * S);
+  if (fabsf(r) < 16777216.f) return (unsigned long long)(long long)__float2int_rn(r);
+  const unsigned b = __float_as_uint(r);
+  const int e = (int)((b >> 23) & 0xffu) - 150;  // r = m 2^e, 1 <= e
+  const unsigned long long v = (unsigned long long)((b & 0x7fffffu) | 0x800000u) << min(e, 63);
+  return (b >> 31) ? (unsigned long long)(-(long long)v) : v;
+}
+// A fixed-point sum back to FP32 (hi and lo words, deterministic rounding).
+__device__ __forceinline__ float from_fx(long long g, float inv_S) {
+  const float hi = (float)(int)(g >> 32), lo = (float)(unsigned)(g & 0xffffffffull);
+  return fmaf(hi, 4294967296.f, lo) * inv_S;
 }
 
 // One work item = up to CHUNK sorted particles of one body whose cells lie
@@ -454,11 +471,11 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   grid_dep_wait();
   // Fixed-point scales of this CTA's scene: S for momentum terms, Sm for
   // masses; fx_ok is the largest term bound S admits.
-  double fxS = 0.0, fxSm = 0.0, fx_ok = 0.0;
+  float fxS = 0.f, fxSm = 0.f, fx_ok = 0.f;
   bool fx_bad = false;
   if constexpr (DET) {
     const unsigned* fxs = p.fx_max + (int64_t)info.z * p.fx_stride;
-    double unused;
+    float unused;
     if (MODE == kModeMassV || MODE == kModeMu) fxSm = fx_scale(fxs, 0, 0, S.n, &unused);
     if (MODE == kModeMassV) fxS = fx_scale(fxs, 1, 0, S.n, &fx_ok);
     if (MODE == kModeFirst || MODE == kModeMid)
@@ -533,7 +550,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         while (other) {
           const int bo = __ffs(other) - 1;
           other &= other - 1;
-          const T M = DET ? (T)((double)p.gmb_fx[(int64_t)bo * p.n_nodes + node] / fxSm)
+          const T M = DET ? (T)from_fx(p.gmb_fx[(int64_t)bo * p.n_nodes + node], 1.f / fxSm)
                           : p.gmb[(int64_t)bo * p.n_nodes + node];
           num += w * p.mu_table[S.mu_off + body * S.n_bodies + bo] * M;
           den += w * M;
@@ -855,30 +872,30 @@ __global__ void k_normalize_fx(int64_t n_nodes, const int* __restrict__ blist, c
   const int scene = scene_of_page(sc, ns, blist[i / kNodesPerBlock]);
   const unsigned* fxs = fx_max + (int64_t)scene * fx_stride;
   const int n = sc[scene].n;
-  double unused;
+  float unused;
   long long* g = gfx + 4 * i;
   float m;
   if (all64) {
-    m = (float)((double)g[3] / fx_scale(fxs, 0, 0, n, &unused));
+    m = from_fx(g[3], 1.f / fx_scale(fxs, 0, 0, n, &unused));
     gm[i] = m;
     g[3] = 0;
   } else {
     m = gm[i];
   }
-  const double S = fx_scale(fxs, slot, all64 ? 0 : fx_head(fx_err, attempt, scene), n, &unused);
+  const float S = fx_scale(fxs, slot, all64 ? 0 : fx_head(fx_err, attempt, scene), n, &unused);
   V4<float> v{0.f, 0.f, 0.f, 0.f};
   if (m > 0.f) {
-    const double md = (double)m * S;
-    const float vz = (float)((double)g[2] / md);
-    v = V4<float>{(float)((double)g[0] / md), (float)((double)g[1] / md), vz, vz};
+    const float inv = 1.f / S;
+    const float vz = from_fx(g[2], inv) / m;
+    v = V4<float>{from_fx(g[0], inv) / m, from_fx(g[1], inv) / m, vz, vz};
   }
   g[0] = g[1] = g[2] = 0;
   gv[i] = v;
 }
 
 // Deterministic mode: per scene, the largest mass (slot 0) and the largest
-// term bound b_p of V (slot 1); a non-finite bound sets the scene's range
-// flag (err_row).  Each CTA covers a contiguous run of sorted particles and
+// term bound b_p of V (slot 1); a bound that is not finite, or beyond the
+// 2^90 the scales cover, sets the scene's range flag (err_row).  Each CTA covers a contiguous run of sorted particles and
 // keeps the maxima of its first scene in shared memory.
 __global__ void k_fx_prep(int64_t n, const SceneDev* __restrict__ sc, int ns, const int* __restrict__ perm,
                           const V4<float>* __restrict__ pt, const V4<float>* __restrict__ V, unsigned* fx_max,
@@ -899,7 +916,7 @@ __global__ void k_fx_prep(int64_t n, const SceneDev* __restrict__ sc, int ns, co
     const float Ch[9] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
     const float m = pt[s].w;
     const float b = fx_bound(m, w, Ch);
-    if (!isfinite(b)) atomicOr(err_row + scene, 1);
+    if (!(b <= 0x1p90f) || !(m <= 0x1p90f)) atomicOr(err_row + scene, 1);  // NaN, inf or beyond the scales
     const unsigned bm = __float_as_uint(m), bv = __float_as_uint(b);
     if (scene == first_scene) {
       atomicMax(&smax[0], bm);
