@@ -83,6 +83,10 @@ struct apic_ctx {
   bool overlap_on = true;  // programmatic dependent launch between the passes
   GraphSlot gsizing, gseries;
   cudaStream_t cap_stream = nullptr;
+  // side stream of the host path (v and C cross the host link while the
+  // sizing sequence runs) and its two events
+  cudaStream_t side = nullptr;
+  cudaEvent_t side_ev[2] = {nullptr, nullptr};
   uint64_t alloc_gen = 0;  // bumped whenever a scratch buffer moves
 };
 
@@ -248,6 +252,28 @@ struct CtxEnv {
     }
     return c->h_copies;
   }
+  // Side stream and events for overlapping host-to-device staging (nullptr
+  // if they cannot be created: the caller then stages on its own stream).
+  cudaStream_t side_stream() {
+    if (!c->side) {
+      if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->side = nullptr;
+        return nullptr;
+      }
+      for (cudaEvent_t& e : c->side_ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+          cudaGetLastError();
+          for (cudaEvent_t& f : c->side_ev)
+            if (f) cudaEventDestroy(f), f = nullptr;
+          cudaStreamDestroy(c->side);
+          c->side = nullptr;
+          return nullptr;
+        }
+    }
+    return c->side;
+  }
+  cudaEvent_t side_event(int k) { return c->side_ev[k]; }
   // The device's address of a page-locked host array, or nullptr (pageable
   // memory, device memory, or no mapping).
   static const void* device_view(const void* p) {
@@ -480,6 +506,9 @@ apic_status apic_destroy(apic_ctx* c) {
   if (c->h_scenes) cudaFreeHost(c->h_scenes);
   if (c->h_copies) cudaFreeHost(c->h_copies);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side) cudaStreamDestroy(c->side);
+  for (cudaEvent_t e : c->side_ev)
+    if (e) cudaEventDestroy(e);
   delete c;
   return APIC_OK;
 }

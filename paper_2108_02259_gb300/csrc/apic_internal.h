@@ -138,9 +138,14 @@ cudaError_t launch_cells(int64_t n, const SceneDev* sc, int ns, int4* cellb, int
 template <class K>
 cudaError_t launch_keys(int64_t n, const SceneDev* sc, int ns, const int4* cellb, int max_bodies, K* keys,
                         int* vals, int* err, cudaStream_t s);
+// V == nullptr: pt and pn's cell bits only (launch_gather_v fills the
+// normals and V later).
 template <class T>
 cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm, const int4* cellb, V4<T>* pt,
                           V4<T>* pn, V4<T>* V, cudaStream_t s);
+template <class T>
+cudaError_t launch_gather_v(int64_t n, const SceneDev* sc, int ns, const int* perm, V4<T>* pn, V4<T>* V,
+                            cudaStream_t s);
 // Run heads: flags[s] = 1 where the (grid block, body) of sorted particle s
 // differs from s - 1.
 template <class K>

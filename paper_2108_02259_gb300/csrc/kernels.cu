@@ -1074,8 +1074,38 @@ __global__ void k_gather(int64_t n, const SceneDev* __restrict__ sc, int ns, con
   const T tz = (T)(x[3 * i + 2] * S.inv_h - (double)c.z);
   pt[s] = V4<T>{tx, ty, tz, static_cast<const T*>(S.m)[i]};
   const uint32_t loc = (uint32_t)(((c.z & 3) << 4) | ((c.y & 3) << 2) | (c.x & 3));
+  if (V == nullptr) {  // normals and V planes gathered later (k_gather_v)
+    pn[s] = V4<T>{T(0), T(0), T(0), bits_to(T(0), loc)};
+    return;
+  }
   const T* nrm = static_cast<const T*>(S.nrm);
   pn[s] = V4<T>{nrm[3 * i + 0], nrm[3 * i + 1], nrm[3 * i + 2], bits_to(T(0), loc)};
+  const T hh = (T)S.h;
+  const T* v = static_cast<const T*>(S.v);
+  const T* C = static_cast<const T*>(S.C);
+  T vv[3], Ch[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) vv[a] = v[3 * i + a];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) Ch[a] = C[9 * i + a] * hh;
+  store12(V, (int)n, (int)s, vv, Ch);
+}
+
+// The normals (into pn's first three components) and the V = (v, h C)
+// planes, in sorted order, when v, C and the normals arrive after the sizing
+// sequence has started.
+template <class T>
+__global__ void k_gather_v(int64_t n, const SceneDev* __restrict__ sc, int ns, const int* __restrict__ perm,
+                           V4<T>* pn, V4<T>* V) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int64_t g = perm[s];
+  const SceneDev& S = sc[scene_of_particle(sc, ns, g)];
+  const int64_t i = g - S.part_off;
+  const T* nrm = static_cast<const T*>(S.nrm);
+  pn[s].x = nrm[3 * i + 0];
+  pn[s].y = nrm[3 * i + 1];
+  pn[s].z = nrm[3 * i + 2];
   const T hh = (T)S.h;
   const T* v = static_cast<const T*>(S.v);
   const T* C = static_cast<const T*>(S.C);
@@ -1265,6 +1295,14 @@ cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm
                           V4<T>* pn, V4<T>* V, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_gather<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, perm, cellb, pt, pn, V);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_gather_v(int64_t n, const SceneDev* sc, int ns, const int* perm, V4<T>* pn, V4<T>* V,
+                            cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_gather_v<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, perm, pn, V);
   return cudaGetLastError();
 }
 
@@ -1725,6 +1763,8 @@ cudaError_t launch_copy_table(const CopyEntry* table, int n_entries, long long m
   template cudaError_t launch_cells<T>(int64_t, const SceneDev*, int, int4*, int*, int*, cudaStream_t); \
   template cudaError_t launch_gather<T>(int64_t, const SceneDev*, int, const int*, const int4*, V4<T>*,  \
                                         V4<T>*, V4<T>*, cudaStream_t);                                  \
+  template cudaError_t launch_gather_v<T>(int64_t, const SceneDev*, int, const int*, V4<T>*, V4<T>*,     \
+                                          cudaStream_t);                                                \
   template cudaError_t launch_items<T>(const IterParams<T>&, int, int, bool, cudaStream_t);             \
   template cudaError_t launch_normalize<T>(int64_t, const T*, const uint32_t*, V4<T>*, V4<double>*,     \
                                            V4<T>*, int, bool, cudaStream_t);                            \

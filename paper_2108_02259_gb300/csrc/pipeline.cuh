@@ -248,6 +248,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     return pfail(APIC_ERR_INVALID_ARG, "the batch holds %lld particles, beyond the per-call limit %d", (long long)n,
                  INT32_MAX / 4);
 
+  bool split_v = false;  // V planes gathered after the sizing sequence (see below)
   if (host) {
     double* dx;
     int32_t* db;
@@ -260,33 +261,54 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     P_TRY(env.take(kSlotHN, 3 * n, &dn, "staged normals"));
     P_TRY(env.take(kSlotHVo, 3 * n, &dvo, "staged v_out"));
     P_TRY(env.take(kSlotHCo, 9 * n, &dCo, "staged C_out"));
-    // Page-locked caller arrays are staged by one table-driven copy kernel
-    // (the host link is the limit either way, but per-copy overheads add up
-    // over many scenes); otherwise, or when a table is not available, one
-    // copy per array.
+    // Page-locked caller arrays are staged by table-driven copy kernels (the
+    // host link is the limit either way, but per-copy overheads add up over
+    // many scenes); otherwise, or when a table is not available, one copy
+    // per array.  With a side stream, normals, v and C (60 of the 92 bytes
+    // per FP32 particle) cross the link while the sizing sequence runs: only
+    // the passes need them (split_v).  Table layout: [0, 3 ns) x, body, m
+    // (all six arrays in [0, 6 ns) without the side stream); [3 ns, 6 ns)
+    // nrm, v, C; [6 ns, 8 ns) the results on the way back, written while the
+    // second copy may still be reading its own entries.
     CopyEntry* tab = env.copy_table(8 * ns);
     bool direct = tab != nullptr;
-    int nt = 0;
-    long long max_bytes = 0;
+    cudaStream_t side = direct ? env.side_stream() : nullptr;
+    int na = 0, nb = 0;
+    long long max_a = 0, max_b = 0;
     for (int i = 0; i < ns && direct; ++i) {
       const apic_step_args& a = scenes[i];
       const int64_t o = hsc[i].part_off, m = a.n;
       if (m == 0) continue;
       const std::pair<const void*, std::pair<void*, long long>> parts[6] = {
           {a.x, {dx + 3 * o, 3 * m * (long long)sizeof(double)}}, {a.body, {db + o, m * (long long)sizeof(int32_t)}},
-          {a.v, {dv + 3 * o, 3 * m * (long long)sizeof(T)}},      {a.C, {dC + 9 * o, 9 * m * (long long)sizeof(T)}},
-          {a.m, {dm + o, m * (long long)sizeof(T)}},               {a.nrm, {dn + 3 * o, 3 * m * (long long)sizeof(T)}}};
-      for (const auto& pt : parts) {
-        const void* src = env.device_view(pt.first);
+          {a.m, {dm + o, m * (long long)sizeof(T)}},               {a.nrm, {dn + 3 * o, 3 * m * (long long)sizeof(T)}},
+          {a.v, {dv + 3 * o, 3 * m * (long long)sizeof(T)}},      {a.C, {dC + 9 * o, 9 * m * (long long)sizeof(T)}}};
+      for (int k = 0; k < 6; ++k) {
+        const void* src = env.device_view(parts[k].first);
         if (!src) {
           direct = false;
           break;
         }
-        tab[nt++] = CopyEntry{src, pt.second.first, pt.second.second};
-        max_bytes = std::max(max_bytes, pt.second.second);
+        const CopyEntry e{src, parts[k].second.first, parts[k].second.second};
+        if (k < 3 || !side) {
+          tab[na++] = e;
+          max_a = std::max(max_a, e.bytes);
+        } else {
+          tab[3 * ns + nb++] = e;
+          max_b = std::max(max_b, e.bytes);
+        }
       }
     }
-    if (direct) P_LAUNCH(env, launch_copy_table(tab, nt, max_bytes, s));
+    split_v = direct && side != nullptr && nb > 0;
+    if (direct) P_LAUNCH(env, launch_copy_table(tab, na, max_a, s));
+    if (split_v) {
+      // after the first copy (which the sizing sequence waits for, so the
+      // two do not share the link) and everything queued before it
+      P_CUDA(cudaEventRecord(env.side_event(0), s));
+      P_CUDA(cudaStreamWaitEvent(side, env.side_event(0), 0));
+      P_LAUNCH(env, launch_copy_table(tab + 3 * ns, nb, max_b, side));
+      P_CUDA(cudaEventRecord(env.side_event(1), side));
+    }
     for (int i = 0; i < ns; ++i) {
       const apic_step_args& a = scenes[i];
       const int64_t o = hsc[i].part_off, m = a.n;
@@ -346,8 +368,9 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       P_TRY((sort_keys<uint64_t>(env, n, sc, ns, cellb, max_bodies, &ds->err, sb, q)));
     else
       P_TRY((sort_keys<uint32_t>(env, n, sc, ns, cellb, max_bodies, &ds->err, sb, q)));
-    // 4. sorted SoA.
-    P_LAUNCH(env, launch_gather<T>(n, sc, ns, sb.perm, cellb, pt, pn, V, q));
+    // 4. sorted SoA (normals and V planes later when they are still in
+    //    transit).
+    P_LAUNCH(env, launch_gather<T>(n, sc, ns, sb.perm, cellb, pt, pn, split_v ? nullptr : V, q));
     // 5. work items: runs of equal (grid block, body), each split into
     //    equal items of at most `chunk` particles (the variant's CTA size).
     if (sb.k64)
@@ -398,10 +421,11 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       }
       struct SizingKey {
         int64_t n, NB;
-        int ns, max_bodies, tsize, host, chunk, pad;
+        int ns, max_bodies, tsize, host, chunk, split_v;
       } key;
       std::memset(&key, 0, sizeof(key));
       key.chunk = chunk;
+      key.split_v = split_v ? 1 : 0;
       key.n = n;
       key.NB = NB;
       key.ns = ns;
@@ -522,7 +546,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   struct PassKey {
     IterParams<T> p;
     T* mup;
-    int n_iter, any_mu, variant, pad;
+    int n_iter, any_mu, variant, split_v;
   };
   PassKey key;
   std::memset(&key, 0, sizeof(key));  // padding bytes take part in the comparison
@@ -560,10 +584,12 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   key.n_iter = N;
   key.any_mu = any_mu ? 1 : 0;
   key.variant = variant;
+  key.split_v = split_v ? 1 : 0;
 
   auto series = [&](cudaStream_t q) -> apic_status {
     IterParams<T> pp = key.p;
     const int var = key.variant;
+    if (split_v) P_LAUNCH(env, launch_gather_v<T>(n, sc, ns, perm, pn, V, q));
     // every launch after the mass pass follows a k_items or k_normalize launch
     const bool ov = env.overlap();
     typename Env::Span span_mass(env, q, 3);
@@ -610,6 +636,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     }
     return APIC_OK;
   };
+  if (split_v) P_CUDA(cudaStreamWaitEvent(s, env.side_event(1), 0));  // v and C staged
   P_TRY(env.run_series(&key, sizeof(key), s, series));
   if (det) {
     // A pass whose terms outgrew the headroom of its fixed-point scale left

@@ -96,6 +96,8 @@ struct StaticEnv {
   void done(int64_t, int64_t) {}
   // device pointers only: no host staging
   CopyEntry* copy_table(int) { return nullptr; }
+  cudaStream_t side_stream() { return nullptr; }
+  cudaEvent_t side_event(int) { return nullptr; }
   static const void* device_view(const void*) { return nullptr; }
   // default kernel variant, launched directly (no graph, no tuning state)
   int variant(size_t, int64_t) { return 0; }

@@ -212,3 +212,33 @@ def test_page_locked_host_arrays(ctx):
                           pinned(f.m, np.float32, 1), pinned(f.nrm, np.float32), pinned(f.body, np.int32, 1), s.h, s.mu,
                           3, n_bodies=s.n_bodies, v_out=vo, C_out=Co)
     _check(s, r.v.astype(np.float64), r.C.astype(np.float64).reshape(-1, 3, 3), None, label="pinned single")
+
+
+def test_page_locked_repeat_calls_pick_up_new_inputs(ctx):
+    """With page-locked arrays, v and C are staged on a side stream while the
+    sizing sequence runs, and their sorted planes are gathered at the start
+    of the passes.  Repeated calls (direct, captured, replayed) must each see
+    the velocities written into the same host buffers just before the call."""
+    import torch
+
+    from paper_2108_02259_gb300 import apic
+
+    def pinned(a, dt):
+        a = np.ascontiguousarray(a, dt)
+        t = torch.empty(a.shape, dtype=getattr(torch, np.dtype(dt).name)).pin_memory()
+        v = t.numpy()
+        v[...] = a
+        return v
+
+    s = scenes.four_bodies(scale=0.05, n_iter=3)
+    f = s.astype(np.float32)
+    X, V, Cc, M, NR, B = (pinned(f.x, np.float64), pinned(f.v, np.float32), pinned(f.C, np.float32),
+                          pinned(f.m, np.float32), pinned(f.nrm, np.float32), pinned(f.body, np.int32))
+    vo, Co = pinned(np.zeros_like(f.v), np.float32), pinned(np.zeros_like(f.C), np.float32)
+    for k in range(4):
+        scale = 1.0 + 0.5 * k
+        V[...] = f.v * scale
+        Cc[...] = f.C * scale
+        apic.contact_step(ctx, X, V, Cc, M, NR, B, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies, v_out=vo, C_out=Co)
+        sk = scenes.Scene(**{**s.__dict__, "v": s.v * scale, "C": s.C * scale})
+        _check(sk, vo.astype(np.float64), Co.astype(np.float64).reshape(-1, 3, 3), None, label=f"call {k}")
