@@ -195,6 +195,8 @@ def algorithmic_bytes_per_pass(P, G):
 FLOP_PER_PARTICLE_PASS = 2400.0
 # GB300 FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (maximum SM clock).
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Shared-memory peak: one 128-byte wavefront per SM per clock.
+SMEM_PEAK_GWAVEFRONTS = 152 * 2.07
 
 
 def bounded_sample(s, max_particles=1_100_000):
@@ -419,15 +421,16 @@ def main():
     alg = algorithmic_bytes_per_pass(P, G)
     peak, peak_kind = measured_peak_hbm()
     achieved = alg / (iter_avg_ms / 1e3) / 1e9
-    traffic = None
+    traffic = wavefronts = None
     tfile = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
     if os.path.exists(tfile):
         try:
             tj = json.load(open(tfile))
             if tj.get("kernel_source_hash") == kernel_source_hash() and not args.deterministic:
                 traffic = tj.get("dram_bytes_per_launch")
+                wavefronts = tj.get("shared_wavefronts_per_launch")
         except Exception:
-            traffic = None
+            traffic = wavefronts = None
 
     # end to end: the same step through the C ABI from pinned host buffers
     e2e = None
@@ -496,6 +499,14 @@ def main():
                           "frac": FLOP_PER_PARTICLE_PASS * P / (iter_avg_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
                           "flop_per_particle_pass": FLOP_PER_PARTICLE_PASS,
                           "peak_from": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"},
+        # the unit that binds: shared-memory wavefronts of one launch (ncu,
+        # same kernel source) over its live duration
+        "roofline_smem": None if wavefronts is None else {
+            "bound": "shared", "kernel": "k_items (fused G2P + projection + P2G pass)",
+            "achieved": wavefronts / (iter_avg_ms / 1e3) / 1e9, "peak": SMEM_PEAK_GWAVEFRONTS,
+            "unit": "G wavefronts/s", "frac": wavefronts / (iter_avg_ms / 1e3) / 1e9 / SMEM_PEAK_GWAVEFRONTS,
+            "wavefronts_per_launch": wavefronts, "peak_from": "152 SMs x 1 wavefront/clock x 2.07 GHz",
+            "wavefronts_from": f"profiles/traffic_{args.workload}.json (ncu)"},
         "step_breakdown_ms": step_breakdown(prof),
         "momentum_check": {"P_drift_rel": drift,
                            "multibody_nodes": int(sum(x["multibody_nodes"] for x in st)),

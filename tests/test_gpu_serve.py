@@ -76,26 +76,29 @@ def test_served_steps_match_oracle(apic):
             hdl.close()
 
 
-def test_same_result_alone_and_in_the_mix(apic):
+@pytest.mark.parametrize("det", [False, True])
+def test_same_result_alone_and_in_the_mix(apic, det):
     """A simulation stepped alone and stepped while many others are submitted
     concurrently (so its requests share batches and overlap with other
-    batches on the GPU) reaches the same state."""
+    batches on the GPU) reaches the same state: within the FP32 tolerance,
+    and bit for bit when every simulation runs with APIC_DETERMINISTIC."""
     target = _sims(1, seed=7)[0]
     others = _sims(12, seed=8)
     steps = 4
     dt = 0.1 * target.h / np.abs(target.v).max()
+    flags = apic.APIC_DETERMINISTIC if det else 0
 
     def run(with_mix):
         with apic.Server(0, n_workers=3, max_batch_scenes=16) as srv:
             f = target.astype(np.float32)
             a = srv.open_sim(f.x, f.v, f.C, f.m, f.nrm, f.body, target.h, target.mu, target.n_iter,
-                             n_bodies=target.n_bodies)
+                             n_bodies=target.n_bodies, flags=flags)
             mix = []
             if with_mix:
                 for s in others:
                     g = s.astype(np.float32)
                     mix.append(srv.open_sim(g.x, g.v, g.C, g.m, g.nrm, g.body, s.h, s.mu, s.n_iter,
-                                            n_bodies=s.n_bodies))
+                                            n_bodies=s.n_bodies, flags=flags))
             stop = threading.Event()
 
             def churn():
@@ -121,8 +124,10 @@ def test_same_result_alone_and_in_the_mix(apic):
     mixed, mean_batch = run(True)
     assert mean_batch > 1.0  # the target really shared batches
     ev, ec, ex = _err(target, mixed, alone)
-    print(f"[serve] alone vs mix: v {ev:.2e} C {ec:.2e} x {ex:.2e}, mean batch {mean_batch:.2f}")
+    print(f"[serve] alone vs mix (det={det}): v {ev:.2e} C {ec:.2e} x {ex:.2e}, mean batch {mean_batch:.2f}")
     assert ev <= TOL_V and ec <= TOL_C and ex <= steps * dt * TOL_V * np.abs(target.v).max()
+    if det:
+        assert all(np.array_equal(p, q) for p, q in zip(mixed, alone))
 
 
 def test_admission_by_budget(apic):
