@@ -72,6 +72,10 @@ typedef int32_t apic_status;
                                         fails (or inputs are non-finite) the call returns
                                         APIC_ERR_INVALID_ARG and leaves that scene's outputs
                                         untouched.  Statistics (apic_stats) are still FP64 sums.  */
+#define APIC_CHECK (1u << 6)         /* Also validate v, C and nrm: every component finite, each
+                                        normal 0 or of unit length (|n|^2 within 1e-3 of 1);
+                                        otherwise APIC_ERR_INVALID_ARG.  Positions, masses and body
+                                        ids are always validated.  Reads v, C and nrm once more.   */
 
 typedef struct apic_ctx apic_ctx;
 
@@ -424,6 +428,23 @@ apic_status apic_autotune(apic_ctx* ctx, const apic_step_args* scenes, int32_t n
  * launch them one by one (0).  Profiling (apic_set_profiling) launches them
  * one by one regardless, to time each pass. */
 apic_status apic_set_graphs(apic_ctx* ctx, int32_t on);
+
+/* Device memory for the context's scratch (sort buffers, sorted particle
+ * planes, grid nodes, staging) from the caller's allocator instead of
+ * cudaMalloc, e.g. a framework's caching allocator.  alloc(user, bytes,
+ * device) returns a device pointer aligned to 256 bytes, or NULL (the call
+ * that needed it fails with APIC_ERR_OUT_OF_MEMORY); free(user, ptr, bytes,
+ * device) takes back a block alloc returned.  The library synchronises the
+ * device before it hands a block back (scratch grows rarely, and a caching
+ * allocator may reuse the block at once) and frees everything in
+ * apic_destroy.  The budget of apic_create still applies.  Give both
+ * functions, or neither (cudaMalloc); set them before the first step:
+ * APIC_ERR_INVALID_ARG once the context holds scratch.  Small fixed buffers
+ * (device counters, page-locked staging tables) stay the library's.  Not in
+ * the paper. */
+typedef void* (*apic_alloc_fn)(void* user, size_t bytes, int32_t device);
+typedef void (*apic_free_fn)(void* user, void* ptr, size_t bytes, int32_t device);
+apic_status apic_set_allocator(apic_ctx* ctx, apic_alloc_fn alloc, apic_free_fn free_fn, void* user);
 
 /* Launch each transfer pass and node normalisation with programmatic
  * dependent launch (1, the default), so that a grid's prologue overlaps the

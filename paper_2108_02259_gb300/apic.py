@@ -32,6 +32,7 @@ APIC_HOST_PTRS = 1 << 1
 APIC_VARIANT_PIC = 1 << 2
 APIC_VARIANT_SEP23 = 1 << 3
 APIC_DETERMINISTIC = 1 << 5
+APIC_CHECK = 1 << 6
 APIC_AUGURY_INIT = 1 << 4
 
 EXPORTED = [
@@ -40,9 +41,14 @@ EXPORTED = [
     "apic_contact_step_batched", "apic_server_create", "apic_server_destroy", "apic_sim_open", "apic_sim_submit",
     "apic_ticket_poll", "apic_ticket_wait", "apic_sim_read", "apic_sim_close", "apic_server_get_stats",
     "apic_variant_count", "apic_variant_name", "apic_set_variant", "apic_get_variant", "apic_autotune",
-    "apic_set_graphs", "apic_set_overlap", "apic_server_set_policy", "apic_node_normals", "apic_augury_steps",
+    "apic_set_graphs", "apic_set_overlap", "apic_set_allocator", "apic_server_set_policy", "apic_node_normals",
+    "apic_augury_steps",
     "apic_sim_export", "apic_sim_import",
 ]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_int32)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_size_t, C.c_int32)
 
 
 class StepArgs(C.Structure):
@@ -155,6 +161,7 @@ def load(path: str = LIB_PATH):
     lib.apic_autotune.argtypes = [P, C.POINTER(StepArgs), C.c_int32, P, C.POINTER(C.c_int32)]
     lib.apic_set_graphs.argtypes = [P, C.c_int32]
     lib.apic_set_overlap.argtypes = [P, C.c_int32]
+    lib.apic_set_allocator.argtypes = [P, ALLOC_FN, FREE_FN, P]
     lib.apic_server_set_policy.argtypes = [P, C.c_int32, C.c_int32]
     lib.apic_node_normals.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_uint32, P]
     lib.apic_node_normals.restype = C.c_int32
@@ -167,7 +174,7 @@ def load(path: str = LIB_PATH):
     lib.apic_server_set_policy.restype = C.c_int32
     for f in ("apic_create", "apic_destroy", "apic_contact_step", "apic_set_profiling", "apic_get_profile",
               "apic_scratch_bytes", "apic_set_variant", "apic_get_variant", "apic_autotune", "apic_set_graphs",
-              "apic_set_overlap"):
+              "apic_set_overlap", "apic_set_allocator"):
         getattr(lib, f).restype = C.c_int32
     _lib = lib
     return lib
@@ -243,6 +250,24 @@ class Context:
     def set_graphs(self, on: bool):
         """Replay the transfer passes as a CUDA graph (default) or not."""
         _check(load().apic_set_graphs(self._h, 1 if on else 0))
+
+    def set_allocator(self, alloc, free):
+        """Serve the context's scratch from alloc(nbytes, device) -> int
+        device pointer (256-byte aligned, 0 on failure) and free(ptr, nbytes,
+        device), e.g. torch.cuda.caching_allocator_alloc / _delete.  Before
+        the first step only."""
+        def a(_user, nbytes, device):
+            try:
+                return int(alloc(int(nbytes), int(device)))
+            except Exception:
+                return 0
+
+        def f(_user, ptr, nbytes, device):
+            free(int(ptr), int(nbytes), int(device))
+
+        cbs = (ALLOC_FN(a), FREE_FN(f))
+        _check(load().apic_set_allocator(self._h, cbs[0], cbs[1], None))
+        self._alloc_cbs = cbs  # the library calls them until the context is destroyed
 
     def set_overlap(self, on: bool):
         """Let each pass start while the grid before it finishes (default) or not."""

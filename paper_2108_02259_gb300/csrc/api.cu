@@ -88,6 +88,10 @@ struct apic_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t side_ev[2] = {nullptr, nullptr};
   uint64_t alloc_gen = 0;  // bumped whenever a scratch buffer moves
+  // the caller's device allocator for scratch (apic_set_allocator), or none
+  apic_alloc_fn ualloc = nullptr;
+  apic_free_fn ufree = nullptr;
+  void* uuser = nullptr;
 };
 
 namespace {
@@ -102,26 +106,52 @@ apic_status grow(apic_ctx* c, Buf& b, size_t bytes) {
                    bytes, c->held, c->budget);
   }
   if (b.ptr) {
-    cudaError_t e = cudaFree(b.ptr);
-    if (e != cudaSuccess) return pfail(APIC_ERR_CUDA, "cudaFree: %s", cudaGetErrorString(e));
+    if (c->ufree) {
+      // the caller's allocator may hand the block out again at once: every
+      // queued kernel that could still use it finishes first (cudaFree
+      // implies the same wait)
+      const cudaError_t e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) return pfail(APIC_ERR_CUDA, "cudaDeviceSynchronize: %s", cudaGetErrorString(e));
+      c->ufree(c->uuser, b.ptr, b.bytes, c->device);
+    } else {
+      const cudaError_t e = cudaFree(b.ptr);
+      if (e != cudaSuccess) return pfail(APIC_ERR_CUDA, "cudaFree: %s", cudaGetErrorString(e));
+    }
     c->held -= b.bytes;
     b.ptr = nullptr;
     b.bytes = 0;
   }
   c->alloc_gen += 1;
-  cudaError_t e = cudaMalloc(&b.ptr, want);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    b.ptr = nullptr;
-    return pfail(APIC_ERR_OUT_OF_MEMORY, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
+  if (c->ualloc) {
+    b.ptr = c->ualloc(c->uuser, want, c->device);
+    if (!b.ptr) return pfail(APIC_ERR_OUT_OF_MEMORY, "the caller's allocator returned NULL for %zu bytes", want);
+    if (reinterpret_cast<uintptr_t>(b.ptr) % 256 != 0) {
+      c->ufree(c->uuser, b.ptr, want, c->device);
+      b.ptr = nullptr;
+      return pfail(APIC_ERR_INVALID_ARG, "the caller's allocator returned a block not aligned to 256 bytes");
+    }
+  } else {
+    const cudaError_t e = cudaMalloc(&b.ptr, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b.ptr = nullptr;
+      return pfail(APIC_ERR_OUT_OF_MEMORY, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
+    }
   }
   b.bytes = want;
   c->held += want;
   return APIC_OK;
 }
 
+// (apic_destroy synchronises the device before it frees through the
+// caller's allocator)
 void free_buf(apic_ctx* c, Buf& b) {
-  if (b.ptr) cudaFree(b.ptr);
+  if (b.ptr) {
+    if (c->ufree)
+      c->ufree(c->uuser, b.ptr, b.bytes, c->device);
+    else
+      cudaFree(b.ptr);
+  }
   c->held -= b.bytes;
   b = Buf{};
 }
@@ -439,7 +469,7 @@ struct CtxEnv {
 };
 
 constexpr uint32_t kAllFlags =
-    APIC_FP64 | APIC_HOST_PTRS | APIC_VARIANT_PIC | APIC_VARIANT_SEP23 | APIC_DETERMINISTIC;
+    APIC_FP64 | APIC_HOST_PTRS | APIC_VARIANT_PIC | APIC_VARIANT_SEP23 | APIC_DETERMINISTIC | APIC_CHECK;
 
 apic_status run(apic_ctx* c, const apic_step_args* scenes, int ns, void* stream, apic_stats* stats) {
   P_CUDA(cudaSetDevice(c->device));
@@ -495,6 +525,7 @@ apic_status apic_create(apic_ctx** out, int32_t device, size_t hbm_budget_bytes)
 apic_status apic_destroy(apic_ctx* c) {
   if (!c) return APIC_OK;
   cudaSetDevice(c->device);
+  if (c->ufree) cudaDeviceSynchronize();
   for (Buf& b : c->bufs) free_buf(c, b);
   if (c->ds) cudaFree(c->ds);
   if (c->hs) cudaFreeHost(c->hs);
@@ -669,6 +700,19 @@ apic_status apic_set_graphs(apic_ctx* c, int32_t on) {
     g->captured = false;
     g->failed = false;
   }
+  return APIC_OK;
+}
+
+apic_status apic_set_allocator(apic_ctx* c, apic_alloc_fn alloc, apic_free_fn free_fn, void* user) {
+  if (!c) return pfail(APIC_ERR_INVALID_ARG, "ctx is NULL");
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return pfail(APIC_ERR_INVALID_ARG, "give both allocator functions, or neither");
+  if (c->held != 0)
+    return pfail(APIC_ERR_INVALID_ARG, "the context already holds %zu bytes of scratch: set the allocator first",
+                 c->held);
+  c->ualloc = alloc;
+  c->ufree = free_fn;
+  c->uuser = user;
   return APIC_OK;
 }
 

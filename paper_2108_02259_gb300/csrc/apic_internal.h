@@ -32,6 +32,8 @@ constexpr int kErrBody = 1;
 constexpr int kErrMass = 2;
 constexpr int kErrPos = 4;
 constexpr int kErrBox = 8;  // a particle lies outside a page-table box reused from an earlier step
+constexpr int kErrFinite = 16;  // v, C or a normal not finite (checked with APIC_CHECK)
+constexpr int kErrNormal = 32;  // a normal neither 0 nor of unit length (checked with APIC_CHECK)
 
 // Device-side scalars the host reads back while sizing the grid.
 struct DevScalars {
@@ -133,7 +135,8 @@ constexpr int kFxRetryHeadLog2 = 24;
 
 // Cells, validation, per-scene bounding boxes of particle blocks (sbbox[6 s]).
 template <class T>
-cudaError_t launch_cells(int64_t n, const SceneDev* sc, int ns, int4* cellb, int* sbbox, int* err,
+// check: also validate v, C and the normals (APIC_CHECK).
+cudaError_t launch_cells(int64_t n, const SceneDev* sc, int ns, int4* cellb, int* sbbox, int* err, int check,
                          cudaStream_t s);
 template <class K>
 cudaError_t launch_keys(int64_t n, const SceneDev* sc, int ns, const int4* cellb, int max_bodies, K* keys,

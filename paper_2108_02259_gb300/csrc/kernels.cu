@@ -938,7 +938,8 @@ __global__ void k_fx_prep(int64_t n, const SceneDev* __restrict__ sc, int ns, co
 // one scene reduces the box in shared memory and adds it with one set of
 // atomics; CTAs that straddle scenes add per particle.
 template <class T>
-__global__ void k_cells(int64_t n, const SceneDev* __restrict__ sc, int ns, int4* cellb, int* sbbox, int* errp) {
+__global__ void k_cells(int64_t n, const SceneDev* __restrict__ sc, int ns, int4* cellb, int* sbbox, int* errp,
+                        int check) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t p_first = blockIdx.x * (int64_t)blockDim.x;
   const int64_t p_last = min(p_first + blockDim.x, n) - 1;
@@ -971,6 +972,19 @@ __global__ void k_cells(int64_t n, const SceneDev* __restrict__ sc, int ns, int4
     const int b = S.body[i];
     if (b < 0 || b >= S.n_bodies) err |= kErrBody;
     if (bad_mass(static_cast<const T*>(S.m)[i])) err |= kErrMass;
+    if (check) {
+      const T* v = static_cast<const T*>(S.v) + 3 * i;
+      const T* C = static_cast<const T*>(S.C) + 9 * i;
+      const T* nr = static_cast<const T*>(S.nrm) + 3 * i;
+      bool fin = true;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) fin = fin && isfinite(v[a]) && isfinite(nr[a]);
+#pragma unroll
+      for (int a = 0; a < 9; ++a) fin = fin && isfinite(C[a]);
+      if (!fin) err |= kErrFinite;
+      const T n2 = nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2];
+      if (fin && n2 != T(0) && fabs(n2 - T(1)) > T(1e-3)) err |= kErrNormal;
+    }
     cellb[p] = make_int4(c[0], c[1], c[2], b);
     if (uniform_scene < 0) {
 #pragma unroll
@@ -1275,10 +1289,10 @@ inline unsigned grid_for(int64_t n, int threads) {
 }  // namespace
 
 template <class T>
-cudaError_t launch_cells(int64_t n, const SceneDev* sc, int ns, int4* cellb, int* sbbox, int* err,
+cudaError_t launch_cells(int64_t n, const SceneDev* sc, int ns, int4* cellb, int* sbbox, int* err, int check,
                          cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_cells<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, cellb, sbbox, err);
+  k_cells<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, cellb, sbbox, err, check);
   return cudaGetLastError();
 }
 
@@ -1760,7 +1774,7 @@ cudaError_t launch_copy_table(const CopyEntry* table, int n_entries, long long m
 }
 
 #define APIC_INST_T(T)                                                                                  \
-  template cudaError_t launch_cells<T>(int64_t, const SceneDev*, int, int4*, int*, int*, cudaStream_t); \
+  template cudaError_t launch_cells<T>(int64_t, const SceneDev*, int, int4*, int*, int*, int, cudaStream_t); \
   template cudaError_t launch_gather<T>(int64_t, const SceneDev*, int, const int*, const int4*, V4<T>*,  \
                                         V4<T>*, V4<T>*, cudaStream_t);                                  \
   template cudaError_t launch_gather_v<T>(int64_t, const SceneDev*, int, const int*, V4<T>*, V4<T>*,     \

@@ -203,6 +203,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   const uint32_t flags = scenes[0].flags;
   const bool host = (flags & APIC_HOST_PTRS) != 0;
   const bool det = (flags & APIC_DETERMINISTIC) != 0;
+  const int check = (flags & APIC_CHECK) ? 1 : 0;
   const int N = scenes[0].n_iter;
   if (det && sizeof(T) != 4)
     return pfail(APIC_ERR_INVALID_ARG, "APIC_DETERMINISTIC applies to the FP32 path (not with APIC_FP64)");
@@ -272,7 +273,8 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     // second copy may still be reading its own entries.
     CopyEntry* tab = env.copy_table(8 * ns);
     bool direct = tab != nullptr;
-    cudaStream_t side = direct ? env.side_stream() : nullptr;
+    // (APIC_CHECK reads v, C and the normals in the cell kernel: no split)
+    cudaStream_t side = direct && !check ? env.side_stream() : nullptr;
     int na = 0, nb = 0;
     long long max_a = 0, max_b = 0;
     for (int i = 0; i < ns && direct; ++i) {
@@ -361,7 +363,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     if (with_cells) {
       P_CUDA(cudaMemcpyAsync(ds, hs, sizeof(DevScalars), cudaMemcpyHostToDevice, q));
       P_CUDA(cudaMemcpyAsync(sc, hsc, ns * sizeof(SceneDev), cudaMemcpyHostToDevice, q));
-      P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, sbbox, &ds->err, q));
+      P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, sbbox, &ds->err, check, q));
     }
     // 3. keys and one radix sort over all scenes.
     if (sb.k64)
@@ -421,9 +423,10 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       }
       struct SizingKey {
         int64_t n, NB;
-        int ns, max_bodies, tsize, host, chunk, split_v;
+        int ns, max_bodies, tsize, host, chunk, split_v, check, pad;
       } key;
       std::memset(&key, 0, sizeof(key));
+      key.check = check;
       key.chunk = chunk;
       key.split_v = split_v ? 1 : 0;
       key.n = n;
@@ -444,7 +447,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       P_CUDA(cudaMemcpyAsync(sbbox, hbbox, 6 * ns * sizeof(int), cudaMemcpyHostToDevice, s));
       P_CUDA(cudaMemcpyAsync(ds, hs, sizeof(DevScalars), cudaMemcpyHostToDevice, s));
       P_CUDA(cudaMemcpyAsync(sc, hsc, ns * sizeof(SceneDev), cudaMemcpyHostToDevice, s));
-      P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, sbbox, &ds->err, s));
+      P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, sbbox, &ds->err, check, s));
       // 2. page-table boxes: one block of stencil margin plus kBoxSlack
       //    blocks of room for motion in later steps; laid end to end.
       P_CUDA(cudaMemcpyAsync(hbbox, sbbox, 6 * ns * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -496,9 +499,11 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   if (hs->err) {
     const int e = hs->err;
     env.forget_box();
-    return pfail(APIC_ERR_INVALID_ARG, "invalid particle data:%s%s%s%s", (e & kErrBody) ? " body id out of range" : "",
+    return pfail(APIC_ERR_INVALID_ARG, "invalid particle data:%s%s%s%s%s%s", (e & kErrBody) ? " body id out of range" : "",
                  (e & kErrMass) ? " mass not finite and > 0" : "",
                  (e & kErrPos) ? " position not finite or |x/h| >= 2^29" : "",
+                 (e & kErrFinite) ? " v, C or normal not finite" : "",
+                 (e & kErrNormal) ? " normal neither 0 nor of unit length" : "",
                  (e & kErrBox) ? " (internal: page-table box)" : "");
   }
   const int n_items = hs->n_items;

@@ -316,7 +316,8 @@ apic_status apic_sim_open(apic_server* srv, const apic_step_args* a, apic_sim** 
     return sfail(APIC_ERR_INVALID_ARG, "invalid n_bodies, n_iter, h or mu");
   if (!a->x || !a->body || !a->v || !a->C || !a->m || !a->nrm)
     return sfail(APIC_ERR_INVALID_ARG, "a required array pointer is NULL");
-  const uint32_t known = APIC_FP64 | APIC_HOST_PTRS | APIC_VARIANT_PIC | APIC_VARIANT_SEP23 | APIC_DETERMINISTIC;
+  const uint32_t known =
+      APIC_FP64 | APIC_HOST_PTRS | APIC_VARIANT_PIC | APIC_VARIANT_SEP23 | APIC_DETERMINISTIC | APIC_CHECK;
   if (a->flags & ~known) return sfail(APIC_ERR_INVALID_ARG, "unknown flag bits");
   const size_t es = (a->flags & APIC_FP64) ? 8 : 4;
   const size_t n = (size_t)a->n;

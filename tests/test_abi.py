@@ -43,13 +43,20 @@ def test_flags_match_header():
     from paper_2108_02259_gb300 import apic
 
     hdr = open(os.path.join(ROOT, "include", "apiccontact.h")).read()
-    for name in ("APIC_FP64", "APIC_HOST_PTRS", "APIC_VARIANT_PIC", "APIC_VARIANT_SEP23"):
+    for name in ("APIC_FP64", "APIC_HOST_PTRS", "APIC_VARIANT_PIC", "APIC_VARIANT_SEP23", "APIC_AUGURY_INIT",
+                 "APIC_DETERMINISTIC", "APIC_CHECK"):
         m = re.search(rf"#define {name} \(1u << (\d+)\)", hdr)
         assert m, name
         assert getattr(apic, name) == 1 << int(m.group(1))
     for name in ("APIC_OK", "APIC_ERR_INVALID_ARG", "APIC_ERR_OUT_OF_MEMORY", "APIC_ERR_CUDA", "APIC_ERR_TIMEOUT"):
         m = re.search(rf"#define {name} \(?(-?\d+)\)?", hdr)
         assert m and getattr(apic, name) == int(m.group(1)), name
+
+
+def test_flag_bits_are_distinct():
+    hdr = open(os.path.join(ROOT, "include", "apiccontact.h")).read()
+    bits = [int(b) for b in re.findall(r"#define APIC_[A-Z0-9_]+ \(1u << (\d+)\)", hdr)]
+    assert len(bits) >= 7 and len(bits) == len(set(bits))
 
 
 def test_struct_layout_matches_header(lib):
