@@ -70,8 +70,9 @@ typedef int32_t apic_status;
                                         step.  A scene whose terms grow past the scale's headroom
                                         within one pass is repeated with a wider one; if that also
                                         fails (or inputs are non-finite) the call returns
-                                        APIC_ERR_INVALID_ARG and leaves that scene's outputs
-                                        untouched.  Statistics (apic_stats) are still FP64 sums.  */
+                                        APIC_ERR_INVALID_ARG and leaves the outputs of every scene
+                                        in the call untouched.  Statistics (apic_stats) are still
+                                        FP64 sums.                                                 */
 #define APIC_CHECK (1u << 6)         /* Also validate v, C and nrm: every component finite, each
                                         normal 0 or of unit length (|n|^2 within 1e-3 of 1);
                                         otherwise APIC_ERR_INVALID_ARG.  Positions, masses and body

@@ -118,8 +118,10 @@ struct IterParams {
   // Fixed-point node sums (deterministic mode): per scene, fx_max[scene *
   // fx_stride + k] holds the float bits of a bound on the particle terms a
   // pass scatters (k = 0: masses, 1: V, 2 + j: W of pass j); fx_err[attempt
-  // * n_scenes + scene] is set when a term exceeded the bound its scale
-  // allowed; gmb_fx replaces gmb.  The pass's own slot is fx_slot.
+  // * (n_scenes + 1) + scene] is set when a term exceeded the bound its scale
+  // allowed, and fx_err[attempt * (n_scenes + 1) + n_scenes] when that
+  // happened in any scene; gmb_fx replaces gmb.  The pass's own slot is
+  // fx_slot.
   unsigned* fx_max;
   int* fx_err;
   long long* gmb_fx;

@@ -619,9 +619,10 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         for (int a = 0; a < 9; ++a) dC[a] = p.pic ? T(0) : pC[a] + hC[a] - wC[a];
         out = MODE == kModeLast;
       }
-      if (DET && out && __ldcg(p.fx_err + p.fx_attempt * p.n_scenes + info.z) != 0) {
-        // an earlier pass of this attempt exceeded its fixed-point range: the
-        // step is repeated, and the caller's outputs stay untouched
+      if (DET && out && __ldcg(p.fx_err + p.fx_attempt * (p.n_scenes + 1) + p.n_scenes) != 0) {
+        // an earlier pass of this attempt exceeded its fixed-point range in
+        // some scene: the step is repeated (or fails), and no scene's outputs
+        // are written by this attempt
       } else if (out) {
         // V_hat = V + Delta_N, back in caller order, C = Ch / h
         T v[3], C[9];
@@ -756,7 +757,11 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
 
   // ---------------- add the tile to the global grid ----------------
   if constexpr (DET && kP2G && kMom) {
-    if (fx_bad) atomicOr(p.fx_err + p.fx_attempt * p.n_scenes + info.z, 1);
+    if (fx_bad) {
+      int* row = p.fx_err + p.fx_attempt * (p.n_scenes + 1);
+      atomicOr(row + info.z, 1);
+      atomicOr(row + p.n_scenes, 1);  // any scene of this attempt
+    }
     if (MODE != kModeMassV && tid == 0) atomicMax(p.fx_max + (int64_t)info.z * p.fx_stride + p.fx_slot + 1, s_fxmax);
     for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
       const int node = tile_node(snb, t);
@@ -895,7 +900,8 @@ __global__ void k_normalize_fx(int64_t n_nodes, const int* __restrict__ blist, c
 
 // Deterministic mode: per scene, the largest mass (slot 0) and the largest
 // term bound b_p of V (slot 1); a bound that is not finite, or beyond the
-// 2^90 the scales cover, sets the scene's range flag (err_row).  Each CTA covers a contiguous run of sorted particles and
+// 2^90 the scales cover, sets the scene's range flag (err_row[scene]) and
+// the attempt's (err_row[ns]).  Each CTA covers a contiguous run of sorted particles and
 // keeps the maxima of its first scene in shared memory.
 __global__ void k_fx_prep(int64_t n, const SceneDev* __restrict__ sc, int ns, const int* __restrict__ perm,
                           const V4<float>* __restrict__ pt, const V4<float>* __restrict__ V, unsigned* fx_max,
@@ -916,7 +922,10 @@ __global__ void k_fx_prep(int64_t n, const SceneDev* __restrict__ sc, int ns, co
     const float Ch[9] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
     const float m = pt[s].w;
     const float b = fx_bound(m, w, Ch);
-    if (!(b <= 0x1p90f) || !(m <= 0x1p90f)) atomicOr(err_row + scene, 1);  // NaN, inf or beyond the scales
+    if (!(b <= 0x1p90f) || !(m <= 0x1p90f)) {  // NaN, inf or beyond the scales
+      atomicOr(err_row + scene, 1);
+      atomicOr(err_row + ns, 1);  // any scene of this attempt
+    }
     const unsigned bm = __float_as_uint(m), bv = __float_as_uint(b);
     if (scene == first_scene) {
       atomicMax(&smax[0], bm);

@@ -529,7 +529,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   const int fx_stride = N + 2;
   if (det) {
     P_TRY(env.take(kSlotFxMax, (size_t)ns * fx_stride, &fx_max, "fixed-point bounds"));
-    P_TRY(env.take(kSlotFxErr, (size_t)2 * ns, &fx_err, "fixed-point range flags"));
+    P_TRY(env.take(kSlotFxErr, (size_t)2 * (ns + 1), &fx_err, "fixed-point range flags"));
     if (any_mu) P_TRY(env.take(kSlotGmbFx, (size_t)max_bodies * n_nodes, &gmb_fx, "per-body grid mass (fixed)"));
   }
   if (any_mu) {
@@ -609,10 +609,10 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     if (det) {
       if (gmb_fx) P_CUDA(cudaMemsetAsync(gmb_fx, 0, (size_t)max_bodies * n_nodes * sizeof(long long), q));
       P_CUDA(cudaMemsetAsync(fx_max, 0, (size_t)ns * fx_stride * sizeof(unsigned), q));
-      P_CUDA(cudaMemsetAsync(fx_err + pp.fx_attempt * ns, 0, ns * sizeof(int), q));
+      P_CUDA(cudaMemsetAsync(fx_err + pp.fx_attempt * (ns + 1), 0, (ns + 1) * sizeof(int), q));
       P_LAUNCH(env, launch_fx_prep(n, sc, ns, perm, reinterpret_cast<const V4<float>*>(pt),
                                    reinterpret_cast<const V4<float>*>(V), fx_max, fx_stride,
-                                   fx_err + pp.fx_attempt * ns, q));
+                                   fx_err + pp.fx_attempt * (ns + 1), q));
     }
     auto normalize = [&](int slot, int all64) -> cudaError_t {
       if (det)
@@ -645,11 +645,13 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   P_TRY(env.run_series(&key, sizeof(key), s, series));
   if (det) {
     // A pass whose terms outgrew the headroom of its fixed-point scale left
-    // the outputs of its scene untouched: repeat the series once with a wider
-    // headroom for those scenes (the sorted inputs are unchanged).
+    // every scene's outputs untouched: repeat the series once with a wider
+    // headroom for the scenes concerned (the sorted inputs are unchanged; the
+    // others compute the same bits again).
     std::vector<int> bad(ns);
     for (int attempt = 0;; ++attempt) {
-      P_CUDA(cudaMemcpyAsync(bad.data(), fx_err + attempt * ns, ns * sizeof(int), cudaMemcpyDeviceToHost, s));
+      P_CUDA(cudaMemcpyAsync(bad.data(), fx_err + attempt * (ns + 1), ns * sizeof(int), cudaMemcpyDeviceToHost,
+                             s));
       P_CUDA(cudaStreamSynchronize(s));
       int first_bad = -1;
       for (int i = 0; i < ns && first_bad < 0; ++i)

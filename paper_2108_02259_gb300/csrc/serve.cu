@@ -16,6 +16,7 @@
 #include <deque>
 #include <iterator>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <unordered_set>
@@ -68,6 +69,7 @@ struct Ticket {
   Clock::time_point t_submit, t_done;
   int state = 0;  // 0 queued, 1 running, 2 done
   apic_status status = APIC_OK;
+  std::string error;  // the failed call's message
 };
 
 }  // namespace
@@ -190,20 +192,34 @@ void worker_main(apic_server* srv, int wid) {
         dts[i % 1024] = tk.dt;
       }
     }
-    apic_status st = ok ? apic_contact_step_batched(ctx, args.data(), (int32_t)args.size(), stream, nullptr)
-                        : APIC_ERR_CUDA;
-    if (st == APIC_OK) {
+    const apic_status st = ok ? apic_contact_step_batched(ctx, args.data(), (int32_t)args.size(), stream, nullptr)
+                              : APIC_ERR_CUDA;
+    std::vector<apic_status> each(args.size(), st);
+    std::vector<std::string> why(args.size(), st == APIC_OK ? std::string() : std::string(apic_last_error()));
+    if (st == APIC_ERR_INVALID_ARG && args.size() > 1) {
+      // Some simulation's data is invalid.  A call that fails that way
+      // leaves every scene as it was, so step them one by one: only the
+      // offending requests fail.
+      for (size_t i = 0; i < args.size(); ++i) {
+        each[i] = apic_contact_step_batched(ctx, &args[i], 1, stream, nullptr);
+        why[i] = each[i] == APIC_OK ? std::string() : std::string(apic_last_error());
+      }
+    }
+    bool any_ok = false;
+    for (apic_status e : each) any_ok = any_ok || e == APIC_OK;
+    if (any_ok) {
       for (size_t i = 0; i < args.size(); ++i) {
         const double dt = dts[i % 1024];
-        if (dt == 0.0 || args[i].n == 0) continue;
+        if (each[i] != APIC_OK || dt == 0.0 || args[i].n == 0) continue;
         cudaError_t e = (args[i].flags & APIC_FP64)
                             ? apic::launch_advect<double>(args[i].n, const_cast<double*>(args[i].x),
                                                           static_cast<const double*>(args[i].v), dt, stream)
                             : apic::launch_advect<float>(args[i].n, const_cast<double*>(args[i].x),
                                                          static_cast<const float*>(args[i].v), dt, stream);
-        if (e != cudaSuccess) st = APIC_ERR_CUDA;
+        if (e != cudaSuccess) each[i] = APIC_ERR_CUDA;
       }
-      if (cudaStreamSynchronize(stream) != cudaSuccess) st = APIC_ERR_CUDA;
+      if (cudaStreamSynchronize(stream) != cudaSuccess)
+        for (apic_status& e : each) e = APIC_ERR_CUDA;
     }
     size_t held = 0;
     if (ctx) apic_scratch_bytes(ctx, &held);
@@ -213,13 +229,14 @@ void worker_main(apic_server* srv, int wid) {
       srv->worker_scratch[wid] = held;
       srv->batches += 1;
       srv->batch_scenes += (int64_t)batch.size();
-      for (uint64_t t : batch) {
-        Ticket& tk = srv->tickets[t];
+      for (size_t i = 0; i < batch.size(); ++i) {
+        Ticket& tk = srv->tickets[batch[i]];
         tk.state = 2;
-        tk.status = st;
+        tk.status = each[i];
+        tk.error = each[i] == APIC_OK ? std::string() : (why[i].empty() ? std::string("CUDA error") : why[i]);
         tk.t_done = now;
         tk.sim->busy = false;
-        if (st == APIC_OK) {
+        if (each[i] == APIC_OK) {
           srv->completed += 1;
           srv->particle_iters += tk.sim->n * (int64_t)(tk.sim->n_iter + 1);
           if (srv->lat_ms.size() >= kMaxLatencySamples)  // keep the most recent half
@@ -400,8 +417,9 @@ apic_status apic_ticket_poll(apic_server* srv, uint64_t ticket, int32_t* done, d
   if (latency_ms)
     *latency_ms = std::chrono::duration<double, std::milli>(it->second.t_done - it->second.t_submit).count();
   const apic_status st = it->second.status;
+  const std::string why = "the request failed: " + it->second.error;
   srv->tickets.erase(it);  // reported: forgotten
-  if (st != APIC_OK) return sfail(st, "the request failed");
+  if (st != APIC_OK) return sfail(st, why.c_str());
   return APIC_OK;
 }
 
@@ -418,8 +436,9 @@ apic_status apic_ticket_wait(apic_server* srv, uint64_t ticket, double timeout_s
   if (latency_ms)
     *latency_ms = std::chrono::duration<double, std::milli>(done->second.t_done - done->second.t_submit).count();
   const apic_status st = done->second.status;
+  const std::string why = "the request failed: " + done->second.error;
   srv->tickets.erase(done);  // reported: forgotten
-  if (st != APIC_OK) return sfail(st, "the request failed");
+  if (st != APIC_OK) return sfail(st, why.c_str());
   return APIC_OK;
 }
 

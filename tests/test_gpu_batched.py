@@ -242,3 +242,31 @@ def test_page_locked_repeat_calls_pick_up_new_inputs(ctx):
         apic.contact_step(ctx, X, V, Cc, M, NR, B, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies, v_out=vo, C_out=Co)
         sk = scenes.Scene(**{**s.__dict__, "v": s.v * scale, "C": s.C * scale})
         _check(sk, vo.astype(np.float64), Co.astype(np.float64).reshape(-1, 3, 3), None, label=f"call {k}")
+
+
+def test_failed_batch_leaves_every_scene_untouched(ctx):
+    """A batched call refused for one scene's data (here APIC_CHECK finds a
+    NaN velocity) writes no scene's outputs, so a caller can step the valid
+    scenes again on their own."""
+    import torch
+
+    from paper_2108_02259_gb300 import apic
+
+    d = torch.device("cuda:0")
+    sc = _mixed_batch()[:3]
+    bs = []
+    for k, s in enumerate(sc):
+        f = s.astype(np.float32)
+        t = [torch.as_tensor(np.ascontiguousarray(a), device=d) for a in (f.x, f.v, f.C, f.m, f.nrm)]
+        t[0] = t[0].double()
+        if k == 1:
+            t[1][4, 0] = float("nan")
+        body = torch.as_tensor(f.body, device=d, dtype=torch.int32)
+        bs.append(apic.BatchScene(*t, body, s.h, s.mu, n_bodies=s.n_bodies, v_out=torch.full_like(t[1], 7.0),
+                                  C_out=torch.full_like(t[2], 7.0)))
+    for flags, msg in ((apic.APIC_CHECK, "not finite"), (apic.APIC_CHECK | apic.APIC_DETERMINISTIC, "not finite"),
+                       (apic.APIC_DETERMINISTIC, "fixed-point range")):  # the last: refused after the passes ran
+        with pytest.raises(apic.ApicError, match=msg):
+            apic.contact_step_batched(ctx, bs, 3, flags=flags)
+        torch.cuda.synchronize()
+        assert all(bool((b.v_out == 7.0).all()) and bool((b.C_out == 7.0).all()) for b in bs)

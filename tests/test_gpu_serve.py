@@ -253,3 +253,49 @@ def test_checkpoint_and_resume(apic, dt):
             assert e.value.code == apic.APIC_ERR_INVALID_ARG
         ref.close()
         back.close()
+
+
+@pytest.mark.parametrize("det", [False, True])
+def test_invalid_request_fails_alone(apic, det):
+    """One simulation with a NaN velocity among valid ones (all with
+    APIC_CHECK, so they may share a batch): its request fails with the
+    validation message, the batch is stepped again scene by scene, and every
+    other request completes and matches the oracle."""
+    flags = apic.APIC_CHECK | (apic.APIC_DETERMINISTIC if det else 0)
+    sims = _sims(6, seed=21)
+    bad = 2
+    with apic.Server(0, n_workers=1, max_batch_scenes=16) as srv:
+        # a larger request (other flags, so a batch of its own) keeps the one
+        # worker busy while the six queue up and are then taken together
+        big = scenes.four_bodies(scale=0.5)
+        g = big.astype(np.float32)
+        blocker = srv.open_sim(g.x, g.v, g.C, g.m, g.nrm, g.body, big.h, big.mu, big.n_iter,
+                               n_bodies=big.n_bodies)
+        t_block = blocker.submit(0.0)
+        hs = []
+        for k, s in enumerate(sims):
+            f = s.astype(np.float32)
+            v = f.v.copy()
+            if k == bad:
+                v[3, 1] = np.nan
+            hs.append(srv.open_sim(f.x, v, f.C, f.m, f.nrm, f.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
+                                   flags=flags))
+        tickets = [h.submit(0.0) for h in hs]
+        for k, t in enumerate(tickets):
+            if k == bad:
+                with pytest.raises(apic.ApicError, match="not finite"):
+                    srv.wait(t, 60.0)
+            else:
+                srv.wait(t, 60.0)
+        srv.wait(t_block, 60.0)
+        st = srv.stats()
+        assert st["failed"] == 1 and st["completed"] == len(sims)
+        print(f"[serve] invalid request (det={det}): mean batch {st['mean_batch_scenes']:.2f}")
+        for k, (s, h) in enumerate(zip(sims, hs)):
+            x, v, Cm = h.read()
+            if k == bad:
+                assert np.isnan(v[3, 1])  # left as it was
+                continue
+            ref = _oracle_steps(s, 1, 0.0)
+            ev, ec, ex = _err(s, (x, v, Cm), ref)
+            assert ev <= TOL_V and ec <= TOL_C and ex == 0.0, (k, ev, ec)
