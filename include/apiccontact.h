@@ -425,6 +425,16 @@ apic_status apic_get_variant(apic_ctx* ctx, int64_t n_particles, int32_t* varian
 apic_status apic_autotune(apic_ctx* ctx, const apic_step_args* scenes, int32_t n_scenes, void* stream,
                           int32_t* variant);
 
+/* The autotuner's decisions, to keep across processes (e.g. in a file keyed
+ * by the GPU model): *count = the number of decided size classes (the FP32
+ * particle count's bit length); the first min(count, cap) go to classes[] and
+ * variants[].  apic_set_tuning marks the given classes decided with the given
+ * variants (no timing); APIC_ERR_INVALID_ARG for a class outside [0, 62] or a
+ * variant outside [0, apic_variant_count()), and then nothing is set.  Not in
+ * the paper. */
+apic_status apic_get_tuning(apic_ctx* ctx, int32_t* classes, int32_t* variants, int32_t cap, int32_t* count);
+apic_status apic_set_tuning(apic_ctx* ctx, const int32_t* classes, const int32_t* variants, int32_t count);
+
 /* Capture and replay the transfer passes as a CUDA graph (1, the default) or
  * launch them one by one (0).  Profiling (apic_set_profiling) launches them
  * one by one regardless, to time each pass. */

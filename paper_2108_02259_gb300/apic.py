@@ -41,7 +41,8 @@ EXPORTED = [
     "apic_contact_step_batched", "apic_server_create", "apic_server_destroy", "apic_sim_open", "apic_sim_submit",
     "apic_ticket_poll", "apic_ticket_wait", "apic_sim_read", "apic_sim_close", "apic_server_get_stats",
     "apic_variant_count", "apic_variant_name", "apic_set_variant", "apic_get_variant", "apic_autotune",
-    "apic_set_graphs", "apic_set_overlap", "apic_set_allocator", "apic_server_set_policy", "apic_node_normals",
+    "apic_set_graphs", "apic_set_overlap", "apic_set_allocator", "apic_get_tuning", "apic_set_tuning",
+    "apic_server_set_policy", "apic_node_normals",
     "apic_augury_steps",
     "apic_sim_export", "apic_sim_import",
 ]
@@ -162,6 +163,9 @@ def load(path: str = LIB_PATH):
     lib.apic_set_graphs.argtypes = [P, C.c_int32]
     lib.apic_set_overlap.argtypes = [P, C.c_int32]
     lib.apic_set_allocator.argtypes = [P, ALLOC_FN, FREE_FN, P]
+    I32P = C.POINTER(C.c_int32)
+    lib.apic_get_tuning.argtypes = [P, I32P, I32P, C.c_int32, I32P]
+    lib.apic_set_tuning.argtypes = [P, I32P, I32P, C.c_int32]
     lib.apic_server_set_policy.argtypes = [P, C.c_int32, C.c_int32]
     lib.apic_node_normals.argtypes = [P, C.c_int64, P, C.c_int64, P, P, C.c_uint32, P]
     lib.apic_node_normals.restype = C.c_int32
@@ -174,7 +178,7 @@ def load(path: str = LIB_PATH):
     lib.apic_server_set_policy.restype = C.c_int32
     for f in ("apic_create", "apic_destroy", "apic_contact_step", "apic_set_profiling", "apic_get_profile",
               "apic_scratch_bytes", "apic_set_variant", "apic_get_variant", "apic_autotune", "apic_set_graphs",
-              "apic_set_overlap", "apic_set_allocator"):
+              "apic_set_overlap", "apic_set_allocator", "apic_get_tuning", "apic_set_tuning"):
         getattr(lib, f).restype = C.c_int32
     _lib = lib
     return lib
@@ -268,6 +272,47 @@ class Context:
         cbs = (ALLOC_FN(a), FREE_FN(f))
         _check(load().apic_set_allocator(self._h, cbs[0], cbs[1], None))
         self._alloc_cbs = cbs  # the library calls them until the context is destroyed
+
+    def tuning(self) -> dict:
+        """{size class: variant} for every class the autotuner has decided."""
+        lib, cnt = load(), C.c_int32()
+        _check(lib.apic_get_tuning(self._h, None, None, 0, C.byref(cnt)))
+        n = cnt.value
+        cls, var = (C.c_int32 * max(n, 1))(), (C.c_int32 * max(n, 1))()
+        _check(lib.apic_get_tuning(self._h, cls, var, n, C.byref(cnt)))
+        return {int(cls[i]): int(var[i]) for i in range(min(n, cnt.value))}
+
+    def set_tuning(self, table: dict):
+        """Mark size classes decided: {size class: variant}."""
+        n = len(table)
+        cls = (C.c_int32 * max(n, 1))(*[int(k) for k in table])
+        var = (C.c_int32 * max(n, 1))(*[int(v) for v in table.values()])
+        _check(load().apic_set_tuning(self._h, cls, var, n))
+
+    def save_tuning(self, path: str):
+        """Write the decided classes to a JSON file keyed by GPU model and
+        the library's variant list."""
+        import json
+
+        import torch
+
+        doc = {"gpu": torch.cuda.get_device_name(self.device), "variants": variants(),
+               "classes": {str(k): v for k, v in sorted(self.tuning().items())}}
+        with open(path, "w") as fh:
+            json.dump(doc, fh, indent=1)
+
+    def load_tuning(self, path: str) -> bool:
+        """Apply a file from save_tuning if it was made on this GPU model with
+        these variants; returns whether it was applied."""
+        import json
+
+        import torch
+
+        doc = json.load(open(path))
+        if doc.get("gpu") != torch.cuda.get_device_name(self.device) or doc.get("variants") != variants():
+            return False
+        self.set_tuning({int(k): int(v) for k, v in doc.get("classes", {}).items()})
+        return True
 
     def set_overlap(self, on: bool):
         """Let each pass start while the grid before it finishes (default) or not."""

@@ -671,6 +671,37 @@ apic_status apic_get_variant(apic_ctx* c, int64_t n_particles, int32_t* variant,
   return APIC_OK;
 }
 
+apic_status apic_get_tuning(apic_ctx* c, int32_t* classes, int32_t* variants, int32_t cap, int32_t* count) {
+  if (!c || !count || cap < 0 || (cap > 0 && (!classes || !variants)))
+    return pfail(APIC_ERR_INVALID_ARG, "NULL argument or negative capacity");
+  collect_tuning(c);
+  int32_t k = 0;
+  for (const auto& [cls, tc] : c->tune) {
+    if (tc.chosen < 0) continue;
+    if (k < cap) {
+      classes[k] = cls;
+      variants[k] = tc.chosen;
+    }
+    ++k;
+  }
+  *count = k;
+  return APIC_OK;
+}
+
+apic_status apic_set_tuning(apic_ctx* c, const int32_t* classes, const int32_t* variants, int32_t count) {
+  if (!c || count < 0 || (count > 0 && (!classes || !variants)))
+    return pfail(APIC_ERR_INVALID_ARG, "NULL argument or negative count");
+  for (int32_t i = 0; i < count; ++i) {
+    if (classes[i] < 0 || classes[i] > 62)
+      return pfail(APIC_ERR_INVALID_ARG, "entry %d: size class %d outside [0, 62]", i, classes[i]);
+    if (variants[i] < 0 || variants[i] >= kNumVariants)
+      return pfail(APIC_ERR_INVALID_ARG, "entry %d: variant %d outside [0, %d)", i, variants[i], kNumVariants);
+  }
+  collect_tuning(c);
+  for (int32_t i = 0; i < count; ++i) c->tune[classes[i]].chosen = variants[i];
+  return APIC_OK;
+}
+
 apic_status apic_autotune(apic_ctx* c, const apic_step_args* scenes, int32_t n_scenes, void* stream,
                           int32_t* variant) {
   if (!c) return pfail(APIC_ERR_INVALID_ARG, "ctx is NULL");

@@ -179,3 +179,40 @@ def test_dependent_launch_keeps_parity(apic, case):
                 _close(s, r.v.cpu().double().numpy(), r.C.cpu().double().numpy(), ref[0], ref[1],
                        f"overlap {on}, call {k}")
             assert ctx.profile()["graph_launches"] >= 2
+
+
+def test_tuning_table_round_trip(apic, tmp_path):
+    """The autotuner's decision exported, saved to a file keyed by the GPU
+    model, and loaded into a fresh context: the size class is decided there
+    without timing, and its steps still match the oracle."""
+    import json
+
+    import torch
+
+    s = scenes.four_bodies(scale=0.25)
+    n = s.x.shape[0]
+    X, V, Cc, M, NR, B = _dev(s)
+    path = str(tmp_path / "tuning.json")
+    with apic.Context(0) as a:
+        sc = [apic.BatchScene(X, V, Cc, M, NR, B, s.h, s.mu, n_bodies=s.n_bodies)]
+        chosen = a.autotune(sc, s.n_iter)
+        assert a.tuning() == {n.bit_length(): chosen}
+        a.save_tuning(path)
+    ref = oracle.contact_step(s.x, s.v, s.C, s.m, s.nrm, s.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies)
+    with apic.Context(0) as b:
+        assert b.variant(n) == (0, False)
+        assert b.load_tuning(path)
+        assert b.variant(n) == (chosen, True)
+        r = apic.contact_step(b, X, V, Cc, M, NR, B, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies)
+        torch.cuda.synchronize()
+        _close(s, r.v.cpu().double().numpy(), r.C.cpu().double().numpy(), ref[0], ref[1], "loaded tuning")
+        for bad in ({5: len(apic.variants())}, {63: 0}, {-1: 0}):
+            with pytest.raises(apic.ApicError):
+                b.set_tuning(bad)
+        assert b.tuning() == {n.bit_length(): chosen}  # nothing set by the refused calls
+    doc = json.load(open(path))
+    doc["gpu"] = "another GPU"
+    json.dump(doc, open(path, "w"))
+    with apic.Context(0) as c:
+        assert not c.load_tuning(path)
+        assert c.variant(n) == (0, False)
