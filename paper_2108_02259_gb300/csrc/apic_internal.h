@@ -75,10 +75,9 @@ struct SceneDev {
   double h, inv_h, mu;
 };
 
-// Iteration-kernel modes (one transfer pair each; Sec. 2.3).
+// Iteration-kernel modes (one transfer pair each; Sec. 2.3).  The numbers
+// appear in profiles; 0 and 1 are not used.
 enum Mode : int {
-  kModeMass = 0,   // m_i and the body mask (once per step)
-  kModeP2GV = 1,   // P2G of V (first half of H V)
   kModeFirst = 2,  // G2P -> Delta_0 = H V - V -> W_1 -> P2G(W_1)
   kModeMid = 3,    // G2P -> Delta_m = Delta_{m-1} + H W_m - W_m -> W_{m+1} -> P2G
   kModeLast = 4,   // G2P -> Delta_N -> V_hat = V + Delta_N in caller order

@@ -404,11 +404,9 @@ template <class T, int MODE, int MINB, int CHUNK, bool ROWTAB, bool DET = false>
 __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   constexpr int kStashN = CHUNK + CHUNK / 16;
   constexpr bool kG2P = MODE == kModeFirst || MODE == kModeMid || MODE == kModeLast || MODE == kModeOnly;
-  constexpr bool kP2G = MODE == kModeMass || MODE == kModeP2GV || MODE == kModeMassV || MODE == kModeFirst ||
-                        MODE == kModeMid;
-  constexpr bool kMass = MODE == kModeMass || MODE == kModeMassV;  // accumulates m_i and the body mask
-  constexpr bool kMom = MODE != kModeMass;                          // accumulates momentum
-  constexpr int kComp = MODE == kModeMass ? 1 : MODE == kModeMassV ? 4 : 3;
+  constexpr bool kP2G = MODE == kModeMassV || MODE == kModeFirst || MODE == kModeMid;
+  constexpr bool kMass = MODE == kModeMassV;  // also accumulates m_i and the body mask
+  constexpr int kComp = kMass ? 4 : 3;         // momentum (x, y, z) [, mass]
   __shared__ V4<T> sv[kG2P ? kTile3 : 1];
   __shared__ uint32_t smask[MODE == kModeMu ? kTile3 : 1];
   using Acc = typename std::conditional<DET, long long, T>::type;
@@ -445,7 +443,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   // Issue this thread's particle loads first so that they are in flight
   // while the CTA fetches its grid tile.
   constexpr bool kReadD = MODE == kModeMid || MODE == kModeLast;
-  constexpr bool kReadV = MODE == kModeP2GV || MODE == kModeMassV || MODE == kModeFirst || MODE == kModeOnly;
+  constexpr bool kReadV = MODE == kModeMassV || MODE == kModeFirst || MODE == kModeOnly;
   V4<T> pt{}, pn{}, q0{}, q1{}, q2{};
   if (tid < count) {
     const int s = s0 + tid;
@@ -557,7 +555,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         }
       }
       p.mup_out[s] = den > T(0) ? num / den : p.mu_table[S.mu_off + body * S.n_bodies + body];
-    } else if (MODE == kModeMass || MODE == kModeP2GV || MODE == kModeMassV) {
+    } else if (MODE == kModeMassV) {
       T wx[4], dx[4];
       bspline(pt.x, wx, dx);
       if constexpr (ROWTAB) {
@@ -566,7 +564,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         bspline(pt.z, wz, dz);
         stash[0][sidx(tid)] = V4<T>{pt.w * wy[0], pt.w * wy[1], pt.w * wy[2], pt.w * wy[3]};
         stash[ROWTAB ? 6 : 0][sidx(tid)] = V4<T>{wz[0], wz[1], wz[2], wz[3]};
-        if (MODE != kModeMass && !p.pic) {
+        if (!p.pic) {
           // fold the particle's own offset into v: v_c - Ch_c1 t_y - Ch_c2 t_z
           q0.x -= q1.x * pt.y + q1.y * pt.z;
           q0.y -= q1.w * pt.y + q2.x * pt.z;
@@ -577,11 +575,9 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
       }
       stash[4][sidx(tid)] = V4<T>{wx[0], wx[1], wx[2], wx[3]};
       stash[5][sidx(tid)] = V4<T>{wx[0] * dx[0], wx[1] * dx[1], wx[2] * dx[2], wx[3] * dx[3]};
-      if (MODE != kModeMass) {
-        stash[1][sidx(tid)] = q0;
-        stash[2][sidx(tid)] = q1;
-        stash[3][sidx(tid)] = q2;
-      }
+      stash[1][sidx(tid)] = q0;
+      stash[2][sidx(tid)] = q1;
+      stash[3][sidx(tid)] = q2;
     } else {
       T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4];
       bspline(pt.x, wx, dx);
@@ -677,7 +673,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
     row_poly(kz, cz0, cz1, cz2);
     const T oy = T(ky - 1), oz = T(kz - 1);
     const bool aff = !p.pic;
-    RowAcc<T, kMom ? 3 : 1> acc;
+    RowAcc<T, 3> acc;
     RowAcc<T, 1> macc;  // mass, when this pass also scatters mass (kModeMassV)
     acc.zero();
     macc.zero();
@@ -689,13 +685,13 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
       for (int k = 0; k < 4; ++k) {
         if constexpr (DET) {
 #pragma unroll
-          for (int c = 0; c < (kMom ? 3 : 1); ++c)
+          for (int c = 0; c < 3; ++c)
             atomicAdd(reinterpret_cast<unsigned long long*>(&sacc[c][row + k]), to_fx(acc.get(k, c), fxS));
           if constexpr (MODE == kModeMassV)
             atomicAdd(reinterpret_cast<unsigned long long*>(&sacc[3][row + k]), to_fx(macc.get(k, 0), fxSm));
         } else {
 #pragma unroll
-          for (int c = 0; c < (kMom ? 3 : 1); ++c) atomicAdd(&sacc[c][row + k], acc.get(k, c));
+          for (int c = 0; c < 3; ++c) atomicAdd(&sacc[c][row + k], acc.get(k, c));
           if constexpr (MODE == kModeMassV) atomicAdd(&sacc[3][row + k], macc.get(k, 0));
         }
       }
@@ -721,14 +717,11 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         ty = a.y;
         tz = a.z;
       }
-      if (kMass) {
+      if constexpr (kMass) {
         const T A[1] = {wyzm};
-        if constexpr (MODE == kModeMass)
-          acc.add(X, XD, A, nullptr);
-        else
-          macc.add(X, XD, A, nullptr);
+        macc.add(X, XD, A, nullptr);
       }
-      if constexpr (kMom) {
+      {
         const V4<T> w0 = stash[1][sidx(j)], w1 = stash[2][sidx(j)], w2 = stash[3][sidx(j)];
         // W = (u, Ch); Ch rows (w0.w w1.x w1.y) (w1.z w1.w w2.x) (w2.y w2.z w2.w).
         // Node k of this row gets wx_k A + wx_k dx_k B with
@@ -756,7 +749,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   __syncthreads();
 
   // ---------------- add the tile to the global grid ----------------
-  if constexpr (DET && kP2G && kMom) {
+  if constexpr (DET && kP2G) {
     if (fx_bad) {
       int* row = p.fx_err + p.fx_attempt * (p.n_scenes + 1);
       atomicOr(row + info.z, 1);
@@ -787,17 +780,17 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
     const int node = tile_node(snb, t);
     if (node < 0) continue;
     if constexpr (kMass) {
-      const T mv = sacc[MODE == kModeMassV ? 3 : 0][t];
+      const T mv = sacc[3][t];
       if (mv != T(0)) {
         atomicAdd(&p.gm[node], mv);
         atomicOr(&p.gmask[node], 1u << body);
         if (p.gmb) atomicAdd(&p.gmb[(int64_t)body * p.n_nodes + node], mv);
       }
     }
-    if constexpr (kMom) {
+    {
       const T x = sacc[0][t], y = sacc[1][t], z = sacc[2][t];
       if (x != T(0) || y != T(0) || z != T(0)) {
-        if (MODE == kModeMassV && p.gp64 != nullptr) {
+        if (kMass && p.gp64 != nullptr) {
           // the body mask is not final yet: P2G of V goes to FP64 everywhere
           atomicAdd(&p.gp64[node].x, (double)x);
           atomicAdd(&p.gp64[node].y, (double)y);
@@ -1396,8 +1389,6 @@ cudaError_t launch_items_cfg(const IterParams<T>& p, int mode, bool overlap, cud
   switch (mode) {
 #define APIC_MODE(m) \
   case m: return launch_ex(k_items<T, m, MINB, CHUNK, ROWTAB>, grid, CHUNK, overlap, s, p);
-    APIC_MODE(kModeMass)
-    APIC_MODE(kModeP2GV)
     APIC_MODE(kModeFirst)
     APIC_MODE(kModeMid)
     APIC_MODE(kModeLast)
