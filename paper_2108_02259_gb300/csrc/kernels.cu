@@ -749,6 +749,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   __syncthreads();
 
   // ---------------- add the tile to the global grid ----------------
+  // (only the P2G modes get here)
   if constexpr (DET && kP2G) {
     if (fx_bad) {
       int* row = p.fx_err + p.fx_attempt * (p.n_scenes + 1);
@@ -774,20 +775,18 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
       for (int c = 0; c < 3; ++c)
         if (sacc[c][t] != 0) atomicAdd(g + c, (unsigned long long)sacc[c][t]);
     }
-    return;
-  }
-  for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
-    const int node = tile_node(snb, t);
-    if (node < 0) continue;
-    if constexpr (kMass) {
-      const T mv = sacc[3][t];
-      if (mv != T(0)) {
-        atomicAdd(&p.gm[node], mv);
-        atomicOr(&p.gmask[node], 1u << body);
-        if (p.gmb) atomicAdd(&p.gmb[(int64_t)body * p.n_nodes + node], mv);
+  } else if constexpr (!DET && kP2G) {
+    for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
+      const int node = tile_node(snb, t);
+      if (node < 0) continue;
+      if constexpr (kMass) {
+        const T mv = sacc[3][t];
+        if (mv != T(0)) {
+          atomicAdd(&p.gm[node], mv);
+          atomicOr(&p.gmask[node], 1u << body);
+          if (p.gmb) atomicAdd(&p.gmb[(int64_t)body * p.n_nodes + node], mv);
+        }
       }
-    }
-    {
       const T x = sacc[0][t], y = sacc[1][t], z = sacc[2][t];
       if (x != T(0) || y != T(0) || z != T(0)) {
         if (kMass && p.gp64 != nullptr) {
