@@ -150,17 +150,17 @@ cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm
 template <class T>
 cudaError_t launch_gather_v(int64_t n, const SceneDev* sc, int ns, const int* perm, V4<T>* pn, V4<T>* V,
                             cudaStream_t s);
-// Run heads: flags[s] = 1 where the (grid block, body) of sorted particle s
-// differs from s - 1.
+// Work items from the sorted keys: at each run head (a new (grid block,
+// body)) the run's end and its item count ceil(len / chunk) (16 <= chunk <=
+// kChunk), 0 elsewhere; then, with the exclusive sum of the counts, every
+// item's start (equal split of its run) and (global page index, body, scene,
+// 0), and the item count.
 template <class K>
-cudaError_t launch_heads(int64_t n, const K* keys, int* flags, cudaStream_t s);
-// Item heads: runs (from their flags, exclusive offsets and compacted starts)
-// split into ceil(len / chunk) equal items (16 <= chunk <= kChunk).
-cudaError_t launch_item_heads(int64_t n, const int* run_flags, const int* run_offs, const int* run_start,
-                              const int* n_runs, int chunk, int* flags, cudaStream_t s);
+cudaError_t launch_run_items(int64_t n, const K* keys, int chunk, int* cnt, int* rend, cudaStream_t s);
 template <class K>
-cudaError_t launch_item_info(const int* item_start, const int* n_items, const K* keys, int max_bodies,
-                             const SceneDev* sc, int ns, int4* item_info, int max_items, cudaStream_t s);
+cudaError_t launch_item_write(int64_t n, const K* keys, const int* cnt, const int* off, const int* rend,
+                              int max_bodies, const SceneDev* sc, int ns, int* item_start, int4* item_info,
+                              int* n_items, cudaStream_t s);
 cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* list, int* page,
                            int* count, cudaStream_t s);
 template <class K>

@@ -1132,37 +1132,50 @@ __global__ void k_gather_v(int64_t n, const SceneDev* __restrict__ sc, int ns, c
   store12(V, (int)n, (int)s, vv, Ch);
 }
 
+// Work items, from the sorted keys.  A run is a maximal range of equal
+// (grid block, body); a run of len particles splits into k = ceil(len /
+// chunk) items of equal size (within one), item j starting at ceil(j len /
+// k), so no item is a short tail.  k_run_items: at each run head s, the run's
+// end (binary search over the sorted keys) and k; 0 elsewhere.
 template <class K>
-__global__ void k_heads(int64_t n, const K* __restrict__ keys, int* flags) {
+__global__ void k_run_items(int64_t n, const K* __restrict__ keys, int chunk, int* cnt, int* rend) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
-  // a new run at every (grid block, body) change
-  flags[s] = (s == 0 || (keys[s] >> 6) != (keys[s - 1] >> 6)) ? 1 : 0;
+  const K q = keys[s] >> 6;
+  if (s > 0 && (keys[s - 1] >> 6) == q) {
+    cnt[s] = 0;
+    return;
+  }
+  int64_t lo = s + 1, hi = n;  // first index past the run
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((keys[mid] >> 6) == q) lo = mid + 1; else hi = mid;
+  }
+  cnt[s] = (int)((lo - s + chunk - 1) / chunk);
+  rend[s] = (int)lo;
 }
 
-// Work items: each run of len particles splits into ceil(len / chunk)
-// items of equal size (within one), so no item is a short tail.
-__global__ void k_item_heads(int64_t n, const int* __restrict__ run_flags, const int* __restrict__ run_offs,
-                             const int* __restrict__ run_start, const int* __restrict__ n_runs, int chunk,
-                             int* flags) {
+// The items of each run at their offsets (exclusive sum of cnt): start and
+// (global page index of the block, body, scene, 0); the last thread stores
+// the item count.
+template <class K>
+__global__ void k_item_write(int64_t n, const K* __restrict__ keys, const int* __restrict__ cnt,
+                             const int* __restrict__ off, const int* __restrict__ rend, int max_bodies,
+                             const SceneDev* __restrict__ sc, int ns, int* item_start, int4* item_info,
+                             int* n_items) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
-  const int r = run_offs[s] + run_flags[s] - 1;  // the run holding s
-  const int64_t a = run_start[r];
-  const int64_t b = r + 1 < *n_runs ? run_start[r + 1] : n;
-  const int64_t len = b - a, items = (len + chunk - 1) / chunk, off = s - a;
-  flags[s] = (off == 0 || (off * items) / len != ((off - 1) * items) / len) ? 1 : 0;
-}
-
-template <class K>
-__global__ void k_item_info(const int* __restrict__ item_start, const int* __restrict__ n_items,
-                            const K* __restrict__ keys, int max_bodies, const SceneDev* __restrict__ sc, int ns,
-                            int4* info) {
-  const int count = *n_items;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-    const uint64_t q = (uint64_t)(keys[item_start[i]] >> 6);
-    const long long gpage = (long long)(q / (uint64_t)max_bodies);
-    info[i] = make_int4((int)gpage, (int)(q % (uint64_t)max_bodies), scene_of_page(sc, ns, gpage), 0);
+  const int k = cnt[s];
+  if (s == n - 1) *n_items = off[s] + k;
+  if (k == 0) return;
+  const int64_t len = rend[s] - s;
+  const uint64_t q = (uint64_t)(keys[s] >> 6);
+  const long long gpage = (long long)(q / (uint64_t)max_bodies);
+  const int4 info = make_int4((int)gpage, (int)(q % (uint64_t)max_bodies), scene_of_page(sc, ns, gpage), 0);
+  const int o = off[s];
+  for (int j = 0; j < k; ++j) {
+    item_start[o + j] = (int)(s + (j * len + k - 1) / k);
+    item_info[o + j] = info;
   }
 }
 
@@ -1322,26 +1335,20 @@ cudaError_t launch_gather_v(int64_t n, const SceneDev* sc, int ns, const int* pe
 }
 
 template <class K>
-cudaError_t launch_heads(int64_t n, const K* keys, int* flags, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  k_heads<K><<<grid_for(n, 256), 256, 0, s>>>(n, keys, flags);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_item_heads(int64_t n, const int* run_flags, const int* run_offs, const int* run_start,
-                              const int* n_runs, int chunk, int* flags, cudaStream_t s) {
+cudaError_t launch_run_items(int64_t n, const K* keys, int chunk, int* cnt, int* rend, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   if (chunk < 16 || chunk > kChunk) return cudaErrorInvalidValue;
-  k_item_heads<<<grid_for(n, 256), 256, 0, s>>>(n, run_flags, run_offs, run_start, n_runs, chunk, flags);
+  k_run_items<K><<<grid_for(n, 256), 256, 0, s>>>(n, keys, chunk, cnt, rend);
   return cudaGetLastError();
 }
 
 template <class K>
-cudaError_t launch_item_info(const int* item_start, const int* n_items, const K* keys, int max_bodies,
-                             const SceneDev* sc, int ns, int4* item_info, int max_items, cudaStream_t s) {
-  if (max_items <= 0) return cudaSuccess;
-  const unsigned grid = (unsigned)std::min<int64_t>(grid_for(max_items, 256), 152 * 8);
-  k_item_info<K><<<grid, 256, 0, s>>>(item_start, n_items, keys, max_bodies, sc, ns, item_info);
+cudaError_t launch_item_write(int64_t n, const K* keys, const int* cnt, const int* off, const int* rend,
+                              int max_bodies, const SceneDev* sc, int ns, int* item_start, int4* item_info,
+                              int* n_items, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_item_write<K><<<grid_for(n, 256), 256, 0, s>>>(n, keys, cnt, off, rend, max_bodies, sc, ns, item_start,
+                                                   item_info, n_items);
   return cudaGetLastError();
 }
 
@@ -1799,9 +1806,9 @@ APIC_INST_T(double)
 #define APIC_INST_K(K)                                                                                     \
   template cudaError_t launch_keys<K>(int64_t, const SceneDev*, int, const int4*, int, K*, int*, int*,     \
                                       cudaStream_t);                                                       \
-  template cudaError_t launch_heads<K>(int64_t, const K*, int*, cudaStream_t);                             \
-  template cudaError_t launch_item_info<K>(const int*, const int*, const K*, int, const SceneDev*, int,    \
-                                           int4*, int, cudaStream_t);                                      \
+  template cudaError_t launch_run_items<K>(int64_t, const K*, int, int*, int*, cudaStream_t);            \
+  template cudaError_t launch_item_write<K>(int64_t, const K*, const int*, const int*, const int*, int,     \
+                                            const SceneDev*, int, int*, int4*, int*, cudaStream_t);         \
   template cudaError_t launch_mark_items<K>(const int*, const int4*, const int*, const K*, int64_t, int,   \
                                             const SceneDev*, int*, cudaStream_t);
 APIC_INST_K(uint32_t)

@@ -6,7 +6,8 @@
 //   2. per-scene page-table boxes laid end to end          (host, or reused)
 //   3. keys and one radix sort over all scenes              (k_keys, CUB)
 //   4. sorted SoA planes                                    (k_gather)
-//   5. work items of <= chunk particles of one (block, body)
+//   5. work items of <= chunk particles of one (block, body) (k_run_items,
+//      scan, k_item_write)
 //   6. active blocks and the page table                     (k_mark_items, scan, k_compact)
 //   7. mass, body mask and P2G(V); optional friction blend; normalise
 //   8. N + 1 fused transfer passes (Sec. 2.3 series, Sec. 2.4 projection)
@@ -35,11 +36,11 @@ namespace apic {
 
 enum Slot : int {
   kSlotCells = 0, kSlotKeysA, kSlotKeysB, kSlotVals, kSlotPerm, kSlotPt, kSlotPn, kSlotV, kSlotD, kSlotMup,
-  kSlotHeads, kSlotOffs, kSlotItemStart, kSlotItemInfo, kSlotBFlags, kSlotBOffs, kSlotBList, kSlotPage,
+  kSlotItemStart, kSlotItemInfo, kSlotBFlags, kSlotBOffs, kSlotBList, kSlotPage,
   kSlotGm, kSlotGmask, kSlotGp, kSlotGp64, kSlotGv, kSlotGmb, kSlotMuTable, kSlotCubTmp, kSlotScenes,
   kSlotSBbox, kSlotSMom, kSlotSCount, kSlotHX, kSlotHBody, kSlotHV, kSlotHC, kSlotHM, kSlotHN, kSlotHVo,
   kSlotHCo, kSlotDS, kSlotNrmAcc, kSlotNrmX, kSlotNrmTri, kSlotNrmOut, kSlotAugF, kSlotAugAm, kSlotAugVbar,
-  kSlotAugVhat, kSlotAugChat, kSlotAugNrm, kSlotAugOut, kSlotRunFlags, kSlotRunOffs, kSlotRunStart, kSlotFxMax,
+  kSlotAugVhat, kSlotAugChat, kSlotAugNrm, kSlotAugOut, kSlotRunCnt, kSlotRunOffs, kSlotRunEnd, kSlotFxMax,
   kSlotFxErr, kSlotGmbFx, kSlotCount
 };
 
@@ -131,8 +132,8 @@ struct SizingBufs {
   int *va = nullptr, *perm = nullptr; // sort values, sorted permutation
   char* tmp = nullptr;                 // CUB temporaries (max of the three uses)
   size_t tmp_sort = 0, tmp_scan_n = 0, tmp_scan_nb = 0;
-  int *run_flags = nullptr, *run_offs = nullptr, *run_start = nullptr;
-  int *heads = nullptr, *offs = nullptr, *item_start = nullptr;
+  int *run_cnt = nullptr, *run_offs = nullptr, *run_end = nullptr;  // per run head: items, their offset, end
+  int* item_start = nullptr;
   int4* item_info = nullptr;
   int *bflags = nullptr, *boffs = nullptr, *blist = nullptr, *page = nullptr;
 };
@@ -158,18 +159,16 @@ apic_status plan_sizing(Env& env, int64_t n, int64_t NB, int max_bodies, SizingB
     P_TRY(plan_keys<uint64_t>(env, n, b));
   else
     P_TRY(plan_keys<uint32_t>(env, n, b));
-  P_TRY(env.take(kSlotRunFlags, n, &b.run_flags, "run heads"));
-  P_TRY(env.take(kSlotRunOffs, n, &b.run_offs, "run offsets"));
-  P_TRY(env.take(kSlotRunStart, n, &b.run_start, "run starts"));
-  P_TRY(env.take(kSlotHeads, n, &b.heads, "item heads"));
-  P_TRY(env.take(kSlotOffs, n, &b.offs, "item offsets"));
+  P_TRY(env.take(kSlotRunCnt, n, &b.run_cnt, "items per run"));
+  P_TRY(env.take(kSlotRunOffs, n, &b.run_offs, "item offsets"));
+  P_TRY(env.take(kSlotRunEnd, n, &b.run_end, "run ends"));
   P_TRY(env.take(kSlotItemStart, n, &b.item_start, "item starts"));
   P_TRY(env.take(kSlotItemInfo, n, &b.item_info, "item info"));
   P_TRY(env.take(kSlotBFlags, NB, &b.bflags, "block flags"));
   P_TRY(env.take(kSlotBOffs, NB, &b.boffs, "block offsets"));
   P_TRY(env.take(kSlotBList, NB, &b.blist, "block list"));
   P_TRY(env.take(kSlotPage, NB, &b.page, "page table"));
-  P_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, b.tmp_scan_n, b.heads, b.offs, n));
+  P_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, b.tmp_scan_n, b.run_cnt, b.run_offs, n));
   P_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, b.tmp_scan_nb, b.bflags, b.boffs, NB));
   const size_t t = std::max(b.tmp_sort, std::max(b.tmp_scan_n, b.tmp_scan_nb));
   P_TRY(env.take(kSlotCubTmp, t, &b.tmp, "sort and scan temporaries"));
@@ -375,21 +374,19 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     P_LAUNCH(env, launch_gather<T>(n, sc, ns, sb.perm, cellb, pt, pn, split_v ? nullptr : V, q));
     // 5. work items: runs of equal (grid block, body), each split into
     //    equal items of at most `chunk` particles (the variant's CTA size).
-    if (sb.k64)
-      P_LAUNCH(env, launch_heads<uint64_t>(n, static_cast<const uint64_t*>(sb.kb), sb.run_flags, q));
-    else
-      P_LAUNCH(env, launch_heads<uint32_t>(n, static_cast<const uint32_t*>(sb.kb), sb.run_flags, q));
-    P_TRY(exclusive_sum(env, sb, sb.tmp_scan_n, sb.run_flags, sb.run_offs, n, q));
-    P_LAUNCH(env, launch_compact(n, sb.run_flags, sb.run_offs, sb.run_start, nullptr, &ds->n_runs, q));
-    P_LAUNCH(env, launch_item_heads(n, sb.run_flags, sb.run_offs, sb.run_start, &ds->n_runs, chunk, sb.heads, q));
-    P_TRY(exclusive_sum(env, sb, sb.tmp_scan_n, sb.heads, sb.offs, n, q));
-    P_LAUNCH(env, launch_compact(n, sb.heads, sb.offs, sb.item_start, nullptr, &ds->n_items, q));
-    if (sb.k64)
-      P_LAUNCH(env, launch_item_info<uint64_t>(sb.item_start, &ds->n_items, static_cast<const uint64_t*>(sb.kb),
-                                               max_bodies, sc, ns, sb.item_info, (int)n, q));
-    else
-      P_LAUNCH(env, launch_item_info<uint32_t>(sb.item_start, &ds->n_items, static_cast<const uint32_t*>(sb.kb),
-                                               max_bodies, sc, ns, sb.item_info, (int)n, q));
+    if (sb.k64) {
+      const uint64_t* kb = static_cast<const uint64_t*>(sb.kb);
+      P_LAUNCH(env, launch_run_items<uint64_t>(n, kb, chunk, sb.run_cnt, sb.run_end, q));
+      P_TRY(exclusive_sum(env, sb, sb.tmp_scan_n, sb.run_cnt, sb.run_offs, n, q));
+      P_LAUNCH(env, launch_item_write<uint64_t>(n, kb, sb.run_cnt, sb.run_offs, sb.run_end, max_bodies, sc, ns,
+                                                sb.item_start, sb.item_info, &ds->n_items, q));
+    } else {
+      const uint32_t* kb = static_cast<const uint32_t*>(sb.kb);
+      P_LAUNCH(env, launch_run_items<uint32_t>(n, kb, chunk, sb.run_cnt, sb.run_end, q));
+      P_TRY(exclusive_sum(env, sb, sb.tmp_scan_n, sb.run_cnt, sb.run_offs, n, q));
+      P_LAUNCH(env, launch_item_write<uint32_t>(n, kb, sb.run_cnt, sb.run_offs, sb.run_end, max_bodies, sc, ns,
+                                                sb.item_start, sb.item_info, &ds->n_items, q));
+    }
     // 6. active grid blocks: every block some stencil reaches; page table.
     P_CUDA(cudaMemsetAsync(sb.bflags, 0, NB * sizeof(int), q));
     if (sb.k64)
