@@ -334,6 +334,9 @@ def _ptr(a):
         return None
     if _is_torch(a):
         return a.data_ptr()
+    if a.flags.writeable and a.size:
+        # (cheaper than a.ctypes.data, which builds a helper object per call)
+        return C.addressof(C.c_char.from_buffer(a))
     return a.ctypes.data
 
 
