@@ -86,3 +86,18 @@ def test_no_gpu_call_fails_cleanly_without_device(lib):
     rc = lib.apic_create(ctypes.byref(h), 0, 0)
     assert rc != 0
     assert lib.apic_last_error()
+
+
+def test_binding_pointer_of_numpy_arrays():
+    """The binding's data pointers of host arrays (writable or not, views
+    that start inside a buffer, empty) equal numpy's own."""
+    import numpy as np
+
+    from paper_2108_02259_gb300.apic import _ptr
+
+    base = np.zeros((10, 3, 3), np.float32)
+    ro = np.zeros(7)
+    ro.setflags(write=False)
+    for a in (base, base[3:], base.reshape(-1)[5:], np.arange(9, dtype=np.int32), ro, np.zeros((0, 3))):
+        assert _ptr(a) == a.ctypes.data
+    assert _ptr(None) is None
