@@ -510,11 +510,21 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
     __syncthreads();
   }
   if (MODE == kModeMu) {
+    const uint32_t own = 1u << body;
+    int other = 0;
     for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
       const int node = tile_node(snb, t);
-      smask[t] = node >= 0 ? p.gmask[node] : 0u;
+      const uint32_t m = node >= 0 ? p.gmask[node] : 0u;
+      smask[t] = m;
+      other |= (m & ~own) != 0u;
     }
-    __syncthreads();
+    if (!__syncthreads_or(other)) {
+      // no other body anywhere in the tile: every particle keeps mu(b, b),
+      // as the blend below would give it (no other body's mass in reach)
+      if (tid < count)
+        p.mup_out[s0 + tid] = S.mu_off < 0 ? (T)S.mu : p.mu_table[S.mu_off + body * S.n_bodies + body];
+      return;
+    }
   }
 
   // ---------------- phase 1: one thread per particle ----------------
