@@ -24,7 +24,8 @@
  *     on failure apic_last_error() holds a message for the calling thread.
  *   - The caller owns every pointer it passes.  The library keeps none past
  *     the call.  Scratch (grid, sort buffers) is owned by the context and
- *     grows on demand; it counts against the context's HBM budget.
+ *     grows on demand (cudaMalloc, or the caller's allocator given to
+ *     apic_set_allocator); it counts against the context's HBM budget.
  *   - Array pointers are device pointers on the context's device unless the
  *     APIC_HOST_PTRS flag is set.  Work is queued on the caller's CUDA stream
  *     (cudaStream_t passed as void*, NULL = legacy default stream).
