@@ -128,6 +128,8 @@ typedef struct {
   int64_t multibody_nodes; /* grid nodes with mass from two or more bodies */
   int64_t active_blocks;   /* 4x4x4-node grid blocks allocated this step   */
   int64_t work_items;      /* (grid block, body) particle segments         */
+  double E_in, E_out;      /* generalised kinetic energy (1/2) sum m (|v|^2 + (h^2/2) |C|_F^2),
+                              FP64, of the inputs and of the outputs          */
 } apic_stats;
 
 /* Per-context kernel timing (CUDA events on the caller's stream), for the

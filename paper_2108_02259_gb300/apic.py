@@ -65,13 +65,14 @@ class Stats(C.Structure):
     _fields_ = [
         ("P_in", C.c_double * 3), ("P_out", C.c_double * 3), ("L_in", C.c_double * 3),
         ("L_out", C.c_double * 3), ("multibody_nodes", C.c_int64), ("active_blocks", C.c_int64),
-        ("work_items", C.c_int64),
+        ("work_items", C.c_int64), ("E_in", C.c_double), ("E_out", C.c_double),
     ]
 
     def as_dict(self):
         return dict(P_in=np.array(self.P_in[:]), P_out=np.array(self.P_out[:]), L_in=np.array(self.L_in[:]),
                     L_out=np.array(self.L_out[:]), multibody_nodes=int(self.multibody_nodes),
-                    active_blocks=int(self.active_blocks), work_items=int(self.work_items))
+                    active_blocks=int(self.active_blocks), work_items=int(self.work_items),
+                    E_in=float(self.E_in), E_out=float(self.E_out))
 
 
 class ServerStats(C.Structure):

@@ -196,10 +196,10 @@ cudaError_t launch_fx_prep(int64_t n, const SceneDev* sc, int ns, const int* per
 cudaError_t launch_normalize_fx(int64_t n_nodes, const int* blist, const SceneDev* sc, int ns, float* gm,
                                 long long* gfx, V4<float>* gv, const unsigned* fx_max, const int* fx_err,
                                 int fx_stride, int slot, int attempt, int all64, bool overlap, cudaStream_t s);
-// FP64 totals of one scene: out6 = (P, L).
+// FP64 totals of one scene: out7 = (P, L, E).
 template <class T>
 cudaError_t launch_momentum(int64_t n, const double* x, const T* v, const T* C, const T* m, double h,
-                            double* out6, cudaStream_t s);
+                            double* out7, cudaStream_t s);
 // Per-scene counts: out[3 s] = (multi-body nodes, active blocks, work items).
 cudaError_t launch_scene_counts(int n_blocks, const int* blist, const uint32_t* gmask, int n_items,
                                 const int4* item_info, const SceneDev* sc, int ns, unsigned long long* out,

@@ -1242,12 +1242,14 @@ __global__ void k_compact(int64_t n, const int* __restrict__ flags, const int* _
   if (i == n - 1) *count = o + f;
 }
 
-// FP64 totals P = sum m v and L = sum m [x cross v + (h^2/2) axial(C)].
+// FP64 totals P = sum m v, L = sum m [x cross v + (h^2/2) axial(C)] and the
+// generalised kinetic energy E = sum m (|v|^2 + (h^2/2) |C|_F^2) / 2 (the
+// energy of the mass inner product under which H is a contraction).
 template <class T>
 __global__ void k_momentum(int64_t n, const double* __restrict__ x, const T* __restrict__ v,
                            const T* __restrict__ C, const T* __restrict__ m, double h2half,
-                           double* out6) {
-  double acc[6] = {0, 0, 0, 0, 0, 0};
+                           double* out7) {
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     const double mm = (double)m[p];
@@ -1260,24 +1262,28 @@ __global__ void k_momentum(int64_t n, const double* __restrict__ x, const T* __r
     acc[3] += mm * (x1 * v2 - x2 * v1 + h2half * ((double)c[7] - (double)c[5]));
     acc[4] += mm * (x2 * v0 - x0 * v2 + h2half * ((double)c[2] - (double)c[6]));
     acc[5] += mm * (x0 * v1 - x1 * v0 + h2half * ((double)c[3] - (double)c[1]));
+    double cc = 0.0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) cc += (double)c[a] * (double)c[a];
+    acc[6] += 0.5 * mm * (v0 * v0 + v1 * v1 + v2 * v2 + h2half * cc);
   }
 #pragma unroll
-  for (int k = 0; k < 6; ++k)
+  for (int k = 0; k < 7; ++k)
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
-  __shared__ double red[6][32];
+  __shared__ double red[7][32];
   const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if ((threadIdx.x & 31) == 0)
 #pragma unroll
-    for (int k = 0; k < 6; ++k) red[k][w] = acc[k];
+    for (int k = 0; k < 7; ++k) red[k][w] = acc[k];
   __syncthreads();
   if (threadIdx.x < 32) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < 7; ++k) {
       double v = threadIdx.x < nw ? red[k][threadIdx.x] : 0.0;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      if (threadIdx.x == 0) atomicAdd(&out6[k], v);
+      if (threadIdx.x == 0) atomicAdd(&out7[k], v);
     }
   }
 }
@@ -1487,11 +1493,11 @@ cudaError_t launch_normalize_fx(int64_t n_nodes, const int* blist, const SceneDe
 
 template <class T>
 cudaError_t launch_momentum(int64_t n, const double* x, const T* v, const T* C, const T* m, double h,
-                            double* out6, cudaStream_t s) {
+                            double* out7, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   unsigned g = grid_for(n, 256);
   if (g > 608) g = 608;
-  k_momentum<T><<<g, 256, 0, s>>>(n, x, v, C, m, 0.5 * h * h, out6);
+  k_momentum<T><<<g, 256, 0, s>>>(n, x, v, C, m, 0.5 * h * h, out7);
   return cudaGetLastError();
 }
 

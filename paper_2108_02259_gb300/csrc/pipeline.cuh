@@ -668,9 +668,10 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   if (stats) {
     double* smom;
     unsigned long long* scount;
-    P_TRY(env.take(kSlotSMom, 12 * ns, &smom, "scene momenta"));
+    // per scene: (P, L, E) of the inputs, then of the outputs
+    P_TRY(env.take(kSlotSMom, 14 * ns, &smom, "scene momenta"));
     P_TRY(env.take(kSlotSCount, 3 * ns, &scount, "scene counts"));
-    P_CUDA(cudaMemsetAsync(smom, 0, 12 * ns * sizeof(double), s));
+    P_CUDA(cudaMemsetAsync(smom, 0, 14 * ns * sizeof(double), s));
     P_CUDA(cudaMemsetAsync(scount, 0, 3 * ns * sizeof(unsigned long long), s));
     for (int i = 0; i < ns; ++i) {
       const SceneDev& d = hsc[i];
@@ -678,24 +679,26 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       const double* x = d.x;
       const T* m = static_cast<const T*>(d.m);
       P_LAUNCH(env, launch_momentum<T>(d.n, x, static_cast<const T*>(d.v), static_cast<const T*>(d.C), m, d.h,
-                                       smom + 12 * i, s));
+                                       smom + 14 * i, s));
       P_LAUNCH(env, launch_momentum<T>(d.n, x, static_cast<const T*>(d.v_out), static_cast<const T*>(d.C_out),
-                                       m, d.h, smom + 12 * i + 6, s));
+                                       m, d.h, smom + 14 * i + 7, s));
     }
     P_LAUNCH(env, launch_scene_counts(n_blocks, blist, gmask, n_items, item_info, sc, ns, scount, s));
-    double* hm = static_cast<double*>(env.host_buf(12 * ns * sizeof(double) + 3 * ns * sizeof(unsigned long long)));
+    double* hm = static_cast<double*>(env.host_buf(14 * ns * sizeof(double) + 3 * ns * sizeof(unsigned long long)));
     if (!hm) return pfail(APIC_ERR_INVALID_ARG, "too many scenes for statistics on this entry point");
-    unsigned long long* hc = reinterpret_cast<unsigned long long*>(hm + 12 * ns);
-    P_CUDA(cudaMemcpyAsync(hm, smom, 12 * ns * sizeof(double), cudaMemcpyDeviceToHost, s));
+    unsigned long long* hc = reinterpret_cast<unsigned long long*>(hm + 14 * ns);
+    P_CUDA(cudaMemcpyAsync(hm, smom, 14 * ns * sizeof(double), cudaMemcpyDeviceToHost, s));
     P_CUDA(cudaMemcpyAsync(hc, scount, 3 * ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     P_CUDA(cudaStreamSynchronize(s));
     for (int i = 0; i < ns; ++i) {
       for (int k = 0; k < 3; ++k) {
-        stats[i].P_in[k] = hm[12 * i + k];
-        stats[i].L_in[k] = hm[12 * i + 3 + k];
-        stats[i].P_out[k] = hm[12 * i + 6 + k];
-        stats[i].L_out[k] = hm[12 * i + 9 + k];
+        stats[i].P_in[k] = hm[14 * i + k];
+        stats[i].L_in[k] = hm[14 * i + 3 + k];
+        stats[i].P_out[k] = hm[14 * i + 7 + k];
+        stats[i].L_out[k] = hm[14 * i + 10 + k];
       }
+      stats[i].E_in = hm[14 * i + 6];
+      stats[i].E_out = hm[14 * i + 13];
       stats[i].multibody_nodes = (int64_t)hc[3 * i];
       stats[i].active_blocks = (int64_t)hc[3 * i + 1];
       stats[i].work_items = (int64_t)hc[3 * i + 2];

@@ -64,7 +64,7 @@ def test_struct_layout_matches_header(lib):
     from paper_2108_02259_gb300 import apic
 
     assert ctypes.sizeof(apic.StepArgs) == 8 + 4 + 4 + 8 * 8 + 8 + 8 + 8 + 8  # 112 with padding
-    assert ctypes.sizeof(apic.Stats) == 12 * 8 + 3 * 8
+    assert ctypes.sizeof(apic.Stats) == 12 * 8 + 3 * 8 + 2 * 8
 
 
 def test_oracle_flags_match_library():

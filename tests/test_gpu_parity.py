@@ -314,3 +314,39 @@ def test_limits_rejected_cleanly():
         ref = run_oracle(ok)
         check(ok, (r.v.astype(np.float64), r.C.astype(np.float64).reshape(-1, 3, 3), None), ref, 3 * TOL_V32,
               TOL_C32, None, "after limits", count_multibody=False)
+
+
+@pytest.mark.parametrize("case", ["two_cubes_fp64", "four_bodies", "cloud", "affine_cloud"])
+def test_energy_diagnostics(ctx, case):
+    """apic_stats E_in / E_out: the generalised kinetic energy (1/2) sum m
+    (|v|^2 + (h^2/2) |C|_F^2) of the inputs and outputs, in FP64 on the
+    device.  Each matches the same sum over the arrays on the host, E_out
+    matches the oracle's output energy, contact dissipates it, and an affine
+    velocity field keeps it."""
+    dt = np.float32
+    if case == "two_cubes_fp64":
+        s, dt = scenes.two_cubes(mu=0.3, n_iter=10), np.float64
+    elif case == "four_bodies":
+        s = scenes.four_bodies(scale=0.05)
+    elif case == "cloud":
+        s = scenes.random_cloud(3000, n_bodies=3, seed=5, h=0.05, n_iter=4)
+    else:
+        s = scenes.random_cloud(3000, n_bodies=3, seed=6, h=0.05, n_iter=4, affine=True)
+
+    def energy(v, Cm):
+        return 0.5 * np.sum(s.m.astype(dt).astype(np.float64) * (np.sum(v * v, axis=1)
+                                                                 + 0.5 * s.h * s.h * np.sum(Cm.reshape(-1, 9) ** 2, axis=1)))
+
+    v, Cm, st = run_gpu(ctx, s, dtype=dt)
+    f = s.astype(dt)
+    e_in_host = energy(f.v.astype(np.float64), f.C.astype(np.float64))
+    assert abs(st["E_in"] - e_in_host) <= 1e-12 * e_in_host
+    assert abs(st["E_out"] - energy(v, Cm)) <= 1e-12 * e_in_host
+    rv, rC, _ = run_oracle(s)
+    e_ref = energy(rv, rC)
+    tol = 1e-12 if dt == np.float64 else 1e-5
+    assert abs(st["E_out"] - e_ref) <= tol * e_in_host, (st["E_out"], e_ref)
+    if case == "affine_cloud":
+        assert abs(st["E_out"] - st["E_in"]) <= 10 * tol * st["E_in"]
+    else:
+        assert st["E_out"] < st["E_in"]
