@@ -511,7 +511,10 @@ def main():
         "momentum_check": {"P_drift_rel": drift,
                            "multibody_nodes": int(sum(x["multibody_nodes"] for x in st)),
                            "active_blocks": int(sum(x["active_blocks"] for x in st)),
-                           "work_items": int(sum(x["work_items"] for x in st))},
+                           "work_items": int(sum(x["work_items"] for x in st)),
+                           # generalised kinetic energy, outputs over inputs (contact dissipates)
+                           "E_change_rel": float(sum(x["E_out"] - x["E_in"] for x in st)
+                                                 / max(sum(x["E_in"] for x in st), 1e-300))},
         "clocks": ck,
     }
     if not args.no_extras:
