@@ -431,6 +431,25 @@ def test_mu_pair_uniform_equals_scalar():
     np.testing.assert_allclose(a[0], b[0], atol=1e-13)
 
 
+def test_mu_pair_two_rigid_bodies_use_the_cross_coefficient():
+    """Two rigid bodies, one series term (N = 1): only particles whose stencil
+    reaches the other body are projected (elsewhere Delta = 0, App. A), and
+    for them the blend of the pair table is mu(0, 1) whatever the diagonal.
+    So a table with very different diagonal entries gives exactly the scalar
+    step with mu = mu(0, 1) -- and a blend that counted the particle's own
+    body, or the other body's self-friction, would not."""
+    s = scenes.two_cubes(mu=0.2, n_iter=1)
+    a = oracle.contact_step(s.x, s.v, s.C, s.m, s.nrm, s.body, s.h, 0.2, 1)
+    b = oracle.contact_step(s.x, s.v, s.C, s.m, s.nrm, s.body, s.h, 0.0, 1,
+                            mu_pair=np.array([[0.9, 0.2], [0.2, 0.05]]))
+    np.testing.assert_allclose(b[0], a[0], atol=1e-13)
+    np.testing.assert_allclose(b[1], a[1], atol=1e-10)
+    # and the cross coefficient does matter here
+    c = oracle.contact_step(s.x, s.v, s.C, s.m, s.nrm, s.body, s.h, 0.0, 1,
+                            mu_pair=np.array([[0.9, 0.6], [0.6, 0.05]]))
+    assert np.abs(c[0] - a[0]).max() > 1e-3
+
+
 # ------------------------------------------------- planted mistakes ----
 
 MISTAKES = [
