@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libapiccontact.so")
-SOURCES = ["kernels.cu", "api.cu", "static_step.cu", "serve.cu", "augury.cu"]
+SOURCES = ["kernels.cu", "sort.cu", "api.cu", "static_step.cu", "serve.cu", "augury.cu"]
 HEADERS = [os.path.join(CSRC, "apic_internal.h"), os.path.join(CSRC, "pipeline.cuh"),
            os.path.join(ROOT, "include", "apiccontact.h")]
 

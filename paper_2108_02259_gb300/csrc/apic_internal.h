@@ -235,6 +235,23 @@ cudaError_t launch_aug_energy(int64_t n, const double* x, const T* v, const T* m
                               const int32_t* springs, const double* rest, const double* k, double* out,
                               cudaStream_t s);
 
+// Stable LSD radix sort of (key, value) pairs over the low end_bit bits of
+// the keys (sort.cu): radix_passes(end_bit) passes of at most 8 bits, each
+// from (keys, vals) to (keys_alt, vals_alt) and back, so the result is in
+// (keys_alt, vals_alt) when the pass count is odd and in (keys, vals) when it
+// is even.  vals_iota: the input values are the indices 0..n-1 (not read).
+// temp holds radix_temp_ints<K>(n, end_bit) ints.
+int radix_passes(int end_bit);
+template <class K>
+int64_t radix_temp_ints(int64_t n, int end_bit);
+template <class K>
+cudaError_t launch_radix_sort(K* keys, int* vals, K* keys_alt, int* vals_alt, int64_t n, int end_bit,
+                              bool vals_iota, int* temp, cudaStream_t s);
+// Exclusive sum of n ints (in == out allowed); temp holds scan_temp_ints(n)
+// ints.
+int64_t scan_temp_ints(int64_t n);
+cudaError_t launch_exclusive_scan(const int* in, int* out, int64_t n, int* temp, cudaStream_t s);
+
 // One copy of `bytes` bytes between device-visible addresses (device memory
 // or page-locked host memory seen through its device pointer).
 struct CopyEntry {

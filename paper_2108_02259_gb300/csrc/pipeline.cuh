@@ -4,7 +4,7 @@
 // A call steps a batch of independent scenes (one scene is a batch of one):
 //   1. cells + validation + per-scene bounding boxes      (k_cells)
 //   2. per-scene page-table boxes laid end to end          (host, or reused)
-//   3. keys and one radix sort over all scenes              (k_keys, CUB)
+//   3. keys and one radix sort over all scenes              (k_keys, sort.cu)
 //   4. sorted SoA planes                                    (k_gather)
 //   5. work items of <= chunk particles of one (block, body) (k_run_items,
 //      scan, k_item_write)
@@ -17,9 +17,6 @@
 // The environment `Env` supplies device scratch by slot, a host mirror of
 // the device counters, an optional per-scene box cache and profiling hooks.
 #pragma once
-
-#include <cub/device/device_radix_sort.cuh>
-#include <cub/device/device_scan.cuh>
 
 #include <algorithm>
 #include <cmath>
@@ -37,7 +34,7 @@ namespace apic {
 enum Slot : int {
   kSlotCells = 0, kSlotKeysA, kSlotKeysB, kSlotVals, kSlotPerm, kSlotPt, kSlotPn, kSlotV, kSlotD, kSlotMup,
   kSlotItemStart, kSlotItemInfo, kSlotBFlags, kSlotBOffs, kSlotBList, kSlotPage,
-  kSlotGm, kSlotGmask, kSlotGp, kSlotGp64, kSlotGv, kSlotGmb, kSlotMuTable, kSlotCubTmp, kSlotScenes,
+  kSlotGm, kSlotGmask, kSlotGp, kSlotGp64, kSlotGv, kSlotGmb, kSlotMuTable, kSlotSortTmp, kSlotScenes,
   kSlotSBbox, kSlotSMom, kSlotSCount, kSlotHX, kSlotHBody, kSlotHV, kSlotHC, kSlotHM, kSlotHN, kSlotHVo,
   kSlotHCo, kSlotDS, kSlotNrmAcc, kSlotNrmX, kSlotNrmTri, kSlotNrmOut, kSlotAugF, kSlotAugAm, kSlotAugVbar,
   kSlotAugVhat, kSlotAugChat, kSlotAugNrm, kSlotAugOut, kSlotRunCnt, kSlotRunOffs, kSlotRunEnd, kSlotFxMax,
@@ -122,16 +119,15 @@ inline apic_status validate_scene(const apic_step_args* a, int idx, uint32_t all
 }
 
 // Scratch of steps 3-6 for n particles and NB page-table entries.  Every
-// buffer and every CUB temporary size is fixed here, before any of those
-// steps is enqueued, so that the enqueue sequence itself allocates nothing
-// and assigns nothing (it may be captured once and replayed as a graph).
+// buffer and every temporary size is fixed here, before any of those steps
+// is enqueued, so that the enqueue sequence itself allocates nothing and
+// assigns nothing (it may be captured once and replayed as a graph).
 struct SizingBufs {
   int end_bit = 0;
   bool k64 = false;
-  void *ka = nullptr, *kb = nullptr;  // keys, sorted keys (uint32_t or uint64_t)
-  int *va = nullptr, *perm = nullptr; // sort values, sorted permutation
-  char* tmp = nullptr;                 // CUB temporaries (max of the three uses)
-  size_t tmp_sort = 0, tmp_scan_n = 0, tmp_scan_nb = 0;
+  void *ka = nullptr, *kb = nullptr;  // key buffers (uint32_t or uint64_t); sorted keys end in kb
+  int *va = nullptr, *perm = nullptr; // value buffers; the sorted permutation ends in perm
+  int* tmp = nullptr;                  // sort and scan temporaries
   int *run_cnt = nullptr, *run_offs = nullptr, *run_end = nullptr;  // per run head: items, their offset, end
   int* item_start = nullptr;
   int4* item_info = nullptr;
@@ -139,13 +135,13 @@ struct SizingBufs {
 };
 
 template <class K, class Env>
-apic_status plan_keys(Env& env, int64_t n, SizingBufs& b) {
+apic_status plan_keys(Env& env, int64_t n, SizingBufs& b, int64_t* tmp_ints) {
   K *ka, *kb;
   P_TRY(env.take(kSlotKeysA, n, &ka, "sort keys"));
   P_TRY(env.take(kSlotKeysB, n, &kb, "sorted keys"));
   P_TRY(env.take(kSlotVals, n, &b.va, "sort values"));
   P_TRY(env.take(kSlotPerm, n, &b.perm, "permutation"));
-  P_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, b.tmp_sort, ka, kb, b.va, b.perm, (int)n, 0, b.end_bit));
+  *tmp_ints = radix_temp_ints<K>(n, b.end_bit);
   b.ka = ka;
   b.kb = kb;
   return APIC_OK;
@@ -155,10 +151,11 @@ template <class Env>
 apic_status plan_sizing(Env& env, int64_t n, int64_t NB, int max_bodies, SizingBufs& b) {
   b.end_bit = bits_for((uint64_t)NB * (uint64_t)max_bodies - 1) + 6;
   b.k64 = b.end_bit > 32;
+  int64_t t_sort = 0;
   if (b.k64)
-    P_TRY(plan_keys<uint64_t>(env, n, b));
+    P_TRY(plan_keys<uint64_t>(env, n, b, &t_sort));
   else
-    P_TRY(plan_keys<uint32_t>(env, n, b));
+    P_TRY(plan_keys<uint32_t>(env, n, b, &t_sort));
   P_TRY(env.take(kSlotRunCnt, n, &b.run_cnt, "items per run"));
   P_TRY(env.take(kSlotRunOffs, n, &b.run_offs, "item offsets"));
   P_TRY(env.take(kSlotRunEnd, n, &b.run_end, "run ends"));
@@ -168,29 +165,31 @@ apic_status plan_sizing(Env& env, int64_t n, int64_t NB, int max_bodies, SizingB
   P_TRY(env.take(kSlotBOffs, NB, &b.boffs, "block offsets"));
   P_TRY(env.take(kSlotBList, NB, &b.blist, "block list"));
   P_TRY(env.take(kSlotPage, NB, &b.page, "page table"));
-  P_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, b.tmp_scan_n, b.run_cnt, b.run_offs, n));
-  P_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, b.tmp_scan_nb, b.bflags, b.boffs, NB));
-  const size_t t = std::max(b.tmp_sort, std::max(b.tmp_scan_n, b.tmp_scan_nb));
-  P_TRY(env.take(kSlotCubTmp, t, &b.tmp, "sort and scan temporaries"));
+  const int64_t t = std::max(t_sort, std::max(scan_temp_ints(n), scan_temp_ints(NB)));
+  P_TRY(env.take(kSlotSortTmp, (size_t)t, &b.tmp, "sort and scan temporaries"));
   return APIC_OK;
 }
 
+// Keys of every particle, then the radix sort; the sorted keys land in kb
+// and the permutation in perm (the keys start in the buffer that makes the
+// last pass end there).
 template <class K, class Env>
 apic_status sort_keys(Env& env, int64_t n, const SceneDev* sc, int ns, const int4* cellb, int max_bodies,
                       int* err, const SizingBufs& b, cudaStream_t s) {
-  K* ka = static_cast<K*>(b.ka);
-  K* kb = static_cast<K*>(b.kb);
-  P_LAUNCH(env, launch_keys<K>(n, sc, ns, cellb, max_bodies, ka, b.va, err, s));
-  size_t tmp = b.tmp_sort;
-  P_CUDA(cub::DeviceRadixSort::SortPairs(b.tmp, tmp, ka, kb, b.va, b.perm, (int)n, 0, b.end_bit, s));
+  const bool odd = radix_passes(b.end_bit) % 2 == 1;
+  K* k0 = static_cast<K*>(odd ? b.ka : b.kb);
+  K* k1 = static_cast<K*>(odd ? b.kb : b.ka);
+  int* v0 = odd ? b.va : b.perm;
+  int* v1 = odd ? b.perm : b.va;
+  P_LAUNCH(env, launch_keys<K>(n, sc, ns, cellb, max_bodies, k0, v0, err, s));
+  P_CUDA(launch_radix_sort<K>(k0, v0, k1, v1, n, b.end_bit, true, b.tmp, s));
   env.sorted();
   return APIC_OK;
 }
 
 template <class Env>
-apic_status exclusive_sum(Env& env, const SizingBufs& b, size_t tmp, const int* in, int* out, int64_t n,
-                          cudaStream_t s) {
-  P_CUDA(cub::DeviceScan::ExclusiveSum(b.tmp, tmp, in, out, n, s));
+apic_status exclusive_sum(Env& env, const SizingBufs& b, const int* in, int* out, int64_t n, cudaStream_t s) {
+  P_CUDA(launch_exclusive_scan(in, out, n, b.tmp, s));
   env.sorted();
   return APIC_OK;
 }
@@ -377,13 +376,13 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     if (sb.k64) {
       const uint64_t* kb = static_cast<const uint64_t*>(sb.kb);
       P_LAUNCH(env, launch_run_items<uint64_t>(n, kb, chunk, sb.run_cnt, sb.run_end, q));
-      P_TRY(exclusive_sum(env, sb, sb.tmp_scan_n, sb.run_cnt, sb.run_offs, n, q));
+      P_TRY(exclusive_sum(env, sb, sb.run_cnt, sb.run_offs, n, q));
       P_LAUNCH(env, launch_item_write<uint64_t>(n, kb, sb.run_cnt, sb.run_offs, sb.run_end, max_bodies, sc, ns,
                                                 sb.item_start, sb.item_info, &ds->n_items, q));
     } else {
       const uint32_t* kb = static_cast<const uint32_t*>(sb.kb);
       P_LAUNCH(env, launch_run_items<uint32_t>(n, kb, chunk, sb.run_cnt, sb.run_end, q));
-      P_TRY(exclusive_sum(env, sb, sb.tmp_scan_n, sb.run_cnt, sb.run_offs, n, q));
+      P_TRY(exclusive_sum(env, sb, sb.run_cnt, sb.run_offs, n, q));
       P_LAUNCH(env, launch_item_write<uint32_t>(n, kb, sb.run_cnt, sb.run_offs, sb.run_end, max_bodies, sc, ns,
                                                 sb.item_start, sb.item_info, &ds->n_items, q));
     }
@@ -395,7 +394,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     else
       P_LAUNCH(env, launch_mark_items<uint32_t>(sb.item_start, sb.item_info, &ds->n_items,
                                                 static_cast<const uint32_t*>(sb.kb), n, (int)n, sc, sb.bflags, q));
-    P_TRY(exclusive_sum(env, sb, sb.tmp_scan_nb, sb.bflags, sb.boffs, NB, q));
+    P_TRY(exclusive_sum(env, sb, sb.bflags, sb.boffs, NB, q));
     P_LAUNCH(env, launch_compact(NB, sb.bflags, sb.boffs, sb.blist, sb.page, &ds->n_blocks, q));
     P_CUDA(cudaMemcpyAsync(hs, ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, q));
     return APIC_OK;
