@@ -164,10 +164,18 @@ apic_status apic_create(apic_ctx** out, int32_t device, size_t hbm_budget_bytes)
 apic_status apic_destroy(apic_ctx* ctx);
 
 /* One contact step (Sec. 2.3 series with the Sec. 2.4 projection).
- * Asynchronous on `stream` except: it synchronises the stream twice while
- * sizing the sparse grid, and at the end when `stats` is non-NULL or
- * APIC_HOST_PTRS is set.  Invalid particle data (body out of range, m <= 0,
- * non-finite or out-of-range positions) returns INVALID_ARG. */
+ * Asynchronous on `stream` except for these host synchronisations of the
+ * stream:
+ *   - while sizing the sparse grid: once when the context reuses the
+ *     page-table box of its previous step (the steady state of a
+ *     simulation), twice when a box must be fitted (the first step, or a
+ *     particle that left the reused box);
+ *   - at the end when `stats` is non-NULL or APIC_HOST_PTRS is set;
+ *   - with APIC_DETERMINISTIC, once more after the series to read the
+ *     fixed-point range flags, and, if a range was exceeded, a second run of
+ *     the series followed by one more synchronisation.
+ * Invalid particle data (body out of range, m <= 0, non-finite or
+ * out-of-range positions) returns INVALID_ARG. */
 apic_status apic_contact_step(apic_ctx* ctx, const apic_step_args* args, void* stream, apic_stats* stats);
 
 /* Several independent scenes in one call (Sec. 2.3 series on each).
@@ -187,23 +195,32 @@ apic_status apic_contact_step_batched(apic_ctx* ctx, const apic_step_args* scene
  * Some hosts may not call cudaMalloc during a step: an application whose own
  * memory pool has already reserved (nearly) all of the GPU and hands out
  * nothing else, or a real-time loop that cannot afford the device-wide
- * synchronisation cudaMalloc and cudaFree imply.  This call computes exactly
- * what apic_contact_step computes, on the same apic_step_args and apic_stats,
- * but takes every scratch buffer from one static device array of 32 MiB that
- * the library defines (one per GPU that loads the library, held until the
- * process exits).  It allocates nothing and needs no context.
+ * synchronisation cudaMalloc and cudaFree imply.  This call computes the
+ * same contact step as apic_contact_step, on the same apic_step_args and
+ * apic_stats (within floating-point rounding: it always runs the default
+ * kernel variant with direct launches; with APIC_DETERMINISTIC the bits are
+ * identical), but takes every scratch buffer from one static device array of
+ * 32 MiB that the library defines (one per GPU that loads the library, held
+ * until the process exits).  It allocates nothing and needs no context.
  *   - Device pointers only (APIC_HOST_PTRS is rejected).
  *   - A scene whose scratch would exceed the 32 MiB array (roughly 100,000
  *     FP32 particles in compact bodies; fewer for sparse scenes or FP64) is
  *     rejected with APIC_ERR_INVALID_ARG and a message naming the limit.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture begins.
+ *   - The array belongs to the current device (cudaGetDevice): make the
+ *     device of the arrays and the stream current before the call.
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress; nothing is cached, so a device reset does not
+ *     leave a stale address).  The first call on a device loads the
+ *     library's device code there; make that first call before any stream
+ *     capture begins.
  *   - Every call uses the same array and leaves its data there; each call
  *     clears what must start at zero.  Calls whose GPU work overlaps (other
  *     streams, other host threads) race on the array: serialise them.
- *   - Synchronises the stream twice while sizing the grid, and at the end
- *     when stats is non-NULL.  Errors are reported by apic_last_error(). */
+ *   - Synchronises the stream twice while sizing the grid (there is no
+ *     page-table box to reuse between calls), and at the end when stats is
+ *     non-NULL; with APIC_DETERMINISTIC once more after the series, and, if
+ *     a fixed-point range was exceeded, after a second run of the series.
+ *     Errors are reported by apic_last_error(). */
 apic_status apic_contact_step_static(const apic_step_args* args, void* stream, apic_stats* stats);
 
 /* ---------------------------------------------------------------------------

@@ -52,6 +52,21 @@ ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_int32)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_size_t, C.c_int32)
 
 
+MAX_BODIES = 32  # bodies per scene (the width of the node body masks)
+
+
+def _default_n_bodies(body, n: int) -> int:
+    """n_bodies when the caller gives none: one more than the largest body
+    id for host arrays; for device tensors the limit of 32, an upper bound
+    that needs no device read (results do not depend on it; a per-pair
+    friction table needs the true count)."""
+    if n == 0:
+        return 1
+    if _is_torch(body):
+        return MAX_BODIES
+    return int(np.asarray(body).max()) + 1
+
+
 class StepArgs(C.Structure):
     _fields_ = [
         ("n", C.c_int64), ("n_bodies", C.c_int32), ("n_iter", C.c_int32),
@@ -393,7 +408,9 @@ def contact_step(ctx: Context, x, v, Cm, m, nrm, body, h: float, mu: float, n_it
     if fp64:
         flags |= APIC_FP64
     if n_bodies is None:
-        n_bodies = (int(body.max()) + 1) if n else 1
+        if mu_pair is not None:
+            raise ValueError("a per-pair friction table needs n_bodies")
+        n_bodies = _default_n_bodies(body, n)
     mp = None
     if mu_pair is not None:
         mp = np.ascontiguousarray(np.asarray(mu_pair, np.float64).reshape(n_bodies, n_bodies))
@@ -418,6 +435,13 @@ def contact_step_static(x, v, Cm, m, nrm, body, h: float, mu: float, n_iter: int
     for t in (x, v, Cm, m, nrm, body):
         if not t.is_cuda or not t.is_contiguous():
             raise ValueError("apic_contact_step_static wants contiguous CUDA tensors")
+        if t.device != x.device:
+            raise ValueError(f"apic_contact_step_static: tensors on {t.device} and {x.device}")
+    for t in (v_out, C_out):
+        if t is not None and (t.device != x.device or not t.is_contiguous()):
+            raise ValueError("apic_contact_step_static: outputs must be contiguous tensors on the inputs' device")
+    if stream is not None and stream.device != x.device:
+        raise ValueError(f"apic_contact_step_static: stream of {stream.device}, tensors on {x.device}")
     if dt == torch.float64:
         flags |= APIC_FP64
     if v_out is None:
@@ -427,14 +451,19 @@ def contact_step_static(x, v, Cm, m, nrm, body, h: float, mu: float, n_iter: int
     if stream is None:
         stream = torch.cuda.current_stream(x.device)
     if n_bodies is None:
-        n_bodies = (int(body.max()) + 1) if n else 1
+        if mu_pair is not None:
+            raise ValueError("a per-pair friction table needs n_bodies")
+        n_bodies = _default_n_bodies(body, n)
     mp = None
     if mu_pair is not None:
         mp = np.ascontiguousarray(np.asarray(mu_pair, np.float64).reshape(n_bodies, n_bodies))
     a = StepArgs(n, int(n_bodies), int(n_iter), _ptr(body), _ptr(x), _ptr(v), _ptr(Cm), _ptr(m), _ptr(nrm),
                  _ptr(v_out), _ptr(C_out), float(h), float(mu), None if mp is None else mp.ctypes.data, int(flags))
     st = Stats() if stats else None
-    _check(lib.apic_contact_step_static(C.byref(a), stream.cuda_stream, C.byref(st) if stats else None))
+    # the library's static array belongs to the current device: make it the
+    # tensors' device for the call
+    with torch.cuda.device(x.device):
+        _check(lib.apic_contact_step_static(C.byref(a), stream.cuda_stream, C.byref(st) if stats else None))
     return StepResult(v_out, C_out, st.as_dict() if stats else None)
 
 
@@ -485,7 +514,9 @@ def augury_steps(ctx: Context, x, v, Cm, av, aC, m, body, springs, rest, stiffne
         flags |= APIC_AUGURY_INIT
     n = int(x.shape[0])
     if n_bodies is None:
-        n_bodies = int(body.max().item()) + 1
+        if mu_pair is not None:
+            raise ValueError("a per-pair friction table needs n_bodies")
+        n_bodies = _default_n_bodies(body, n)
     mp = None
     if mu_pair is not None:
         mp = np.ascontiguousarray(np.asarray(mu_pair, np.float64).reshape(n_bodies, n_bodies))
@@ -511,7 +542,9 @@ class BatchScene:
         self.x, self.v, self.C, self.m, self.nrm, self.body = x, v, Cm, m, nrm, body
         self.h, self.mu, self.mu_pair = float(h), float(mu), mu_pair
         n = int(x.shape[0])
-        self.n_bodies = n_bodies if n_bodies is not None else ((int(body.max()) + 1) if n else 1)
+        if n_bodies is None and mu_pair is not None:
+            raise ValueError("a per-pair friction table needs n_bodies")
+        self.n_bodies = n_bodies if n_bodies is not None else _default_n_bodies(body, n)
         if v_out is None:
             v_out = v.new_empty(v.shape) if _is_torch(v) else np.empty_like(v)
         if C_out is None:
@@ -643,7 +676,9 @@ class Sim:
             flags |= APIC_FP64
         self.n = int(x.shape[0])
         self.dtype = np.float64 if fp64 else np.float32
-        nb = n_bodies if n_bodies is not None else int(body.max()) + 1
+        if n_bodies is None and mu_pair is not None:
+            raise ValueError("a per-pair friction table needs n_bodies")
+        nb = n_bodies if n_bodies is not None else _default_n_bodies(body, self.n)
         mp = None
         if mu_pair is not None:
             mp = np.ascontiguousarray(np.asarray(mu_pair, np.float64).reshape(nb, nb))

@@ -235,7 +235,6 @@ struct CtxEnv {
   SceneDev* host_scenes(int ns) {
     if (ns > c->h_scenes_cap) {
       if (c->h_scenes) cudaFreeHost(c->h_scenes);
-  if (c->h_copies) cudaFreeHost(c->h_copies);
       c->h_scenes = nullptr;
       c->h_scenes_cap = 0;
       if (cudaMallocHost(&c->h_scenes, ns * sizeof(SceneDev)) != cudaSuccess) {
@@ -541,6 +540,7 @@ apic_status apic_destroy(apic_ctx* c) {
   for (cudaEvent_t e : c->side_ev)
     if (e) cudaEventDestroy(e);
   delete c;
+  cudaGetLastError();  // a failed release is not left pending for the caller's next launch
   return APIC_OK;
 }
 

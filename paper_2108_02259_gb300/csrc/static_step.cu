@@ -18,12 +18,13 @@
 // calls whose GPU work overlaps (two streams, two host threads) race on the
 // array and corrupt each other's results: serialise them.
 //
-// In host code the array's name is only a host-side stand-in, so the device
-// address is looked up with cudaGetSymbolAddress once per device, on the
-// first call made with that device current; make that first call before
-// any stream capture begins.
-#include <mutex>
-
+// In host code the array's name is only a host-side stand-in, so every call
+// looks up the array's device address on the current device with
+// cudaGetSymbolAddress (a host-side table lookup once the module is loaded).
+// The address is not cached: a device reset, or a primary context torn down
+// and created again, reloads the module at another address, and a cached
+// pointer would then be stale.  The first call on a device loads the module
+// there; make that first call before any stream capture begins.
 #include "pipeline.cuh"
 
 using namespace apic;
@@ -31,28 +32,20 @@ using namespace apic;
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_setup_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the static array on the current device (set up once).
+// Device address of the static array on the current device, looked up on
+// every call (never cached, so that it stays valid across device resets).
 apic_status scratch_base(void** out) {
   int dev = 0;
   P_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return pfail(APIC_ERR_INVALID_ARG, "device %d beyond %d", dev, kMaxDevices);
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || p == nullptr)
-      return pfail(APIC_ERR_CUDA, "cudaGetSymbolAddress(static scratch) on device %d: %s", dev,
-                   cudaGetErrorString(e));
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || p == nullptr)
+    return pfail(APIC_ERR_CUDA, "cudaGetSymbolAddress(static scratch) on device %d: %s", dev,
+                 cudaGetErrorString(e));
+  *out = p;
   return APIC_OK;
 }
 
