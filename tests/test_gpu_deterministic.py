@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+import parity_log
 from paper_2108_02259_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -47,6 +48,7 @@ def _close(s, v, Cm, rv, rC, label):
     cs = cs if cs > 0 else 2 * vs / s.h
     ev = np.abs(v - rv).max() / vs
     ec = np.abs(Cm - rC).max() / cs
+    parity_log.record(f"deterministic {label}", s.n, {"v": ev, "C": ec}, {"v": TOL_V, "C": TOL_C})
     assert ev <= TOL_V and ec <= TOL_C, f"{label}: v err {ev:.3g}, C err {ec:.3g}"
 
 

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+import parity_log
 from paper_2108_02259_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -79,7 +80,7 @@ def check(s, got, ref, tol_v, tol_c, tol_mom=None, label="", count_multibody=Tru
     vs, cs, sP, sL = scales(s, rC)
     ev = np.abs(v - rv).max() / vs
     ec = np.abs(Cm - rC).max() / cs
-    print(f"[parity] {label}: n={s.n} v err {ev:.2e} C err {ec:.2e}")
+    parity_log.record(label, s.n, {"v": ev, "C": ec}, {"v": tol_v, "C": tol_c})
     assert ev <= tol_v, f"{label} v error {ev:.3e} > {tol_v}"
     assert ec <= tol_c, f"{label} C error {ec:.3e} > {tol_c}"
     if tol_mom is not None and st is not None:
@@ -134,7 +135,7 @@ def test_random_nonaffine(ctx, seed, nb, n_iter, origin):
     """Random non-affine states, dense clouds (many particles per cell),
     negative coordinates, up to 32 bodies."""
     s = scenes.random_cloud(3000, n_bodies=nb, seed=seed, h=0.1, n_iter=n_iter, origin=origin, spread=1.3)
-    check(s, run_gpu(ctx, s), run_oracle(s), 3 * TOL_V32, TOL_C32, TOL_MOM32, f"random seed={seed}")
+    check(s, run_gpu(ctx, s), run_oracle(s), TOL_V32, TOL_C32, TOL_MOM32, f"random seed={seed}")
     check(s, run_gpu(ctx, s, np.float64), run_oracle(s), TOL64, TOL64, 1e-12, f"random fp64 seed={seed}")
 
 
@@ -153,7 +154,7 @@ def test_mu_pair(ctx):
     rng = np.random.default_rng(10)
     mp = rng.uniform(0.1, 0.5, (4, 4))
     mp = np.triu(mp) + np.triu(mp, 1).T
-    check(s, run_gpu(ctx, s, mu_pair=mp), run_oracle(s, mu_pair=mp), 3 * TOL_V32, TOL_C32, TOL_MOM32, "mu_pair")
+    check(s, run_gpu(ctx, s, mu_pair=mp), run_oracle(s, mu_pair=mp), TOL_V32, TOL_C32, TOL_MOM32, "mu_pair")
     check(s, run_gpu(ctx, s, np.float64, mu_pair=mp), run_oracle(s, mu_pair=mp), TOL64, TOL64, None, "mu_pair fp64")
 
 
@@ -178,7 +179,7 @@ def test_empty(ctx):
 def test_single_particle_and_single_cell(ctx):
     for n in (1, 2, 40):
         s = scenes.random_cloud(n, n_bodies=2, seed=n, h=1.0, spread=0.999, origin=(5.0, 5.0, 5.0), n_iter=2)
-        check(s, run_gpu(ctx, s), run_oracle(s), 3 * TOL_V32, TOL_C32, TOL_MOM32, f"n={n}")
+        check(s, run_gpu(ctx, s), run_oracle(s), TOL_V32, TOL_C32, TOL_MOM32, f"n={n}")
 
 
 def test_single_rigid_body_unchanged(ctx):
@@ -205,7 +206,7 @@ def test_cell_boundaries(ctx):
     # The multi-body node count is not compared here: 1e-9 below a grid line
     # the offset t = 1 - 4e-9 rounds to 1 in FP32, so a node whose FP64 weight
     # is ~1e-17 receives no mass on the FP32 path and is not counted.
-    check(s, run_gpu(ctx, s), run_oracle(s), 3 * TOL_V32, TOL_C32, TOL_MOM32, "cell boundaries",
+    check(s, run_gpu(ctx, s), run_oracle(s), TOL_V32, TOL_C32, TOL_MOM32, "cell boundaries",
           count_multibody=False)
     check(s, run_gpu(ctx, s, np.float64), run_oracle(s), TOL64, TOL64, 1e-12, "cell boundaries fp64")
 
@@ -232,7 +233,7 @@ def test_invalid_inputs_rejected(ctx):
     with pytest.raises(apic.ApicError):
         apic.contact_step(ctx, x, f.v, f.C, f.m, f.nrm, f.body, s.h, 0.3, 2)
     # the context is still usable afterwards
-    check(s, run_gpu(ctx, s), run_oracle(s), 3 * TOL_V32, TOL_C32, TOL_MOM32, "after errors")
+    check(s, run_gpu(ctx, s), run_oracle(s), TOL_V32, TOL_C32, TOL_MOM32, "after errors")
 
 
 def test_repeat_calls_reuse_scratch(ctx):
@@ -267,19 +268,27 @@ def _subset(s, keep, bodies):
 
 def test_eight_bodies_full_size(ctx):
     """The 4,000,000-node 8-body scene (h = 1/512, per-pair mu, N = 8) as one
-    launch.  Its four approaching pairs are ~0.3 apart, far beyond the
-    2h stencil reach, so the oracle run on one pair alone gives exactly the
-    full-scene answer for that pair's 1,000,000 particles; the full scene
-    must also keep its momentum."""
+    launch, every particle against the oracle.  Its four approaching pairs
+    (bodies 2k and 2k+1) are ~0.3 apart, far beyond the 2h stencil reach, so
+    the oracle run on one pair alone gives exactly the full-scene answer for
+    that pair's 1,000,000 particles; the four pairs run in parallel threads
+    (the oracle holds no global state).  The full scene must also keep its
+    momentum."""
+    from concurrent.futures import ThreadPoolExecutor
+
     s = scenes.eight_bodies()
     v, Cm, st = run_gpu(ctx, s, mu_pair=s.mu_pair)
     vs, _, sP, sL = scales(s, s.C)
     assert np.abs(st["P_out"] - st["P_in"]).max() <= TOL_MOM32 * sP
     assert np.abs(st["L_out"] - st["L_in"]).max() <= TOL_MOM32 * sL
-    keep = (s.body == 0) | (s.body == 1)
-    sub = _subset(s, keep, (0, 1))
-    rv, rC, rst = run_oracle(sub, mu_pair=sub.mu_pair)
-    check(sub, (v[keep], Cm[keep], None), (rv, rC, rst), TOL_V32, TOL_C32, None, "eight bodies, pair 0 of full scene")
+    pairs = []
+    for k in range(4):
+        keep = (s.body == 2 * k) | (s.body == 2 * k + 1)
+        pairs.append((keep, _subset(s, keep, (2 * k, 2 * k + 1))))
+    with ThreadPoolExecutor(4) as ex:
+        refs = list(ex.map(lambda ks: run_oracle(ks[1], mu_pair=ks[1].mu_pair), pairs))
+    for k, ((keep, sub), ref) in enumerate(zip(pairs, refs)):
+        check(sub, (v[keep], Cm[keep], None), ref, TOL_V32, TOL_C32, None, f"eight bodies, pair {k} of full scene")
 
 
 def test_limits_rejected_cleanly():
@@ -312,7 +321,7 @@ def test_limits_rejected_cleanly():
         assert c.scratch_bytes() <= 8 << 20
         r = apic.contact_step(c, f.x, f.v, f.C, f.m, f.nrm, f.body, ok.h, ok.mu, ok.n_iter, n_bodies=2)
         ref = run_oracle(ok)
-        check(ok, (r.v.astype(np.float64), r.C.astype(np.float64).reshape(-1, 3, 3), None), ref, 3 * TOL_V32,
+        check(ok, (r.v.astype(np.float64), r.C.astype(np.float64).reshape(-1, 3, 3), None), ref, TOL_V32,
               TOL_C32, None, "after limits", count_multibody=False)
 
 

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+import parity_log
 from paper_2108_02259_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
@@ -70,9 +71,11 @@ def test_served_steps_match_oracle(apic):
         for s, hdl, dt in zip(sims, handles, dts):
             got = hdl.read()
             ev, ec, ex = _err(s, got, _oracle_steps(s, steps, dt))
-            print(f"[serve] n={s.n}: v err {ev:.2e} C err {ec:.2e} x err {ex:.2e}")
+            xtol = steps * dt * TOL_V * np.abs(s.v).max()
+            parity_log.record(f"served, {steps} steps", s.n, {"v": ev, "C": ec, "x": ex / xtol},
+                              {"v": TOL_V, "C": TOL_C, "x": 1.0})
             # x moves by dt * v_hat each step: its error is bounded by the v error times steps * dt
-            assert ev <= 3 * TOL_V and ec <= TOL_C and ex <= steps * dt * 3 * TOL_V * np.abs(s.v).max()
+            assert ev <= TOL_V and ec <= TOL_C and ex <= xtol
             hdl.close()
 
 
@@ -124,7 +127,8 @@ def test_same_result_alone_and_in_the_mix(apic, det):
     mixed, mean_batch = run(True)
     assert mean_batch > 1.0  # the target really shared batches
     ev, ec, ex = _err(target, mixed, alone)
-    print(f"[serve] alone vs mix (det={det}): v {ev:.2e} C {ec:.2e} x {ex:.2e}, mean batch {mean_batch:.2f}")
+    parity_log.record(f"served alone vs in the mix (det={det}, mean batch {mean_batch:.2f})", target.n,
+                      {"v": ev, "C": ec}, {"v": TOL_V, "C": TOL_C})
     assert ev <= TOL_V and ec <= TOL_C and ex <= steps * dt * TOL_V * np.abs(target.v).max()
     if det:
         assert all(np.array_equal(p, q) for p, q in zip(mixed, alone))
@@ -209,7 +213,11 @@ def test_mixed_precisions_variants_and_iterations(apic):
             x, gv, gC = h.read()
             vs = np.abs(s.v).max()
             cs = max(np.abs(Cm).max(), np.abs(s.C).max(), 2 * vs / s.h)
-            tol = (1e-11, 1e-11) if dt == np.float64 else (3 * TOL_V, TOL_C)
+            tol = (1e-11, 1e-11) if dt == np.float64 else (TOL_V, TOL_C)
+            parity_log.record(f"served mixed kinds {np.dtype(dt).name} flags={flags} N={s.n_iter}", s.n,
+                              {"v": np.abs(gv - v).max() / vs,
+                               "C": np.abs(gC.reshape(-1, 9) - Cm.reshape(-1, 9)).max() / cs},
+                              {"v": tol[0], "C": tol[1]})
             assert np.abs(gv - v).max() <= tol[0] * vs, (dt, flags, s.n_iter)
             assert np.abs(gC.reshape(-1, 9) - Cm.reshape(-1, 9)).max() <= tol[1] * cs, (dt, flags, s.n_iter)
             assert np.all(x == s.x)  # dt_advect = 0
@@ -244,7 +252,7 @@ def test_checkpoint_and_resume(apic, dt):
         xr, vr, Cr = ref.read()
         xb, vb, Cb = back.read()
         vs = np.abs(s.v).max()
-        tol = 1e-12 if dt == np.float64 else 3 * TOL_V
+        tol = 1e-12 if dt == np.float64 else TOL_V
         assert np.abs(vb - vr).max() <= tol * vs
         assert np.abs(xb - xr).max() <= 4 * step_dt * tol * vs + 1e-15
         for bad in (ck[:-1], b"NOTACKPT" + ck[8:], ck[:20]):
