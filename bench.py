@@ -2,7 +2,7 @@
 
 One "step" is one full contact step through the C ABI: keys, sort, sparse
 grid activation, mass P2G, then N + 1 fused transfer passes (the paper's
-series with the Coulomb projection), on one synthetic scene resident in HBM.
+series with the Coulomb projection), on synthetic scenes resident in HBM.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
@@ -10,17 +10,25 @@ Prints one JSON line.  The metric is contact particle-iterations per second,
 P * (N + 1) per step (each particle through each transfer pair).
 
 Workloads (seeded, synthetic, shaped like the paper's bodies):
-  four_bodies   4 bodies, 200,000 FE nodes, h = 1/256, mu = 0.3, N = 8, FP32 (default)
-  two_cubes     2 cubes of 8^3 nodes, h = 1/32, mu = 0.3, N = 10, FP64
   eight_bodies  8 bodies, 4,000,000 nodes, h = 1/512, per-pair mu, N = 8, FP32
+                (default).  The default line also carries the metric's other
+                parts: "batched64" (the batched scenes below against the same
+                scenes stepped one call each) and "served" (the serving loop
+                below with 3 s per offered load: throughput, p50/p99 latency)
+  four_bodies   4 bodies, 200,000 FE nodes, h = 1/256, mu = 0.3, N = 8, FP32
+  two_cubes     2 cubes of 8^3 nodes, h = 1/32, mu = 0.3, N = 10, FP64
   batched64     64 independent scenes, 1k-200k nodes and 2-6 bodies each, h in
                 {1/64, 1/128, 1/256}, mu = 0.3, N = 8, FP32, one batched call per
                 step; also reports the same scenes stepped one call each
-  served        256 resident simulations (2k-1M nodes, 2-8 bodies, mu in [0, 0.5],
-                N = 8, 43.8M nodes in total) behind the serving loop; Poisson step
-                requests at 0.5 / 0.8 / 0.95 of the measured batched capacity;
-                reports throughput and p50/p99 request latency (value: load 0.8);
-                one GPU (under torchrun only rank 0 runs it)
+  served        256 resident simulations (2k-1M nodes each, 2-8 bodies, mu in
+                [0, 0.5], N = 8) behind the serving loop; Poisson step requests
+                at 0.5 / 0.8 / 0.95 of the measured batched capacity; reports
+                throughput and p50/p99 request latency (value: load 0.8); one GPU
+                (under torchrun only rank 0 runs it)
+
+The CPU baseline (and the reference arm, --impl reference) is the FP64
+oracle as it stands, on the host cores: one thread per independent bounded
+sample of the workload, as many threads as cores (up to 16).
 
 Multi-GPU (torchrun): every rank steps its own scene(s) of the workload's shape
 and size, drawn from seed + 1000 * rank (independent problems: no collective
@@ -199,61 +207,120 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 SMEM_PEAK_GWAVEFRONTS = 152 * 2.07
 
 
-def bounded_sample(s, max_particles=1_100_000):
-    """The oracle's bounded sample of a scene: the whole scene when small,
-    else its first approaching pair of bodies (bodies 0 and 1)."""
+SAMPLE_PARTICLES = 60_000  # one oracle sample: about half a second of single-threaded FP64 work per step
+
+
+def _sub_scene(s, keep):
+    """The particles `keep` of scene s, body ids renumbered 0.. over the
+    bodies present (with the matching block of a per-pair friction table)."""
     from paper_2108_02259_gb300 import scenes
 
-    if s.n <= max_particles:
-        return s, f"the whole scene ({s.n} particles)"
-    keep = (s.body == 0) | (s.body == 1)
-    mp = None if s.mu_pair is None else s.mu_pair[:2, :2].copy()
-    sub = scenes.Scene(s.x[keep], s.v[keep], s.C[keep], s.m[keep], s.nrm[keep], s.body[keep], 2, s.h, s.mu,
-                       s.n_iter, mp)
-    return sub, f"bodies 0 and 1 of the scene ({sub.n} of {s.n} particles)"
+    present = np.unique(s.body[keep])
+    remap = np.full(s.n_bodies, -1, np.int32)
+    remap[present] = np.arange(len(present), dtype=np.int32)
+    mp = None if s.mu_pair is None else s.mu_pair[np.ix_(present, present)].copy()
+    return scenes.Scene(s.x[keep], s.v[keep], s.C[keep], s.m[keep], s.nrm[keep], remap[s.body[keep]], len(present),
+                        s.h, s.mu, s.n_iter, mp)
 
 
-def oracle_sample(sc):
-    """The oracle's bounded sample of a workload: whole scenes (the first
-    ones of a batch, up to ~300k particles), or for one large scene its
-    first approaching pair of bodies."""
-    if len(sc) == 1:
-        s, what = bounded_sample(sc[0])
-        return [s], what
-    out, P = [], 0
-    for s in sc:
-        if P + s.n > 300_000 and out:
-            break
-        out.append(s)
-        P += s.n
-    return out, f"the first {len(out)} of {len(sc)} scenes ({P} particles)"
+def oracle_samples(sc, max_samples=16):
+    """Independent bounded samples of a workload for the oracle, each about
+    SAMPLE_PARTICLES particles, with the contact the workload has:
+      - a batch: its first scenes (whole), up to max_samples;
+      - one small scene: the whole scene (each thread steps its own copy);
+      - one large scene (the 4 M-node scene): per approaching pair of bodies
+        (2k, 2k+1), the particles nearest the pair's contact plane x = 0.5,
+        split into slabs along y, so that each sample holds both bodies
+        where they meet."""
+    if len(sc) > 1:
+        out = [s for s in sc if s.n <= 4 * SAMPLE_PARTICLES][:max_samples]
+        P = sum(s.n for s in out)
+        return out, f"{len(out)} whole scenes of the batch ({P} particles)"
+    s = sc[0]
+    if s.n <= 4 * SAMPLE_PARTICLES:
+        return [s], f"the whole scene ({s.n} particles)"
+    pairs = s.n_bodies // 2
+    per_pair = max(1, max_samples // max(pairs, 1))
+    out = []
+    for k in range(pairs):
+        inp = (s.body == 2 * k) | (s.body == 2 * k + 1)
+        idx = np.nonzero(inp)[0]
+        d = np.abs(s.x[idx, 0] - 0.5)
+        near = idx[np.argsort(d, kind="stable")[:per_pair * SAMPLE_PARTICLES]]
+        ys = s.x[near, 1]
+        cuts = np.quantile(ys, np.linspace(0, 1, per_pair + 1))
+        for j in range(per_pair):
+            lo, hi = cuts[j], cuts[j + 1]
+            sel = near[(ys >= lo) & ((ys < hi) if j + 1 < per_pair else (ys <= hi))]
+            keep = np.zeros(s.n, bool)
+            keep[sel] = True
+            out.append(_sub_scene(s, keep))
+    P = sum(x.n for x in out)
+    return out, (f"{len(out)} slabs of ~{SAMPLE_PARTICLES} particles across the contact planes of the scene's "
+                 f"{pairs} approaching pairs ({P} of {s.n} particles)")
 
 
-def run_oracle_steps(sample):
+def run_oracle_steps(samples):
+    """One oracle contact step of each sample, one host thread per sample
+    (the oracle holds no global state, and ctypes releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     import oracle
 
-    for s in sample:
+    def one(s):
         oracle.contact_step(s.x, s.v, s.C, s.m, s.nrm, s.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
                             mu_pair=s.mu_pair)
-    return sum(s.n * (s.n_iter + 1) for s in sample)
+        return s.n * (s.n_iter + 1)
+
+    if len(samples) == 1:
+        return one(samples[0])
+    with ThreadPoolExecutor(len(samples)) as ex:
+        return sum(ex.map(one, samples))
 
 
-def cpu_baseline(sc, budget_s=12.0):
-    """The FP64 oracle as it stands, single-threaded, on the host cores."""
-    sample, what = oracle_sample(sc)
-    t0 = time.perf_counter()
-    steps = units = 0
-    while True:
-        units += run_oracle_steps(sample)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el > budget_s or steps >= 8:
-            break
-    return {"value": units / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} step(s) of {what}, N={sample[0].n_iter}, {el:.1f} s single-threaded FP64"}
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(sc, budget_s=8.0):
+    """The FP64 oracle as it stands, on the machine's host cores: one thread per
+    independent sample, as many threads as cores (and samples), plus the
+    same oracle on one thread for reference."""
+    import oracle
+
+    oracle.build()
+    samples, what = oracle_samples(sc)
+    cores = host_cores()
+    threads = max(1, min(cores, 16))
+    par = [samples[i % len(samples)] for i in range(threads)]
+
+    def rate(batch):
+        t0 = time.perf_counter()
+        steps = units = 0
+        while True:
+            units += run_oracle_steps(batch)
+            steps += 1
+            el = time.perf_counter() - t0
+            if el > budget_s or steps >= 8:
+                return units / el, steps, el
+
+    one_v, one_steps, one_el = rate(samples[:1])
+    all_v, all_steps, all_el = rate(par)
+    return {"value": all_v, "unit": UNIT, "cores": threads, "nproc": cores, "kind": "oracle",
+            "sample": f"{all_steps} step(s) of {threads} independent samples in parallel threads "
+                      f"(from {what}), N={samples[0].n_iter}, {all_el:.1f} s, FP64",
+            "single_thread": {"value": one_v, "unit": UNIT, "cores": 1,
+                              "sample": f"{one_steps} step(s) of the first sample ({samples[0].n} particles), "
+                                        f"{one_el:.1f} s"}}
 
 
 def run_reference(args):
+    """The reference arm: the oracle (the only other implementation of the
+    method) on the host cores, each step one oracle step of every bounded
+    sample of the workload, one thread per sample."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
@@ -261,21 +328,25 @@ def run_reference(args):
 
     oracle.build()
     sc, dt, _ = make_workload(args.workload)
-    sample, what = oracle_sample(sc)
+    samples, what = oracle_samples(sc)
+    cores = host_cores()
+    threads = max(1, min(cores, 16))
+    par = [samples[i % len(samples)] for i in range(threads)]
     for _ in range(args.warmup):
-        run_oracle_steps(sample)
+        run_oracle_steps(par)
     t0 = time.perf_counter()
     units = 0
     for _ in range(args.steps):
-        units += run_oracle_steps(sample)
+        units += run_oracle_steps(par)
     el = time.perf_counter() - t0
     value = units / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args.workload, sc, dt),
-        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
-                         "sample": f"each step: {what}, single-threaded FP64 oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": threads, "nproc": cores,
+                         "sample": f"each step: {threads} independent samples in parallel threads (from {what}), "
+                                   "FP64 oracle"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -287,9 +358,10 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="four_bodies",
+    ap.add_argument("--workload", default="eight_bodies",
                     choices=["four_bodies", "two_cubes", "eight_bodies", "batched64", "served"])
-    ap.add_argument("--served-seconds", type=float, default=6.0)
+    ap.add_argument("--served-seconds", type=float, default=6.0,
+                    help="open-loop seconds per offered load (the served workload; 3 s in the default line's leg)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -301,7 +373,7 @@ def main():
     ap.add_argument("--no-overlap", action="store_true",
                     help="launch each pass strictly after the grid before it (no programmatic dependent launch)")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the node-normal and augury-driver measurements (contact step only)")
+                    help="skip every measurement beside the workload's own (normals, augury, batched and served legs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -327,7 +399,63 @@ def main():
         build.build()
     if ws > 1:
         torch.distributed.barrier()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = apic.Context(dev.index)
     sc, dt, batched = make_workload(args.workload, rank)
+    m = measure(args, apic, ctx, sc, dt, batched, dev, stream, flush, ws, with_e2e=not args.no_e2e,
+                with_clocks=True)
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    line = {
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if dt == np.float64 else "f32", "data": "synthetic",
+        "config": workload_config(args.workload, sc, dt),
+    }
+    line.update({k: m[k] for k in ("e2e", "gpu_launches", "kernel_variant", "cuda_graph", "dependent_launch",
+                                   "deterministic", "sort_primitive_calls_per_step", "roofline", "roofline_fp32",
+                                   "roofline_smem", "step_breakdown_ms", "momentum_check", "clocks")})
+    if "plain_single_scene" in m:
+        line["plain_single_scene"] = m["plain_single_scene"]
+    if not args.no_extras:
+        line["node_normals"] = bench_node_normals(apic, ctx, dev, stream, flush)
+        line["augury_dynamics"] = bench_augury(apic, ctx, dev, stream)
+    if not args.no_extras and args.workload == "eight_bodies" and ws == 1:
+        # the metric's other two parts on the same line: batched scenes
+        # against the plain single-scene path, and the served loop's p50/p99
+        b_sc, b_dt, _ = make_workload("batched64", rank)
+        b = measure(args, apic, ctx, b_sc, b_dt, True, dev, stream, flush, ws, with_e2e=not args.no_e2e,
+                    with_clocks=False)
+        line["batched64"] = {
+            "what": "config 4: 64 independent scenes in one batched call per step, against the same scenes "
+                    "one apic_contact_step call each (plain single-scene path)",
+            "config": workload_config("batched64", b_sc, b_dt), "value": b["value"], "unit": UNIT,
+            "ms_per_step": b["ms_per_step"], "kernel_variant": b["kernel_variant"], "e2e": b["e2e"],
+            "plain_single_scene": b["plain_single_scene"], "roofline": b["roofline"],
+            "gpu_launches": b["gpu_launches"], "momentum_check": b["momentum_check"]}
+        ctx.close()
+        ctx = None
+        line["served"] = served_measure(args, seconds=3.0, squeezed=False)
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc)
+    print(json.dumps(line), flush=True)
+    if ctx is not None:
+        ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def measure(args, apic, ctx, sc, dt, batched, dev, stream, flush, ws, with_e2e=True, with_clocks=True):
+    """Time K contact steps of one workload (device buffers, L2 flushed
+    before each step), then the per-pass roofline from an untimed profiling
+    run, the plain path for a batch, and the end-to-end host-buffer figure."""
+    import torch
+
     tdt = torch.float32 if dt == np.float32 else torch.float64
     N = sc[0].n_iter
     P = sum(s.n for s in sc)
@@ -340,9 +468,6 @@ def main():
         f = s.astype(dt)
         bs.append(apic.BatchScene(t(f.x, torch.float64), t(f.v, tdt), t(f.C, tdt), t(f.m, tdt), t(f.nrm, tdt),
                                   t(f.body, torch.int32), s.h, s.mu, n_bodies=s.n_bodies, mu_pair=s.mu_pair))
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
-    ctx = apic.Context(dev.index)
     FL = apic.APIC_DETERMINISTIC if args.deterministic else 0
 
     def step_one(b):
@@ -382,19 +507,22 @@ def main():
         torch.cuda.synchronize(dev)
         return sum(a.elapsed_time(b) for a, b in zip(starts, ends))
 
-    try:  # nvidia-smi wants the physical GPU: address it by UUID
-        clocks = Clocks("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
-    except Exception:
-        clocks = Clocks(dev.index)
+    clocks = None
+    if with_clocks:
+        try:  # nvidia-smi wants the physical GPU: address it by UUID
+            clocks = Clocks("GPU-" + str(torch.cuda.get_device_properties(dev).uuid))
+        except Exception:
+            clocks = Clocks(dev.index)
     ctx.set_profiling(False)  # resets the launch counter; passes replay as a graph
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
-    clocks.start()
+    if clocks:
+        clocks.start()
     t_ms = timed(step, args.steps)
     if ws > 1:
         torch.distributed.barrier()
-    ck = clocks.stop()
+    ck = clocks.stop() if clocks else None
     launches = ctx.profile()["kernel_launches"]
     # per-pass kernel times for the roofline: a separate, untimed run with
     # an event pair around every pass (launched one by one)
@@ -405,15 +533,19 @@ def main():
     t_ms = max_over_ranks(t_ms, ws, dev)
     units = P * (N + 1) * args.steps * ws
     value = units / (t_ms / 1e3)
+    out = {"value": value, "ms_per_step": t_ms / args.steps}
 
     # the same scenes one call each (the plain single-scene path)
-    plain = None
     if batched:
         for b in bs:
             step_one(b)
         torch.cuda.synchronize(dev)
-        t_plain = timed(lambda: [step_one(b) for b in bs], max(2, args.steps // 4))
-        plain = P * (N + 1) * max(2, args.steps // 4) / (t_plain / 1e3)
+        k = max(2, args.steps // 4)
+        t_plain = timed(lambda: [step_one(b) for b in bs], k)
+        plain = P * (N + 1) * k / (t_plain / 1e3)
+        out["plain_single_scene"] = {"value": plain, "unit": UNIT, "ms_per_step": t_plain / k,
+                                     "what": "the same scenes, one apic_contact_step call each",
+                                     "batched_over_plain": value / plain}
 
     # roofline of the fused transfer kernel (timed live with events on the launch stream)
     G = prof["active_nodes"]
@@ -422,7 +554,8 @@ def main():
     peak, peak_kind = measured_peak_hbm()
     achieved = alg / (iter_avg_ms / 1e3) / 1e9
     traffic = wavefronts = None
-    tfile = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
+    wl = args.workload if not batched or args.workload == "batched64" else "batched64"
+    tfile = os.path.join(ROOT, "profiles", f"traffic_{wl}.json")
     if os.path.exists(tfile):
         try:
             tj = json.load(open(tfile))
@@ -434,7 +567,7 @@ def main():
 
     # end to end: the same step through the C ABI from pinned host buffers
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         def pin(a, d):
             return torch.as_tensor(np.ascontiguousarray(a), dtype=d).pin_memory().numpy()
 
@@ -470,17 +603,9 @@ def main():
                "h2d_bytes_per_step": int(P * (24 + 4 + isz * (3 + 9 + 1 + 3))),
                "d2h_bytes_per_step": int(P * isz * (3 + 9))}
 
-    if rank != 0:
-        if ws > 1:
-            torch.distributed.destroy_process_group()
-        return 0
     sP = float(sum(np.sum(s.m * np.linalg.norm(s.v, axis=1)) for s in sc))
     drift = float(sum(np.abs(x["P_out"] - x["P_in"]).max() for x in st)) / sP
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if dt == np.float64 else "f32", "data": "synthetic",
-        "config": workload_config(args.workload, sc, dt),
+    out.update({
         "e2e": e2e,
         "gpu_launches": int(launches),
         "kernel_variant": apic.variants()[variant],
@@ -506,7 +631,7 @@ def main():
             "achieved": wavefronts / (iter_avg_ms / 1e3) / 1e9, "peak": SMEM_PEAK_GWAVEFRONTS,
             "unit": "G wavefronts/s", "frac": wavefronts / (iter_avg_ms / 1e3) / 1e9 / SMEM_PEAK_GWAVEFRONTS,
             "wavefronts_per_launch": wavefronts, "peak_from": "152 SMs x 1 wavefront/clock x 2.07 GHz",
-            "wavefronts_from": f"profiles/traffic_{args.workload}.json (ncu)"},
+            "wavefronts_from": f"profiles/traffic_{wl}.json (ncu)"},
         "step_breakdown_ms": step_breakdown(prof),
         "momentum_check": {"P_drift_rel": drift,
                            "multibody_nodes": int(sum(x["multibody_nodes"] for x in st)),
@@ -516,36 +641,42 @@ def main():
                            "E_change_rel": float(sum(x["E_out"] - x["E_in"] for x in st)
                                                  / max(sum(x["E_in"] for x in st), 1e-300))},
         "clocks": ck,
-    }
-    if not args.no_extras:
-        line["node_normals"] = bench_node_normals(apic, ctx, dev, stream, flush)
-        line["augury_dynamics"] = bench_augury(apic, ctx, dev, stream)
-    if plain is not None:
-        line["plain_single_scene"] = {"value": plain, "unit": UNIT,
-                                      "what": "the same scenes, one apic_contact_step call each",
-                                      "batched_over_plain": value / plain}
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sc)
-    print(json.dumps(line), flush=True)
-    if ws > 1:
-        torch.distributed.destroy_process_group()
-    return 0
+    })
+    return out
 
 
 def run_served(args):
-    """Serving benchmark: capacity in a closed loop, then open-loop Poisson
-    step requests at fractions of that capacity."""
-    import threading
-
-    import torch
-
-    from paper_2108_02259_gb300 import apic, build, scenes
-
+    """The served workload as the bench line itself (value: throughput at
+    offered load 0.8)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0  # one server on one GPU: under torchrun the other ranks have nothing to do
+    sv = served_measure(args, seconds=args.served_seconds, squeezed=True)
+    mid = sv["loads"]["0.8"]
+    line = {
+        "metric": METRIC, "value": mid["throughput"], "unit": UNIT, "n_gpus": 1, "steps": mid["requests"],
+        "warmup": args.warmup, "ms_per_step": mid["mean_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": sv.pop("config"),
+        "served": sv,
+        "e2e": {"value": mid["throughput"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "state is resident on the device; latency is submit to completion"},
+        "roofline": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def served_measure(args, seconds=6.0, squeezed=True):
+    """Serving: 256 resident simulations behind the serving loop.  Capacity
+    in a closed loop, then open-loop Poisson step requests at 0.5 / 0.8 /
+    0.95 of that capacity (`seconds` each), throughput and p50/p99 request
+    latency; optionally the same simulations against a budget of about half
+    their resident state, to exercise admission."""
+    import torch  # noqa: F401
+
+    from paper_2108_02259_gb300 import apic, build, scenes
+
     build.build()
-    dev = torch.device("cuda:0")
     sims = scenes.served_simulations()
     srv = apic.Server(0, hbm_budget_bytes=80 << 30, n_workers=2, max_batch_scenes=64)
     srv.set_policy(args.variant, not args.no_graphs)
@@ -578,10 +709,10 @@ def run_served(args):
     # light load (new size classes to tune, new buffer sizes) before timing
     for rho in ("warm", 0.5, 0.8, 0.95):
         lam = (0.5 if rho == "warm" else rho) * capacity / units.sum()  # requests per second per simulation
-        T = 1.0 if rho == "warm" else args.served_seconds
+        T = 1.0 if rho == "warm" else seconds
         events = []
         for i in range(len(sims)):
-            t, k = 0.0, 0
+            t = 0.0
             while True:
                 t += rng.exponential(1.0 / lam)
                 if t >= T:
@@ -611,53 +742,50 @@ def run_served(args):
     for h in hs:
         h.close()
     srv.close()
+    resident = res["resident_bytes"]
 
-    # the same simulations against a budget of half their resident state
-    # (2 GiB of 4.0 GB): admission refuses what does not fit; the admitted
-    # ones run a closed-loop round
-    squeezed = {"budget_bytes": 2 << 30}
-    with apic.Server(0, hbm_budget_bytes=2 << 30, n_workers=2, max_batch_scenes=64) as sq:
-        sq.set_policy(args.variant, not args.no_graphs)
-        adm, refused = [], 0
-        for s, dt_i in zip(sims, dts):
-            f = s.astype(np.float32)
-            try:
-                adm.append((sq.open_sim(f.x, f.v, f.C, f.m, f.nrm, f.body, s.h, s.mu, s.n_iter,
-                                        n_bodies=s.n_bodies), dt_i, s.n * (s.n_iter + 1)))
-            except apic.ApicError as e:
-                if e.code != apic.APIC_ERR_ADMISSION:
-                    raise
-                refused += 1
-        t0 = time.perf_counter()
-        ts = [h.submit(dt_i) for h, dt_i, _ in adm]
-        for t in ts:
-            sq.wait(t, 600.0)
-        wall = time.perf_counter() - t0
-        st = sq.stats()
-        squeezed.update({"admitted": len(adm), "refused": refused,
-                         "admitted_particles": int(sum(u for _, _, u in adm) / (sims[0].n_iter + 1)),
-                         "resident_bytes": st["resident_bytes"], "round_particle_iters_per_s":
-                         sum(u for _, _, u in adm) / wall, "failed": st["failed"]})
-        for h, _, _ in adm:
-            h.close()
-    mid = loads["0.8"]
-    line = {
-        "metric": METRIC, "value": mid["throughput"], "unit": UNIT, "n_gpus": 1, "steps": mid["requests"],
-        "warmup": args.warmup, "ms_per_step": mid["mean_ms"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"served: {len(sims)} resident simulations, {P} FE nodes in total (2k-1M per "
-                               f"simulation, 2-8 bodies, mu in [0, 0.5], N = {sims[0].n_iter}), Poisson step "
-                               "requests, each step advects x by 0.1 h / max|v|, 80 GiB budget, 2 workers",
-                   "launch_policy": {"variant": args.variant, "graphs": not args.no_graphs},
-                   "particles": P, "simulations": len(sims), "l2": "working set far above L2 (43.8M nodes)"},
-        "served": {"capacity_closed_loop": capacity, "capacity_mean_batch_scenes": cap_stats["mean_batch_scenes"],
-                   "loads": loads, "resident_bytes": res["resident_bytes"], "budget_squeezed": squeezed},
-        "e2e": {"value": mid["throughput"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
-                "note": "state is resident on the device; latency is submit to completion"},
-        "roofline": None,
-    }
-    print(json.dumps(line), flush=True)
-    return 0
+    out = {"config": {"workload": f"served: {len(sims)} resident simulations, {P} FE nodes in total (2k-1M per "
+                                  f"simulation, each size drawn on its own, 2-8 bodies, mu in [0, 0.5], "
+                                  f"N = {sims[0].n_iter}), Poisson step requests, each step advects x by "
+                                  "0.1 h / max|v|, 80 GiB budget, 2 workers",
+                      "launch_policy": {"variant": args.variant, "graphs": not args.no_graphs},
+                      "particles": P, "simulations": len(sims), "seconds_per_load": seconds,
+                      "l2": f"working set far above L2 ({P / 1e6:.1f}M nodes)"},
+           "capacity_closed_loop": capacity, "capacity_mean_batch_scenes": cap_stats["mean_batch_scenes"],
+           "loads": loads, "resident_bytes": resident,
+           "p50_ms_at_0.8": loads["0.8"]["p50_ms"], "p99_ms_at_0.8": loads["0.8"]["p99_ms"]}
+    if squeezed:
+        # the same simulations against a budget of about half their resident
+        # state: admission refuses what does not fit; the admitted ones run a
+        # closed-loop round
+        budget = int(resident // 2)
+        sq_out = {"budget_bytes": budget}
+        with apic.Server(0, hbm_budget_bytes=budget, n_workers=2, max_batch_scenes=64) as sq:
+            sq.set_policy(args.variant, not args.no_graphs)
+            adm, refused = [], 0
+            for s, dt_i in zip(sims, dts):
+                f = s.astype(np.float32)
+                try:
+                    adm.append((sq.open_sim(f.x, f.v, f.C, f.m, f.nrm, f.body, s.h, s.mu, s.n_iter,
+                                            n_bodies=s.n_bodies), dt_i, s.n * (s.n_iter + 1)))
+                except apic.ApicError as e:
+                    if e.code != apic.APIC_ERR_ADMISSION:
+                        raise
+                    refused += 1
+            t0 = time.perf_counter()
+            ts = [h.submit(dt_i) for h, dt_i, _ in adm]
+            for t in ts:
+                sq.wait(t, 600.0)
+            wall = time.perf_counter() - t0
+            st = sq.stats()
+            sq_out.update({"admitted": len(adm), "refused": refused,
+                           "admitted_particles": int(sum(u for _, _, u in adm) / (sims[0].n_iter + 1)),
+                           "resident_bytes": st["resident_bytes"], "round_particle_iters_per_s":
+                           sum(u for _, _, u in adm) / wall, "failed": st["failed"]})
+            for h, _, _ in adm:
+                h.close()
+        out["budget_squeezed"] = sq_out
+    return out
 
 
 def bench_node_normals(apic, ctx, dev, stream, flush, reps=10):

@@ -18,6 +18,7 @@ surface at the node.  Interior nodes get 0.
 """
 from __future__ import annotations
 
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -322,26 +323,29 @@ def batch_of_scenes(n_scenes: int = 64, seed: int = SEED_BASE + 4, min_nodes: fl
     return out
 
 
-def served_simulations(n_sims: int = 256, n_shapes: int = 32, seed: int = SEED_BASE + 5, min_nodes: float = 2e3,
-                       max_nodes: float = 1e6, bodies=(2, 8), n_iter: int = 8):
-    """Simulations for the serving benchmark: `n_shapes` distinct scenes with
-    ln P ~ U(ln min, ln max) nodes and U{bodies} bodies, h in {1/128, 1/256,
-    1/512} by size, each instantiated n_sims / n_shapes times at a shifted
-    position with its own friction mu ~ U[0, 0.5]."""
-    rng = np.random.default_rng(seed)
-    shapes = []
-    for i in range(n_shapes):
+def served_simulations(n_sims: int = 256, seed: int = SEED_BASE + 5, min_nodes: float = 2e3,
+                       max_nodes: float = 1e6, bodies=(2, 8), n_iter: int = 8, threads: int | None = None):
+    """Simulations for the serving benchmark, each drawn on its own: ln P ~
+    U(ln min, ln max) nodes, U{bodies} bodies, h in {1/128, 1/256, 1/512} by
+    size (so that bodies span about 20-40 cells), friction mu ~ U[0, 0.5],
+    and a shift of the whole scene by whole cells.  Simulation k draws from
+    the generator seeded with (seed, k), so the set does not depend on how
+    many threads build it (numpy releases the GIL in its array kernels)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(k):
+        rng = np.random.default_rng([seed, k])
         P = int(np.exp(rng.uniform(np.log(min_nodes), np.log(max_nodes))))
         nb = int(rng.integers(bodies[0], bodies[1] + 1))
         h = 1.0 / 128 if P < 2e4 else 1.0 / 256 if P < 2e5 else 1.0 / 512
-        shapes.append(multi_body_scene(rng, P, nb, h, 0.3, n_iter, name=f"shape{i}"))
-    sims = []
-    for k in range(n_sims):
-        s = shapes[k % n_shapes]
+        s = multi_body_scene(rng, P, nb, h, 0.3, n_iter, name=f"sim{k}_{P}_{nb}b")
         shift = rng.integers(-50, 50, 3) * s.h
-        sims.append(Scene(s.x + shift, s.v, s.C, s.m, s.nrm, s.body, s.n_bodies, s.h, float(rng.uniform(0, 0.5)),
-                          n_iter, None, f"sim{k}_{s.name}"))
-    return sims
+        return Scene(s.x + shift, s.v, s.C, s.m, s.nrm, s.body, s.n_bodies, s.h, float(rng.uniform(0, 0.5)),
+                     n_iter, None, s.name)
+
+    workers = threads if threads is not None else min(16, os.cpu_count() or 1)
+    with ThreadPoolExecutor(max(1, workers)) as ex:
+        return list(ex.map(one, range(n_sims)))
 
 
 # ----------------------------------------------------------- surface meshes
