@@ -34,6 +34,7 @@ constexpr int kErrPos = 4;
 constexpr int kErrBox = 8;  // a particle lies outside a page-table box reused from an earlier step
 constexpr int kErrFinite = 16;  // v, C or a normal not finite (checked with APIC_CHECK)
 constexpr int kErrNormal = 32;  // a normal neither 0 nor of unit length (checked with APIC_CHECK)
+constexpr int kErrSort = 64;    // a bounded wait of the radix sort gave up (internal)
 
 // Device-side scalars the host reads back while sizing the grid.
 struct DevScalars {
@@ -236,17 +237,19 @@ cudaError_t launch_aug_energy(int64_t n, const double* x, const T* v, const T* m
                               cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) pairs over the low end_bit bits of
-// the keys (sort.cu): radix_passes(end_bit) passes of at most 8 bits, each
+// the keys (sort.cu): radix_passes(end_bit) passes of at most 9 bits, each
 // from (keys, vals) to (keys_alt, vals_alt) and back, so the result is in
 // (keys_alt, vals_alt) when the pass count is odd and in (keys, vals) when it
 // is even.  vals_iota: the input values are the indices 0..n-1 (not read).
-// temp holds radix_temp_ints<K>(n, end_bit) ints.
+// temp holds radix_temp_ints<K>(n, end_bit) ints.  A bounded device-side
+// wait that gives up sets kErrSort in *err (the sorted output is then not
+// valid).
 int radix_passes(int end_bit);
 template <class K>
 int64_t radix_temp_ints(int64_t n, int end_bit);
 template <class K>
 cudaError_t launch_radix_sort(K* keys, int* vals, K* keys_alt, int* vals_alt, int64_t n, int end_bit,
-                              bool vals_iota, int* temp, cudaStream_t s);
+                              bool vals_iota, int* temp, int* err, cudaStream_t s);
 // Exclusive sum of n ints (in == out allowed); temp holds scan_temp_ints(n)
 // ints.
 int64_t scan_temp_ints(int64_t n);

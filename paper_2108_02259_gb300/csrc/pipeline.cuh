@@ -182,7 +182,7 @@ apic_status sort_keys(Env& env, int64_t n, const SceneDev* sc, int ns, const int
   int* v0 = odd ? b.va : b.perm;
   int* v1 = odd ? b.perm : b.va;
   P_LAUNCH(env, launch_keys<K>(n, sc, ns, cellb, max_bodies, k0, v0, err, s));
-  P_CUDA(launch_radix_sort<K>(k0, v0, k1, v1, n, b.end_bit, true, b.tmp, s));
+  P_CUDA(launch_radix_sort<K>(k0, v0, k1, v1, n, b.end_bit, true, b.tmp, err, s));
   env.sorted();
   return APIC_OK;
 }
@@ -492,6 +492,10 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   const int4* item_info = sb.item_info;
   const int* page = sb.page;
   const int* blist = sb.blist;
+  if (hs->err & kErrSort) {
+    env.forget_box();
+    return pfail(APIC_ERR_TIMEOUT, "the radix sort's bounded device-side wait gave up (no result was written)");
+  }
   if (hs->err) {
     const int e = hs->err;
     env.forget_box();

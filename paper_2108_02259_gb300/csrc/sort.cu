@@ -4,26 +4,34 @@
 // scene's page-table box, body, cell in block), so that every work item is
 // a run of particles of one body in one grid block, cell by cell.  It is a
 // stable least-significant-digit radix sort over the key's significant bits
-// (end_bit), with digits of at most 8 bits, three launches per digit:
+// (end_bit), in passes of at most 9-bit digits:
 //
-//   k_radix_hist     per tile of keys, the count of every digit value
-//                    (digit-major table hist[d * n_tiles + tile]);
-//   scan             exclusive sum of that table: the output position of the
-//                    first key of digit d in tile t (all keys of smaller
-//                    digits, then those of digit d in earlier tiles);
-//   k_radix_scatter  each key's rank among the keys of its digit in its tile
-//                    (warp by warp, in index order, so the sort is stable),
-//                    the tile staged in shared memory in sorted order, then
-//                    written out with runs of equal digits contiguous.
+//   k_radix_counts  one read of all keys: for every pass, how many keys have
+//                   each digit value (the digit's first output position is
+//                   the sum over smaller digits);
+//   k_onesweep      one launch per pass.  Tiles take their index in launch
+//                   order from a counter.  A tile ranks its keys among the
+//                   keys of equal digit, warp by warp in index order (so the
+//                   sort is stable), publishes its digit counts, and finds
+//                   how many keys of each digit the tiles before it hold by
+//                   looking back through their published counts ("decoupled
+//                   look-back": a tile that has its own full prefix publishes
+//                   it, so a look-back stops at the first such tile).  It
+//                   then stages the tile in sorted order in shared memory and
+//                   writes it out, runs of equal digits contiguous.
+//
+// A tile waits only for tiles that took their index before it (so they are
+// running or done).  Each wait is bounded: a tile that gives up sets
+// kErrSort in the call's error word, writes nothing, and still publishes a
+// prefix so that no later tile waits on it; the host then fails the call.
 //
 // Values are the particles' original indices, so the sorted permutation is
 // unique for given keys (ties keep index order).  The first pass takes its
 // values as the index itself instead of reading them.
 //
-// The exclusive scan (run counts, block flags, the digit tables) is a
-// reduce-then-scan in three launches: tile sums, one CTA scanning the tile
-// sums, then every tile scanned from its offset.  No kernel waits on another
-// CTA; every launch depends only on the launches before it in the stream.
+// The exclusive scan (run counts, block flags) is a reduce-then-scan in
+// three launches: tile sums, one CTA scanning the tile sums, then every tile
+// scanned from its offset.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,19 +42,27 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kRadixMaxBits = 8;
+constexpr int kRadixMaxBits = 9;
 constexpr int kRadixBins = 1 << kRadixMaxBits;
-static_assert(kSortThreads == kRadixBins, "phase B of the scatter gives each thread one digit");
+constexpr int kBinsPerThread = kRadixBins / kSortThreads;
+static_assert(kRadixBins % kSortThreads == 0, "each thread owns whole digits");
 
-// Keys per thread and per tile: 32-bit keys 16 per thread (4096 a tile),
+// Keys per thread and per tile: 32-bit keys 12 per thread (3072 a tile),
 // 64-bit keys 8 (2048), so that the tile's staging stays in static shared
 // memory (48 KB).
 template <class K>
 struct SortTile {
-  static constexpr int kItems = sizeof(K) == 4 ? 16 : 8;
+  static constexpr int kItems = sizeof(K) == 4 ? 12 : 8;
   static constexpr int kTile = kSortThreads * kItems;
   static constexpr int kWarpTile = 32 * kItems;
 };
+
+// Look-back status words: two flag bits over a 30-bit count (a scene holds
+// at most 2^29 particles).
+constexpr unsigned kStatAggregate = 1u << 30;  // this tile's own count
+constexpr unsigned kStatPrefix = 2u << 30;     // count of this and every earlier tile
+constexpr unsigned kStatValue = (1u << 30) - 1u;
+constexpr int kLookbackSpins = 1 << 22;  // per status word, then the tile gives up
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
@@ -54,19 +70,24 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
+// A status word carries its flag and its count together, and no other
+// memory is read on the strength of it, so relaxed device-scope accesses are
+// enough (no fences).
+__device__ __forceinline__ void st_status(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_status(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Lanes of the warp whose digit equals this lane's, among the valid lanes
-// (0 for an invalid lane): one ballot per digit bit.  Every lane of the warp
-// must call it (bits is the same on all lanes).
-__device__ __forceinline__ unsigned digit_peers(unsigned d, int bits, bool valid) {
-  unsigned peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-  for (int b = 0; b < kRadixMaxBits; ++b) {
-    if (b < bits) {
-      const unsigned set = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-      peers &= ((d >> b) & 1u) ? set : ~set;
-    }
-  }
-  return valid ? peers : 0u;
+// (0 for an invalid lane).  Every lane of the warp must call it.
+__device__ __forceinline__ unsigned digit_peers(unsigned d, bool valid) {
+  const unsigned v = __ballot_sync(0xffffffffu, valid);
+  const unsigned m = __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu);
+  return valid ? (m & v) : 0u;
 }
 
 template <class K>
@@ -74,28 +95,53 @@ __device__ __forceinline__ unsigned digit_of(K k, int shift, unsigned mask) {
   return (unsigned)(k >> shift) & mask;
 }
 
+// Digit counts of every pass: counts[p * kRadixBins + d].  Pass p covers
+// bits [p per, p per + bits_p) with bits_p = min(per, end_bit - p per).
+// Each thread reads kCountRun consecutive keys at a time and keeps, per
+// pass, the current digit and its run length, adding a run to the CTA's
+// shared histogram when the digit changes (the keys arrive in the caller's
+// order, which is spatially coherent, so runs are long in the high digits).
+constexpr int kMaxPasses = 8;  // 64-bit keys at 9 bits a pass
+constexpr int kCountRun = 16;
 template <class K>
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const K* __restrict__ keys, int64_t n, int shift,
-                                                              int bits, int n_tiles, int* __restrict__ hist) {
-  using TT = SortTile<K>;
-  __shared__ int cnt[kRadixBins];
-  const unsigned mask = (1u << bits) - 1u;
-  const int tile = blockIdx.x;
-  for (int d = threadIdx.x; d < kRadixBins; d += kSortThreads) cnt[d] = 0;
+__global__ void __launch_bounds__(kSortThreads) k_radix_counts(const K* __restrict__ keys, int64_t n, int end_bit,
+                                                                int per, int passes, int* __restrict__ counts) {
+  __shared__ int cnt[kMaxPasses][kRadixBins];
+  for (int i = threadIdx.x; i < passes * kRadixBins; i += kSortThreads) (&cnt[0][0])[i] = 0;
   __syncthreads();
-  const int64_t base = (int64_t)tile * TT::kTile;
-  const int lane = threadIdx.x & 31;
-#pragma unroll 4
-  for (int i = 0; i < TT::kItems; ++i) {
-    const int64_t idx = base + (int64_t)i * kSortThreads + threadIdx.x;
-    const bool valid = idx < n;
-    const unsigned d = valid ? digit_of(keys[idx], shift, mask) : 0u;
-    // one shared atomic per distinct digit of the warp
-    const unsigned peers = digit_peers(d, bits, valid);
-    if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[d], __popc(peers));
+  const int64_t stride = (int64_t)gridDim.x * kSortThreads * kCountRun;
+  for (int64_t c0 = ((int64_t)blockIdx.x * kSortThreads + threadIdx.x) * kCountRun; c0 < n; c0 += stride) {
+    const int64_t c1 = c0 + kCountRun < n ? c0 + kCountRun : n;
+    unsigned prev[kMaxPasses];
+    int run[kMaxPasses];
+#pragma unroll
+    for (int p = 0; p < kMaxPasses; ++p) {
+      prev[p] = 0u;
+      run[p] = 0;
+    }
+    for (int64_t i = c0; i < c1; ++i) {
+      const K k = keys[i];
+#pragma unroll
+      for (int p = 0; p < kMaxPasses; ++p) {
+        if (p >= passes) break;
+        const int shift = p * per;
+        const int bits = end_bit - shift < per ? end_bit - shift : per;
+        const unsigned d = digit_of(k, shift, (1u << bits) - 1u);
+        if (run[p] > 0 && d != prev[p]) {
+          atomicAdd(&cnt[p][prev[p]], run[p]);
+          run[p] = 0;
+        }
+        prev[p] = d;
+        ++run[p];
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < kMaxPasses; ++p)
+      if (p < passes && run[p] > 0) atomicAdd(&cnt[p][prev[p]], run[p]);
   }
   __syncthreads();
-  for (int d = threadIdx.x; d <= (int)mask; d += kSortThreads) hist[(int64_t)d * n_tiles + tile] = cnt[d];
+  for (int i = threadIdx.x; i < passes * kRadixBins; i += kSortThreads)
+    if ((&cnt[0][0])[i]) atomicAdd(&counts[i], (&cnt[0][0])[i]);
 }
 
 // Exclusive scan of one value per thread over the CTA (kSortThreads); also
@@ -127,38 +173,50 @@ __device__ __forceinline__ int cta_exclusive_scan(int x, int* warp_tot, int* tot
   return r;
 }
 
+// One pass: keys (kin, vin) -> (kout, vout) by the digit [shift, shift +
+// bits).  counts: this pass's digit counts over all keys; status: n_tiles *
+// kRadixBins words and tile_ctr, zero on entry; vin == nullptr: the values
+// are the indices.
 template <class K>
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const K* __restrict__ kin, const int* __restrict__ vin,
-                                                                 K* __restrict__ kout, int* __restrict__ vout,
-                                                                 int64_t n, int shift, int bits, int n_tiles,
-                                                                 const int* __restrict__ hist) {
+__global__ void __launch_bounds__(kSortThreads, 4)
+    k_onesweep(const K* __restrict__ kin, const int* __restrict__ vin, K* __restrict__ kout, int* __restrict__ vout,
+               int64_t n, int shift, int bits, const int* __restrict__ counts, unsigned* status, int* tile_ctr,
+               int* err) {
   using TT = SortTile<K>;
-  __shared__ int wcnt[kSortWarps][kRadixBins];  // per warp: keys of each digit so far, then offsets
-  __shared__ int tstart[kRadixBins];            // first tile position of each digit
-  __shared__ int gbase[kRadixBins];             // output position of the tile's first key of each digit
-  __shared__ int warp_tot[kSortWarps + 1];
+  __shared__ int wcnt[kSortWarps][kRadixBins];  // per warp: keys of each digit so far, then warp offsets
+  __shared__ int tstart[kRadixBins];            // the tile's count of each digit, then its first tile position
+  __shared__ int gbase[kRadixBins];             // earlier tiles' keys of each digit, then its first output position
+  __shared__ int scan_a[kSortWarps + 1], scan_b[kSortWarps + 1];
+  __shared__ int s_tile, s_bad;
   __shared__ K skey[TT::kTile];
   __shared__ int sval[TT::kTile];
   const unsigned mask = (1u << bits) - 1u;
-  const int tile = blockIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    s_tile = atomicAdd(tile_ctr, 1);  // tiles in the order their CTAs start
+    s_bad = 0;
+  }
   for (int i = threadIdx.x; i < kSortWarps * kRadixBins; i += kSortThreads) (&wcnt[0][0])[i] = 0;
   __syncthreads();
+  const int tile = s_tile;
   const int64_t base = (int64_t)tile * TT::kTile;
   const int tile_n = (int)(n - base < TT::kTile ? n - base : TT::kTile);
+
   // Phase A: warp w ranks the keys [w kWarpTile, (w + 1) kWarpTile) of the
   // tile, 32 at a time in index order.
   K key[TT::kItems];
-  int val[TT::kItems];
   int rank[TT::kItems];
 #pragma unroll
   for (int r = 0; r < TT::kItems; ++r) {
     const int t = w * TT::kWarpTile + r * 32 + lane;
+    key[r] = t < tile_n ? kin[base + t] : K(0);
+  }
+#pragma unroll
+  for (int r = 0; r < TT::kItems; ++r) {
+    const int t = w * TT::kWarpTile + r * 32 + lane;
     const bool valid = t < tile_n;
-    key[r] = valid ? kin[base + t] : K(0);
-    val[r] = valid ? (vin ? vin[base + t] : (int)(base + t)) : 0;
     const unsigned d = digit_of(key[r], shift, mask);
-    const unsigned peers = digit_peers(d, bits, valid);
+    const unsigned peers = digit_peers(d, valid);
     const int prior = valid ? wcnt[w][d] : 0;
     rank[r] = prior + __popc(peers & lanemask_lt());
     __syncwarp();
@@ -166,11 +224,14 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const K* __restr
     __syncwarp();
   }
   __syncthreads();
-  // Phase B: per digit, exclusive offsets of the warps, the tile's digit
-  // runs (exclusive scan over digits) and the output base of each run.
-  int dtot = 0;
-  {
-    const int d = threadIdx.x;  // kSortThreads == kRadixBins
+
+  // Phase B: for each digit (thread t owns t, t + kSortThreads, ...), the
+  // warps' exclusive offsets and the tile's count; publish the count, look
+  // back for the earlier tiles' total, publish this tile's prefix.
+  int dtot[kBinsPerThread];
+#pragma unroll
+  for (int j = 0; j < kBinsPerThread; ++j) {
+    const int d = threadIdx.x + j * kSortThreads;
     int run = 0;
 #pragma unroll
     for (int q = 0; q < kSortWarps; ++q) {
@@ -178,12 +239,104 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const K* __restr
       wcnt[q][d] = run;
       run += c;
     }
-    dtot = run;
-    gbase[d] = d <= (int)mask ? hist[(int64_t)d * n_tiles + tile] : 0;
+    dtot[j] = run;
+    tstart[d] = run;
+    if (d <= (int)mask)
+      st_status(status + (int64_t)tile * kRadixBins + d, (tile == 0 ? kStatPrefix : kStatAggregate) | (unsigned)run);
   }
-  tstart[threadIdx.x] = cta_exclusive_scan(dtot, warp_tot, nullptr);
+  // Look-back over a window of kWindow earlier tiles at a time, for all of
+  // the thread's digits together: the status words of the window load at
+  // once, then each digit folds them from the nearest tile back to the first
+  // one that carries a full prefix (waiting, bounded, on any that has not
+  // published yet).
+  constexpr int kWindow = 8;
+  {
+    unsigned excl[kBinsPerThread];
+    bool live[kBinsPerThread];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < kBinsPerThread; ++j) {
+      excl[j] = 0u;
+      live[j] = tile > 0 && (int)(threadIdx.x + j * kSortThreads) <= (int)mask;
+    }
+    for (int t0 = tile - 1; t0 >= 0 && ok; t0 -= kWindow) {
+      bool any = false;
+#pragma unroll
+      for (int j = 0; j < kBinsPerThread; ++j) any |= live[j];
+      if (!any) break;
+      unsigned v[kBinsPerThread][kWindow];
+#pragma unroll
+      for (int j = 0; j < kBinsPerThread; ++j)
+#pragma unroll
+        for (int q = 0; q < kWindow; ++q)
+          v[j][q] = live[j] && t0 - q >= 0
+                        ? ld_status(status + (int64_t)(t0 - q) * kRadixBins + threadIdx.x + j * kSortThreads)
+                        : kStatPrefix;
+#pragma unroll
+      for (int j = 0; j < kBinsPerThread; ++j) {
+#pragma unroll
+        for (int q = 0; q < kWindow; ++q) {
+          if (!live[j] || !ok) continue;
+          int spins = 0;
+          while ((v[j][q] & ~kStatValue) == 0u) {
+            if (++spins > kLookbackSpins) {
+              ok = false;  // give up: the tile writes nothing and the call fails
+              break;
+            }
+            __nanosleep(32);
+            v[j][q] = ld_status(status + (int64_t)(t0 - q) * kRadixBins + threadIdx.x + j * kSortThreads);
+          }
+          if (!ok) break;
+          excl[j] += v[j][q] & kStatValue;
+          if (v[j][q] & kStatPrefix) live[j] = false;
+        }
+      }
+    }
+    if (!ok) s_bad = 1;
+#pragma unroll
+    for (int j = 0; j < kBinsPerThread; ++j) {
+      const int d = threadIdx.x + j * kSortThreads;
+      // published even after giving up, so that no later tile waits here
+      if (tile > 0 && d <= (int)mask)
+        st_status(status + (int64_t)tile * kRadixBins + d, kStatPrefix | ((excl[j] + (unsigned)dtot[j]) & kStatValue));
+      gbase[d] = (int)excl[j];
+    }
+  }
   __syncthreads();
-  // Phase C: stage the tile in sorted order.
+
+  // Each digit's first output position (keys of smaller digits in the whole
+  // input, then earlier tiles' keys of this digit) and first tile position
+  // (exclusive scans over the digits; thread t owns kBinsPerThread
+  // consecutive digits here).
+  {
+    int c[kBinsPerThread], tc[kBinsPerThread], cs = 0, ts = 0;
+#pragma unroll
+    for (int j = 0; j < kBinsPerThread; ++j) {
+      const int d = threadIdx.x * kBinsPerThread + j;
+      c[j] = d <= (int)mask ? counts[d] : 0;
+      tc[j] = tstart[d];
+      cs += c[j];
+      ts += tc[j];
+    }
+    int g = cta_exclusive_scan(cs, scan_a, nullptr);
+    int h = cta_exclusive_scan(ts, scan_b, nullptr);
+#pragma unroll
+    for (int j = 0; j < kBinsPerThread; ++j) {
+      const int d = threadIdx.x * kBinsPerThread + j;
+      gbase[d] += g;
+      tstart[d] = h;
+      g += c[j];
+      h += tc[j];
+    }
+  }
+  __syncthreads();
+  if (s_bad) {
+    if (threadIdx.x == 0) atomicOr(err, kErrSort);
+    return;  // nothing written: the host fails the call
+  }
+
+  // Phase C: stage the tile in sorted order (values read here, so that they
+  // hold no registers across the look-back).
 #pragma unroll
   for (int r = 0; r < TT::kItems; ++r) {
     const int t = w * TT::kWarpTile + r * 32 + lane;
@@ -191,7 +344,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const K* __restr
       const unsigned d = digit_of(key[r], shift, mask);
       const int pos = tstart[d] + wcnt[w][d] + rank[r];
       skey[pos] = key[r];
-      sval[pos] = val[r];
+      sval[pos] = vin ? vin[base + t] : (int)(base + t);
     }
   }
   __syncthreads();
@@ -291,34 +444,45 @@ cudaError_t launch_exclusive_scan(const int* in, int* out, int64_t n, int* temp,
 
 int radix_passes(int end_bit) { return end_bit <= 0 ? 0 : (end_bit + kRadixMaxBits - 1) / kRadixMaxBits; }
 
+// temp layout (ints): digit counts [passes][kRadixBins], tile counters
+// [32], look-back status [passes][tiles][kRadixBins]; all zeroed per sort.
 template <class K>
 int64_t radix_temp_ints(int64_t n, int end_bit) {
   const int64_t tiles = cdiv(n > 0 ? n : 1, SortTile<K>::kTile);
-  const int64_t hist = tiles * kRadixBins;
-  return hist + scan_temp_ints(hist);
+  const int passes = radix_passes(end_bit) > 0 ? radix_passes(end_bit) : 1;
+  return (int64_t)passes * kRadixBins + 32 + (int64_t)passes * tiles * kRadixBins;
 }
 
 template <class K>
 cudaError_t launch_radix_sort(K* keys, int* vals, K* keys_alt, int* vals_alt, int64_t n, int end_bit, bool vals_iota,
-                              int* temp, cudaStream_t s) {
+                              int* temp, int* err, cudaStream_t s) {
   const int passes = radix_passes(end_bit);
   if (n <= 0 || passes == 0) return cudaSuccess;
   const int64_t tiles = cdiv(n, SortTile<K>::kTile);
-  if (tiles * kRadixBins > INT32_MAX) return cudaErrorInvalidValue;
-  int* hist = temp;
-  int* scan_tmp = temp + tiles * kRadixBins;
-  // spread the bits evenly over the passes (each <= 8)
+  if (tiles > INT32_MAX / kRadixBins || n > (int64_t)kStatValue || passes > kMaxPasses) return cudaErrorInvalidValue;
+  int* counts = temp;
+  int* tile_ctr = counts + passes * kRadixBins;
+  unsigned* status = reinterpret_cast<unsigned*>(tile_ctr + 32);
+  cudaError_t e = cudaMemsetAsync(temp, 0, (size_t)radix_temp_ints<K>(n, end_bit) * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  // the digits spread evenly over the passes (each at most kRadixMaxBits)
   const int per = (end_bit + passes - 1) / passes;
+  // up to 8 CTAs per SM: each adds its histograms to the global counts once
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = 8 * (int64_t)sms;
+  const int64_t chunks = cdiv(n, (int64_t)kSortThreads * kCountRun);
+  const int count_ctas = (int)(chunks < want ? chunks : want);
+  k_radix_counts<K><<<count_ctas, kSortThreads, 0, s>>>(keys, n, end_bit, per, passes, counts);
   K *kin = keys, *kout = keys_alt;
   int *vin = vals, *vout = vals_alt;
-  for (int p = 0, shift = 0; p < passes; ++p) {
+  for (int p = 0; p < passes; ++p) {
+    const int shift = p * per;
     const int bits = end_bit - shift < per ? end_bit - shift : per;
-    const int64_t nh = tiles * ((int64_t)1 << bits);
-    k_radix_hist<K><<<(unsigned)tiles, kSortThreads, 0, s>>>(kin, n, shift, bits, (int)tiles, hist);
-    cudaError_t e = launch_exclusive_scan(hist, hist, nh, scan_tmp, s);
-    if (e != cudaSuccess) return e;
-    k_radix_scatter<K><<<(unsigned)tiles, kSortThreads, 0, s>>>(kin, (p == 0 && vals_iota) ? nullptr : vin, kout,
-                                                                 vout, n, shift, bits, (int)tiles, hist);
+    k_onesweep<K><<<(unsigned)tiles, kSortThreads, 0, s>>>(kin, (p == 0 && vals_iota) ? nullptr : vin, kout, vout, n,
+                                                            shift, bits, counts + p * kRadixBins,
+                                                            status + (int64_t)p * tiles * kRadixBins, tile_ctr + p,
+                                                            err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     K* tk = kin;
@@ -327,16 +491,15 @@ cudaError_t launch_radix_sort(K* keys, int* vals, K* keys_alt, int* vals_alt, in
     int* tv = vin;
     vin = vout;
     vout = tv;
-    shift += bits;
   }
   return cudaSuccess;
 }
 
 template int64_t radix_temp_ints<uint32_t>(int64_t, int);
 template int64_t radix_temp_ints<uint64_t>(int64_t, int);
-template cudaError_t launch_radix_sort<uint32_t>(uint32_t*, int*, uint32_t*, int*, int64_t, int, bool, int*,
+template cudaError_t launch_radix_sort<uint32_t>(uint32_t*, int*, uint32_t*, int*, int64_t, int, bool, int*, int*,
                                                  cudaStream_t);
-template cudaError_t launch_radix_sort<uint64_t>(uint64_t*, int*, uint64_t*, int*, int64_t, int, bool, int*,
+template cudaError_t launch_radix_sort<uint64_t>(uint64_t*, int*, uint64_t*, int*, int64_t, int, bool, int*, int*,
                                                  cudaStream_t);
 
 }  // namespace apic
