@@ -17,5 +17,8 @@ from .oracle import (  # noqa: F401
     contact_step,
     apic1d_linear,
     node_normals,
+    weight_grads,
+    mass_normals,
+    MASS_NORMAL_THRESHOLD,
     augury_steps,
 )

@@ -21,6 +21,9 @@
 //                                              Sec. 2.3 separation rule (flag)
 //   * 1-D two-particle linear-hat transfers ... Sec. 3.1
 //   * node normals from boundary faces ....... Sec. 2.3 (area-weighted)
+//   * normals from a body's grid mass ........ a reading for callers with no
+//                                              surface mesh (App. B weights
+//                                              and their derivatives)
 //   * augury dynamics, springs + gravity ...... Sec. 2.2 eq. apic_accel,
 //                                              eq. Newmark (velocity Verlet)
 //
@@ -43,6 +46,12 @@
 //                                    an isolated spring pair and free fall,
 //                                    rigid translation, momentum, mirror
 //                                    symmetry); rebound threshold unpinned
+//   oracle_mass_normals ........... pinned (weight-derivative identities and
+//                                    finite differences, exact face normals
+//                                    of grid-aligned lattice boxes, zero in
+//                                    the interior, integer-shift and axis
+//                                    invariance, bodies independent); the
+//                                    threshold itself is a reading
 //   per-body-pair friction (mu_pair) ... parity unpinned (a reading; the paper
 //                                    has a single scalar mu)
 #include <algorithm>
@@ -87,6 +96,21 @@ void weights_1d(double xi, int64_t* ileft, double N[4]) {
   N[2] = 0.25 * (b + c);
   N[3] = 0.25 * c;
   *ileft = i;
+}
+
+// Derivatives dN_k/dxi of the four App. B functions at xi (cell units),
+// from the same a_i, b_i, c_i: da/dxi = -2 (fi + 1 - xi), db/dxi = 2 - 4 t,
+// dc/dxi = 2 t with t = xi - fi.
+void weight_grads_1d(double xi, double dN[4]) {
+  const double fi = std::floor(xi);
+  const double t = xi - fi;
+  const double da = -2.0 * (fi + 1.0 - xi);
+  const double db = 2.0 - 4.0 * t;
+  const double dc = 2.0 * t;
+  dN[0] = 0.25 * da;
+  dN[1] = 0.25 * (da + db);
+  dN[2] = 0.25 * (db + dc);
+  dN[3] = 0.25 * dc;
 }
 
 bool inv3(const double A[9], double R[9]) {
@@ -650,6 +674,58 @@ int oracle_augury_steps(int64_t n, int32_t n_bodies, const int32_t* body, double
     energy[0] = kin;
     energy[1] = spr;
     energy[2] = grav;
+  }
+  return 0;
+}
+
+// Derivatives of the App. B weights with respect to xi = x/h.
+void oracle_weight_grads(double xi, double dN[4]) { weight_grads_1d(xi, dN); }
+
+// Normals from the bodies' grid mass (for callers with no surface mesh; the
+// paper's normals come from the FE surface, Sec. 2.3, so this is a reading):
+// for particle p of body b, rho_p = sum_i N_i(x_p) m_{b,i} and
+// g_p = sum_i dN_i/dxi(x_p) m_{b,i}, the body's grid mass (eq. massToGrid
+// over body b alone) interpolated back and its gradient in cell units.  The
+// mass falls off outward, so n_p = -g_p / |g_p| where |g_p| > threshold *
+// rho_p, and n_p = 0 inside the body (a uniform mass field has g_p = 0, the
+// App. B weights summing to one).  ratio[p] = |g_p| / rho_p (may be NULL).
+int oracle_mass_normals(int64_t n, int32_t n_bodies, const int32_t* body, const double* x, const double* m,
+                        double h, double threshold, double* nrm, double* ratio) {
+  if (n < 0 || n_bodies < 1 || !(h > 0.0) || !(threshold >= 0.0)) return -1;
+  for (int64_t p = 0; p < n; ++p)
+    if (body[p] < 0 || body[p] >= n_bodies || !(m[p] > 0.0)) return -1;
+  Grid g;
+  std::vector<Stencil> st;
+  build_stencils(n, x, h, g, st);
+  const size_t G = g.keys.size();
+  // per-body node masses
+  std::vector<double> mb((size_t)n_bodies * G, 0.0);
+  for (int64_t p = 0; p < n; ++p)
+    for (int q = 0; q < 64; ++q)
+      mb[(size_t)body[p] * G + (size_t)st[(size_t)p].node[q]] += st[(size_t)p].w[q] * m[p];
+  for (int64_t p = 0; p < n; ++p) {
+    double N[3][4], dN[3][4];
+    int64_t il[3];
+    for (int d = 0; d < 3; ++d) {
+      weights_1d(x[3 * p + d] / h, &il[d], N[d]);
+      weight_grads_1d(x[3 * p + d] / h, dN[d]);
+    }
+    const double* mbb = &mb[(size_t)body[p] * G];
+    double rho = 0.0, gr[3] = {0.0, 0.0, 0.0};
+    int q = 0;
+    for (int kz = 0; kz < 4; ++kz)
+      for (int ky = 0; ky < 4; ++ky)
+        for (int kx = 0; kx < 4; ++kx, ++q) {
+          const double mi = mbb[(size_t)st[(size_t)p].node[q]];
+          rho += N[0][kx] * N[1][ky] * N[2][kz] * mi;
+          gr[0] += dN[0][kx] * N[1][ky] * N[2][kz] * mi;
+          gr[1] += N[0][kx] * dN[1][ky] * N[2][kz] * mi;
+          gr[2] += N[0][kx] * N[1][ky] * dN[2][kz] * mi;
+        }
+    const double len = std::sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+    const double r = rho > 0.0 ? len / rho : 0.0;
+    if (ratio) ratio[p] = r;
+    for (int a = 0; a < 3; ++a) nrm[3 * p + a] = (r > threshold && len > 0.0) ? -gr[a] / len : 0.0;
   }
   return 0;
 }

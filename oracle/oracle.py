@@ -59,6 +59,10 @@ def _load():
             lib.oracle_contact_step.restype = C.c_int
             lib.oracle_apic1d_linear.argtypes = [i64, P, P, P, P, d, d, P, P]
             lib.oracle_apic1d_linear.restype = C.c_int
+            lib.oracle_weight_grads.argtypes = [d, P]
+            lib.oracle_weight_grads.restype = None
+            lib.oracle_mass_normals.argtypes = [i64, i32, P, P, P, d, d, P, P]
+            lib.oracle_mass_normals.restype = C.c_int
             lib.oracle_node_normals.argtypes = [i64, P, i64, P, P]
             lib.oracle_node_normals.restype = C.c_int
             lib.oracle_augury_steps.argtypes = [i64, i32, P, P, P, P, P, P, P, P, i64, P, P, P, P, i64, P, d, d, P,
@@ -194,6 +198,35 @@ def node_normals(x, tri):
     if lib.oracle_node_normals(x.shape[0], _ptr(x), tri.shape[0], tri.ctypes.data, _ptr(out)) != 0:
         raise ValueError("oracle_node_normals: a triangle index is outside [0, n)")
     return out
+
+
+def weight_grads(xi):
+    """Derivatives dN_k/dxi (k = 0..3) of the App. B weights at xi = x/h."""
+    lib = _load()
+    out = np.zeros(4)
+    lib.oracle_weight_grads(float(xi), out.ctypes.data)
+    return out
+
+
+MASS_NORMAL_THRESHOLD = 0.5  # |grad rho| h / rho above which a particle is on the surface
+
+
+def mass_normals(x, m, body, h, n_bodies=None, threshold=MASS_NORMAL_THRESHOLD):
+    """Normals from each body's grid mass: n = -grad rho / |grad rho| where
+    |grad rho| h > threshold rho, else 0.  Returns (nrm [n,3], ratio [n]),
+    ratio = |grad rho| h / rho."""
+    lib = _load()
+    x = _f64(x, (-1, 3))
+    m = _f64(m, -1)
+    body = np.ascontiguousarray(np.asarray(body, np.int32).reshape(-1))
+    if n_bodies is None:
+        n_bodies = int(body.max()) + 1 if body.size else 1
+    nrm = np.zeros_like(x)
+    ratio = np.zeros(x.shape[0])
+    if lib.oracle_mass_normals(x.shape[0], int(n_bodies), body.ctypes.data, _ptr(x), _ptr(m), float(h),
+                               float(threshold), _ptr(nrm), _ptr(ratio)) != 0:
+        raise ValueError("oracle_mass_normals: invalid arguments")
+    return nrm, ratio
 
 
 def augury_steps(x, v, Cm, m, body, springs, rest, stiffness, tri, h, mu, n_iter, dt, tau, n_steps, av=None,
