@@ -79,6 +79,16 @@ typedef int32_t apic_status;
                                         otherwise APIC_ERR_INVALID_ARG.  Positions, masses and body
                                         ids are always validated.  Reads v, C and nrm once more.   */
 
+#define APIC_MASS_NORMALS (1u << 7) /* nrm may be NULL (and is not read): the normals come from
+                                        each body's grid mass instead (not in the paper, whose
+                                        normals come from the FE surface, Sec. 2.3): after the mass
+                                        P2G, n_p = -g/|g| with g the gradient of body b's grid mass
+                                        (eq. massToGrid over that body) interpolated at x_p, where
+                                        |g| h > 0.5 rho_p (rho_p that mass interpolated at x_p), and
+                                        0 inside the body.  About the outermost particle layer of a
+                                        body sampled at node spacing h/2.  apic_mass_normals gives
+                                        the same normals (any threshold) in the caller's order.    */
+
 typedef struct apic_ctx apic_ctx;
 
 /* One contact step of one scene.
@@ -93,7 +103,7 @@ typedef struct apic_ctx apic_ctx;
  *             double with APIC_FP64).
  *   m         [n] masses, > 0.
  *   nrm       [n*3] outward unit normals of surface nodes, 0 for interior
- *             nodes (Sec. 2.3).
+ *             nodes (Sec. 2.3); may be NULL with APIC_MASS_NORMALS.
  *   v_out, C_out  [n*3], [n*9] results; may alias v, C.
  *   h         grid spacing > 0.   mu  scalar friction coefficient >= 0.
  *   mu_pair   NULL, or HOST pointer to n_bodies*n_bodies doubles (symmetric):
@@ -188,6 +198,24 @@ apic_status apic_contact_step(apic_ctx* ctx, const apic_step_args* args, void* s
  * message names the offending scene. */
 apic_status apic_contact_step_batched(apic_ctx* ctx, const apic_step_args* scenes, int32_t n_scenes,
                                       void* stream, apic_stats* stats);
+
+/* Normals from each body's grid mass, for callers with neither normals nor
+ * a surface mesh (the paper's normals come from the FE surface, Sec. 2.3;
+ * this construction is the library's): for particle p of body b,
+ *   rho_p = sum_i N_i(x_p) m_{b,i},   g_p = sum_i grad N_i(x_p) m_{b,i}
+ * with m_{b,i} body b's grid mass (eq. massToGrid over body b alone, App. B
+ * weights), and nrm_out[p] = -g_p / |g_p| where |g_p| h > threshold * rho_p,
+ * else 0.  threshold 0.5 is what APIC_MASS_NORMALS uses.
+ *   args     the scene as for apic_contact_step: n, n_bodies, body, x, m, h
+ *            and flags are read (APIC_FP64 and APIC_DETERMINISTIC only);
+ *            v, C, nrm, v_out, C_out, mu, mu_pair and n_iter are ignored.
+ *   nrm_out  [n*3] DEVICE array (float, or double with APIC_FP64), written
+ *            in the caller's particle order.
+ * Device pointers only; asynchronous on `stream` except for the host
+ * synchronisations of the grid sizing (see apic_contact_step).  Invalid
+ * positions, masses or body ids return INVALID_ARG. */
+apic_status apic_mass_normals(apic_ctx* ctx, const apic_step_args* args, double threshold, void* nrm_out,
+                              void* stream);
 
 /* The contact step for callers that cannot allocate device memory.
  * (The paper has no counterpart; this is a deployment variant.)

@@ -33,6 +33,7 @@ APIC_VARIANT_PIC = 1 << 2
 APIC_VARIANT_SEP23 = 1 << 3
 APIC_DETERMINISTIC = 1 << 5
 APIC_CHECK = 1 << 6
+APIC_MASS_NORMALS = 1 << 7
 APIC_AUGURY_INIT = 1 << 4
 
 EXPORTED = [
@@ -44,7 +45,7 @@ EXPORTED = [
     "apic_set_graphs", "apic_set_overlap", "apic_set_allocator", "apic_get_tuning", "apic_set_tuning",
     "apic_server_set_policy", "apic_node_normals",
     "apic_augury_steps",
-    "apic_sim_export", "apic_sim_import",
+    "apic_sim_export", "apic_sim_import", "apic_mass_normals",
 ]
 
 
@@ -164,6 +165,8 @@ def load(path: str = LIB_PATH):
         getattr(lib, f).restype = C.c_int32
     lib.apic_contact_step_batched.argtypes = [P, C.POINTER(StepArgs), C.c_int32, P, C.POINTER(Stats)]
     lib.apic_contact_step_batched.restype = C.c_int32
+    lib.apic_mass_normals.argtypes = [P, C.POINTER(StepArgs), C.c_double, P, P]
+    lib.apic_mass_normals.restype = C.c_int32
     lib.apic_contact_step_static.argtypes = [C.POINTER(StepArgs), P, C.POINTER(Stats)]
     lib.apic_contact_step_static.restype = C.c_int32
     lib.apic_set_profiling.argtypes = [P, C.c_int32]
@@ -381,11 +384,11 @@ def contact_step(ctx: Context, x, v, Cm, m, nrm, body, h: float, mu: float, n_it
 
         fp64 = dt == torch.float64
         for t in (x, v, Cm, m, nrm, body):
-            if not t.is_cuda or not t.is_contiguous():
+            if t is not None and (not t.is_cuda or not t.is_contiguous()):
                 raise ValueError("device path wants contiguous CUDA tensors")
         if x.dtype != torch.float64 or body.dtype != torch.int32:
             raise ValueError("x must be float64 and body int32")
-        if any(t.dtype != dt for t in (Cm, m, nrm)):
+        if any(t.dtype != dt for t in (Cm, m, nrm) if t is not None):
             raise ValueError("v, C, m, nrm must share one dtype")
         if v_out is None:
             v_out = torch.empty_like(v)
@@ -398,7 +401,8 @@ def contact_step(ctx: Context, x, v, Cm, m, nrm, body, h: float, mu: float, n_it
         fp64 = dt == np.float64
         x = np.ascontiguousarray(x, np.float64)
         body = np.ascontiguousarray(body, np.int32)
-        v, Cm, m, nrm = (np.ascontiguousarray(a, dt) for a in (v, Cm, m, nrm))
+        v, Cm, m = (np.ascontiguousarray(a, dt) for a in (v, Cm, m))
+        nrm = None if nrm is None else np.ascontiguousarray(nrm, dt)
         if v_out is None:
             v_out = np.empty_like(v)
         if C_out is None:
@@ -407,6 +411,8 @@ def contact_step(ctx: Context, x, v, Cm, m, nrm, body, h: float, mu: float, n_it
         flags |= APIC_HOST_PTRS
     if fp64:
         flags |= APIC_FP64
+    if nrm is None:
+        flags |= APIC_MASS_NORMALS  # normals from the bodies' grid mass
     if n_bodies is None:
         if mu_pair is not None:
             raise ValueError("a per-pair friction table needs n_bodies")
@@ -419,6 +425,36 @@ def contact_step(ctx: Context, x, v, Cm, m, nrm, body, h: float, mu: float, n_it
     st = Stats() if stats else None
     _check(lib.apic_contact_step(ctx.handle, C.byref(a), sptr, C.byref(st) if stats else None))
     return StepResult(v_out, C_out, st.as_dict() if stats else None)
+
+
+MASS_NORMAL_THRESHOLD = 0.5  # the threshold APIC_MASS_NORMALS uses
+
+
+def mass_normals(ctx: Context, x, m, body, h: float, n_bodies: int | None = None,
+                 threshold: float = MASS_NORMAL_THRESHOLD, out=None, stream=None, deterministic: bool = False):
+    """apic_mass_normals: normals from each body's grid mass, in the
+    caller's order.  x [n,3] float64, m [n] float32 (or float64 for the
+    FP64 path), body [n] int32: torch CUDA tensors.  Returns out [n,3]."""
+    import torch
+
+    lib = load()
+    n = int(x.shape[0])
+    for t in (x, m, body):
+        if not t.is_cuda or not t.is_contiguous() or t.device != x.device:
+            raise ValueError("apic_mass_normals wants contiguous CUDA tensors on one device")
+    flags = APIC_FP64 if m.dtype == torch.float64 else 0
+    if deterministic:
+        flags |= APIC_DETERMINISTIC
+    if out is None:
+        out = torch.empty((n, 3), dtype=m.dtype, device=x.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    if n_bodies is None:
+        n_bodies = _default_n_bodies(body, n)
+    a = StepArgs(n, int(n_bodies), 0, _ptr(body), _ptr(x), None, None, _ptr(m), None, None, None, float(h), 0.0,
+                 None, int(flags))
+    _check(lib.apic_mass_normals(ctx.handle, C.byref(a), float(threshold), _ptr(out), stream.cuda_stream))
+    return out
 
 
 def contact_step_static(x, v, Cm, m, nrm, body, h: float, mu: float, n_iter: int, n_bodies: int | None = None,

@@ -467,15 +467,17 @@ struct CtxEnv {
   };
 };
 
-constexpr uint32_t kAllFlags =
-    APIC_FP64 | APIC_HOST_PTRS | APIC_VARIANT_PIC | APIC_VARIANT_SEP23 | APIC_DETERMINISTIC | APIC_CHECK;
+constexpr uint32_t kAllFlags = APIC_FP64 | APIC_HOST_PTRS | APIC_VARIANT_PIC | APIC_VARIANT_SEP23 |
+                               APIC_DETERMINISTIC | APIC_CHECK | APIC_MASS_NORMALS;
 
-apic_status run(apic_ctx* c, const apic_step_args* scenes, int ns, void* stream, apic_stats* stats) {
+apic_status run(apic_ctx* c, const apic_step_args* scenes, int ns, void* stream, apic_stats* stats,
+                bool normals_only = false, double nthr = kMassNormalThreshold) {
   P_CUDA(cudaSetDevice(c->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CtxEnv env{c};
-  const apic_status st = (scenes[0].flags & APIC_FP64) ? run_batch<double>(env, scenes, ns, s, stats)
-                                                      : run_batch<float>(env, scenes, ns, s, stats);
+  const apic_status st = (scenes[0].flags & APIC_FP64)
+                             ? run_batch<double>(env, scenes, ns, s, stats, normals_only, nthr)
+                             : run_batch<float>(env, scenes, ns, s, stats, normals_only, nthr);
   if (st != APIC_OK) {
     c->spans.clear();  // drop unfinished profile spans
     c->ev_used = 0;
@@ -567,6 +569,28 @@ apic_status apic_contact_step_batched(apic_ctx* c, const apic_step_args* scenes,
                    scenes[i].n_iter, scenes[0].n_iter);
   }
   return run(c, scenes, n_scenes, stream, stats);
+}
+
+apic_status apic_mass_normals(apic_ctx* c, const apic_step_args* a, double threshold, void* nrm_out, void* stream) {
+  if (!c) return pfail(APIC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!a) return pfail(APIC_ERR_INVALID_ARG, "args is NULL");
+  if (!(threshold >= 0.0) || !std::isfinite(threshold))
+    return pfail(APIC_ERR_INVALID_ARG, "threshold = %g must be finite and >= 0", threshold);
+  if (a->flags & ~(APIC_FP64 | APIC_DETERMINISTIC))
+    return pfail(APIC_ERR_INVALID_ARG, "flag bits 0x%x not accepted here (APIC_FP64, APIC_DETERMINISTIC only)",
+                 a->flags & ~(APIC_FP64 | APIC_DETERMINISTIC));
+  if (a->n > 0 && (!a->x || !a->body || !a->m || !nrm_out))
+    return pfail(APIC_ERR_INVALID_ARG, "x, body, m and nrm_out are required");
+  // the step's own checks, on a copy whose velocities are unused stand-ins
+  apic_step_args b = *a;
+  b.v = b.C = b.v_out = b.C_out = nrm_out;
+  b.nrm = nullptr;
+  b.mu_pair = nullptr;
+  b.flags = a->flags | APIC_MASS_NORMALS;
+  P_TRY(validate_scene(&b, 0, kAllFlags));
+  if (b.n == 0) return APIC_OK;
+  b.v_out = nrm_out;  // where the normals go
+  return run(c, &b, 1, stream, nullptr, true, threshold);
 }
 
 apic_status apic_set_profiling(apic_ctx* c, int32_t on) {

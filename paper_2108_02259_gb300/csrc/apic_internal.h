@@ -70,7 +70,7 @@ struct SceneDev {
   int n;
   int n_bodies;
   int mu_off;          // offset of the scene's body-pair friction table, or -1
-  int pad;
+  float nthr;          // normals from the grid mass: surface where |grad rho| h > nthr rho
   Box box;
   int pad2[2];
   double h, inv_h, mu;
@@ -85,7 +85,14 @@ enum Mode : int {
   kModeOnly = 5,   // N = 0: G2P -> V_hat = H V in caller order
   kModeMu = 6,     // per-particle friction blend from a body-pair table
   kModeMassV = 7,  // m_i, body mask and P2G of V in one pass (momentum to FP64)
+  kModeNormals = 8,  // normals from each body's grid mass (needs the per-body node masses)
 };
+
+// Normals from a body's grid mass: a particle is on the surface where the
+// gradient of its body's interpolated grid mass, times h, exceeds this
+// fraction of the interpolated mass (about the outermost layer of a
+// lattice at node spacing h/2).
+constexpr double kMassNormalThreshold = 0.5;
 
 // Everything the per-item kernel needs, by value.
 template <class T>
@@ -113,6 +120,8 @@ struct IterParams {
   uint32_t* gmask;         // body bits, [nodes]
   V4<double>* gp64;        // FP64 momentum at multi-body nodes (FP32 path), [nodes]
   const int* perm;         // sorted -> batch particle index
+  V4<T>* pn_out;           // kModeNormals: sorted normals written here (the pn plane) ...
+  int normals_out;         // ... or, when set, into each scene's v_out in caller order
   int pic;                 // PIC transfers
   int sep23;               // Sec. 2.3 rule
   // Fixed-point node sums (deterministic mode): per scene, fx_max[scene *

@@ -58,6 +58,16 @@ __device__ __forceinline__ void bspline(T t, T w[4], T d[4]) {
   d[3] = T(2) - t;
 }
 
+// Derivatives of the same four weights with respect to t (cell units):
+//   -(1-t)/2,  -t/2,  (1-t)/2,  t/2.
+template <class T>
+__device__ __forceinline__ void bspline_grad(T t, T g[4]) {
+  g[0] = -T(0.5) * (T(1) - t);
+  g[1] = -T(0.5) * t;
+  g[2] = T(0.5) * (T(1) - t);
+  g[3] = T(0.5) * t;
+}
+
 // Sec. 2.4: the undesirable part of the proposed change (dv, dCh).  dCh is
 // always undesirable; dv loses its admissible part inside the Coulomb cone
 // when dv.n <= 0.  With sep23 the Sec. 2.3 rule is used instead.
@@ -409,6 +419,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   constexpr int kComp = kMass ? 4 : 3;         // momentum (x, y, z) [, mass]
   __shared__ V4<T> sv[kG2P ? kTile3 : 1];
   __shared__ uint32_t smask[MODE == kModeMu ? kTile3 : 1];
+  __shared__ T smass[MODE == kModeNormals ? kTile3 : 1];  // the item's body's node masses
   using Acc = typename std::conditional<DET, long long, T>::type;
   __shared__ Acc sacc[kP2G ? kComp : 1][kTile3];
   __shared__ unsigned s_fxmax;
@@ -474,7 +485,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   if constexpr (DET) {
     const unsigned* fxs = p.fx_max + (int64_t)info.z * p.fx_stride;
     float unused;
-    if (MODE == kModeMassV || MODE == kModeMu) fxSm = fx_scale(fxs, 0, 0, S.n, &unused);
+    if (MODE == kModeMassV || MODE == kModeMu || MODE == kModeNormals) fxSm = fx_scale(fxs, 0, 0, S.n, &unused);
     if (MODE == kModeMassV) fxS = fx_scale(fxs, 1, 0, S.n, &fx_ok);
     if (MODE == kModeFirst || MODE == kModeMid)
       fxS = fx_scale(fxs, p.fx_slot, fx_head(p.fx_err, p.fx_attempt, info.z), S.n, &fx_ok);
@@ -506,6 +517,18 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         const int node = tile_node(snb, t);
         sv[t] = node >= 0 ? p.gv[node] : V4<T>{T(0), T(0), T(0), T(0)};
       }
+    }
+    __syncthreads();
+  }
+  if (MODE == kModeNormals) {
+    for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
+      const int node = tile_node(snb, t);
+      T mi = T(0);
+      if (node >= 0) {
+        const int64_t k = (int64_t)body * p.n_nodes + node;
+        mi = DET ? (T)from_fx(p.gmb_fx[k], 1.f / fxSm) : p.gmb[k];
+      }
+      smass[t] = mi;
     }
     __syncthreads();
   }
@@ -565,6 +588,50 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         }
       }
       p.mup_out[s] = den > T(0) ? num / den : p.mu_table[S.mu_off + body * S.n_bodies + body];
+    } else if (MODE == kModeNormals) {
+      // rho = sum N m_b and g = sum grad N m_b (cell units) over the body's
+      // own node masses, sum-factorised; n = -g/|g| on the surface, else 0
+      T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4], gx[4], gy[4], gz[4];
+      bspline(pt.x, wx, dx);
+      bspline(pt.y, wy, dy);
+      bspline(pt.z, wz, dz);
+      bspline_grad(pt.x, gx);
+      bspline_grad(pt.y, gy);
+      bspline_grad(pt.z, gz);
+      T rho = T(0), g0 = T(0), g1 = T(0), g2 = T(0);
+#pragma unroll
+      for (int kz = 0; kz < 4; ++kz) {
+        T r = T(0), ry = T(0), rx = T(0);  // sum over y of N_y (N_x m), of gN_y (N_x m), of N_y (gN_x m)
+#pragma unroll
+        for (int ky = 0; ky < 4; ++ky) {
+          T a = T(0), ad = T(0);
+#pragma unroll
+          for (int kx = 0; kx < 4; ++kx) {
+            const T mi = smass[base + kz * (kTile * kTile) + ky * kTile + kx];
+            a += wx[kx] * mi;
+            ad += gx[kx] * mi;
+          }
+          r += wy[ky] * a;
+          ry += gy[ky] * a;
+          rx += wy[ky] * ad;
+        }
+        rho += wz[kz] * r;
+        g0 += wz[kz] * rx;
+        g1 += wz[kz] * ry;
+        g2 += gz[kz] * r;
+      }
+      const T len = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
+      const bool surf = rho > T(0) && len > (T)S.nthr * rho;
+      const T inv = surf ? -T(1) / len : T(0);
+      const T nn[3] = {g0 * inv, g1 * inv, g2 * inv};
+      if (p.normals_out) {
+        const int64_t idx = p.perm[s] - S.part_off;
+        T* o = static_cast<T*>(S.v_out);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) o[3 * idx + a] = nn[a];
+      } else {
+        p.pn_out[s] = V4<T>{nn[0], nn[1], nn[2], pn.w};
+      }
     } else if (MODE == kModeMassV) {
       T wx[4], dx[4];
       bspline(pt.x, wx, dx);
@@ -983,18 +1050,22 @@ __global__ void k_cells(int64_t n, const SceneDev* __restrict__ sc, int ns, int4
     const int b = S.body[i];
     if (b < 0 || b >= S.n_bodies) err |= kErrBody;
     if (bad_mass(static_cast<const T*>(S.m)[i])) err |= kErrMass;
-    if (check) {
+    if (check && S.v && S.C) {
       const T* v = static_cast<const T*>(S.v) + 3 * i;
       const T* C = static_cast<const T*>(S.C) + 9 * i;
-      const T* nr = static_cast<const T*>(S.nrm) + 3 * i;
       bool fin = true;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) fin = fin && isfinite(v[a]) && isfinite(nr[a]);
+      for (int a = 0; a < 3; ++a) fin = fin && isfinite(v[a]);
 #pragma unroll
       for (int a = 0; a < 9; ++a) fin = fin && isfinite(C[a]);
+      if (S.nrm) {  // (NULL when the normals are computed on the device)
+        const T* nr = static_cast<const T*>(S.nrm) + 3 * i;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) fin = fin && isfinite(nr[a]);
+        const T n2 = nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2];
+        if (fin && n2 != T(0) && fabs(n2 - T(1)) > T(1e-3)) err |= kErrNormal;
+      }
       if (!fin) err |= kErrFinite;
-      const T n2 = nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2];
-      if (fin && n2 != T(0) && fabs(n2 - T(1)) > T(1e-3)) err |= kErrNormal;
     }
     cellb[p] = make_int4(c[0], c[1], c[2], b);
     if (uniform_scene < 0) {
@@ -1103,8 +1174,9 @@ __global__ void k_gather(int64_t n, const SceneDev* __restrict__ sc, int ns, con
     pn[s] = V4<T>{T(0), T(0), T(0), bits_to(T(0), loc)};
     return;
   }
-  const T* nrm = static_cast<const T*>(S.nrm);
-  pn[s] = V4<T>{nrm[3 * i + 0], nrm[3 * i + 1], nrm[3 * i + 2], bits_to(T(0), loc)};
+  const T* nrm = static_cast<const T*>(S.nrm);  // NULL: normals computed on the device later
+  pn[s] = nrm ? V4<T>{nrm[3 * i + 0], nrm[3 * i + 1], nrm[3 * i + 2], bits_to(T(0), loc)}
+              : V4<T>{T(0), T(0), T(0), bits_to(T(0), loc)};
   const T hh = (T)S.h;
   const T* v = static_cast<const T*>(S.v);
   const T* C = static_cast<const T*>(S.C);
@@ -1128,9 +1200,11 @@ __global__ void k_gather_v(int64_t n, const SceneDev* __restrict__ sc, int ns, c
   const SceneDev& S = sc[scene_of_particle(sc, ns, g)];
   const int64_t i = g - S.part_off;
   const T* nrm = static_cast<const T*>(S.nrm);
-  pn[s].x = nrm[3 * i + 0];
-  pn[s].y = nrm[3 * i + 1];
-  pn[s].z = nrm[3 * i + 2];
+  if (nrm) {  // NULL: normals computed on the device later
+    pn[s].x = nrm[3 * i + 0];
+    pn[s].y = nrm[3 * i + 1];
+    pn[s].z = nrm[3 * i + 2];
+  }
   const T hh = (T)S.h;
   const T* v = static_cast<const T*>(S.v);
   const T* C = static_cast<const T*>(S.C);
@@ -1417,6 +1491,7 @@ cudaError_t launch_items_cfg(const IterParams<T>& p, int mode, bool overlap, cud
     APIC_MODE(kModeOnly)
     APIC_MODE(kModeMu)
     APIC_MODE(kModeMassV)
+    APIC_MODE(kModeNormals)
 #undef APIC_MODE
     default: return cudaErrorInvalidValue;
   }
@@ -1436,6 +1511,7 @@ cudaError_t launch_items_fx(const IterParams<T>& p, int mode, bool overlap, cuda
     APIC_MODE(kModeOnly)
     APIC_MODE(kModeMu)
     APIC_MODE(kModeMassV)
+    APIC_MODE(kModeNormals)
 #undef APIC_MODE
     default: return cudaErrorInvalidValue;
   }

@@ -102,7 +102,8 @@ inline apic_status validate_scene(const apic_step_args* a, int idx, uint32_t all
     return pfail(APIC_ERR_INVALID_ARG, "scene %d: mu = %g must be finite and >= 0", idx, a->mu);
   if (a->flags & ~allowed_flags)
     return pfail(APIC_ERR_INVALID_ARG, "scene %d: flag bits 0x%x not accepted here", idx, a->flags & ~allowed_flags);
-  if (a->n > 0 && (!a->body || !a->x || !a->v || !a->C || !a->m || !a->nrm || !a->v_out || !a->C_out))
+  if (a->n > 0 && (!a->body || !a->x || !a->v || !a->C || !a->m || !a->v_out || !a->C_out ||
+                   (!a->nrm && !(a->flags & APIC_MASS_NORMALS))))
     return pfail(APIC_ERR_INVALID_ARG, "scene %d: a required array pointer is NULL", idx);
   if (a->mu_pair) {
     const int nb = a->n_bodies;
@@ -196,13 +197,22 @@ apic_status exclusive_sum(Env& env, const SizingBufs& b, const int* in, int* out
 
 // Steps `ns` scenes in one batch.  All scenes share the precision and
 // variant flags of scene 0 and its n_iter (checked by the caller).
+//
+// With APIC_MASS_NORMALS the normals come from each body's grid mass
+// (threshold nthr) after the mass pass instead of from the scenes' nrm.
+// normals_only: stop after those normals and write them to each scene's
+// v_out (caller order, [n*3]) instead of stepping (device pointers, no
+// statistics).
 template <class T, class Env>
-apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream_t s, apic_stats* stats) {
+apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream_t s, apic_stats* stats,
+                      bool normals_only = false, double nthr = kMassNormalThreshold) {
   const uint32_t flags = scenes[0].flags;
   const bool host = (flags & APIC_HOST_PTRS) != 0;
   const bool det = (flags & APIC_DETERMINISTIC) != 0;
+  const bool mnrm = normals_only || (flags & APIC_MASS_NORMALS) != 0;
   const int check = (flags & APIC_CHECK) ? 1 : 0;
   const int N = scenes[0].n_iter;
+  if (normals_only && (host || stats)) return pfail(APIC_ERR_INVALID_ARG, "normals: device pointers, no statistics");
   if (det && sizeof(T) != 4)
     return pfail(APIC_ERR_INVALID_ARG, "APIC_DETERMINISTIC applies to the FP32 path (not with APIC_FP64)");
   typename Env::Span span_step(env, s, 0);
@@ -222,7 +232,8 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     d.v = a.v;
     d.C = a.C;
     d.m = a.m;
-    d.nrm = a.nrm;
+    d.nrm = mnrm ? nullptr : a.nrm;  // computed on the device instead
+    d.nthr = (float)nthr;
     d.v_out = a.v_out;
     d.C_out = a.C_out;
     d.part_off = n;
@@ -284,6 +295,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
           {a.m, {dm + o, m * (long long)sizeof(T)}},               {a.nrm, {dn + 3 * o, 3 * m * (long long)sizeof(T)}},
           {a.v, {dv + 3 * o, 3 * m * (long long)sizeof(T)}},      {a.C, {dC + 9 * o, 9 * m * (long long)sizeof(T)}}};
       for (int k = 0; k < 6; ++k) {
+        if (k == 3 && mnrm) continue;  // no normals to stage
         const void* src = env.device_view(parts[k].first);
         if (!src) {
           direct = false;
@@ -319,14 +331,14 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
         P_CUDA(cudaMemcpyAsync(dv + 3 * o, a.v, 3 * m * sizeof(T), cudaMemcpyHostToDevice, s));
         P_CUDA(cudaMemcpyAsync(dC + 9 * o, a.C, 9 * m * sizeof(T), cudaMemcpyHostToDevice, s));
         P_CUDA(cudaMemcpyAsync(dm + o, a.m, m * sizeof(T), cudaMemcpyHostToDevice, s));
-        P_CUDA(cudaMemcpyAsync(dn + 3 * o, a.nrm, 3 * m * sizeof(T), cudaMemcpyHostToDevice, s));
+        if (!mnrm) P_CUDA(cudaMemcpyAsync(dn + 3 * o, a.nrm, 3 * m * sizeof(T), cudaMemcpyHostToDevice, s));
       }
       hsc[i].x = dx + 3 * o;
       hsc[i].body = db + o;
       hsc[i].v = dv + 3 * o;
       hsc[i].C = dC + 9 * o;
       hsc[i].m = dm + o;
-      hsc[i].nrm = dn + 3 * o;
+      hsc[i].nrm = mnrm ? nullptr : dn + 3 * o;
       hsc[i].v_out = dvo + 3 * o;
       hsc[i].C_out = dCo + 9 * o;
     }
@@ -370,7 +382,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       P_TRY((sort_keys<uint32_t>(env, n, sc, ns, cellb, max_bodies, &ds->err, sb, q)));
     // 4. sorted SoA (normals and V planes later when they are still in
     //    transit).
-    P_LAUNCH(env, launch_gather<T>(n, sc, ns, sb.perm, cellb, pt, pn, split_v ? nullptr : V, q));
+    P_LAUNCH(env, launch_gather<T>(n, sc, ns, sb.perm, cellb, pt, pn, (split_v || normals_only) ? nullptr : V, q));
     // 5. work items: runs of equal (grid block, body), each split into
     //    equal items of at most `chunk` particles (the variant's CTA size).
     if (sb.k64) {
@@ -530,10 +542,12 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   if (det) {
     P_TRY(env.take(kSlotFxMax, (size_t)ns * fx_stride, &fx_max, "fixed-point bounds"));
     P_TRY(env.take(kSlotFxErr, (size_t)2 * (ns + 1), &fx_err, "fixed-point range flags"));
-    if (any_mu) P_TRY(env.take(kSlotGmbFx, (size_t)max_bodies * n_nodes, &gmb_fx, "per-body grid mass (fixed)"));
+    if (any_mu || mnrm)
+      P_TRY(env.take(kSlotGmbFx, (size_t)max_bodies * n_nodes, &gmb_fx, "per-body grid mass (fixed)"));
   }
+  if (mnrm && !det) P_TRY(env.take(kSlotGmb, (size_t)max_bodies * n_nodes, &gmb, "per-body grid mass"));
   if (any_mu) {
-    if (!det) P_TRY(env.take(kSlotGmb, (size_t)max_bodies * n_nodes, &gmb, "per-body grid mass"));
+    if (!det && !gmb) P_TRY(env.take(kSlotGmb, (size_t)max_bodies * n_nodes, &gmb, "per-body grid mass"));
     P_TRY(env.take(kSlotMuTable, (size_t)n_mu, &mu_table, "friction tables"));
     P_TRY(env.take(kSlotMup, n, &mup, "particle friction"));
     T* hmu = static_cast<T*>(env.host_buf((size_t)n_mu * sizeof(T)));
@@ -551,7 +565,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   struct PassKey {
     IterParams<T> p;
     T* mup;
-    int n_iter, any_mu, variant, split_v;
+    int n_iter, any_mu, variant, split_v, mnrm, normals_only;
   };
   PassKey key;
   std::memset(&key, 0, sizeof(key));  // padding bytes take part in the comparison
@@ -579,6 +593,8 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   p.gmask = gmask;
   p.gp64 = gp64;
   p.perm = perm;
+  p.pn_out = pn;
+  p.normals_out = normals_only ? 1 : 0;
   p.pic = (flags & APIC_VARIANT_PIC) ? 1 : 0;
   p.sep23 = (flags & APIC_VARIANT_SEP23) ? 1 : 0;
   p.fx_max = fx_max;
@@ -590,6 +606,8 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   key.any_mu = any_mu ? 1 : 0;
   key.variant = variant;
   key.split_v = split_v ? 1 : 0;
+  key.mnrm = mnrm ? 1 : 0;
+  key.normals_only = normals_only ? 1 : 0;
 
   auto series = [&](cudaStream_t q) -> apic_status {
     IterParams<T> pp = key.p;
@@ -621,12 +639,30 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
                                    pp.fx_attempt, all64, ov, q);
       return launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, all64, ov, q);
     };
+    if (normals_only) P_CUDA(cudaMemsetAsync(V, 0, 3 * n * sizeof(V4<T>), q));  // (the mass pass reads V)
     P_LAUNCH(env, launch_items<T>(pp, kModeMassV, var, false, q));
     if (any_mu) {
       P_LAUNCH(env, launch_items<T>(pp, kModeMu, var, ov, q));
       pp.mup = mup;
     }
-    P_LAUNCH(env, normalize(1, 1));
+    if (mnrm) {
+      // normals into the sorted pn plane (or the callers' arrays).  The
+      // passes read pn before their dependent-launch wait, so this grid and
+      // the normalisation after it launch without overlap: every later grid
+      // starts after the normals are complete.
+      P_LAUNCH(env, launch_items<T>(pp, kModeNormals, var, false, q));
+      if (normals_only) return APIC_OK;
+    }
+    if (mnrm) {
+      if (det)
+        P_LAUNCH(env, launch_normalize_fx(n_nodes, blist, sc, ns, reinterpret_cast<float*>(gm), gfx,
+                                          reinterpret_cast<V4<float>*>(gv), fx_max, fx_err, fx_stride, 1,
+                                          pp.fx_attempt, 1, false, q));
+      else
+        P_LAUNCH(env, launch_normalize<T>(n_nodes, gm, gmask, gp, gp64, gv, 1, false, q));
+    } else {
+      P_LAUNCH(env, normalize(1, 1));
+    }
     span_mass.stop();
 
     // 8. the N + 1 transfer passes.

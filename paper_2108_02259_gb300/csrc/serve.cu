@@ -331,10 +331,10 @@ apic_status apic_sim_open(apic_server* srv, const apic_step_args* a, apic_sim** 
   if (a->n <= 0 || a->n > (int64_t)INT32_MAX / 4) return sfail(APIC_ERR_INVALID_ARG, "n out of range");
   if (a->n_bodies < 1 || a->n_bodies > 32 || a->n_iter < 0 || !(a->h > 0.0) || !(a->mu >= 0.0))
     return sfail(APIC_ERR_INVALID_ARG, "invalid n_bodies, n_iter, h or mu");
-  if (!a->x || !a->body || !a->v || !a->C || !a->m || !a->nrm)
+  if (!a->x || !a->body || !a->v || !a->C || !a->m || (!a->nrm && !(a->flags & APIC_MASS_NORMALS)))
     return sfail(APIC_ERR_INVALID_ARG, "a required array pointer is NULL");
-  const uint32_t known =
-      APIC_FP64 | APIC_HOST_PTRS | APIC_VARIANT_PIC | APIC_VARIANT_SEP23 | APIC_DETERMINISTIC | APIC_CHECK;
+  const uint32_t known = APIC_FP64 | APIC_HOST_PTRS | APIC_VARIANT_PIC | APIC_VARIANT_SEP23 | APIC_DETERMINISTIC |
+                         APIC_CHECK | APIC_MASS_NORMALS;
   if (a->flags & ~known) return sfail(APIC_ERR_INVALID_ARG, "unknown flag bits");
   const size_t es = (a->flags & APIC_FP64) ? 8 : 4;
   const size_t n = (size_t)a->n;
@@ -369,7 +369,12 @@ apic_status apic_sim_open(apic_server* srv, const apic_step_args* a, apic_sim** 
   alloc_copy(&s->v, a->v, 3 * n * es);
   alloc_copy(&s->C, a->C, 9 * n * es);
   alloc_copy(&s->m, a->m, n * es);
-  alloc_copy(&s->nrm, a->nrm, 3 * n * es);
+  if (a->nrm) {
+    alloc_copy(&s->nrm, a->nrm, 3 * n * es);
+  } else if (e == cudaSuccess) {  // APIC_MASS_NORMALS: the steps compute them; keep zeros
+    e = cudaMalloc(&s->nrm, 3 * n * es);
+    if (e == cudaSuccess) e = cudaMemset(s->nrm, 0, 3 * n * es);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_sim_memory(s);

@@ -115,7 +115,8 @@ struct StaticEnv {
 extern "C" {
 
 apic_status apic_contact_step_static(const apic_step_args* a, void* stream, apic_stats* stats) {
-  P_TRY(validate_scene(a, 0, APIC_FP64 | APIC_VARIANT_PIC | APIC_VARIANT_SEP23 | APIC_DETERMINISTIC | APIC_CHECK));
+  P_TRY(validate_scene(a, 0, APIC_FP64 | APIC_VARIANT_PIC | APIC_VARIANT_SEP23 | APIC_DETERMINISTIC | APIC_CHECK |
+                                   APIC_MASS_NORMALS));
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (a->n == 0) return APIC_OK;
   StaticEnv env;
