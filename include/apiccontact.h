@@ -337,6 +337,49 @@ apic_status apic_sim_export(apic_sim* sim, void* host_buf, size_t* bytes);
  * buffer that is not a complete checkpoint of this library. */
 apic_status apic_sim_import(apic_server* srv, const void* host_buf, size_t bytes, apic_sim** out);
 
+/* ---------------------------------------------------------------------------
+ * Server groups: simulations spread over several devices by HBM budget.
+ * (Not in the paper.)  Simulations are independent, so a group is one
+ * server per device and nothing crosses devices on the data path: a
+ * simulation lives on the device it was admitted to, and its requests, tickets
+ * and reads go to that device's server (apic_sim_server).
+ * --------------------------------------------------------------------------*/
+typedef struct apic_group apic_group;
+
+/* The device (index into free_bytes) with the most room that still holds
+ * `need` bytes (ties: the lowest index), or -1 when none does.  free_bytes
+ * of a device without a budget is INT64_MAX.  Host function, no GPU. */
+int32_t apic_place_by_budget(const int64_t* free_bytes, int32_t n_devices, int64_t need);
+
+/* One server per listed device (the same device may be listed twice: two
+ * independent servers), each with hbm_budget_per_device (0 = no cap),
+ * n_workers workers and max_batch_scenes as apic_server_create. */
+apic_status apic_group_create(apic_group** out, const int32_t* devices, int32_t n_devices,
+                              size_t hbm_budget_per_device, int32_t n_workers, int32_t max_batch_scenes);
+
+/* Destroy every member server (finishing queued requests first). */
+apic_status apic_group_destroy(apic_group* group);
+
+/* Member `member` (0..n_devices-1) of the group. */
+apic_status apic_group_server(apic_group* group, int32_t member, apic_server** out);
+
+/* apic_server_set_policy on every member. */
+apic_status apic_group_set_policy(apic_group* group, int32_t variant, int32_t graphs);
+
+/* Admit a simulation on the member with the most room for it
+ * (apic_place_by_budget over each member's budget minus its resident state
+ * and worker scratch); *member (may be NULL) receives the member's index.
+ * A member that refuses because others were admitted meanwhile is skipped;
+ * APIC_ERR_ADMISSION when no member has room now. */
+apic_status apic_group_open(apic_group* group, const apic_step_args* init, apic_sim** out, int32_t* member);
+
+/* Statistics summed over the members; latency percentiles over all of their
+ * samples. */
+apic_status apic_group_get_stats(apic_group* group, apic_server_stats* out, int32_t reset);
+
+/* The server that holds `sim` (for its tickets). */
+apic_status apic_sim_server(apic_sim* sim, apic_server** out);
+
 /* Wait for the simulation's steps, then free its resident state. */
 apic_status apic_sim_close(apic_sim* sim);
 

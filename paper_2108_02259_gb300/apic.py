@@ -46,6 +46,8 @@ EXPORTED = [
     "apic_server_set_policy", "apic_node_normals",
     "apic_augury_steps",
     "apic_sim_export", "apic_sim_import", "apic_mass_normals",
+    "apic_place_by_budget", "apic_group_create", "apic_group_destroy", "apic_group_server", "apic_group_set_policy",
+    "apic_group_open", "apic_group_get_stats", "apic_sim_server",
 ]
 
 
@@ -165,6 +167,18 @@ def load(path: str = LIB_PATH):
         getattr(lib, f).restype = C.c_int32
     lib.apic_contact_step_batched.argtypes = [P, C.POINTER(StepArgs), C.c_int32, P, C.POINTER(Stats)]
     lib.apic_contact_step_batched.restype = C.c_int32
+    lib.apic_place_by_budget.argtypes = [P, C.c_int32, C.c_int64]
+    lib.apic_place_by_budget.restype = C.c_int32
+    lib.apic_group_create.argtypes = [C.POINTER(P), P, C.c_int32, C.c_size_t, C.c_int32, C.c_int32]
+    lib.apic_group_destroy.argtypes = [P]
+    lib.apic_group_server.argtypes = [P, C.c_int32, C.POINTER(P)]
+    lib.apic_group_set_policy.argtypes = [P, C.c_int32, C.c_int32]
+    lib.apic_group_open.argtypes = [P, C.POINTER(StepArgs), C.POINTER(P), C.POINTER(C.c_int32)]
+    lib.apic_group_get_stats.argtypes = [P, C.POINTER(ServerStats), C.c_int32]
+    lib.apic_sim_server.argtypes = [P, C.POINTER(P)]
+    for f in ("apic_group_create", "apic_group_destroy", "apic_group_server", "apic_group_set_policy",
+              "apic_group_open", "apic_group_get_stats", "apic_sim_server"):
+        getattr(lib, f).restype = C.c_int32
     lib.apic_mass_normals.argtypes = [P, C.POINTER(StepArgs), C.c_double, P, P]
     lib.apic_mass_normals.restype = C.c_int32
     lib.apic_contact_step_static.argtypes = [C.POINTER(StepArgs), P, C.POINTER(Stats)]
@@ -692,37 +706,50 @@ class Server:
         return {k: getattr(st, k) for k, _ in ServerStats._fields_}
 
 
+def _sim_args(x, v, Cm, m, nrm, body, h, mu, n_iter, n_bodies=None, mu_pair=None, flags=0):
+    """StepArgs admitting a simulation (host numpy arrays or CUDA tensors),
+    with the arrays it points into kept alive in the returned tuple."""
+    dev = _is_torch(x)
+    if not dev:
+        x = np.ascontiguousarray(x, np.float64)
+        body = np.ascontiguousarray(body, np.int32)
+        dt = np.asarray(v).dtype
+        v, Cm, m = (np.ascontiguousarray(a, dt) for a in (v, Cm, m))
+        nrm = None if nrm is None else np.ascontiguousarray(nrm, dt)
+        flags |= APIC_HOST_PTRS
+        fp64 = dt == np.float64
+    else:
+        import torch
+
+        fp64 = v.dtype == torch.float64
+    if fp64:
+        flags |= APIC_FP64
+    if nrm is None:
+        flags |= APIC_MASS_NORMALS
+    n = int(x.shape[0])
+    if n_bodies is None and mu_pair is not None:
+        raise ValueError("a per-pair friction table needs n_bodies")
+    nb = n_bodies if n_bodies is not None else _default_n_bodies(body, n)
+    mp = None
+    if mu_pair is not None:
+        mp = np.ascontiguousarray(np.asarray(mu_pair, np.float64).reshape(nb, nb))
+    a = StepArgs(n, int(nb), int(n_iter), _ptr(body), _ptr(x), _ptr(v), _ptr(Cm), _ptr(m), _ptr(nrm), None,
+                 None, float(h), float(mu), None if mp is None else mp.ctypes.data, int(flags))
+    return a, n, (np.float64 if fp64 else np.float32), (x, v, Cm, m, nrm, body, mp)
+
+
 class Sim:
     def __init__(self, srv, x, v, Cm, m, nrm, body, h, mu, n_iter, n_bodies=None, mu_pair=None, flags=0):
         lib = load()
         self.srv = srv
-        dev = _is_torch(x)
-        if not dev:
-            x = np.ascontiguousarray(x, np.float64)
-            body = np.ascontiguousarray(body, np.int32)
-            dt = np.asarray(v).dtype
-            v, Cm, m, nrm = (np.ascontiguousarray(a, dt) for a in (v, Cm, m, nrm))
-            flags |= APIC_HOST_PTRS
-            fp64 = dt == np.float64
-        else:
-            import torch
-
-            fp64 = v.dtype == torch.float64
-        if fp64:
-            flags |= APIC_FP64
-        self.n = int(x.shape[0])
-        self.dtype = np.float64 if fp64 else np.float32
-        if n_bodies is None and mu_pair is not None:
-            raise ValueError("a per-pair friction table needs n_bodies")
-        nb = n_bodies if n_bodies is not None else _default_n_bodies(body, self.n)
-        mp = None
-        if mu_pair is not None:
-            mp = np.ascontiguousarray(np.asarray(mu_pair, np.float64).reshape(nb, nb))
-        a = StepArgs(self.n, int(nb), int(n_iter), _ptr(body), _ptr(x), _ptr(v), _ptr(Cm), _ptr(m), _ptr(nrm), None,
-                     None, float(h), float(mu), None if mp is None else mp.ctypes.data, int(flags))
+        a, self.n, self.dtype, _keep = _sim_args(x, v, Cm, m, nrm, body, h, mu, n_iter, n_bodies, mu_pair, flags)
         hsim = C.c_void_p()
         _check(lib.apic_sim_open(srv.handle, C.byref(a), C.byref(hsim)))
         self._h = hsim
+
+    def wait(self, ticket, timeout_s: float = 60.0):
+        """Wait for one of this simulation's requests (on its own server)."""
+        return self.srv.wait(ticket, timeout_s)
 
     @classmethod
     def _adopt(cls, srv, handle, n, dtype):
@@ -755,3 +782,76 @@ class Sim:
         if getattr(self, "_h", None):
             load().apic_sim_close(self._h)
             self._h = None
+
+
+class _Member(Server):
+    """A server owned by a Group (not destroyed on its own)."""
+
+    def __init__(self, handle):  # noqa: D401 - no server is created here
+        self._h = handle
+
+    def close(self):
+        self._h = None
+
+
+class Group:
+    """apic_group: one server per device; simulations are admitted on the
+    device with the most HBM budget left (apic_place_by_budget) and stay
+    there.  Nothing crosses devices on the data path."""
+
+    def __init__(self, devices, hbm_budget_per_device: int = 0, n_workers: int = 2, max_batch_scenes: int = 64):
+        lib = load()
+        devs = (C.c_int32 * len(devices))(*[int(d) for d in devices])
+        h = C.c_void_p()
+        _check(lib.apic_group_create(C.byref(h), devs, len(devices), int(hbm_budget_per_device), int(n_workers),
+                                     int(max_batch_scenes)))
+        self._h = h
+        self.members = []
+        for i in range(len(devices)):
+            m = C.c_void_p()
+            _check(lib.apic_group_server(self._h, i, C.byref(m)))
+            self.members.append(_Member(m))
+
+    def open_sim(self, x, v, Cm, m, nrm, body, h, mu, n_iter, n_bodies=None, mu_pair=None, flags=0):
+        """Admit a simulation on the member with the most room; the returned
+        Sim has .member (its index) and waits on its own server."""
+        a, n, dtype, _keep = _sim_args(x, v, Cm, m, nrm, body, h, mu, n_iter, n_bodies, mu_pair, flags)
+        hs, k = C.c_void_p(), C.c_int32()
+        _check(load().apic_group_open(self._h, C.byref(a), C.byref(hs), C.byref(k)))
+        sim = Sim._adopt(self.members[k.value], hs, n, dtype)
+        sim.member = k.value
+        return sim
+
+    def set_policy(self, variant: int = -1, graphs: bool = True):
+        _check(load().apic_group_set_policy(self._h, int(variant), 1 if graphs else 0))
+
+    def stats(self, reset: bool = False) -> dict:
+        st = ServerStats()
+        _check(load().apic_group_get_stats(self._h, C.byref(st), 1 if reset else 0))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().apic_group_destroy(self._h)
+            self._h = None
+            for m in self.members:
+                m.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def place_by_budget(free_bytes, need: int) -> int:
+    """apic_place_by_budget (host only): index of the device with the most
+    room that still holds `need` bytes, or -1."""
+    arr = (C.c_int64 * len(free_bytes))(*[int(b) for b in free_bytes])
+    return int(load().apic_place_by_budget(arr, len(free_bytes), int(need)))

@@ -585,6 +585,158 @@ apic_status apic_sim_close(apic_sim* s) {
   return APIC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Server groups: one server per device, simulations placed by HBM budget.
+// Scenes are independent, so nothing crosses devices on the data path; a
+// request goes to the server that holds its simulation.
+
+int32_t apic_place_by_budget(const int64_t* free_bytes, int32_t n_devices, int64_t need) {
+  if (!free_bytes || n_devices < 1 || need < 0) return -1;
+  int32_t best = -1;
+  for (int32_t i = 0; i < n_devices; ++i)
+    if (free_bytes[i] >= need && (best < 0 || free_bytes[i] > free_bytes[best])) best = i;
+  return best;
+}
+
+apic_status apic_sim_server(apic_sim* s, apic_server** out) {
+  if (!s || !out) return sfail(APIC_ERR_INVALID_ARG, "NULL argument");
+  *out = s->srv;
+  return APIC_OK;
+}
+
+}  // extern "C"
+
+struct apic_group {
+  std::vector<apic_server*> members;
+  std::vector<int32_t> devices;
+};
+
+namespace {
+
+// Bytes a simulation's admission asks of a server (resident state plus the
+// workers' scratch estimate), as apic_sim_open counts them.
+int64_t admission_bytes(const apic_step_args* a) {
+  const size_t es = (a->flags & APIC_FP64) ? 8 : 4;
+  const size_t n = (size_t)a->n;
+  const size_t bytes = n * (3 * sizeof(double) + sizeof(int32_t) + es * (3 + 9 + 1 + 3));
+  return (int64_t)(bytes + n * kScratchPerParticle * (es / 4));
+}
+
+// Bytes a server can still admit (INT64_MAX without a budget).
+int64_t free_bytes(apic_server* srv) {
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (!srv->budget) return INT64_MAX;
+  const size_t used = srv->resident + scratch_total(srv);
+  return used >= srv->budget ? 0 : (int64_t)(srv->budget - used);
+}
+
+}  // namespace
+
+extern "C" {
+
+apic_status apic_group_create(apic_group** out, const int32_t* devices, int32_t n_devices,
+                              size_t hbm_budget_per_device, int32_t n_workers, int32_t max_batch_scenes) {
+  if (!out || !devices || n_devices < 1 || n_devices > 64)
+    return sfail(APIC_ERR_INVALID_ARG, "need 1..64 devices and an output pointer");
+  *out = nullptr;
+  apic_group* g = new apic_group();
+  for (int32_t i = 0; i < n_devices; ++i) {
+    apic_server* srv = nullptr;
+    const apic_status st = apic_server_create(&srv, devices[i], hbm_budget_per_device, n_workers, max_batch_scenes);
+    if (st != APIC_OK) {
+      for (apic_server* m : g->members) apic_server_destroy(m);
+      delete g;
+      return st;
+    }
+    g->members.push_back(srv);
+    g->devices.push_back(devices[i]);
+  }
+  *out = g;
+  return APIC_OK;
+}
+
+apic_status apic_group_destroy(apic_group* g) {
+  if (!g) return APIC_OK;
+  for (apic_server* m : g->members) apic_server_destroy(m);
+  delete g;
+  return APIC_OK;
+}
+
+apic_status apic_group_server(apic_group* g, int32_t member, apic_server** out) {
+  if (!g || !out || member < 0 || member >= (int32_t)g->members.size())
+    return sfail(APIC_ERR_INVALID_ARG, "no such group member");
+  *out = g->members[(size_t)member];
+  return APIC_OK;
+}
+
+apic_status apic_group_set_policy(apic_group* g, int32_t variant, int32_t graphs) {
+  if (!g) return sfail(APIC_ERR_INVALID_ARG, "group is NULL");
+  for (apic_server* m : g->members) {
+    const apic_status st = apic_server_set_policy(m, variant, graphs);
+    if (st != APIC_OK) return st;
+  }
+  return APIC_OK;
+}
+
+apic_status apic_group_open(apic_group* g, const apic_step_args* a, apic_sim** out, int32_t* member) {
+  if (!g || !a || !out) return sfail(APIC_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  const int64_t need = admission_bytes(a);
+  const int32_t nm = (int32_t)g->members.size();
+  std::vector<int64_t> room((size_t)nm);
+  for (int32_t i = 0; i < nm; ++i) room[(size_t)i] = free_bytes(g->members[(size_t)i]);
+  // most room first; a member that refuses (others admitted meanwhile) is
+  // dropped from the candidates
+  for (int32_t tries = 0; tries < nm; ++tries) {
+    const int32_t k = apic_place_by_budget(room.data(), nm, need);
+    if (k < 0) break;
+    const apic_status st = apic_sim_open(g->members[(size_t)k], a, out);
+    if (st == APIC_OK) {
+      if (member) *member = k;
+      return APIC_OK;
+    }
+    if (st != APIC_ERR_ADMISSION) return st;
+    room[(size_t)k] = -1;
+  }
+  return sfail(APIC_ERR_ADMISSION, "no device of the group has room for this simulation now");
+}
+
+apic_status apic_group_get_stats(apic_group* g, apic_server_stats* out, int32_t reset) {
+  if (!g || !out) return sfail(APIC_ERR_INVALID_ARG, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  std::vector<double> lat;
+  int64_t scenes = 0;
+  for (apic_server* m : g->members) {
+    std::lock_guard<std::mutex> lk(m->mu);
+    out->completed += m->completed;
+    out->failed += m->failed;
+    out->batches += m->batches;
+    out->particle_iters += m->particle_iters;
+    out->resident_bytes += (int64_t)m->resident;
+    out->open_sims += m->open;
+    scenes += m->batch_scenes;
+    lat.insert(lat.end(), m->lat_ms.begin(), m->lat_ms.end());
+    if (reset) {
+      m->lat_ms.clear();
+      m->completed = m->failed = m->batches = m->particle_iters = m->batch_scenes = 0;
+    }
+  }
+  out->mean_batch_scenes = out->batches ? (double)scenes / (double)out->batches : 0.0;
+  if (!lat.empty()) {
+    auto pct = [&](double q) {
+      const size_t k = std::min(lat.size() - 1, (size_t)(q * (double)(lat.size() - 1) + 0.5));
+      std::nth_element(lat.begin(), lat.begin() + (ptrdiff_t)k, lat.end());
+      return lat[k];
+    };
+    double sum = 0;
+    for (double d : lat) sum += d;
+    out->latency_mean_ms = sum / (double)lat.size();
+    out->latency_p50_ms = pct(0.50);
+    out->latency_p99_ms = pct(0.99);
+  }
+  return APIC_OK;
+}
+
 apic_status apic_server_get_stats(apic_server* srv, apic_server_stats* out, int32_t reset) {
   if (!srv || !out) return sfail(APIC_ERR_INVALID_ARG, "NULL argument");
   std::lock_guard<std::mutex> lk(srv->mu);
