@@ -20,10 +20,10 @@ constexpr int kBlk = 4;
 constexpr int kTile = 7;
 constexpr int kTile3 = kTile * kTile * kTile;
 constexpr int kNodesPerBlock = kBlk * kBlk * kBlk;
-// A work item holds at most kChunk particles (one per thread of its CTA);
-// kernel variants may use smaller CTAs and items (kVariantChunk).
+// A work item holds at most kChunk particles; each kernel variant has its
+// own largest item (kVariantChunk).
 #ifndef APIC_CHUNK
-#define APIC_CHUNK 128
+#define APIC_CHUNK 256
 #endif
 constexpr int kChunk = APIC_CHUNK;
 
@@ -176,16 +176,20 @@ cudaError_t launch_compact(int64_t n, const int* flags, const int* offs, int* li
 template <class K>
 cudaError_t launch_mark_items(const int* item_start, const int4* item_info, const int* n_items, const K* keys,
                               int64_t n, int max_items, const SceneDev* sc, int* flags, cudaStream_t s);
-// Variants of the fused transfer kernel: CTA size (= the largest work item),
-// resident CTAs per SM it is compiled for (its register cap), and how P2G
-// lanes get their row weights m N_y N_z (recomputed per lane from t, or read
-// from factors stashed per particle in phase 1: fewer instructions, one more
-// stash row).  Variant 0 is the default; the FP32 path exists in all of
-// them, the FP64 path in variant 0 only (which it always uses).
-constexpr int kNumVariants = 7;
-constexpr int kVariantChunk[kNumVariants] = {128, 128, 128, 64, 64, 128, 128};
-constexpr int kVariantMinBlocks[kNumVariants] = {8, 9, 7, 13, 16, 8, 7};
-constexpr bool kVariantRowTab[kNumVariants] = {false, false, false, false, false, true, true};
+// Variants of the fused transfer kernel: CTA size, particles per thread in
+// phase 1 (= stencil rows per lane in phase 2, "RPL"), the largest work item
+// (CTA size x RPL), resident CTAs per SM it is compiled for (its register
+// cap), and how P2G lanes get their row weights m N_y N_z (recomputed per
+// lane from t, or read from factors stashed per particle in phase 1: fewer
+// instructions, one more stash row).  Variant 0 is the default; the FP32
+// path exists in all of them, the FP64 path in variant 0 only (which it
+// always uses).
+constexpr int kNumVariants = 8;
+constexpr int kVariantThreads[kNumVariants] = {128, 128, 128, 64, 64, 128, 128, 128};
+constexpr int kVariantRPL[kNumVariants] = {1, 1, 1, 1, 1, 1, 1, 2};
+constexpr int kVariantChunk[kNumVariants] = {128, 128, 128, 64, 64, 128, 128, 256};
+constexpr int kVariantMinBlocks[kNumVariants] = {8, 9, 7, 13, 16, 8, 7, 5};
+constexpr bool kVariantRowTab[kNumVariants] = {false, false, false, false, false, true, true, false};
 // overlap: launch with programmatic stream serialization, so that the grid's
 // prologue (item metadata, particle loads, page lookups) runs while the grid
 // before it finishes.  Only for a launch that directly follows another

@@ -388,31 +388,38 @@ __device__ __forceinline__ float from_fx(long long g, float inv_S) {
   return fmaf(hi, 4294967296.f, lo) * inv_S;
 }
 
-// One work item = up to CHUNK sorted particles of one body whose cells lie
-// in one grid block.  A CTA of CHUNK threads runs it in two phases:
+// One work item = up to CHUNK * RPL sorted particles of one body whose
+// cells lie in one grid block.  A CTA of CHUNK threads runs it in two
+// phases:
 //
-//  phase 1, one thread per particle (lanes sorted by cell, so neighbouring
-//    lanes read the same tile nodes): G2P from the 7^3-node shared tile of
-//    grid velocities, the Sec. 2.3 series update of Delta, the Sec. 2.4
-//    projection giving W, and a stash of (t, m, W) in shared memory;
-//  phase 2, cell-centric P2G: each half-warp walks 16 consecutive stashed
-//    particles; lane (ky, kz) owns stencil row (., ky, kz) of the current
-//    cell and keeps its 4 nodes x 3 components in registers, adding them to
-//    the shared P2G tile only when the cell changes.  No two lanes of a
-//    half-warp ever add to the same node.
+//  phase 1, one thread per particle, RPL particles per thread (lanes sorted
+//    by cell, so neighbouring lanes read the same tile nodes): G2P from the
+//    7^3-node shared tile of grid velocities, the Sec. 2.3 series update of
+//    Delta, the Sec. 2.4 projection giving W, and a stash of (t, m, W) in
+//    shared memory;
+//  phase 2, cell-centric P2G: a group of 16 / RPL lanes walks 16
+//    consecutive stashed particles; each lane owns RPL stencil rows
+//    (., ky, kz) of the current cell and keeps their 4 nodes x 3 components
+//    in registers, adding them to the shared P2G tile only when the cell
+//    changes.  No two lanes of a group ever add to the same node.  With
+//    RPL = 2 a group is 8 lanes, so a stashed record is read by 8 lanes
+//    instead of 16, and a warp walks 64 particles.
 //
 // The shared P2G tile is then added to the global grid (FP64 at nodes that
 // two or more bodies touch, on the FP32 path).
 //
-// CHUNK is the CTA size (and the largest item), MINB the number of resident
-// CTAs per SM the kernel is compiled for (its register cap); the autotuner
-// picks among the (kVariantChunk, kVariantMinBlocks) pairs.
+// CHUNK is the CTA size, CHUNK * RPL the largest item, MINB the number of
+// resident CTAs per SM the kernel is compiled for (its register cap); the
+// autotuner picks among the variants of apic_internal.h.
 //
 // DET (deterministic mode, FP32): the shared tile and the global node sums
 // hold scaled int64 terms (fixed point) instead of floating-point sums.
-template <class T, int MODE, int MINB, int CHUNK, bool ROWTAB, bool DET = false>
+template <class T, int MODE, int MINB, int CHUNK, bool ROWTAB, bool DET = false, int RPL = 1>
 __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
-  constexpr int kStashN = CHUNK + CHUNK / 16;
+  static_assert(RPL == 1 || RPL == 2, "one or two stencil rows per lane");
+  constexpr int kItem = CHUNK * RPL;  // particles of the largest item
+  constexpr int kStashN = kItem + kItem / 16;
+  constexpr int kGroup = 16 / RPL;    // lanes that walk one run of 16 particles in phase 2
   constexpr bool kG2P = MODE == kModeFirst || MODE == kModeMid || MODE == kModeLast || MODE == kModeOnly;
   constexpr bool kP2G = MODE == kModeMassV || MODE == kModeFirst || MODE == kModeMid;
   constexpr bool kMass = MODE == kModeMassV;  // also accumulates m_i and the body mask
@@ -424,7 +431,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   __shared__ Acc sacc[kP2G ? kComp : 1][kTile3];
   __shared__ unsigned s_fxmax;
   __shared__ V4<T> stash[kP2G ? (ROWTAB ? 7 : 6) : 1][kP2G ? kStashN : 1];
-  __shared__ int sloc[CHUNK];
+  __shared__ int sloc[kItem];
   __shared__ int snb[27];
   const int tid = threadIdx.x;
   const int n = p.n_particles;
@@ -437,15 +444,13 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   const int4 info = p.item_info[item];
   const SceneDev& S = p.sc[info.z];
   const Box box = S.box;
-  const long long page_off = S.page_off;
-  const int blin = (int)(info.x - page_off);
-  const int bx = blin % box.nx;
-  const int by = (blin / box.nx) % box.ny;
-  const int bz = blin / (box.nx * box.ny);
   const int body = info.y;
   const int s0 = p.item_start[item];
   const int s1 = item + 1 < p.n_items ? p.item_start[item + 1] : n;
-  const int count = s1 - s0;  // <= CHUNK
+  const int count = s1 - s0;  // <= kItem
+  // phase-1 slot of this thread's r-th particle: warp w holds the slots
+  // [32 RPL w, 32 RPL (w + 1)), the ones its phase-2 groups walk
+  const int wslot = (tid >> 5) * (32 * RPL) + (tid & 31);
   // Particles are sorted by cell (z-major) inside an item, so its stencils
   // reach only tile layers c in [lz(first), lz(last) + 3]: fetch, clear and
   // flush just those.
@@ -455,20 +460,27 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   // while the CTA fetches its grid tile.
   constexpr bool kReadD = MODE == kModeMid || MODE == kModeLast;
   constexpr bool kReadV = MODE == kModeMassV || MODE == kModeFirst || MODE == kModeOnly;
-  V4<T> pt{}, pn{}, q0{}, q1{}, q2{};
-  if (tid < count) {
-    const int s = s0 + tid;
-    pt = p.pt[s];
-    pn = p.pn[s];
-    if (kReadV) {
-      q0 = p.V[s];
-      q1 = p.V[n + s];
-      q2 = p.V[2 * n + s];
+  V4<T> ptr_[RPL], pnr_[RPL], q0r[RPL], q1r[RPL], q2r[RPL];
+#pragma unroll
+  for (int r = 0; r < RPL; ++r) {
+    ptr_[r] = pnr_[r] = q0r[r] = q1r[r] = q2r[r] = V4<T>{};
+    const int j = wslot + 32 * r;
+    if (j < count) {
+      const int s = s0 + j;
+      ptr_[r] = p.pt[s];
+      pnr_[r] = p.pn[s];
+      if (kReadV) {
+        q0r[r] = p.V[s];
+        q1r[r] = p.V[n + s];
+        q2r[r] = p.V[2 * n + s];
+      }
     }
   }
   if (tid < 27) {
+    // the 3x3x3 blocks around the item's block (info.x is its global page
+    // index; every particle block keeps a one-block margin inside its box)
     const int ox = tid % 3 - 1, oy = (tid / 3) % 3 - 1, oz = tid / 9 - 1;
-    snb[tid] = p.page[page_off + ((bz + oz) * box.ny + (by + oy)) * box.nx + (bx + ox)];
+    snb[tid] = p.page[(long long)info.x + ((long long)oz * box.ny + oy) * box.nx + ox];
   }
   if (kP2G)
     for (int t = t_lo + tid; t < t_hi; t += CHUNK)
@@ -490,11 +502,17 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
     if (MODE == kModeFirst || MODE == kModeMid)
       fxS = fx_scale(fxs, p.fx_slot, fx_head(p.fx_err, p.fx_attempt, info.z), S.n, &fx_ok);
   }
-  if (kReadD && tid < count) {
-    const int s = s0 + tid;
-    q0 = p.D[s];
-    q1 = p.D[n + s];
-    q2 = p.D[2 * n + s];
+  if (kReadD) {
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+      const int j = wslot + 32 * r;
+      if (j < count) {
+        const int s = s0 + j;
+        q0r[r] = p.D[s];
+        q1r[r] = p.D[n + s];
+        q2r[r] = p.D[2 * n + s];
+      }
+    }
   }
   __syncthreads();
   if (kG2P) {
@@ -544,236 +562,257 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
     if (!__syncthreads_or(other)) {
       // no other body anywhere in the tile: every particle keeps mu(b, b),
       // as the blend below would give it (no other body's mass in reach)
-      if (tid < count)
-        p.mup_out[s0 + tid] = S.mu_off < 0 ? (T)S.mu : p.mu_table[S.mu_off + body * S.n_bodies + body];
+#pragma unroll
+      for (int r = 0; r < RPL; ++r)
+        if (wslot + 32 * r < count)
+          p.mup_out[s0 + wslot + 32 * r] =
+              S.mu_off < 0 ? (T)S.mu : p.mu_table[S.mu_off + body * S.n_bodies + body];
       return;
     }
   }
 
   // ---------------- phase 1: one thread per particle ----------------
-  if (tid < count) {
-    const int s = s0 + tid;
-    const uint32_t loc = to_bits(pn.w);
-    const int base = (int)(loc >> 4) * (kTile * kTile) + (int)((loc >> 2) & 3) * kTile + (int)(loc & 3);
-    sloc[tid] = base;
-    if (MODE == kModeMu && S.mu_off < 0) {
-      p.mup_out[s] = (T)S.mu;  // a scene with one scalar mu
-    } else if (MODE == kModeMu) {
-      // mu_p = sum_{b' != b} mu(b,b') M_b'p / sum_{b' != b} M_b'p with
-      // M_b'p = sum_i N_ip m_{b',i}; mu(b,b) when no other body is near.
-      T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4];
-      bspline(pt.x, wx, dx);
-      bspline(pt.y, wy, dy);
-      bspline(pt.z, wz, dz);
-      T num = T(0), den = T(0);
-      const uint32_t own = 1u << body;
-#pragma unroll 1
-      for (int q = 0; q < 64; ++q) {
-        const int kx = q & 3, ky = (q >> 2) & 3, kz = q >> 4;
-        const int tq = base + kz * (kTile * kTile) + ky * kTile + kx;
-        uint32_t other = smask[tq] & ~own;
-        if (!other) continue;
-        const int node = tile_node(snb, tq);
-        T wxk = kx == 0 ? wx[0] : kx == 1 ? wx[1] : kx == 2 ? wx[2] : wx[3];
-        T wyk = ky == 0 ? wy[0] : ky == 1 ? wy[1] : ky == 2 ? wy[2] : wy[3];
-        T wzk = kz == 0 ? wz[0] : kz == 1 ? wz[1] : kz == 2 ? wz[2] : wz[3];
-        const T w = wxk * wyk * wzk;
-        while (other) {
-          const int bo = __ffs(other) - 1;
-          other &= other - 1;
-          const T M = DET ? (T)from_fx(p.gmb_fx[(int64_t)bo * p.n_nodes + node], 1.f / fxSm)
-                          : p.gmb[(int64_t)bo * p.n_nodes + node];
-          num += w * p.mu_table[S.mu_off + body * S.n_bodies + bo] * M;
-          den += w * M;
-        }
-      }
-      p.mup_out[s] = den > T(0) ? num / den : p.mu_table[S.mu_off + body * S.n_bodies + body];
-    } else if (MODE == kModeNormals) {
-      // rho = sum N m_b and g = sum grad N m_b (cell units) over the body's
-      // own node masses, sum-factorised; n = -g/|g| on the surface, else 0
-      T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4], gx[4], gy[4], gz[4];
-      bspline(pt.x, wx, dx);
-      bspline(pt.y, wy, dy);
-      bspline(pt.z, wz, dz);
-      bspline_grad(pt.x, gx);
-      bspline_grad(pt.y, gy);
-      bspline_grad(pt.z, gz);
-      T rho = T(0), g0 = T(0), g1 = T(0), g2 = T(0);
 #pragma unroll
-      for (int kz = 0; kz < 4; ++kz) {
-        T r = T(0), ry = T(0), rx = T(0);  // sum over y of N_y (N_x m), of gN_y (N_x m), of N_y (gN_x m)
-#pragma unroll
-        for (int ky = 0; ky < 4; ++ky) {
-          T a = T(0), ad = T(0);
-#pragma unroll
-          for (int kx = 0; kx < 4; ++kx) {
-            const T mi = smass[base + kz * (kTile * kTile) + ky * kTile + kx];
-            a += wx[kx] * mi;
-            ad += gx[kx] * mi;
-          }
-          r += wy[ky] * a;
-          ry += gy[ky] * a;
-          rx += wy[ky] * ad;
-        }
-        rho += wz[kz] * r;
-        g0 += wz[kz] * rx;
-        g1 += wz[kz] * ry;
-        g2 += gz[kz] * r;
-      }
-      const T len = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
-      const bool surf = rho > T(0) && len > (T)S.nthr * rho;
-      const T inv = surf ? -T(1) / len : T(0);
-      const T nn[3] = {g0 * inv, g1 * inv, g2 * inv};
-      if (p.normals_out) {
-        const int64_t idx = p.perm[s] - S.part_off;
-        T* o = static_cast<T*>(S.v_out);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) o[3 * idx + a] = nn[a];
-      } else {
-        p.pn_out[s] = V4<T>{nn[0], nn[1], nn[2], pn.w};
-      }
-    } else if (MODE == kModeMassV) {
-      T wx[4], dx[4];
-      bspline(pt.x, wx, dx);
-      if constexpr (ROWTAB) {
-        T wy[4], dy[4], wz[4], dz[4];
+  for (int r = 0; r < RPL; ++r) {
+    const int j = wslot + 32 * r;
+    const V4<T> pt = ptr_[r], pn = pnr_[r];
+    V4<T> q0 = q0r[r], q1 = q1r[r], q2 = q2r[r];
+    if (j < count) {
+      const int s = s0 + j;
+      const uint32_t loc = to_bits(pn.w);
+      const int base = (int)(loc >> 4) * (kTile * kTile) + (int)((loc >> 2) & 3) * kTile + (int)(loc & 3);
+      sloc[j] = base;
+      if (MODE == kModeMu && S.mu_off < 0) {
+        p.mup_out[s] = (T)S.mu;  // a scene with one scalar mu
+      } else if (MODE == kModeMu) {
+        // mu_p = sum_{b' != b} mu(b,b') M_b'p / sum_{b' != b} M_b'p with
+        // M_b'p = sum_i N_ip m_{b',i}; mu(b,b) when no other body is near.
+        T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4];
+        bspline(pt.x, wx, dx);
         bspline(pt.y, wy, dy);
         bspline(pt.z, wz, dz);
-        stash[0][sidx(tid)] = V4<T>{pt.w * wy[0], pt.w * wy[1], pt.w * wy[2], pt.w * wy[3]};
-        stash[ROWTAB ? 6 : 0][sidx(tid)] = V4<T>{wz[0], wz[1], wz[2], wz[3]};
-        if (!p.pic) {
-          // fold the particle's own offset into v: v_c - Ch_c1 t_y - Ch_c2 t_z
-          q0.x -= q1.x * pt.y + q1.y * pt.z;
-          q0.y -= q1.w * pt.y + q2.x * pt.z;
-          q0.z -= q2.z * pt.y + q2.w * pt.z;
+        T num = T(0), den = T(0);
+        const uint32_t own = 1u << body;
+  #pragma unroll 1
+        for (int q = 0; q < 64; ++q) {
+          const int kx = q & 3, ky = (q >> 2) & 3, kz = q >> 4;
+          const int tq = base + kz * (kTile * kTile) + ky * kTile + kx;
+          uint32_t other = smask[tq] & ~own;
+          if (!other) continue;
+          const int node = tile_node(snb, tq);
+          T wxk = kx == 0 ? wx[0] : kx == 1 ? wx[1] : kx == 2 ? wx[2] : wx[3];
+          T wyk = ky == 0 ? wy[0] : ky == 1 ? wy[1] : ky == 2 ? wy[2] : wy[3];
+          T wzk = kz == 0 ? wz[0] : kz == 1 ? wz[1] : kz == 2 ? wz[2] : wz[3];
+          const T w = wxk * wyk * wzk;
+          while (other) {
+            const int bo = __ffs(other) - 1;
+            other &= other - 1;
+            const T M = DET ? (T)from_fx(p.gmb_fx[(int64_t)bo * p.n_nodes + node], 1.f / fxSm)
+                            : p.gmb[(int64_t)bo * p.n_nodes + node];
+            num += w * p.mu_table[S.mu_off + body * S.n_bodies + bo] * M;
+            den += w * M;
+          }
         }
-      } else {
-        stash[0][sidx(tid)] = pt;
-      }
-      stash[4][sidx(tid)] = V4<T>{wx[0], wx[1], wx[2], wx[3]};
-      stash[5][sidx(tid)] = V4<T>{wx[0] * dx[0], wx[1] * dx[1], wx[2] * dx[2], wx[3] * dx[3]};
-      stash[1][sidx(tid)] = q0;
-      stash[2][sidx(tid)] = q1;
-      stash[3][sidx(tid)] = q2;
-    } else {
-      T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4];
-      bspline(pt.x, wx, dx);
-      bspline(pt.y, wy, dy);
-      bspline(pt.z, wz, dz);
-      T hv[3], hC[9];
-      if (p.pic)
-        g2p_tile<T, false>(sv, base, wx, dx, wy, dy, wz, dz, hv, hC);
-      else if constexpr (sizeof(T) == 4)
-        g2p_tile_f32(sv, base, wx, dx, wy, dy, wz, dz, hv, hC);
-      else
-        g2p_tile<T, true>(sv, base, wx, dx, wy, dy, wz, dz, hv, hC);
-      const T nrm[3] = {pn.x, pn.y, pn.z};
-      const T mu = p.mup ? p.mup[s] : (T)S.mu;
-      T dv[3], dC[9];
-      bool out = false;
-      if (MODE == kModeFirst || MODE == kModeOnly) {
-        // Delta_0 = H V - V
-        const T v[3] = {q0.x, q0.y, q0.z};
-        const T C[9] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) dv[a] = hv[a] - v[a];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) dC[a] = p.pic ? T(0) : hC[a] - C[a];
-        out = MODE == kModeOnly;
-      } else {
-        // Delta_m = Delta_{m-1} + H W_m - W_m, W_m recomputed from Delta_{m-1}
-        const T pv[3] = {q0.x, q0.y, q0.z};
-        const T pC[9] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
-        T wv[3], wC[9];
-        undesirable(pv, pC, nrm, mu, p.sep23, wv, wC);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) dv[a] = pv[a] + hv[a] - wv[a];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) dC[a] = p.pic ? T(0) : pC[a] + hC[a] - wC[a];
-        out = MODE == kModeLast;
-      }
-      if (DET && out && __ldcg(p.fx_err + p.fx_attempt * (p.n_scenes + 1) + p.n_scenes) != 0) {
-        // an earlier pass of this attempt exceeded its fixed-point range in
-        // some scene: the step is repeated (or fails), and no scene's outputs
-        // are written by this attempt
-      } else if (out) {
-        // V_hat = V + Delta_N, back in caller order, C = Ch / h
-        T v[3], C[9];
-        load12(p.V, n, s, v, C);
-        const int64_t idx = p.perm[s] - S.part_off;
-        T* vo = static_cast<T*>(S.v_out);
-        T* Co = static_cast<T*>(S.C_out);
-        const T inv_h = (T)S.inv_h;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) vo[3 * idx + a] = v[a] + dv[a];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) Co[9 * idx + a] = (C[a] + dC[a]) * inv_h;
-      } else {
-        store12(p.D, n, s, dv, dC);
-        T u[3], uC[9];
-        undesirable(dv, dC, nrm, mu, p.sep23, u, uC);
-        if constexpr (DET) {
-          const float b = fx_bound(pt.w, u, uC);
-          fx_bad = !(b <= fx_ok);
-          atomicMax(&s_fxmax, __float_as_uint(b));
+        p.mup_out[s] = den > T(0) ? num / den : p.mu_table[S.mu_off + body * S.n_bodies + body];
+      } else if (MODE == kModeNormals) {
+        // rho = sum N m_b and g = sum grad N m_b (cell units) over the body's
+        // own node masses, sum-factorised; n = -g/|g| on the surface, else 0
+        T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4], gx[4], gy[4], gz[4];
+        bspline(pt.x, wx, dx);
+        bspline(pt.y, wy, dy);
+        bspline(pt.z, wz, dz);
+        bspline_grad(pt.x, gx);
+        bspline_grad(pt.y, gy);
+        bspline_grad(pt.z, gz);
+        T rho = T(0), g0 = T(0), g1 = T(0), g2 = T(0);
+  #pragma unroll
+        for (int kz = 0; kz < 4; ++kz) {
+          T r = T(0), ry = T(0), rx = T(0);  // sum over y of N_y (N_x m), of gN_y (N_x m), of N_y (gN_x m)
+  #pragma unroll
+          for (int ky = 0; ky < 4; ++ky) {
+            T a = T(0), ad = T(0);
+  #pragma unroll
+            for (int kx = 0; kx < 4; ++kx) {
+              const T mi = smass[base + kz * (kTile * kTile) + ky * kTile + kx];
+              a += wx[kx] * mi;
+              ad += gx[kx] * mi;
+            }
+            r += wy[ky] * a;
+            ry += gy[ky] * a;
+            rx += wy[ky] * ad;
+          }
+          rho += wz[kz] * r;
+          g0 += wz[kz] * rx;
+          g1 += wz[kz] * ry;
+          g2 += gz[kz] * r;
         }
+        const T len = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
+        const bool surf = rho > T(0) && len > (T)S.nthr * rho;
+        const T inv = surf ? -T(1) / len : T(0);
+        const T nn[3] = {g0 * inv, g1 * inv, g2 * inv};
+        if (p.normals_out) {
+          const int64_t idx = p.perm[s] - S.part_off;
+          T* o = static_cast<T*>(S.v_out);
+  #pragma unroll
+          for (int a = 0; a < 3; ++a) o[3 * idx + a] = nn[a];
+        } else {
+          p.pn_out[s] = V4<T>{nn[0], nn[1], nn[2], pn.w};
+        }
+      } else if (MODE == kModeMassV) {
+        T wx[4], dx[4];
+        bspline(pt.x, wx, dx);
         if constexpr (ROWTAB) {
-          stash[0][sidx(tid)] = V4<T>{pt.w * wy[0], pt.w * wy[1], pt.w * wy[2], pt.w * wy[3]};
-          stash[ROWTAB ? 6 : 0][sidx(tid)] = V4<T>{wz[0], wz[1], wz[2], wz[3]};
-          if (!p.pic) {  // fold the particle's own offset into u: u_c - Ch_c1 t_y - Ch_c2 t_z
-            u[0] -= uC[1] * pt.y + uC[2] * pt.z;
-            u[1] -= uC[4] * pt.y + uC[5] * pt.z;
-            u[2] -= uC[7] * pt.y + uC[8] * pt.z;
+          T wy[4], dy[4], wz[4], dz[4];
+          bspline(pt.y, wy, dy);
+          bspline(pt.z, wz, dz);
+          stash[0][sidx(j)] = V4<T>{pt.w * wy[0], pt.w * wy[1], pt.w * wy[2], pt.w * wy[3]};
+          stash[ROWTAB ? 6 : 0][sidx(j)] = V4<T>{wz[0], wz[1], wz[2], wz[3]};
+          if (!p.pic) {
+            // fold the particle's own offset into v: v_c - Ch_c1 t_y - Ch_c2 t_z
+            q0.x -= q1.x * pt.y + q1.y * pt.z;
+            q0.y -= q1.w * pt.y + q2.x * pt.z;
+            q0.z -= q2.z * pt.y + q2.w * pt.z;
           }
         } else {
-          stash[0][sidx(tid)] = pt;
+          stash[0][sidx(j)] = pt;
         }
-        stash[1][sidx(tid)] = V4<T>{u[0], u[1], u[2], uC[0]};
-        stash[2][sidx(tid)] = V4<T>{uC[1], uC[2], uC[3], uC[4]};
-        stash[3][sidx(tid)] = V4<T>{uC[5], uC[6], uC[7], uC[8]};
-        stash[4][sidx(tid)] = V4<T>{wx[0], wx[1], wx[2], wx[3]};
-        stash[5][sidx(tid)] = V4<T>{wx[0] * dx[0], wx[1] * dx[1], wx[2] * dx[2], wx[3] * dx[3]};
+        stash[4][sidx(j)] = V4<T>{wx[0], wx[1], wx[2], wx[3]};
+        stash[5][sidx(j)] = V4<T>{wx[0] * dx[0], wx[1] * dx[1], wx[2] * dx[2], wx[3] * dx[3]};
+        stash[1][sidx(j)] = q0;
+        stash[2][sidx(j)] = q1;
+        stash[3][sidx(j)] = q2;
+      } else {
+        T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4];
+        bspline(pt.x, wx, dx);
+        bspline(pt.y, wy, dy);
+        bspline(pt.z, wz, dz);
+        T hv[3], hC[9];
+        if (p.pic)
+          g2p_tile<T, false>(sv, base, wx, dx, wy, dy, wz, dz, hv, hC);
+        else if constexpr (sizeof(T) == 4)
+          g2p_tile_f32(sv, base, wx, dx, wy, dy, wz, dz, hv, hC);
+        else
+          g2p_tile<T, true>(sv, base, wx, dx, wy, dy, wz, dz, hv, hC);
+        const T nrm[3] = {pn.x, pn.y, pn.z};
+        const T mu = p.mup ? p.mup[s] : (T)S.mu;
+        T dv[3], dC[9];
+        bool out = false;
+        if (MODE == kModeFirst || MODE == kModeOnly) {
+          // Delta_0 = H V - V
+          const T v[3] = {q0.x, q0.y, q0.z};
+          const T C[9] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+  #pragma unroll
+          for (int a = 0; a < 3; ++a) dv[a] = hv[a] - v[a];
+  #pragma unroll
+          for (int a = 0; a < 9; ++a) dC[a] = p.pic ? T(0) : hC[a] - C[a];
+          out = MODE == kModeOnly;
+        } else {
+          // Delta_m = Delta_{m-1} + H W_m - W_m, W_m recomputed from Delta_{m-1}
+          const T pv[3] = {q0.x, q0.y, q0.z};
+          const T pC[9] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+          T wv[3], wC[9];
+          undesirable(pv, pC, nrm, mu, p.sep23, wv, wC);
+  #pragma unroll
+          for (int a = 0; a < 3; ++a) dv[a] = pv[a] + hv[a] - wv[a];
+  #pragma unroll
+          for (int a = 0; a < 9; ++a) dC[a] = p.pic ? T(0) : pC[a] + hC[a] - wC[a];
+          out = MODE == kModeLast;
+        }
+        if (DET && out && __ldcg(p.fx_err + p.fx_attempt * (p.n_scenes + 1) + p.n_scenes) != 0) {
+          // an earlier pass of this attempt exceeded its fixed-point range in
+          // some scene: the step is repeated (or fails), and no scene's outputs
+          // are written by this attempt
+        } else if (out) {
+          // V_hat = V + Delta_N, back in caller order, C = Ch / h
+          T v[3], C[9];
+          load12(p.V, n, s, v, C);
+          const int64_t idx = p.perm[s] - S.part_off;
+          T* vo = static_cast<T*>(S.v_out);
+          T* Co = static_cast<T*>(S.C_out);
+          const T inv_h = (T)S.inv_h;
+  #pragma unroll
+          for (int a = 0; a < 3; ++a) vo[3 * idx + a] = v[a] + dv[a];
+  #pragma unroll
+          for (int a = 0; a < 9; ++a) Co[9 * idx + a] = (C[a] + dC[a]) * inv_h;
+        } else {
+          store12(p.D, n, s, dv, dC);
+          T u[3], uC[9];
+          undesirable(dv, dC, nrm, mu, p.sep23, u, uC);
+          if constexpr (DET) {
+            const float b = fx_bound(pt.w, u, uC);
+            fx_bad = fx_bad || !(b <= fx_ok);
+            atomicMax(&s_fxmax, __float_as_uint(b));
+          }
+          if constexpr (ROWTAB) {
+            stash[0][sidx(j)] = V4<T>{pt.w * wy[0], pt.w * wy[1], pt.w * wy[2], pt.w * wy[3]};
+            stash[ROWTAB ? 6 : 0][sidx(j)] = V4<T>{wz[0], wz[1], wz[2], wz[3]};
+            if (!p.pic) {  // fold the particle's own offset into u: u_c - Ch_c1 t_y - Ch_c2 t_z
+              u[0] -= uC[1] * pt.y + uC[2] * pt.z;
+              u[1] -= uC[4] * pt.y + uC[5] * pt.z;
+              u[2] -= uC[7] * pt.y + uC[8] * pt.z;
+            }
+          } else {
+            stash[0][sidx(j)] = pt;
+          }
+          stash[1][sidx(j)] = V4<T>{u[0], u[1], u[2], uC[0]};
+          stash[2][sidx(j)] = V4<T>{uC[1], uC[2], uC[3], uC[4]};
+          stash[3][sidx(j)] = V4<T>{uC[5], uC[6], uC[7], uC[8]};
+          stash[4][sidx(j)] = V4<T>{wx[0], wx[1], wx[2], wx[3]};
+          stash[5][sidx(j)] = V4<T>{wx[0] * dx[0], wx[1] * dx[1], wx[2] * dx[2], wx[3] * dx[3]};
+        }
       }
     }
   }
   if (!kP2G) return;
-  // Half-warp h of phase 2 walks particles 16h .. 16h+15, which lanes of its
-  // own warp stashed in phase 1: ordering within the warp is enough.
+  // Group g of phase 2 walks particles 16g .. 16g+15, which lanes of its own
+  // warp stashed in phase 1: ordering within the warp is enough.
   __syncwarp();
 
   // ---------------- phase 2: cell-centric P2G ----------------
   {
-    const int hw = tid >> 4, lane = tid & 15;
-    const int ky = lane & 3, kz = lane >> 2;
-    T cy0, cy1, cy2, cz0, cz1, cz2;
+    const int grp = tid / kGroup, lg = tid % kGroup;
+    const int ky = lg & 3, kz0 = lg >> 2;  // rows (ky, kz0 + k 4 / RPL), k < RPL
+    T cy0, cy1, cy2, cz0[RPL], cz1[RPL], cz2[RPL], oz[RPL];
+    int kzr[RPL];
     row_poly(ky, cy0, cy1, cy2);
-    row_poly(kz, cz0, cz1, cz2);
-    const T oy = T(ky - 1), oz = T(kz - 1);
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      kzr[k] = kz0 + k * (4 / RPL);
+      row_poly(kzr[k], cz0[k], cz1[k], cz2[k]);
+      oz[k] = T(kzr[k] - 1);
+    }
+    const T oy = T(ky - 1);
     const bool aff = !p.pic;
-    RowAcc<T, 3> acc;
-    RowAcc<T, 1> macc;  // mass, when this pass also scatters mass (kModeMassV)
-    acc.zero();
-    macc.zero();
+    RowAcc<T, 3> acc[RPL];
+    RowAcc<T, 1> macc[RPL];  // mass, when this pass also scatters mass (kModeMassV)
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      acc[k].zero();
+      macc[k].zero();
+    }
     int cur = -1;
-    const int j0 = hw * 16, j1 = min(j0 + 16, count);
+    const int j0 = grp * 16, j1 = min(j0 + 16, count);
     auto flush = [&](int base) {
-      const int row = base + kz * (kTile * kTile) + ky * kTile;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if constexpr (DET) {
+      for (int kk = 0; kk < RPL; ++kk) {
+        const int row = base + kzr[kk] * (kTile * kTile) + ky * kTile;
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-            atomicAdd(reinterpret_cast<unsigned long long*>(&sacc[c][row + k]), to_fx(acc.get(k, c), fxS));
-          if constexpr (MODE == kModeMassV)
-            atomicAdd(reinterpret_cast<unsigned long long*>(&sacc[3][row + k]), to_fx(macc.get(k, 0), fxSm));
-        } else {
+        for (int k = 0; k < 4; ++k) {
+          if constexpr (DET) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) atomicAdd(&sacc[c][row + k], acc.get(k, c));
-          if constexpr (MODE == kModeMassV) atomicAdd(&sacc[3][row + k], macc.get(k, 0));
+            for (int c = 0; c < 3; ++c)
+              atomicAdd(reinterpret_cast<unsigned long long*>(&sacc[c][row + k]), to_fx(acc[kk].get(k, c), fxS));
+            if constexpr (MODE == kModeMassV)
+              atomicAdd(reinterpret_cast<unsigned long long*>(&sacc[3][row + k]), to_fx(macc[kk].get(k, 0), fxSm));
+          } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) atomicAdd(&sacc[c][row + k], acc[kk].get(k, c));
+            if constexpr (MODE == kModeMassV) atomicAdd(&sacc[3][row + k], macc[kk].get(k, 0));
+          }
         }
+        acc[kk].zero();
+        macc[kk].zero();
       }
-      acc.zero();
-      macc.zero();
     };
     for (int j = j0; j < j1; ++j) {
       const int base = sloc[j];
@@ -782,42 +821,53 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         cur = base;
       }
       const V4<T> X = stash[4][sidx(j)], XD = stash[5][sidx(j)];
-      T wyzm, ty = T(0), tz = T(0);
+      T wyzm[RPL], ty = T(0), tz = T(0);
       if constexpr (ROWTAB) {
-        // this lane's row weight m N_y(ky) N_z(kz), from the stashed factors
+        // this lane's row weights m N_y(ky) N_z(kz), from the stashed factors
         // (the particle's own offset is already folded into u)
-        wyzm = reinterpret_cast<const T*>(&stash[0][sidx(j)])[ky] *
-               reinterpret_cast<const T*>(&stash[ROWTAB ? 6 : 0][sidx(j)])[kz];
+        const T wym = reinterpret_cast<const T*>(&stash[0][sidx(j)])[ky];
+#pragma unroll
+        for (int k = 0; k < RPL; ++k)
+          wyzm[k] = wym * reinterpret_cast<const T*>(&stash[ROWTAB ? 6 : 0][sidx(j)])[kzr[k]];
       } else {
         const V4<T> a = stash[0][sidx(j)];
-        wyzm = a.w * (cy0 + a.y * (cy1 + a.y * cy2)) * (cz0 + a.z * (cz1 + a.z * cz2));
+        const T wym = a.w * (cy0 + a.y * (cy1 + a.y * cy2));
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) wyzm[k] = wym * (cz0[k] + a.z * (cz1[k] + a.z * cz2[k]));
         ty = a.y;
         tz = a.z;
       }
       if constexpr (kMass) {
-        const T A[1] = {wyzm};
-        macc.add(X, XD, A, nullptr);
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          const T A[1] = {wyzm[k]};
+          macc[k].add(X, XD, A, nullptr);
+        }
       }
       {
         const V4<T> w0 = stash[1][sidx(j)], w1 = stash[2][sidx(j)], w2 = stash[3][sidx(j)];
         // W = (u, Ch); Ch rows (w0.w w1.x w1.y) (w1.z w1.w w2.x) (w2.y w2.z w2.w).
-        // Node k of this row gets wx_k A + wx_k dx_k B with
+        // Node k of a row gets wx_k A + wx_k dx_k B with
         //   A_c = m wy wz (u_c + Ch_c1 dy + Ch_c2 dz),  B_c = m wy wz Ch_c0.
-        const T dy = oy - ty, dz = oz - tz;
-        T A[3], B[3];
-        if (aff) {
-          A[0] = wyzm * (w0.x + w1.x * dy + w1.y * dz);
-          A[1] = wyzm * (w0.y + w1.w * dy + w2.x * dz);
-          A[2] = wyzm * (w0.z + w2.z * dy + w2.w * dz);
-          B[0] = wyzm * w0.w;
-          B[1] = wyzm * w1.z;
-          B[2] = wyzm * w2.y;
-          acc.add(X, XD, A, B);
-        } else {
-          A[0] = wyzm * w0.x;
-          A[1] = wyzm * w0.y;
-          A[2] = wyzm * w0.z;
-          acc.add(X, XD, A, nullptr);
+        const T dy = oy - ty;
+#pragma unroll
+        for (int k = 0; k < RPL; ++k) {
+          const T dz = oz[k] - tz;
+          T A[3], B[3];
+          if (aff) {
+            A[0] = wyzm[k] * (w0.x + w1.x * dy + w1.y * dz);
+            A[1] = wyzm[k] * (w0.y + w1.w * dy + w2.x * dz);
+            A[2] = wyzm[k] * (w0.z + w2.z * dy + w2.w * dz);
+            B[0] = wyzm[k] * w0.w;
+            B[1] = wyzm[k] * w1.z;
+            B[2] = wyzm[k] * w2.y;
+            acc[k].add(X, XD, A, B);
+          } else {
+            A[0] = wyzm[k] * w0.x;
+            A[1] = wyzm[k] * w0.y;
+            A[2] = wyzm[k] * w0.z;
+            acc[k].add(X, XD, A, nullptr);
+          }
         }
       }
     }
@@ -1479,12 +1529,12 @@ cudaError_t launch_ex(void (*kernel)(P...), unsigned grid, unsigned block, bool 
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-template <class T, int MINB, int CHUNK, bool ROWTAB>
+template <class T, int MINB, int CHUNK, bool ROWTAB, int RPL>
 cudaError_t launch_items_cfg(const IterParams<T>& p, int mode, bool overlap, cudaStream_t s) {
   const unsigned grid = (unsigned)p.n_items;
   switch (mode) {
 #define APIC_MODE(m) \
-  case m: return launch_ex(k_items<T, m, MINB, CHUNK, ROWTAB>, grid, CHUNK, overlap, s, p);
+  case m: return launch_ex(k_items<T, m, MINB, CHUNK, ROWTAB, false, RPL>, grid, CHUNK, overlap, s, p);
     APIC_MODE(kModeFirst)
     APIC_MODE(kModeMid)
     APIC_MODE(kModeLast)
@@ -1500,7 +1550,7 @@ cudaError_t launch_items_cfg(const IterParams<T>& p, int mode, bool overlap, cud
 // Deterministic mode: the modes of the FP32 step, variant 0's CTA shape.
 template <class T>
 cudaError_t launch_items_fx(const IterParams<T>& p, int mode, bool overlap, cudaStream_t s) {
-  constexpr int B = kVariantMinBlocks[0], C = kVariantChunk[0];
+  constexpr int B = kVariantMinBlocks[0], C = kVariantThreads[0];
   const unsigned grid = (unsigned)p.n_items;
   switch (mode) {
 #define APIC_MODE(m) \
@@ -1526,8 +1576,9 @@ cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, bool ove
   }
   if constexpr (sizeof(T) == 4) {
     // the FP32 path is built in every variant
-#define APIC_VARIANT(v) \
-  launch_items_cfg<T, kVariantMinBlocks[v], kVariantChunk[v], kVariantRowTab[v]>(p, mode, overlap, s)
+#define APIC_VARIANT(v)                                                                                   \
+  launch_items_cfg<T, kVariantMinBlocks[v], kVariantThreads[v], kVariantRowTab[v], kVariantRPL[v]>(p, mode, \
+                                                                                                    overlap, s)
     switch (variant) {
       case 1: return APIC_VARIANT(1);
       case 2: return APIC_VARIANT(2);
@@ -1535,6 +1586,7 @@ cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, bool ove
       case 4: return APIC_VARIANT(4);
       case 5: return APIC_VARIANT(5);
       case 6: return APIC_VARIANT(6);
+      case 7: return APIC_VARIANT(7);
       default: break;
     }
   }
