@@ -118,28 +118,15 @@ __device__ __forceinline__ void store12(V4<T>* planes, int n, int s, const T v[3
 
 // Tile node t = (a, b, c) in [0,7)^3, relative to node 4B-1 of the item's
 // block B, lies in neighbour block ((a+3)>>2, (b+3)>>2, (c+3)>>2) of the
-// 3x3x3 around B at local node ((a+3)&3, (b+3)&3, (c+3)&3).  The table packs
-// (neighbour << 6 | local) for all 343 tile nodes.
-struct TileTable {
-  unsigned short e[kTile3];
-};
-constexpr TileTable make_tile_table() {
-  TileTable t{};
-  for (int i = 0; i < kTile3; ++i) {
-    const int a = i % kTile, b = (i / kTile) % kTile, c = i / (kTile * kTile);
-    const int nb = ((c + 3) >> 2) * 9 + ((b + 3) >> 2) * 3 + ((a + 3) >> 2);
-    const int local = (((c + 3) & 3) << 4) | (((b + 3) & 3) << 2) | ((a + 3) & 3);
-    t.e[i] = (unsigned short)((nb << 6) | local);
-  }
-  return t;
-}
-__device__ const TileTable g_tile = make_tile_table();
-
-// Node index of tile node t, or -1 when its block is not active.
+// 3x3x3 around B at local node ((a+3)&3, (b+3)&3, (c+3)&3).  Computed in
+// registers (a table in memory would add a load per node to the busiest
+// unit).  Node index of tile node t, or -1 when its block is not active.
 __device__ __forceinline__ int tile_node(const int* snb, int t) {
-  const int e = g_tile.e[t];
-  const int nb = snb[e >> 6];
-  return nb < 0 ? -1 : nb * kNodesPerBlock + (e & 63);
+  const int c = t / (kTile * kTile), r = t - c * (kTile * kTile);
+  const int b = r / kTile, a = r - b * kTile;
+  const int nb = snb[((c + 3) >> 2) * 9 + ((b + 3) >> 2) * 3 + ((a + 3) >> 2)];
+  const int local = (((c + 3) & 3) << 4) | (((b + 3) & 3) << 2) | ((a + 3) & 3);
+  return nb < 0 ? -1 : nb * kNodesPerBlock + local;
 }
 
 // G2P from the shared tile: v_hat = sum N v_i, Ch_hat = 2 sum N v_i (x) d,
@@ -427,6 +414,10 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   __shared__ V4<T> sv[kG2P ? kTile3 : 1];
   __shared__ uint32_t smask[MODE == kModeMu ? kTile3 : 1];
   __shared__ T smass[MODE == kModeNormals ? kTile3 : 1];  // the item's body's node masses
+  // FP32 series passes: the tile's node body masks (final since the mass
+  // pass), fetched with the velocities, for the flush's FP64 choice
+  constexpr bool kMaskPre = sizeof(T) == 4 && !DET && (MODE == kModeFirst || MODE == kModeMid);
+  __shared__ uint32_t smk[kMaskPre ? kTile3 : 1];
   using Acc = typename std::conditional<DET, long long, T>::type;
   __shared__ Acc sacc[kP2G ? kComp : 1][kTile3];
   __shared__ unsigned s_fxmax;
@@ -525,8 +516,13 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         if (node >= 0) {
           const unsigned dst = (unsigned)__cvta_generic_to_shared(&sv[t]);
           asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(&p.gv[node]) : "memory");
+          if constexpr (kMaskPre) {
+            const unsigned dm = (unsigned)__cvta_generic_to_shared(&smk[t]);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dm), "l"(&p.gmask[node]) : "memory");
+          }
         } else {
           sv[t] = V4<T>{T(0), T(0), T(0), T(0)};
+          if constexpr (kMaskPre) smk[t] = 0u;
         }
       }
       asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
@@ -921,6 +917,14 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
           atomicAdd(&p.gp64[node].x, (double)x);
           atomicAdd(&p.gp64[node].y, (double)y);
           atomicAdd(&p.gp64[node].z, (double)z);
+        } else if constexpr (kMaskPre) {
+          if (p.gp64 != nullptr && __popc(smk[t]) >= 2) {
+            atomicAdd(&p.gp64[node].x, (double)x);
+            atomicAdd(&p.gp64[node].y, (double)y);
+            atomicAdd(&p.gp64[node].z, (double)z);
+          } else {
+            atomicAdd(reinterpret_cast<float4*>(&p.gp[node]), make_float4((float)x, (float)y, (float)z, 0.f));
+          }
         } else {
           flush_mom(static_cast<T*>(nullptr), p.gp, p.gp64, p.gmask, node, x, y, z);
         }
