@@ -159,6 +159,18 @@ typedef struct {
   int64_t graph_launches;  /* CUDA graph launches (sizing and series regions) */
 } apic_profile;
 
+/* Bounds checks of the kernels' own indexing (not in the paper).  A library
+ * built with -DAPIC_DEBUG_BOUNDS (libapiccontact_debug.so) checks tile-node,
+ * page-table, particle-slot, permutation and sort-output indices on the
+ * device; a failed check records a bit and skips the access (no trap).
+ * apic_debug_build returns 1 for such a library, 0 otherwise;
+ * apic_debug_flags returns the recorded bits (1 tile node, 2 page-table
+ * index, 4 item size or cell bits, 8 permutation entry, 16 sort output
+ * position) of the current device, 0 in the normal build, and clears them
+ * when `clear` is non-zero. */
+int32_t apic_debug_build(void);
+apic_status apic_debug_flags(uint32_t* out, int32_t clear);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* apic_last_error(void);
 

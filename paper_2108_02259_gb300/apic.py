@@ -18,6 +18,10 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libapiccontact.so")
+# APIC_DEBUG_BOUNDS=1 in the environment loads the bounds-checking build
+# (build.build(debug=True)) instead
+if os.environ.get("APIC_DEBUG_BOUNDS") == "1":
+    LIB_PATH = os.path.join(_PKG, "libapiccontact_debug.so")
 
 APIC_OK = 0
 APIC_ERR_INVALID_ARG = -1
@@ -47,7 +51,7 @@ EXPORTED = [
     "apic_augury_steps",
     "apic_sim_export", "apic_sim_import", "apic_mass_normals",
     "apic_place_by_budget", "apic_group_create", "apic_group_destroy", "apic_group_server", "apic_group_set_policy",
-    "apic_group_open", "apic_group_get_stats", "apic_sim_server",
+    "apic_group_open", "apic_group_get_stats", "apic_sim_server", "apic_debug_build", "apic_debug_flags",
 ]
 
 
@@ -167,6 +171,9 @@ def load(path: str = LIB_PATH):
         getattr(lib, f).restype = C.c_int32
     lib.apic_contact_step_batched.argtypes = [P, C.POINTER(StepArgs), C.c_int32, P, C.POINTER(Stats)]
     lib.apic_contact_step_batched.restype = C.c_int32
+    lib.apic_debug_build.restype = C.c_int32
+    lib.apic_debug_flags.argtypes = [C.POINTER(C.c_uint32), C.c_int32]
+    lib.apic_debug_flags.restype = C.c_int32
     lib.apic_place_by_budget.argtypes = [P, C.c_int32, C.c_int64]
     lib.apic_place_by_budget.restype = C.c_int32
     lib.apic_group_create.argtypes = [C.POINTER(P), P, C.c_int32, C.c_size_t, C.c_int32, C.c_int32]
@@ -855,3 +862,11 @@ def place_by_budget(free_bytes, need: int) -> int:
     room that still holds `need` bytes, or -1."""
     arr = (C.c_int64 * len(free_bytes))(*[int(b) for b in free_bytes])
     return int(load().apic_place_by_budget(arr, len(free_bytes), int(need)))
+
+
+def debug_flags(clear: bool = True) -> int:
+    """apic_debug_flags: bounds-check bits recorded on the current device
+    (always 0 in the normal build)."""
+    v = C.c_uint32()
+    _check(load().apic_debug_flags(C.byref(v), 1 if clear else 0))
+    return int(v.value)

@@ -658,6 +658,22 @@ apic_status apic_node_normals(apic_ctx* c, int64_t n, const double* x, int64_t n
   return APIC_OK;
 }
 
+int32_t apic_debug_build(void) {
+#ifdef APIC_DEBUG_BOUNDS
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+apic_status apic_debug_flags(uint32_t* out, int32_t clear) {
+  if (!out) return pfail(APIC_ERR_INVALID_ARG, "out is NULL");
+  const unsigned a = kernels_debug_flags(clear), b = sort_debug_flags(clear);
+  if (a == ~0u || b == ~0u) return pfail(APIC_ERR_CUDA, "reading the bounds-check words failed");
+  *out = a | b;
+  return APIC_OK;
+}
+
 int32_t apic_variant_count(void) { return kNumVariants; }
 
 const char* apic_variant_name(int32_t v) {

@@ -36,6 +36,26 @@ constexpr int kErrFinite = 16;  // v, C or a normal not finite (checked with API
 constexpr int kErrNormal = 32;  // a normal neither 0 nor of unit length (checked with APIC_CHECK)
 constexpr int kErrSort = 64;    // a bounded wait of the radix sort gave up (internal)
 
+// Bounds checks of the kernels' own indexing (a debug build: compiled with
+// -DAPIC_DEBUG_BOUNDS; build.build(debug=True) makes libapiccontact_debug.so).
+// A failed check records its bit in the translation unit's debug word and
+// the access is skipped (no trap, no fault); apic_debug_flags reads and
+// clears the words.  In the normal build every check is `true`.
+constexpr unsigned kDbgTileNode = 1;  // a tile node outside the node arrays
+constexpr unsigned kDbgPage = 2;      // a page-table index outside the table
+constexpr unsigned kDbgSlot = 4;      // an item size or a particle's cell bits out of range
+constexpr unsigned kDbgPerm = 8;      // a permutation entry outside its scene
+constexpr unsigned kDbgSortPos = 16;  // a sort output position outside the keys
+#ifdef APIC_DEBUG_BOUNDS
+#define APIC_DBG_CHECK(cond, bit) ((cond) ? true : (::apic::dbg_record(bit), false))
+#else
+#define APIC_DBG_CHECK(cond, bit) true
+#endif
+// Debug words of the kernel and sort translation units (0 in the normal
+// build); clear: reset them.
+unsigned kernels_debug_flags(int clear);
+unsigned sort_debug_flags(int clear);
+
 // Device-side scalars the host reads back while sizing the grid.
 struct DevScalars {
   int err;       // kErr* bits
@@ -112,6 +132,7 @@ struct IterParams {
   T* gmb;                  // [max_bodies * nodes] per-body node mass, or nullptr
   T* mup_out;              // [n] written by kModeMu
   int64_t n_nodes;
+  int64_t n_pages;         // page-table entries (bounds checks of the debug build)
   const V4<T>* V;          // [3n] sorted V = (v, h C) as 3 planes of n
   V4<T>* D;                // [3n] Delta planes
   const V4<T>* gv;         // grid velocity (normalised), [nodes]

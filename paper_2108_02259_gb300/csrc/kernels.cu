@@ -20,6 +20,29 @@
 #include "apic_internal.h"
 
 namespace apic {
+
+#ifdef APIC_DEBUG_BOUNDS
+__device__ unsigned g_dbg_kernels;  // bounds-check bits of this translation unit
+namespace {
+__device__ __forceinline__ void dbg_record(unsigned bit) { atomicOr(&g_dbg_kernels, bit); }
+}  // namespace
+#endif
+
+unsigned kernels_debug_flags(int clear) {
+#ifdef APIC_DEBUG_BOUNDS
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_dbg_kernels, sizeof(v)) != cudaSuccess) return ~0u;
+  if (clear) {
+    const unsigned z = 0;
+    if (cudaMemcpyToSymbol(g_dbg_kernels, &z, sizeof(z)) != cudaSuccess) return ~0u;
+  }
+  return v;
+#else
+  (void)clear;
+  return 0;
+#endif
+}
+
 namespace {
 
 __device__ __forceinline__ float bits_to(float, uint32_t b) { return __uint_as_float(b); }
@@ -425,6 +448,12 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   __shared__ int sloc[kItem];
   __shared__ int snb[27];
   const int tid = threadIdx.x;
+  // node index of tile node t (-1: inactive block; the debug build also
+  // refuses an index outside the node arrays)
+  auto node_of = [&](int t) {
+    const int nd = tile_node(snb, t);
+    return nd >= 0 && !APIC_DBG_CHECK(nd < p.n_nodes, kDbgTileNode) ? -1 : nd;
+  };
   const int n = p.n_particles;
   const int item = blockIdx.x;
   grid_dep_launch();
@@ -439,6 +468,10 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   const int s0 = p.item_start[item];
   const int s1 = item + 1 < p.n_items ? p.item_start[item + 1] : n;
   const int count = s1 - s0;  // <= kItem
+  if (!APIC_DBG_CHECK(count >= 1 && count <= kItem, kDbgSlot)) {
+    grid_dep_wait();
+    return;
+  }
   // phase-1 slot of this thread's r-th particle: warp w holds the slots
   // [32 RPL w, 32 RPL (w + 1)), the ones its phase-2 groups walk
   const int wslot = (tid >> 5) * (32 * RPL) + (tid & 31);
@@ -471,7 +504,8 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
     // the 3x3x3 blocks around the item's block (info.x is its global page
     // index; every particle block keeps a one-block margin inside its box)
     const int ox = tid % 3 - 1, oy = (tid / 3) % 3 - 1, oz = tid / 9 - 1;
-    snb[tid] = p.page[(long long)info.x + ((long long)oz * box.ny + oy) * box.nx + ox];
+    const long long pg = (long long)info.x + ((long long)oz * box.ny + oy) * box.nx + ox;
+    snb[tid] = APIC_DBG_CHECK(pg >= 0 && pg < p.n_pages, kDbgPage) ? p.page[pg] : -1;
   }
   if (kP2G)
     for (int t = t_lo + tid; t < t_hi; t += CHUNK)
@@ -512,7 +546,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
       // V4<float> is 16-byte aligned in both spaces); all of this thread's
       // copies are in flight together
       for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
-        const int node = tile_node(snb, t);
+        const int node = node_of(t);
         if (node >= 0) {
           const unsigned dst = (unsigned)__cvta_generic_to_shared(&sv[t]);
           asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(&p.gv[node]) : "memory");
@@ -528,7 +562,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
       asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
     } else {
       for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
-        const int node = tile_node(snb, t);
+        const int node = node_of(t);
         sv[t] = node >= 0 ? p.gv[node] : V4<T>{T(0), T(0), T(0), T(0)};
       }
     }
@@ -536,7 +570,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
   }
   if (MODE == kModeNormals) {
     for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
-      const int node = tile_node(snb, t);
+      const int node = node_of(t);
       T mi = T(0);
       if (node >= 0) {
         const int64_t k = (int64_t)body * p.n_nodes + node;
@@ -550,7 +584,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
     const uint32_t own = 1u << body;
     int other = 0;
     for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
-      const int node = tile_node(snb, t);
+      const int node = node_of(t);
       const uint32_t m = node >= 0 ? p.gmask[node] : 0u;
       smask[t] = m;
       other |= (m & ~own) != 0u;
@@ -576,7 +610,8 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
     if (j < count) {
       const int s = s0 + j;
       const uint32_t loc = to_bits(pn.w);
-      const int base = (int)(loc >> 4) * (kTile * kTile) + (int)((loc >> 2) & 3) * kTile + (int)(loc & 3);
+      int base = (int)(loc >> 4) * (kTile * kTile) + (int)((loc >> 2) & 3) * kTile + (int)(loc & 3);
+      if (!APIC_DBG_CHECK(loc < 64u, kDbgSlot)) base = 0;  // (a cell outside its block)
       sloc[j] = base;
       if (MODE == kModeMu && S.mu_off < 0) {
         p.mup_out[s] = (T)S.mu;  // a scene with one scalar mu
@@ -589,13 +624,13 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         bspline(pt.z, wz, dz);
         T num = T(0), den = T(0);
         const uint32_t own = 1u << body;
-  #pragma unroll 1
+#pragma unroll 1
         for (int q = 0; q < 64; ++q) {
           const int kx = q & 3, ky = (q >> 2) & 3, kz = q >> 4;
           const int tq = base + kz * (kTile * kTile) + ky * kTile + kx;
           uint32_t other = smask[tq] & ~own;
           if (!other) continue;
-          const int node = tile_node(snb, tq);
+          const int node = node_of(tq);
           T wxk = kx == 0 ? wx[0] : kx == 1 ? wx[1] : kx == 2 ? wx[2] : wx[3];
           T wyk = ky == 0 ? wy[0] : ky == 1 ? wy[1] : ky == 2 ? wy[2] : wy[3];
           T wzk = kz == 0 ? wz[0] : kz == 1 ? wz[1] : kz == 2 ? wz[2] : wz[3];
@@ -621,13 +656,13 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         bspline_grad(pt.y, gy);
         bspline_grad(pt.z, gz);
         T rho = T(0), g0 = T(0), g1 = T(0), g2 = T(0);
-  #pragma unroll
+#pragma unroll
         for (int kz = 0; kz < 4; ++kz) {
           T r = T(0), ry = T(0), rx = T(0);  // sum over y of N_y (N_x m), of gN_y (N_x m), of N_y (gN_x m)
-  #pragma unroll
+#pragma unroll
           for (int ky = 0; ky < 4; ++ky) {
             T a = T(0), ad = T(0);
-  #pragma unroll
+#pragma unroll
             for (int kx = 0; kx < 4; ++kx) {
               const T mi = smass[base + kz * (kTile * kTile) + ky * kTile + kx];
               a += wx[kx] * mi;
@@ -649,8 +684,9 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         if (p.normals_out) {
           const int64_t idx = p.perm[s] - S.part_off;
           T* o = static_cast<T*>(S.v_out);
-  #pragma unroll
-          for (int a = 0; a < 3; ++a) o[3 * idx + a] = nn[a];
+          if (APIC_DBG_CHECK(idx >= 0 && idx < S.n, kDbgPerm))
+#pragma unroll
+            for (int a = 0; a < 3; ++a) o[3 * idx + a] = nn[a];
         } else {
           p.pn_out[s] = V4<T>{nn[0], nn[1], nn[2], pn.w};
         }
@@ -697,9 +733,9 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
           // Delta_0 = H V - V
           const T v[3] = {q0.x, q0.y, q0.z};
           const T C[9] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
-  #pragma unroll
+#pragma unroll
           for (int a = 0; a < 3; ++a) dv[a] = hv[a] - v[a];
-  #pragma unroll
+#pragma unroll
           for (int a = 0; a < 9; ++a) dC[a] = p.pic ? T(0) : hC[a] - C[a];
           out = MODE == kModeOnly;
         } else {
@@ -708,9 +744,9 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
           const T pC[9] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
           T wv[3], wC[9];
           undesirable(pv, pC, nrm, mu, p.sep23, wv, wC);
-  #pragma unroll
+#pragma unroll
           for (int a = 0; a < 3; ++a) dv[a] = pv[a] + hv[a] - wv[a];
-  #pragma unroll
+#pragma unroll
           for (int a = 0; a < 9; ++a) dC[a] = p.pic ? T(0) : pC[a] + hC[a] - wC[a];
           out = MODE == kModeLast;
         }
@@ -726,10 +762,12 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
           T* vo = static_cast<T*>(S.v_out);
           T* Co = static_cast<T*>(S.C_out);
           const T inv_h = (T)S.inv_h;
-  #pragma unroll
-          for (int a = 0; a < 3; ++a) vo[3 * idx + a] = v[a] + dv[a];
-  #pragma unroll
-          for (int a = 0; a < 9; ++a) Co[9 * idx + a] = (C[a] + dC[a]) * inv_h;
+          if (APIC_DBG_CHECK(idx >= 0 && idx < S.n, kDbgPerm)) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) vo[3 * idx + a] = v[a] + dv[a];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) Co[9 * idx + a] = (C[a] + dC[a]) * inv_h;
+          }
         } else {
           store12(p.D, n, s, dv, dC);
           T u[3], uC[9];
@@ -881,7 +919,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
     }
     if (MODE != kModeMassV && tid == 0) atomicMax(p.fx_max + (int64_t)info.z * p.fx_stride + p.fx_slot + 1, s_fxmax);
     for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
-      const int node = tile_node(snb, t);
+      const int node = node_of(t);
       if (node < 0) continue;
       unsigned long long* g = reinterpret_cast<unsigned long long*>(p.gp64) + 4 * (int64_t)node;
       if constexpr (MODE == kModeMassV) {
@@ -900,7 +938,7 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
     }
   } else if constexpr (!DET && kP2G) {
     for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
-      const int node = tile_node(snb, t);
+      const int node = node_of(t);
       if (node < 0) continue;
       if constexpr (kMass) {
         const T mv = sacc[3][t];
@@ -1215,6 +1253,7 @@ __global__ void k_gather(int64_t n, const SceneDev* __restrict__ sc, int ns, con
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int64_t g = perm[s];
+  if (!APIC_DBG_CHECK(g >= 0 && g < n, kDbgPerm)) return;
   const SceneDev& S = sc[scene_of_particle(sc, ns, g)];
   const int64_t i = g - S.part_off;
   const int4 c = cellb[g];

@@ -585,6 +585,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   p.gmb = gmb;
   p.mup_out = mup;
   p.n_nodes = n_nodes;
+  p.n_pages = NB;
   p.V = V;
   p.D = D;
   p.gv = gv;

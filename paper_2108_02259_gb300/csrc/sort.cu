@@ -38,21 +38,45 @@
 #include "apic_internal.h"
 
 namespace apic {
+
+#ifdef APIC_DEBUG_BOUNDS
+__device__ unsigned g_dbg_sort;  // bounds-check bits of this translation unit
+namespace {
+__device__ __forceinline__ void dbg_record(unsigned bit) { atomicOr(&g_dbg_sort, bit); }
+}  // namespace
+#endif
+
+unsigned sort_debug_flags(int clear) {
+#ifdef APIC_DEBUG_BOUNDS
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_dbg_sort, sizeof(v)) != cudaSuccess) return ~0u;
+  if (clear) {
+    const unsigned z = 0;
+    if (cudaMemcpyToSymbol(g_dbg_sort, &z, sizeof(z)) != cudaSuccess) return ~0u;
+  }
+  return v;
+#else
+  (void)clear;
+  return 0;
+#endif
+}
+
 namespace {
 
-constexpr int kSortThreads = 256;
+constexpr int kSortThreads = 512;  // one thread per digit value in a pass
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kRadixMaxBits = 9;
 constexpr int kRadixBins = 1 << kRadixMaxBits;
 constexpr int kBinsPerThread = kRadixBins / kSortThreads;
 static_assert(kRadixBins % kSortThreads == 0, "each thread owns whole digits");
+constexpr int kCountThreads = 256;  // CTA size of the count kernel
 
-// Keys per thread and per tile: 32-bit keys 12 per thread (3072 a tile),
-// 64-bit keys 8 (2048), so that the tile's staging stays in static shared
+// Keys per thread and per tile: 32-bit keys 6 per thread (3072 a tile),
+// 64-bit keys 4 (2048), so that the tile's staging stays in static shared
 // memory (48 KB).
 template <class K>
 struct SortTile {
-  static constexpr int kItems = sizeof(K) == 4 ? 12 : 8;
+  static constexpr int kItems = sizeof(K) == 4 ? 6 : 4;
   static constexpr int kTile = kSortThreads * kItems;
   static constexpr int kWarpTile = 32 * kItems;
 };
@@ -104,13 +128,13 @@ __device__ __forceinline__ unsigned digit_of(K k, int shift, unsigned mask) {
 constexpr int kMaxPasses = 8;  // 64-bit keys at 9 bits a pass
 constexpr int kCountRun = 16;
 template <class K>
-__global__ void __launch_bounds__(kSortThreads) k_radix_counts(const K* __restrict__ keys, int64_t n, int end_bit,
-                                                                int per, int passes, int* __restrict__ counts) {
+__global__ void __launch_bounds__(kCountThreads) k_radix_counts(const K* __restrict__ keys, int64_t n, int end_bit,
+                                                                 int per, int passes, int* __restrict__ counts) {
   __shared__ int cnt[kMaxPasses][kRadixBins];
-  for (int i = threadIdx.x; i < passes * kRadixBins; i += kSortThreads) (&cnt[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < passes * kRadixBins; i += kCountThreads) (&cnt[0][0])[i] = 0;
   __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * kSortThreads * kCountRun;
-  for (int64_t c0 = ((int64_t)blockIdx.x * kSortThreads + threadIdx.x) * kCountRun; c0 < n; c0 += stride) {
+  const int64_t stride = (int64_t)gridDim.x * kCountThreads * kCountRun;
+  for (int64_t c0 = ((int64_t)blockIdx.x * kCountThreads + threadIdx.x) * kCountRun; c0 < n; c0 += stride) {
     const int64_t c1 = c0 + kCountRun < n ? c0 + kCountRun : n;
     unsigned prev[kMaxPasses];
     int run[kMaxPasses];
@@ -140,12 +164,13 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_counts(const K* __restri
       if (p < passes && run[p] > 0) atomicAdd(&cnt[p][prev[p]], run[p]);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < passes * kRadixBins; i += kSortThreads)
+  for (int i = threadIdx.x; i < passes * kRadixBins; i += kCountThreads)
     if ((&cnt[0][0])[i]) atomicAdd(&counts[i], (&cnt[0][0])[i]);
 }
 
-// Exclusive scan of one value per thread over the CTA (kSortThreads); also
-// returns the total.
+// Exclusive scan of one value per thread over a CTA of WARPS warps; also
+// returns the total.  warp_tot holds WARPS + 1 ints.
+template <int WARPS>
 __device__ __forceinline__ int cta_exclusive_scan(int x, int* warp_tot, int* total) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int incl = x;
@@ -157,19 +182,19 @@ __device__ __forceinline__ int cta_exclusive_scan(int x, int* warp_tot, int* tot
   if (lane == 31) warp_tot[w] = incl;
   __syncthreads();
   if (w == 0) {
-    int t = lane < kSortWarps ? warp_tot[lane] : 0;
+    int t = lane < WARPS ? warp_tot[lane] : 0;
     int ti = t;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, ti, o);
       if (lane >= o) ti += y;
     }
-    if (lane < kSortWarps) warp_tot[lane] = ti - t;  // exclusive warp offsets
-    if (lane == kSortWarps - 1) warp_tot[kSortWarps] = ti;
+    if (lane < WARPS) warp_tot[lane] = ti - t;  // exclusive warp offsets
+    if (lane == WARPS - 1) warp_tot[WARPS] = ti;
   }
   __syncthreads();
   const int r = warp_tot[w] + incl - x;
-  if (total) *total = warp_tot[kSortWarps];
+  if (total) *total = warp_tot[WARPS];
   return r;
 }
 
@@ -178,12 +203,12 @@ __device__ __forceinline__ int cta_exclusive_scan(int x, int* warp_tot, int* tot
 // kRadixBins words and tile_ctr, zero on entry; vin == nullptr: the values
 // are the indices.
 template <class K>
-__global__ void __launch_bounds__(kSortThreads, 4)
+__global__ void __launch_bounds__(kSortThreads, 2)
     k_onesweep(const K* __restrict__ kin, const int* __restrict__ vin, K* __restrict__ kout, int* __restrict__ vout,
                int64_t n, int shift, int bits, const int* __restrict__ counts, unsigned* status, int* tile_ctr,
                int* err) {
   using TT = SortTile<K>;
-  __shared__ int wcnt[kSortWarps][kRadixBins];  // per warp: keys of each digit so far, then warp offsets
+  __shared__ uint16_t wcnt[kSortWarps][kRadixBins];  // per warp: keys of each digit so far, then warp offsets
   __shared__ int tstart[kRadixBins];            // the tile's count of each digit, then its first tile position
   __shared__ int gbase[kRadixBins];             // earlier tiles' keys of each digit, then its first output position
   __shared__ int scan_a[kSortWarps + 1], scan_b[kSortWarps + 1];
@@ -217,10 +242,10 @@ __global__ void __launch_bounds__(kSortThreads, 4)
     const bool valid = t < tile_n;
     const unsigned d = digit_of(key[r], shift, mask);
     const unsigned peers = digit_peers(d, valid);
-    const int prior = valid ? wcnt[w][d] : 0;
+    const int prior = valid ? (int)wcnt[w][d] : 0;
     rank[r] = prior + __popc(peers & lanemask_lt());
     __syncwarp();
-    if (valid && lane == __ffs(peers) - 1) wcnt[w][d] = prior + __popc(peers);
+    if (valid && lane == __ffs(peers) - 1) wcnt[w][d] = (uint16_t)(prior + __popc(peers));
     __syncwarp();
   }
   __syncthreads();
@@ -236,7 +261,7 @@ __global__ void __launch_bounds__(kSortThreads, 4)
 #pragma unroll
     for (int q = 0; q < kSortWarps; ++q) {
       const int c = wcnt[q][d];
-      wcnt[q][d] = run;
+      wcnt[q][d] = (uint16_t)run;
       run += c;
     }
     dtot[j] = run;
@@ -249,7 +274,7 @@ __global__ void __launch_bounds__(kSortThreads, 4)
   // once, then each digit folds them from the nearest tile back to the first
   // one that carries a full prefix (waiting, bounded, on any that has not
   // published yet).
-  constexpr int kWindow = 8;
+  constexpr int kWindow = 16;
   {
     unsigned excl[kBinsPerThread];
     bool live[kBinsPerThread];
@@ -318,8 +343,8 @@ __global__ void __launch_bounds__(kSortThreads, 4)
       cs += c[j];
       ts += tc[j];
     }
-    int g = cta_exclusive_scan(cs, scan_a, nullptr);
-    int h = cta_exclusive_scan(ts, scan_b, nullptr);
+    int g = cta_exclusive_scan<kSortWarps>(cs, scan_a, nullptr);
+    int h = cta_exclusive_scan<kSortWarps>(ts, scan_b, nullptr);
 #pragma unroll
     for (int j = 0; j < kBinsPerThread; ++j) {
       const int d = threadIdx.x * kBinsPerThread + j;
@@ -343,8 +368,10 @@ __global__ void __launch_bounds__(kSortThreads, 4)
     if (t < tile_n) {
       const unsigned d = digit_of(key[r], shift, mask);
       const int pos = tstart[d] + wcnt[w][d] + rank[r];
-      skey[pos] = key[r];
-      sval[pos] = vin ? vin[base + t] : (int)(base + t);
+      if (APIC_DBG_CHECK(pos >= 0 && pos < tile_n, kDbgSortPos)) {
+        skey[pos] = key[r];
+        sval[pos] = vin ? vin[base + t] : (int)(base + t);
+      }
     }
   }
   __syncthreads();
@@ -354,8 +381,10 @@ __global__ void __launch_bounds__(kSortThreads, 4)
     const K k = skey[i];
     const unsigned d = digit_of(k, shift, mask);
     const int64_t o = (int64_t)gbase[d] + (i - tstart[d]);
-    kout[o] = k;
-    vout[o] = sval[i];
+    if (APIC_DBG_CHECK(o >= 0 && o < n, kDbgSortPos)) {
+      kout[o] = k;
+      vout[o] = sval[i];
+    }
   }
 }
 
@@ -394,7 +423,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(int* sums, int n_tile
     const int i = c + threadIdx.x;
     const int x = i < n_tiles ? sums[i] : 0;
     int total;
-    const int e = cta_exclusive_scan(x, warp_tot, &total);
+    const int e = cta_exclusive_scan<kScanThreads / 32>(x, warp_tot, &total);
     if (i < n_tiles) sums[i] = carry + e;
     carry += total;
     __syncthreads();
@@ -415,7 +444,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* in, int6
     x[i] = idx < n ? in[idx] : 0;
     s += x[i];
   }
-  int run = sums[blockIdx.x] + cta_exclusive_scan(s, warp_tot, nullptr);
+  int run = sums[blockIdx.x] + cta_exclusive_scan<kScanThreads / 32>(s, warp_tot, nullptr);
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const int64_t idx = base + i;
@@ -471,9 +500,9 @@ cudaError_t launch_radix_sort(K* keys, int* vals, K* keys_alt, int* vals_alt, in
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t want = 8 * (int64_t)sms;
-  const int64_t chunks = cdiv(n, (int64_t)kSortThreads * kCountRun);
+  const int64_t chunks = cdiv(n, (int64_t)kCountThreads * kCountRun);
   const int count_ctas = (int)(chunks < want ? chunks : want);
-  k_radix_counts<K><<<count_ctas, kSortThreads, 0, s>>>(keys, n, end_bit, per, passes, counts);
+  k_radix_counts<K><<<count_ctas, kCountThreads, 0, s>>>(keys, n, end_bit, per, passes, counts);
   K *kin = keys, *kout = keys_alt;
   int *vin = vals, *vout = vals_alt;
   for (int p = 0; p < passes; ++p) {
