@@ -431,7 +431,7 @@ def main():
         b = measure(args, apic, ctx, b_sc, b_dt, True, dev, stream, flush, ws, with_e2e=not args.no_e2e,
                     with_clocks=False)
         line["batched64"] = {
-            "what": "config 4: 64 independent scenes in one batched call per step, against the same scenes "
+            "what": "64 independent scenes in one batched call per step, against the same scenes "
                     "one apic_contact_step call each (plain single-scene path)",
             "config": workload_config("batched64", b_sc, b_dt), "value": b["value"], "unit": UNIT,
             "ms_per_step": b["ms_per_step"], "kernel_variant": b["kernel_variant"], "e2e": b["e2e"],

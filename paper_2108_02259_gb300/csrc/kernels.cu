@@ -1256,11 +1256,14 @@ __global__ void k_gather(int64_t n, const SceneDev* __restrict__ sc, int ns, con
   if (!APIC_DBG_CHECK(g >= 0 && g < n, kDbgPerm)) return;
   const SceneDev& S = sc[scene_of_particle(sc, ns, g)];
   const int64_t i = g - S.part_off;
-  const int4 c = cellb[g];
+  // the cell again from x, with k_cells' own arithmetic (the same integers;
+  // one gathered read fewer than loading them)
   const double* x = S.x;
-  const T tx = (T)(x[3 * i + 0] * S.inv_h - (double)c.x);
-  const T ty = (T)(x[3 * i + 1] * S.inv_h - (double)c.y);
-  const T tz = (T)(x[3 * i + 2] * S.inv_h - (double)c.z);
+  const double xs = x[3 * i + 0] * S.inv_h, ys = x[3 * i + 1] * S.inv_h, zs = x[3 * i + 2] * S.inv_h;
+  const int3 c = make_int3((int)floor(xs), (int)floor(ys), (int)floor(zs));
+  const T tx = (T)(xs - (double)c.x);
+  const T ty = (T)(ys - (double)c.y);
+  const T tz = (T)(zs - (double)c.z);
   pt[s] = V4<T>{tx, ty, tz, static_cast<const T*>(S.m)[i]};
   const uint32_t loc = (uint32_t)(((c.z & 3) << 4) | ((c.y & 3) << 2) | (c.x & 3));
   if (V == nullptr) {  // normals and V planes gathered later (k_gather_v)
