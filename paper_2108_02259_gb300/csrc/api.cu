@@ -686,6 +686,7 @@ const char* apic_variant_name(int32_t v) {
       "128 threads/CTA, items <= 128, 8 CTAs/SM (64 registers), stashed row weights",
       "128 threads/CTA, items <= 128, 7 CTAs/SM (72 registers), stashed row weights",
       "128 threads/CTA, 2 particles/thread, items <= 256, 8-lane P2G groups, 5 CTAs/SM (96 registers)",
+      "128 threads/CTA, items <= 128, 9 CTAs/SM (56 registers), persistent grid",
   };
   return v >= 0 && v < kNumVariants ? names[v] : "";
 }

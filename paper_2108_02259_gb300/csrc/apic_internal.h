@@ -158,6 +158,9 @@ struct IterParams {
   int fx_stride;
   int fx_slot;
   int fx_attempt;
+  // Persistent grids: a counter of item tickets, 0 between launches (the
+  // launch draws exactly n_items tickets and atomicInc wraps it back to 0).
+  unsigned* ticket;
 };
 
 // Deterministic mode: fixed-point headroom (log2) of a pass's scale over the
@@ -202,15 +205,18 @@ cudaError_t launch_mark_items(const int* item_start, const int4* item_info, cons
 // (CTA size x RPL), resident CTAs per SM it is compiled for (its register
 // cap), and how P2G lanes get their row weights m N_y N_z (recomputed per
 // lane from t, or read from factors stashed per particle in phase 1: fewer
-// instructions, one more stash row).  Variant 0 is the default; the FP32
-// path exists in all of them, the FP64 path in variant 0 only (which it
-// always uses).
-constexpr int kNumVariants = 8;
-constexpr int kVariantThreads[kNumVariants] = {128, 128, 128, 64, 64, 128, 128, 128};
-constexpr int kVariantRPL[kNumVariants] = {1, 1, 1, 1, 1, 1, 1, 2};
-constexpr int kVariantChunk[kNumVariants] = {128, 128, 128, 64, 64, 128, 128, 256};
-constexpr int kVariantMinBlocks[kNumVariants] = {8, 9, 7, 13, 16, 8, 7, 5};
-constexpr bool kVariantRowTab[kNumVariants] = {false, false, false, false, false, true, true, false};
+// instructions, one more stash row), and whether the grid is persistent
+// (as many CTAs as fit on the device at once, each walking items with a grid
+// stride) or one CTA per item.  Variant 0 is the default; the FP32 path
+// exists in all of them, the FP64 path in variant 0 only (which it always
+// uses).
+constexpr int kNumVariants = 9;
+constexpr int kVariantThreads[kNumVariants] = {128, 128, 128, 64, 64, 128, 128, 128, 128};
+constexpr int kVariantRPL[kNumVariants] = {1, 1, 1, 1, 1, 1, 1, 2, 1};
+constexpr int kVariantChunk[kNumVariants] = {128, 128, 128, 64, 64, 128, 128, 256, 128};
+constexpr int kVariantMinBlocks[kNumVariants] = {8, 9, 7, 13, 16, 8, 7, 5, 9};
+constexpr bool kVariantRowTab[kNumVariants] = {false, false, false, false, false, true, true, false, false};
+constexpr bool kVariantPersist[kNumVariants] = {false, false, false, false, false, false, false, false, true};
 // overlap: launch with programmatic stream serialization, so that the grid's
 // prologue (item metadata, particle loads, page lookups) runs while the grid
 // before it finishes.  Only for a launch that directly follows another

@@ -424,8 +424,13 @@ __device__ __forceinline__ float from_fx(long long g, float inv_S) {
 //
 // DET (deterministic mode, FP32): the shared tile and the global node sums
 // hold scaled int64 terms (fixed point) instead of floating-point sums.
-template <class T, int MODE, int MINB, int CHUNK, bool ROWTAB, bool DET = false, int RPL = 1>
-__global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
+//
+// items_body runs one work item with the whole CTA; k_items runs one item
+// per CTA or, persistent (PERSIST), a grid of resident CTAs: CTA b starts
+// with item b and then draws tickets for the items after the first
+// gridDim.x, one at a time, until the items run out.
+template <class T, int MODE, int MINB, int CHUNK, bool ROWTAB, bool DET, int RPL>
+__device__ __forceinline__ void items_body(const IterParams<T>& p, const int item) {
   static_assert(RPL == 1 || RPL == 2, "one or two stencil rows per lane");
   constexpr int kItem = CHUNK * RPL;  // particles of the largest item
   constexpr int kStashN = kItem + kItem / 16;
@@ -455,8 +460,6 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
     return nd >= 0 && !APIC_DBG_CHECK(nd < p.n_nodes, kDbgTileNode) ? -1 : nd;
   };
   const int n = p.n_particles;
-  const int item = blockIdx.x;
-  grid_dep_launch();
   if (item >= p.n_items) {
     grid_dep_wait();
     return;
@@ -968,6 +971,32 @@ __global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
         }
       }
     }
+  }
+}
+
+template <class T, int MODE, int MINB, int CHUNK, bool ROWTAB, bool DET = false, int RPL = 1, bool PERSIST = false>
+__global__ void __launch_bounds__(CHUNK, MINB) k_items(const IterParams<T> p) {
+  grid_dep_launch();
+  if constexpr (PERSIST) {
+    // Tickets are drawn after the item's grid_dep_wait, so the grid before
+    // this one, which used the same counter, has completed.  The launch
+    // draws n_items tickets in all (n_items - gridDim.x that name an item,
+    // one past the end per CTA), so the counter wraps back to 0.
+    __shared__ int s_next;
+    int item = blockIdx.x;
+    while (item < p.n_items) {
+      items_body<T, MODE, MINB, CHUNK, ROWTAB, DET, RPL>(p, item);
+      if (p.n_items <= (int)gridDim.x) break;  // one item per CTA: no tickets
+      if (threadIdx.x == 0) {
+        grid_dep_wait();  // (already passed, unless the item exited early)
+        s_next = (int)gridDim.x + (int)atomicInc(p.ticket, (unsigned)(p.n_items - 1));
+      }
+      __syncthreads();  // also: the next item reuses the shared tiles
+      item = s_next;
+      __syncthreads();  // every thread has read it before thread 0 writes it again
+    }
+  } else {
+    items_body<T, MODE, MINB, CHUNK, ROWTAB, DET, RPL>(p, blockIdx.x);
   }
 }
 
@@ -1575,12 +1604,21 @@ cudaError_t launch_ex(void (*kernel)(P...), unsigned grid, unsigned block, bool 
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-template <class T, int MINB, int CHUNK, bool ROWTAB, int RPL>
+// Resident CTAs of a persistent grid: MINB per SM (the kernel's register
+// cap), never more than the items.
+inline unsigned persistent_grid(int n_items, int minb) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 1;
+  return (unsigned)std::min<long long>((long long)n_items, (long long)sms * minb);
+}
+
+template <class T, int MINB, int CHUNK, bool ROWTAB, int RPL, bool PERSIST>
 cudaError_t launch_items_cfg(const IterParams<T>& p, int mode, bool overlap, cudaStream_t s) {
-  const unsigned grid = (unsigned)p.n_items;
+  const unsigned grid = PERSIST ? persistent_grid(p.n_items, MINB) : (unsigned)p.n_items;
   switch (mode) {
 #define APIC_MODE(m) \
-  case m: return launch_ex(k_items<T, m, MINB, CHUNK, ROWTAB, false, RPL>, grid, CHUNK, overlap, s, p);
+  case m: return launch_ex(k_items<T, m, MINB, CHUNK, ROWTAB, false, RPL, PERSIST>, grid, CHUNK, overlap, s, p);
     APIC_MODE(kModeFirst)
     APIC_MODE(kModeMid)
     APIC_MODE(kModeLast)
@@ -1622,9 +1660,9 @@ cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, bool ove
   }
   if constexpr (sizeof(T) == 4) {
     // the FP32 path is built in every variant
-#define APIC_VARIANT(v)                                                                                   \
-  launch_items_cfg<T, kVariantMinBlocks[v], kVariantThreads[v], kVariantRowTab[v], kVariantRPL[v]>(p, mode, \
-                                                                                                    overlap, s)
+#define APIC_VARIANT(v)                                                                               \
+  launch_items_cfg<T, kVariantMinBlocks[v], kVariantThreads[v], kVariantRowTab[v], kVariantRPL[v],       \
+                   kVariantPersist[v]>(p, mode, overlap, s)
     switch (variant) {
       case 1: return APIC_VARIANT(1);
       case 2: return APIC_VARIANT(2);
@@ -1633,6 +1671,7 @@ cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, bool ove
       case 5: return APIC_VARIANT(5);
       case 6: return APIC_VARIANT(6);
       case 7: return APIC_VARIANT(7);
+      case 8: return APIC_VARIANT(8);
       default: break;
     }
   }

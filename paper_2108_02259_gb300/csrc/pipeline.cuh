@@ -38,7 +38,7 @@ enum Slot : int {
   kSlotSBbox, kSlotSMom, kSlotSCount, kSlotHX, kSlotHBody, kSlotHV, kSlotHC, kSlotHM, kSlotHN, kSlotHVo,
   kSlotHCo, kSlotDS, kSlotNrmAcc, kSlotNrmX, kSlotNrmTri, kSlotNrmOut, kSlotAugF, kSlotAugAm, kSlotAugVbar,
   kSlotAugVhat, kSlotAugChat, kSlotAugNrm, kSlotAugOut, kSlotRunCnt, kSlotRunOffs, kSlotRunEnd, kSlotFxMax,
-  kSlotFxErr, kSlotGmbFx, kSlotCount
+  kSlotFxErr, kSlotGmbFx, kSlotTicket, kSlotCount
 };
 
 constexpr int kMaxBodies = 32;
@@ -534,6 +534,8 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   P_TRY(env.take(kSlotGmask, n_nodes, &gmask, "grid body mask"));
   P_TRY(env.take(kSlotGp, n_nodes, &gp, "grid momentum"));
   P_TRY(env.take(kSlotGv, n_nodes, &gv, "grid velocity"));
+  unsigned* ticket = nullptr;
+  P_TRY(env.take(kSlotTicket, 1, &ticket, "item tickets"));
   if (sizeof(T) == 4) P_TRY(env.take(kSlotGp64, n_nodes, &gp64, "FP64 node momentum"));
   unsigned* fx_max = nullptr;
   int* fx_err = nullptr;
@@ -602,6 +604,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   p.fx_err = fx_err;
   p.gmb_fx = gmb_fx;
   p.fx_stride = fx_stride;
+  p.ticket = ticket;
   key.mup = mup;
   key.n_iter = N;
   key.any_mu = any_mu ? 1 : 0;
@@ -619,6 +622,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     typename Env::Span span_mass(env, q, 3);
     P_CUDA(cudaMemsetAsync(gm, 0, n_nodes * sizeof(T), q));
     P_CUDA(cudaMemsetAsync(gmask, 0, n_nodes * sizeof(uint32_t), q));
+    P_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), q));
     P_CUDA(cudaMemsetAsync(gp, 0, n_nodes * sizeof(V4<T>), q));
     if (gp64) P_CUDA(cudaMemsetAsync(gp64, 0, n_nodes * sizeof(V4<double>), q));
     if (gmb) P_CUDA(cudaMemsetAsync(gmb, 0, (size_t)max_bodies * n_nodes * sizeof(T), q));

@@ -86,6 +86,27 @@ def test_every_variant_matches_oracle(apic, case):
             ctx.set_variant(len(apic.variants()))
 
 
+def test_persistent_grid_walks_several_items_per_cta(apic):
+    """The persistent variant launches only as many CTAs as fit on the device
+    at once; the 200,000-particle scene has about 2,000 work items, more than
+    the 152 x 9 resident CTAs, so CTAs run several items one after another and
+    reuse their shared tiles."""
+    import torch
+
+    names = apic.variants()
+    var = next(i for i, nm in enumerate(names) if "persistent" in nm)
+    s = scenes.four_bodies()
+    ref = oracle.contact_step(s.x, s.v, s.C, s.m, s.nrm, s.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies)
+    with apic.Context(0) as ctx:
+        ctx.set_variant(var)
+        X, V, Cc, M, NR, B = _dev(s)
+        for rep in range(3):  # direct launches, then the captured graph, then a replay
+            r = apic.contact_step(ctx, X, V, Cc, M, NR, B, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies)
+            torch.cuda.synchronize()
+            _close(s, r.v.cpu().double().numpy(), r.C.cpu().double().numpy(), ref[0], ref[1],
+                   f"persistent variant, call {rep}")
+
+
 def test_graph_replay_matches_direct_launches(apic):
     """Same sizes and buffers on consecutive calls: the second call captures
     the passes, later ones replay them.  Each call gets new velocities and
