@@ -339,10 +339,13 @@ struct RowAcc<float, K> {
   }
 };
 
-// ---- Fixed-point node sums (deterministic mode, FP32 path) ----
+// ---- Fixed-point node sums (FP32 path) ----
 // A pass scatters, per particle and node, N m (w_c + sum_k Ch_ck d_k) with
 // N <= 1 and |d_k| <= 2 (cell units), so every component is bounded by
 //   b_p = m_p max_c (|w_c| + 2 sum_k |Ch_ck|).
+// The default path uses the bound per work item: the item's shared P2G tile
+// holds 32-bit integers at a scale from the sum of its particles' b_p (see
+// k_items).  The deterministic mode uses it per scene, with int64 sums:
 // If every b_p of a scene is at most B, a node sum over the scene's n
 // particles stays below n B; the scale S = 2^e with S n B <= 2^62 then keeps
 // it inside int64, and integer atomics add the scaled terms exactly, in any
@@ -446,9 +449,15 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
   // pass), fetched with the velocities, for the flush's FP64 choice
   constexpr bool kMaskPre = sizeof(T) == 4 && !DET && (MODE == kModeFirst || MODE == kModeMid);
   __shared__ uint32_t smk[kMaskPre ? kTile3 : 1];
-  using Acc = typename std::conditional<DET, long long, T>::type;
+  // FP32 default path: the tile's momentum sums are 32-bit fixed point with a
+  // per-item power-of-two scale (native integer atomics; a float add to
+  // shared memory is a compare-and-swap loop); the mass sums stay float,
+  // stored in the same int array.
+  constexpr bool kFix = sizeof(T) == 4 && !DET && kP2G;
+  using Acc = typename std::conditional<DET, long long, typename std::conditional<kFix, int, T>::type>::type;
   __shared__ Acc sacc[kP2G ? kComp : 1][kTile3];
   __shared__ unsigned s_fxmax;
+  __shared__ float s_bw[kFix ? CHUNK / 32 : 1];  // per-warp sums of the term bounds
   __shared__ V4<T> stash[kP2G ? (ROWTAB ? 7 : 6) : 1][kP2G ? kStashN : 1];
   __shared__ int sloc[kItem];
   __shared__ int snb[27];
@@ -605,6 +614,7 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
   }
 
   // ---------------- phase 1: one thread per particle ----------------
+  float bsum = 0.f;  // kFix: sum of this thread's particle term bounds
 #pragma unroll
   for (int r = 0; r < RPL; ++r) {
     const int j = wslot + 32 * r;
@@ -696,6 +706,11 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
       } else if (MODE == kModeMassV) {
         T wx[4], dx[4];
         bspline(pt.x, wx, dx);
+        if constexpr (kFix) {
+          const float vv[3] = {q0.x, q0.y, q0.z};
+          const float Cc[9] = {q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+          bsum += fx_bound(pt.w, vv, Cc);
+        }
         if constexpr (ROWTAB) {
           T wy[4], dy[4], wz[4], dz[4];
           bspline(pt.y, wy, dy);
@@ -775,6 +790,7 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
           store12(p.D, n, s, dv, dC);
           T u[3], uC[9];
           undesirable(dv, dC, nrm, mu, p.sep23, u, uC);
+          if constexpr (kFix) bsum += fx_bound(pt.w, u, uC);
           if constexpr (DET) {
             const float b = fx_bound(pt.w, u, uC);
             fx_bad = fx_bad || !(b <= fx_ok);
@@ -802,8 +818,31 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
   }
   if (!kP2G) return;
   // Group g of phase 2 walks particles 16g .. 16g+15, which lanes of its own
-  // warp stashed in phase 1: ordering within the warp is enough.
-  __syncwarp();
+  // warp stashed in phase 1: ordering within the warp is enough, except for
+  // the fixed-point scale, which needs every warp's bound.
+  float fxT = 0.f, fxInvT = 0.f;  // kFix: tile scale T = 2^e and 1/T
+  bool fx_nonfinite = false;
+  if constexpr (kFix) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+    if ((tid & 31) == 0) s_bw[tid >> 5] = bsum;
+    __syncthreads();
+    float B = 0.f;
+#pragma unroll
+    for (int w = 0; w < CHUNK / 32; ++w) B += s_bw[w];
+    // every node sum of the tile, and every partial sum a lane adds, is at
+    // most B / 8: a particle adds at most N b_p to a node, and N <= 1/8
+    // (each one-dimensional App. B weight is at most 1/2).  With B < 2^k,
+    // T = 2^(33 - k) keeps them below 2^30 in magnitude.
+    fx_nonfinite = !(B <= 3.0e38f);
+    int k = 0;
+    if (!fx_nonfinite && B > 0.f) (void)frexpf(B, &k);
+    const int e = fx_nonfinite ? 0 : min(33 - k, 126);
+    fxT = ldexpf(1.f, e);
+    fxInvT = ldexpf(1.f, -e);
+  } else {
+    __syncwarp();
+  }
 
   // ---------------- phase 2: cell-centric P2G ----------------
   {
@@ -841,6 +880,11 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
               atomicAdd(reinterpret_cast<unsigned long long*>(&sacc[c][row + k]), to_fx(acc[kk].get(k, c), fxS));
             if constexpr (MODE == kModeMassV)
               atomicAdd(reinterpret_cast<unsigned long long*>(&sacc[3][row + k]), to_fx(macc[kk].get(k, 0), fxSm));
+          } else if constexpr (kFix) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) atomicAdd(&sacc[c][row + k], __float2int_rn(acc[kk].get(k, c) * fxT));
+            if constexpr (MODE == kModeMassV)
+              atomicAdd(reinterpret_cast<float*>(&sacc[3][row + k]), macc[kk].get(k, 0));
           } else {
 #pragma unroll
             for (int c = 0; c < 3; ++c) atomicAdd(&sacc[c][row + k], acc[kk].get(k, c));
@@ -944,25 +988,45 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
       const int node = node_of(t);
       if (node < 0) continue;
       if constexpr (kMass) {
-        const T mv = sacc[3][t];
+        T mv;
+        if constexpr (kFix) mv = __int_as_float(sacc[3][t]);
+        else mv = sacc[3][t];
         if (mv != T(0)) {
           atomicAdd(&p.gm[node], mv);
           atomicOr(&p.gmask[node], 1u << body);
           if (p.gmb) atomicAdd(&p.gmb[(int64_t)body * p.n_nodes + node], mv);
         }
       }
-      const T x = sacc[0][t], y = sacc[1][t], z = sacc[2][t];
-      if (x != T(0) || y != T(0) || z != T(0)) {
+      // the node's sums in the working type (from the fixed-point integers:
+      // int -> float, times the power of two 1/T; a non-finite bound in the
+      // item gives its nodes NaN, as float sums would)
+      T x, y, z;
+      bool any;
+      if constexpr (kFix) {
+        const int ix = sacc[0][t], iy = sacc[1][t], iz = sacc[2][t];
+        any = (ix | iy | iz) != 0 || fx_nonfinite;
+        const float inv = fx_nonfinite ? __int_as_float(0x7fc00000) : fxInvT;
+        x = (float)ix * inv;
+        y = (float)iy * inv;
+        z = (float)iz * inv;
+      } else {
+        x = sacc[0][t];
+        y = sacc[1][t];
+        z = sacc[2][t];
+        any = x != T(0) || y != T(0) || z != T(0);
+      }
+      const double xd = (double)x, yd = (double)y, zd = (double)z;  // (used by the FP64 branches only)
+      if (any) {
         if (kMass && p.gp64 != nullptr) {
           // the body mask is not final yet: P2G of V goes to FP64 everywhere
-          atomicAdd(&p.gp64[node].x, (double)x);
-          atomicAdd(&p.gp64[node].y, (double)y);
-          atomicAdd(&p.gp64[node].z, (double)z);
+          atomicAdd(&p.gp64[node].x, xd);
+          atomicAdd(&p.gp64[node].y, yd);
+          atomicAdd(&p.gp64[node].z, zd);
         } else if constexpr (kMaskPre) {
           if (p.gp64 != nullptr && __popc(smk[t]) >= 2) {
-            atomicAdd(&p.gp64[node].x, (double)x);
-            atomicAdd(&p.gp64[node].y, (double)y);
-            atomicAdd(&p.gp64[node].z, (double)z);
+            atomicAdd(&p.gp64[node].x, xd);
+            atomicAdd(&p.gp64[node].y, yd);
+            atomicAdd(&p.gp64[node].z, zd);
           } else {
             atomicAdd(reinterpret_cast<float4*>(&p.gp[node]), make_float4((float)x, (float)y, (float)z, 0.f));
           }
