@@ -303,7 +303,11 @@ struct CopyEntry {
   long long bytes;
 };
 // All copies of a table (itself device-visible) in one launch.
-cudaError_t launch_copy_table(const CopyEntry* table, int n_entries, long long max_bytes, cudaStream_t s);
+// max_ctas > 0: at most that many CTAs in all (about, at least one per
+// entry), for a copy that runs beside compute kernels: CTAs that wait on the
+// host link hold SM slots the compute kernels need.
+cudaError_t launch_copy_table(const CopyEntry* table, int n_entries, long long max_bytes, cudaStream_t s,
+                              int max_ctas = 0);
 
 // Set the calling thread's message returned by apic_last_error().
 void set_last_error(const char* msg);

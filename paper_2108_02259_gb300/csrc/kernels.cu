@@ -2037,7 +2037,23 @@ __global__ void k_copy_table(const CopyEntry* __restrict__ table, int n_entries)
     const uint32_t* src = static_cast<const uint32_t*>(c.src);
     uint32_t* dst = static_cast<uint32_t*>(c.dst);
     int64_t done_words = 0;
-    if (s16 || d16) {
+    if (s16 && d16) {
+      // four 16-byte loads in flight per thread: a small grid still keeps
+      // enough bytes in flight to fill the host link
+      const int64_t n16 = c.bytes / 16;
+      const uint4* s4 = static_cast<const uint4*>(c.src);
+      uint4* d4 = static_cast<uint4*>(c.dst);
+      for (int64_t i = t0; i < n16; i += 4 * stride) {
+        uint4 w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (i + k * stride < n16) w[k] = s4[i + k * stride];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (i + k * stride < n16) d4[i + k * stride] = w[k];
+      }
+      done_words = 4 * n16;
+    } else if (s16 || d16) {
       const int64_t n16 = c.bytes / 16;
       for (int64_t i = t0; i < n16; i += stride) {
         uint4 w;
@@ -2065,11 +2081,13 @@ __global__ void k_copy_table(const CopyEntry* __restrict__ table, int n_entries)
   }
 }
 
-cudaError_t launch_copy_table(const CopyEntry* table, int n_entries, long long max_bytes, cudaStream_t s) {
+cudaError_t launch_copy_table(const CopyEntry* table, int n_entries, long long max_bytes, cudaStream_t s,
+                              int max_ctas) {
   if (n_entries <= 0 || max_bytes <= 0) return cudaSuccess;
   if (n_entries > 65535) return cudaErrorInvalidValue;
-  const unsigned gx = (unsigned)std::min<long long>(std::max<long long>((max_bytes + 16383) / 16384, 1), 304);
-  k_copy_table<<<dim3(gx, (unsigned)n_entries), 256, 0, s>>>(table, n_entries);
+  long long gx = std::min<long long>(std::max<long long>((max_bytes + 16383) / 16384, 1), 304);
+  if (max_ctas > 0) gx = std::max<long long>(1, std::min<long long>(gx, max_ctas / n_entries));
+  k_copy_table<<<dim3((unsigned)gx, (unsigned)n_entries), 256, 0, s>>>(table, n_entries);
   return cudaGetLastError();
 }
 

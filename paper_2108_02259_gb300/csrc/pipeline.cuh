@@ -259,6 +259,9 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
                  INT32_MAX / 4);
 
   bool split_v = false;  // V planes gathered after the sizing sequence (see below)
+  // CTAs of the copy that runs beside the sizing sequence (with four 16-byte
+  // loads in flight per thread, 64 CTAs keep the host link full)
+  constexpr int kSideCopyCtas = 64;
   if (host) {
     double* dx;
     int32_t* db;
@@ -318,7 +321,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       // two do not share the link) and everything queued before it
       P_CUDA(cudaEventRecord(env.side_event(0), s));
       P_CUDA(cudaStreamWaitEvent(side, env.side_event(0), 0));
-      P_LAUNCH(env, launch_copy_table(tab + 3 * ns, nb, max_b, side));
+      P_LAUNCH(env, launch_copy_table(tab + 3 * ns, nb, max_b, side, kSideCopyCtas));
       P_CUDA(cudaEventRecord(env.side_event(1), side));
     }
     for (int i = 0; i < ns; ++i) {
