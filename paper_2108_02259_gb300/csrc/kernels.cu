@@ -452,8 +452,9 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
   // FP32 default path: the tile's momentum sums are 32-bit fixed point with a
   // per-item power-of-two scale (native integer atomics; a float add to
   // shared memory is a compare-and-swap loop).  The mass sums of the mass
-  // pass stay float, stored in the same int array: any positive contribution
-  // must leave a nonzero mass, since it also sets the node's body bit.
+  // pass stay float, stored in the same int array: a node's mass is used in
+  // ratios (the per-pair friction blend, mass normals) and sets its body
+  // bit, so a mass term below a fixed-point unit must not vanish.
   constexpr bool kFix = sizeof(T) == 4 && !DET && kP2G;
   using Acc = typename std::conditional<DET, long long, typename std::conditional<kFix, int, T>::type>::type;
   __shared__ Acc sacc[kP2G ? kComp : 1][kTile3];
