@@ -301,12 +301,14 @@ struct CopyEntry {
   const void* src;
   void* dst;
   long long bytes;
+  long long chunk0;  // with a CTA budget: the entry's first chunk (set by launch_copy_table)
 };
 // All copies of a table (itself device-visible) in one launch.
-// max_ctas > 0: at most that many CTAs in all (about, at least one per
-// entry), for a copy that runs beside compute kernels: CTAs that wait on the
-// host link hold SM slots the compute kernels need.
-cudaError_t launch_copy_table(const CopyEntry* table, int n_entries, long long max_bytes, cudaStream_t s,
+// max_ctas > 0: at most that many CTAs, each taking an equal share of the
+// entries' bytes, for a copy that runs beside compute kernels (CTAs that
+// wait on the host link hold SM slots the compute kernels need).  The table
+// is then host memory: its chunk0 fields are filled here.
+cudaError_t launch_copy_table(CopyEntry* table, int n_entries, long long max_bytes, cudaStream_t s,
                               int max_ctas = 0);
 
 // Set the calling thread's message returned by apic_last_error().

@@ -2026,24 +2026,21 @@ cudaError_t launch_aug_energy(int64_t n, const double* x, const T* v, const T* m
 // 16-byte aligned (that end, usually the host side of the link, gets whole
 // 16-byte accesses; the other is split into 4-byte ones), then a 4-byte tail;
 // otherwise bytes.
-__global__ void k_copy_table(const CopyEntry* __restrict__ table, int n_entries) {
-  const int e = blockIdx.y;
-  if (e >= n_entries) return;
-  const CopyEntry c = table[e];
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const uintptr_t sa = (uintptr_t)c.src, da = (uintptr_t)c.dst;
-  if (((sa | da | (uintptr_t)c.bytes) & 3) == 0) {
+// Copy bytes [0, len) of src to dst with the threads t0, t0 + stride, ...:
+// 16-byte accesses when both ends allow them (four in flight per thread, so
+// that a small grid still fills the host link), 4-byte ones when only one
+// does, then a 4-byte tail; bytes when the ends are not 4-byte aligned.
+__device__ __forceinline__ void copy_range(const void* srcp, void* dstp, long long len, int64_t t0, int64_t stride) {
+  const uintptr_t sa = (uintptr_t)srcp, da = (uintptr_t)dstp;
+  if (((sa | da | (uintptr_t)len) & 3) == 0) {
     const bool s16 = (sa & 15) == 0, d16 = (da & 15) == 0;
-    const uint32_t* src = static_cast<const uint32_t*>(c.src);
-    uint32_t* dst = static_cast<uint32_t*>(c.dst);
+    const uint32_t* src = static_cast<const uint32_t*>(srcp);
+    uint32_t* dst = static_cast<uint32_t*>(dstp);
     int64_t done_words = 0;
+    const int64_t n16 = len / 16;
     if (s16 && d16) {
-      // four 16-byte loads in flight per thread: a small grid still keeps
-      // enough bytes in flight to fill the host link
-      const int64_t n16 = c.bytes / 16;
-      const uint4* s4 = static_cast<const uint4*>(c.src);
-      uint4* d4 = static_cast<uint4*>(c.dst);
+      const uint4* s4 = static_cast<const uint4*>(srcp);
+      uint4* d4 = static_cast<uint4*>(dstp);
       for (int64_t i = t0; i < n16; i += 4 * stride) {
         uint4 w[4];
 #pragma unroll
@@ -2055,16 +2052,15 @@ __global__ void k_copy_table(const CopyEntry* __restrict__ table, int n_entries)
       }
       done_words = 4 * n16;
     } else if (s16 || d16) {
-      const int64_t n16 = c.bytes / 16;
       for (int64_t i = t0; i < n16; i += stride) {
         uint4 w;
         if (s16) {
-          w = static_cast<const uint4*>(c.src)[i];
+          w = static_cast<const uint4*>(srcp)[i];
         } else {
           w = make_uint4(src[4 * i], src[4 * i + 1], src[4 * i + 2], src[4 * i + 3]);
         }
         if (d16) {
-          static_cast<uint4*>(c.dst)[i] = w;
+          static_cast<uint4*>(dstp)[i] = w;
         } else {
           dst[4 * i] = w.x;
           dst[4 * i + 1] = w.y;
@@ -2074,20 +2070,70 @@ __global__ void k_copy_table(const CopyEntry* __restrict__ table, int n_entries)
       }
       done_words = 4 * n16;
     }
-    for (int64_t i = done_words + t0; i < c.bytes / 4; i += stride) dst[i] = src[i];
+    for (int64_t i = done_words + t0; i < len / 4; i += stride) dst[i] = src[i];
   } else {
-    const unsigned char* src = static_cast<const unsigned char*>(c.src);
-    unsigned char* dst = static_cast<unsigned char*>(c.dst);
-    for (int64_t i = t0; i < c.bytes; i += stride) dst[i] = src[i];
+    const unsigned char* src = static_cast<const unsigned char*>(srcp);
+    unsigned char* dst = static_cast<unsigned char*>(dstp);
+    for (int64_t i = t0; i < len; i += stride) dst[i] = src[i];
   }
 }
 
-cudaError_t launch_copy_table(const CopyEntry* table, int n_entries, long long max_bytes, cudaStream_t s,
+// One entry per grid row, its bytes spread over the row's CTAs.
+__global__ void k_copy_table(const CopyEntry* __restrict__ table, int n_entries) {
+  const int e = blockIdx.y;
+  if (e >= n_entries) return;
+  const CopyEntry c = table[e];
+  copy_range(c.src, c.dst, c.bytes, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+
+// With a CTA budget: the entries' bytes as one sequence of kCopyChunk-byte
+// chunks (an entry's last one may be short); CTA b copies the contiguous
+// chunks [b C / G, (b + 1) C / G) of the C chunks, walking the entries in
+// order (chunk0 is each entry's first chunk).
+constexpr long long kCopyChunk = 64 << 10;
+__global__ void k_copy_chunks(const CopyEntry* __restrict__ table, int n_entries, long long n_chunks) {
+  __shared__ int s_e;
+  const long long c0 = (long long)blockIdx.x * n_chunks / gridDim.x;
+  const long long c1 = (long long)(blockIdx.x + 1) * n_chunks / gridDim.x;
+  if (c0 >= c1) return;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n_entries - 1;  // the last entry whose first chunk is <= c0
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (table[mid].chunk0 <= c0) lo = mid;
+      else hi = mid - 1;
+    }
+    s_e = lo;
+  }
+  __syncthreads();
+  int e = s_e;
+  CopyEntry ent = table[e];
+  for (long long c = c0; c < c1; ++c) {
+    while (e + 1 < n_entries && table[e + 1].chunk0 <= c) ent = table[++e];
+    const long long off = (c - ent.chunk0) * kCopyChunk;
+    const long long len = ent.bytes - off < kCopyChunk ? ent.bytes - off : kCopyChunk;
+    if (len > 0)
+      copy_range(static_cast<const char*>(ent.src) + off, static_cast<char*>(ent.dst) + off, len, threadIdx.x,
+                 blockDim.x);
+  }
+}
+
+cudaError_t launch_copy_table(CopyEntry* table, int n_entries, long long max_bytes, cudaStream_t s,
                               int max_ctas) {
   if (n_entries <= 0 || max_bytes <= 0) return cudaSuccess;
   if (n_entries > 65535) return cudaErrorInvalidValue;
-  long long gx = std::min<long long>(std::max<long long>((max_bytes + 16383) / 16384, 1), 304);
-  if (max_ctas > 0) gx = std::max<long long>(1, std::min<long long>(gx, max_ctas / n_entries));
+  if (max_ctas > 0) {
+    long long chunks = 0;
+    for (int e = 0; e < n_entries; ++e) {
+      table[e].chunk0 = chunks;
+      chunks += (table[e].bytes + kCopyChunk - 1) / kCopyChunk;
+    }
+    if (chunks == 0) return cudaSuccess;
+    const unsigned g = (unsigned)std::min<long long>(chunks, max_ctas);
+    k_copy_chunks<<<g, 256, 0, s>>>(table, n_entries, chunks);
+    return cudaGetLastError();
+  }
+  const long long gx = std::min<long long>(std::max<long long>((max_bytes + 16383) / 16384, 1), 304);
   k_copy_table<<<dim3((unsigned)gx, (unsigned)n_entries), 256, 0, s>>>(table, n_entries);
   return cudaGetLastError();
 }
