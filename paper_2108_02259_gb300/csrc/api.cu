@@ -86,7 +86,7 @@ struct apic_ctx {
   // side stream of the host path (v and C cross the host link while the
   // sizing sequence runs) and its two events
   cudaStream_t side = nullptr;
-  cudaEvent_t side_ev[2] = {nullptr, nullptr};
+  cudaEvent_t side_ev[3] = {nullptr, nullptr, nullptr};
   uint64_t alloc_gen = 0;  // bumped whenever a scratch buffer moves
   // the caller's device allocator for scratch (apic_set_allocator), or none
   apic_alloc_fn ualloc = nullptr;

@@ -181,9 +181,10 @@ cudaError_t launch_keys(int64_t n, const SceneDev* sc, int ns, const int4* cellb
 template <class T>
 cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm, const int4* cellb, V4<T>* pt,
                           V4<T>* pn, V4<T>* V, cudaStream_t s);
+// what: 1 the V planes, 2 the normals, 3 both.
 template <class T>
 cudaError_t launch_gather_v(int64_t n, const SceneDev* sc, int ns, const int* perm, V4<T>* pn, V4<T>* V,
-                            cudaStream_t s);
+                            int what, cudaStream_t s);
 // Work items from the sorted keys: at each run head (a new (grid block,
 // body)) the run's end and its item count ceil(len / chunk) (16 <= chunk <=
 // kChunk), 0 elsewhere; then, with the exclusive sum of the counts, every

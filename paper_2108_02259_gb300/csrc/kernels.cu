@@ -1379,23 +1379,24 @@ __global__ void k_gather(int64_t n, const SceneDev* __restrict__ sc, int ns, con
   store12(V, (int)n, (int)s, vv, Ch);
 }
 
-// The normals (into pn's first three components) and the V = (v, h C)
-// planes, in sorted order, when v, C and the normals arrive after the sizing
-// sequence has started.
+// The normals (into pn's first three components; what & 2) and the V = (v,
+// h C) planes (what & 1), in sorted order, when v, C and the normals arrive
+// after the sizing sequence has started.
 template <class T>
 __global__ void k_gather_v(int64_t n, const SceneDev* __restrict__ sc, int ns, const int* __restrict__ perm,
-                           V4<T>* pn, V4<T>* V) {
+                           V4<T>* pn, V4<T>* V, int what) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int64_t g = perm[s];
   const SceneDev& S = sc[scene_of_particle(sc, ns, g)];
   const int64_t i = g - S.part_off;
   const T* nrm = static_cast<const T*>(S.nrm);
-  if (nrm) {  // NULL: normals computed on the device later
+  if ((what & 2) && nrm) {  // NULL: normals computed on the device later
     pn[s].x = nrm[3 * i + 0];
     pn[s].y = nrm[3 * i + 1];
     pn[s].z = nrm[3 * i + 2];
   }
+  if (!(what & 1)) return;
   const T hh = (T)S.h;
   const T* v = static_cast<const T*>(S.v);
   const T* C = static_cast<const T*>(S.C);
@@ -1609,9 +1610,9 @@ cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm
 
 template <class T>
 cudaError_t launch_gather_v(int64_t n, const SceneDev* sc, int ns, const int* perm, V4<T>* pn, V4<T>* V,
-                            cudaStream_t s) {
+                            int what, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_gather_v<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, perm, pn, V);
+  k_gather_v<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, perm, pn, V, what);
   return cudaGetLastError();
 }
 
@@ -2143,7 +2144,7 @@ cudaError_t launch_copy_table(CopyEntry* table, int n_entries, long long max_byt
   template cudaError_t launch_gather<T>(int64_t, const SceneDev*, int, const int*, const int4*, V4<T>*,  \
                                         V4<T>*, V4<T>*, cudaStream_t);                                  \
   template cudaError_t launch_gather_v<T>(int64_t, const SceneDev*, int, const int*, V4<T>*, V4<T>*,     \
-                                          cudaStream_t);                                                \
+                                          int, cudaStream_t);                                                \
   template cudaError_t launch_items<T>(const IterParams<T>&, int, int, bool, cudaStream_t);             \
   template cudaError_t launch_normalize<T>(int64_t, const T*, const uint32_t*, V4<T>*, V4<double>*,     \
                                            V4<T>*, int, bool, cudaStream_t);                            \

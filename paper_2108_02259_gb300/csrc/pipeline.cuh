@@ -259,6 +259,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
                  INT32_MAX / 4);
 
   bool split_v = false;  // V planes gathered after the sizing sequence (see below)
+  bool split_n = false;  // ... and the normals after the mass pass
   // CTAs of the copy that runs beside the sizing sequence (with four 16-byte
   // loads in flight per thread, 64 CTAs keep the host link full)
   constexpr int kSideCopyCtas = 64;
@@ -279,16 +280,18 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     // many scenes); otherwise, or when a table is not available, one copy
     // per array.  With a side stream, normals, v and C (60 of the 92 bytes
     // per FP32 particle) cross the link while the sizing sequence runs: only
-    // the passes need them (split_v).  Table layout: [0, 3 ns) x, body, m
-    // (all six arrays in [0, 6 ns) without the side stream); [3 ns, 6 ns)
-    // nrm, v, C; [6 ns, 8 ns) the results on the way back, written while the
-    // second copy may still be reading its own entries.
+    // the passes need them (split_v): v and C first (the mass pass needs
+    // them), then the normals, which cross while the mass pass runs (only the
+    // transfer passes read them: split_n).  Table layout: [0, 3 ns) x, body,
+    // m (all six arrays in [0, 6 ns) without the side stream); [3 ns, 5 ns)
+    // v, C; [5 ns, 6 ns) nrm; [6 ns, 8 ns) the results on the way back,
+    // written while the side copies may still be reading their own entries.
     CopyEntry* tab = env.copy_table(8 * ns);
     bool direct = tab != nullptr;
     // (APIC_CHECK reads v, C and the normals in the cell kernel: no split)
     cudaStream_t side = direct && !check ? env.side_stream() : nullptr;
-    int na = 0, nb = 0;
-    long long max_a = 0, max_b = 0;
+    int na = 0, nb = 0, nn = 0;
+    long long max_a = 0, max_b = 0, max_n = 0;
     for (int i = 0; i < ns && direct; ++i) {
       const apic_step_args& a = scenes[i];
       const int64_t o = hsc[i].part_off, m = a.n;
@@ -308,6 +311,9 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
         if (k < 3 || !side) {
           tab[na++] = e;
           max_a = std::max(max_a, e.bytes);
+        } else if (k == 3) {
+          tab[5 * ns + nn++] = e;
+          max_n = std::max(max_n, e.bytes);
         } else {
           tab[3 * ns + nb++] = e;
           max_b = std::max(max_b, e.bytes);
@@ -315,6 +321,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       }
     }
     split_v = direct && side != nullptr && nb > 0;
+    split_n = split_v && nn > 0;
     if (direct) P_LAUNCH(env, launch_copy_table(tab, na, max_a, s));
     if (split_v) {
       // after the first copy (which the sizing sequence waits for, so the
@@ -323,6 +330,10 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       P_CUDA(cudaStreamWaitEvent(side, env.side_event(0), 0));
       P_LAUNCH(env, launch_copy_table(tab + 3 * ns, nb, max_b, side, kSideCopyCtas));
       P_CUDA(cudaEventRecord(env.side_event(1), side));
+      if (split_n) {
+        P_LAUNCH(env, launch_copy_table(tab + 5 * ns, nn, max_n, side, kSideCopyCtas));
+        P_CUDA(cudaEventRecord(env.side_event(2), side));
+      }
     }
     for (int i = 0; i < ns; ++i) {
       const apic_step_args& a = scenes[i];
@@ -570,7 +581,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   struct PassKey {
     IterParams<T> p;
     T* mup;
-    int n_iter, any_mu, variant, split_v, mnrm, normals_only;
+    int n_iter, any_mu, variant, split_v, split_n, mnrm, normals_only;
   };
   PassKey key;
   std::memset(&key, 0, sizeof(key));  // padding bytes take part in the comparison
@@ -613,13 +624,14 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   key.any_mu = any_mu ? 1 : 0;
   key.variant = variant;
   key.split_v = split_v ? 1 : 0;
+  key.split_n = split_n ? 1 : 0;
   key.mnrm = mnrm ? 1 : 0;
   key.normals_only = normals_only ? 1 : 0;
 
   auto series = [&](cudaStream_t q) -> apic_status {
     IterParams<T> pp = key.p;
     const int var = key.variant;
-    if (split_v) P_LAUNCH(env, launch_gather_v<T>(n, sc, ns, perm, pn, V, q));
+    if (split_v) P_LAUNCH(env, launch_gather_v<T>(n, sc, ns, perm, pn, V, split_n ? 1 : 3, q));
     // every launch after the mass pass follows a k_items or k_normalize launch
     const bool ov = env.overlap();
     typename Env::Span span_mass(env, q, 3);
@@ -673,13 +685,25 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     }
     span_mass.stop();
 
+    // Staged normals that crossed the link during the mass pass: wait for
+    // their copy (in a captured graph, as an external event) and gather them;
+    // the first transfer pass then launches without overlap, since it reads
+    // the normals before its dependent-launch wait.
+    if (split_n) {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      P_CUDA(cudaStreamIsCapturing(q, &cs));
+      P_CUDA(cudaStreamWaitEvent(q, env.side_event(2),
+                                 cs == cudaStreamCaptureStatusActive ? cudaEventWaitExternal : cudaEventWaitDefault));
+      P_LAUNCH(env, launch_gather_v<T>(n, sc, ns, perm, pn, V, 2, q));
+    }
+
     // 8. the N + 1 transfer passes.
     for (int pass = 0; pass <= N; ++pass) {
       const int mode = N == 0 ? kModeOnly : pass == 0 ? kModeFirst : pass == N ? kModeLast : kModeMid;
       pp.fx_slot = 1 + pass;  // bound of the W this pass scatters, measured by the pass before
       {
         typename Env::Span span_pass(env, q, 2);
-        P_LAUNCH(env, launch_items<T>(pp, mode, var, ov, q));
+        P_LAUNCH(env, launch_items<T>(pp, mode, var, ov && !(pass == 0 && split_n), q));
       }
       if (pass < N) P_LAUNCH(env, normalize(1 + pass, 0));
     }
