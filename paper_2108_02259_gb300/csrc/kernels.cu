@@ -1225,12 +1225,16 @@ __global__ void k_cells(int64_t n, const SceneDev* __restrict__ sc, int ns, int4
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const double xs = S.x[3 * i + d] * S.inv_h;
-      // |x/h| < 2^29 keeps cells, blocks and their margins inside int32
-      if (!(fabs(xs) < 536870912.0)) {
+      // |x/h| < 2^29 keeps cells, blocks and their margins inside int32; the
+      // test reads the exponent bits (also false for inf and NaN), and the
+      // floor is the rounding mode of the conversion: two FP64-pipe
+      // instructions an axis, the pipe being narrow on this GPU
+      const int bexp = (int)((__double_as_longlong(xs) >> 52) & 0x7ff);
+      if (bexp >= 1023 + 29) {
         err |= kErrPos;
         c[d] = 0;
       } else {
-        c[d] = (int)floor(xs);
+        c[d] = __double2int_rd(xs);
       }
       lo[d] = hi[d] = c[d] >> 2;
     }
@@ -1351,14 +1355,29 @@ __global__ void k_gather(int64_t n, const SceneDev* __restrict__ sc, int ns, con
   if (!APIC_DBG_CHECK(g >= 0 && g < n, kDbgPerm)) return;
   const SceneDev& S = sc[scene_of_particle(sc, ns, g)];
   const int64_t i = g - S.part_off;
-  // the cell again from x, with k_cells' own arithmetic (the same integers;
-  // one gathered read fewer than loading them)
+  // the cell again from x (one gathered read fewer than loading it), and the
+  // offset in the cell: x (2^32 / h) is x / h scaled exactly, so its floor
+  // as a 64-bit integer holds floor(x / h) (k_cells' integer) above bit 32
+  // and the offset's first 32 bits below (two FP64-pipe instructions an axis)
+  // (The FP64 path keeps the exact FP64 difference x / h - floor(x / h).)
   const double* x = S.x;
-  const double xs = x[3 * i + 0] * S.inv_h, ys = x[3 * i + 1] * S.inv_h, zs = x[3 * i + 2] * S.inv_h;
-  const int3 c = make_int3((int)floor(xs), (int)floor(ys), (int)floor(zs));
-  const T tx = (T)(xs - (double)c.x);
-  const T ty = (T)(ys - (double)c.y);
-  const T tz = (T)(zs - (double)c.z);
+  const double s32 = S.inv_h * 4294967296.0;
+  int cc[3];
+  T tt[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if constexpr (sizeof(T) == 4) {
+      const long long q = __double2ll_rd(x[3 * i + d] * s32);
+      cc[d] = (int)(q >> 32);
+      tt[d] = (T)((float)(unsigned)(q & 0xffffffffll) * 0x1p-32f);
+    } else {
+      const double xs = x[3 * i + d] * S.inv_h;
+      cc[d] = __double2int_rd(xs);
+      tt[d] = (T)(xs - (double)cc[d]);
+    }
+  }
+  const int3 c = make_int3(cc[0], cc[1], cc[2]);
+  const T tx = tt[0], ty = tt[1], tz = tt[2];
   pt[s] = V4<T>{tx, ty, tz, static_cast<const T*>(S.m)[i]};
   const uint32_t loc = (uint32_t)(((c.z & 3) << 4) | ((c.y & 3) << 2) | (c.x & 3));
   if (V == nullptr) {  // normals and V planes gathered later (k_gather_v)
