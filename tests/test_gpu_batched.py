@@ -240,9 +240,57 @@ def test_page_locked_repeat_calls_pick_up_new_inputs(ctx):
         scale = 1.0 + 0.5 * k
         V[...] = f.v * scale
         Cc[...] = f.C * scale
+        # the normals cross in a copy of their own, waited for inside the
+        # captured series: every other call takes them away (all interior)
+        nrm = s.nrm if k % 2 == 0 else np.zeros_like(s.nrm)
+        NR[...] = nrm
         apic.contact_step(ctx, X, V, Cc, M, NR, B, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies, v_out=vo, C_out=Co)
-        sk = scenes.Scene(**{**s.__dict__, "v": s.v * scale, "C": s.C * scale})
+        sk = scenes.Scene(**{**s.__dict__, "v": s.v * scale, "C": s.C * scale, "nrm": nrm})
         _check(sk, vo.astype(np.float64), Co.astype(np.float64).reshape(-1, 3, 3), None, label=f"call {k}")
+
+
+def test_page_locked_arrays_of_many_chunks(ctx):
+    """The copy beside the sizing sequence splits the arrays into 64 KB
+    chunks over a bounded grid, so each CTA walks several chunks across
+    array boundaries.  A 200,000-particle scene (about 180 chunks of
+    normals, v and C) with arrays starting off 16-byte boundaries must give
+    what the device-pointer call gives."""
+    import torch
+
+    from paper_2108_02259_gb300 import apic
+
+    def pinned(a, dt, offset_rows):
+        a = np.ascontiguousarray(a, dt)
+        t = torch.empty((a.shape[0] + offset_rows,) + a.shape[1:], dtype=getattr(torch, np.dtype(dt).name)).pin_memory()
+        v = t.numpy()[offset_rows:]
+        v[...] = a
+        return v
+
+    s = scenes.four_bodies(n_iter=3)
+    f = s.astype(np.float32)
+    d = torch.device("cuda:0")
+
+    def dev(a, dt):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=d)
+
+    ref = apic.contact_step(ctx, dev(f.x, torch.float64), dev(f.v, torch.float32), dev(f.C, torch.float32),
+                            dev(f.m, torch.float32), dev(f.nrm, torch.float32), dev(f.body, torch.int32), s.h, s.mu,
+                            s.n_iter, n_bodies=s.n_bodies)
+    rv, rC = ref.v.cpu().numpy().astype(np.float64), ref.C.cpu().numpy().astype(np.float64)
+    vs = np.abs(s.v).max()
+    cs = max(np.linalg.norm(rC.reshape(-1, 9), axis=1).max(), 2 * vs / s.h)
+    for off in (0, 1):
+        vo, Co = pinned(np.zeros_like(f.v), np.float32, off), pinned(np.zeros_like(f.C), np.float32, off)
+        for _ in range(3):  # direct launches, capture, replay
+            apic.contact_step(ctx, pinned(f.x, np.float64, off), pinned(f.v, np.float32, off),
+                              pinned(f.C, np.float32, off), pinned(f.m, np.float32, off),
+                              pinned(f.nrm, np.float32, off), pinned(f.body, np.int32, off), s.h, s.mu, s.n_iter,
+                              n_bodies=s.n_bodies, v_out=vo, C_out=Co)
+            ev = np.abs(vo - rv).max() / vs
+            ec = np.abs(Co.reshape(-1, 9) - rC.reshape(-1, 9)).max() / cs
+            parity_log.record(f"pinned, many chunks, offset {off} vs device call", s.n, {"v": ev, "C": ec},
+                              {"v": TOL_V, "C": TOL_C})
+            assert ev <= TOL_V and ec <= TOL_C, (off, ev, ec)
 
 
 def test_failed_batch_leaves_every_scene_untouched(ctx):
