@@ -399,3 +399,37 @@ def test_growing_scene_table_keeps_the_copy_table():
         f = s.astype(np.float32)
         r = apic.contact_step(c, f.x, f.v, f.C, f.m, f.nrm, f.body, s.h, s.mu, 3, n_bodies=s.n_bodies)
         _check(s, r.v.astype(np.float64), r.C.astype(np.float64).reshape(-1, 3, 3), None, label="after destroy")
+
+
+def test_non_finite_velocity_stays_in_its_scene(ctx):
+    """Without APIC_CHECK a NaN velocity is not refused: as with floating-point
+    sums it reaches the outputs of its own scene (the transfer kernel's
+    fixed-point node sums turn a non-finite term bound into NaN node sums),
+    and an independent scene of the same batch keeps its oracle result."""
+    import torch
+
+    from paper_2108_02259_gb300 import apic
+
+    rng = np.random.default_rng(5)
+    bad = scenes.multi_body_scene(rng, 3000, 3, 1 / 64, n_iter=3)
+    good = scenes.multi_body_scene(rng, 2000, 2, 1 / 128, mu=0.2, n_iter=3)
+    d = torch.device("cuda:0")
+
+    def dev(a, dt):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=d)
+
+    batch = []
+    for k, s in enumerate((bad, good)):
+        f = s.astype(np.float32)
+        v = f.v.copy()
+        if k == 0:
+            v[1234, 1] = np.nan
+        batch.append(apic.BatchScene(dev(f.x, torch.float64), dev(v, torch.float32), dev(f.C, torch.float32),
+                                     dev(f.m, torch.float32), dev(f.nrm, torch.float32), dev(f.body, torch.int32),
+                                     s.h, s.mu, n_bodies=s.n_bodies))
+    apic.contact_step_batched(ctx, batch, 3)
+    torch.cuda.synchronize()
+    vb = batch[0].v_out.cpu().numpy()
+    assert np.isnan(vb[1234]).any()
+    _check(good, batch[1].v_out.cpu().double().numpy(), batch[1].C_out.cpu().double().numpy().reshape(-1, 3, 3),
+           None, label="finite scene beside a NaN one")
