@@ -79,6 +79,19 @@ typedef int32_t apic_status;
                                         otherwise APIC_ERR_INVALID_ARG.  Positions, masses and body
                                         ids are always validated.  Reads v, C and nrm once more.   */
 
+#define APIC_PARTITIONED (1u << 8)  /* apic_contact_step_batched only: the scenes are partitions of
+                                        the particles of ONE scene (any split; a spatial one keeps
+                                        the shared part of the grid small), all with the same h,
+                                        n_bodies, mu and mu_pair table.  Each partition keeps its
+                                        own sparse grid; after every particle-to-grid transfer
+                                        (eq. massToGrid with the momenta, and each P2G of the Sec.
+                                        2.3 series) the nodes of grid blocks active in several
+                                        partitions are summed across them (the halo exchange a
+                                        spatial decomposition over devices needs once per
+                                        transfer pair), so every partition sees the whole scene's
+                                        grid and the outputs equal those of one call on the whole
+                                        scene, up to FP32 summation order.  Statistics are per
+                                        partition.  Not with APIC_DETERMINISTIC.                    */
 #define APIC_MASS_NORMALS (1u << 7) /* nrm may be NULL (and is not read): the normals come from
                                         each body's grid mass instead (not in the paper, whose
                                         normals come from the FE surface, Sec. 2.3): after the mass

@@ -38,6 +38,7 @@ APIC_VARIANT_SEP23 = 1 << 3
 APIC_DETERMINISTIC = 1 << 5
 APIC_CHECK = 1 << 6
 APIC_MASS_NORMALS = 1 << 7
+APIC_PARTITIONED = 1 << 8  # batched scenes are partitions of one scene (grid sums shared)
 APIC_AUGURY_INIT = 1 << 4
 
 EXPORTED = [

@@ -468,7 +468,7 @@ struct CtxEnv {
 };
 
 constexpr uint32_t kAllFlags = APIC_FP64 | APIC_HOST_PTRS | APIC_VARIANT_PIC | APIC_VARIANT_SEP23 |
-                               APIC_DETERMINISTIC | APIC_CHECK | APIC_MASS_NORMALS;
+                               APIC_DETERMINISTIC | APIC_CHECK | APIC_MASS_NORMALS | APIC_PARTITIONED;
 
 apic_status run(apic_ctx* c, const apic_step_args* scenes, int ns, void* stream, apic_stats* stats,
                 bool normals_only = false, double nthr = kMassNormalThreshold) {
@@ -567,6 +567,22 @@ apic_status apic_contact_step_batched(apic_ctx* c, const apic_step_args* scenes,
     if (scenes[i].n_iter != scenes[0].n_iter)
       return pfail(APIC_ERR_INVALID_ARG, "scene %d: n_iter %d differs from scene 0 (%d); a batch shares it", i,
                    scenes[i].n_iter, scenes[0].n_iter);
+  }
+  if (scenes[0].flags & APIC_PARTITIONED) {
+    // partitions of one scene: one grid spacing, one set of bodies, one friction law
+    if (scenes[0].flags & APIC_DETERMINISTIC)
+      return pfail(APIC_ERR_INVALID_ARG, "APIC_PARTITIONED does not combine with APIC_DETERMINISTIC");
+    const apic_step_args& a0 = scenes[0];
+    for (int i = 1; i < n_scenes; ++i) {
+      const apic_step_args& a = scenes[i];
+      if (a.h != a0.h || a.n_bodies != a0.n_bodies || a.mu != a0.mu || (a.mu_pair == nullptr) != (a0.mu_pair == nullptr))
+        return pfail(APIC_ERR_INVALID_ARG,
+                     "partition %d: h, n_bodies, mu and the presence of mu_pair must equal partition 0's", i);
+      if (a.mu_pair)  // (a host table)
+        for (int k = 0; k < a.n_bodies * a.n_bodies; ++k)
+          if (a.mu_pair[k] != a0.mu_pair[k])
+            return pfail(APIC_ERR_INVALID_ARG, "partition %d: mu_pair differs from partition 0's", i);
+    }
   }
   return run(c, scenes, n_scenes, stream, stats);
 }

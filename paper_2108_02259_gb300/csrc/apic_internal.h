@@ -224,6 +224,18 @@ constexpr bool kVariantPersist[kNumVariants] = {false, false, false, false, fals
 // k_items or k_normalize launch in the same stream.
 template <class T>
 cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, bool overlap, cudaStream_t s);
+// Partitions of one scene (APIC_PARTITIONED): rep[cb] = the compact id of
+// block cb's copy in the lowest-numbered partition where the same grid
+// block is active, or -1 (cb is that copy, or no other partition has it).
+cudaError_t launch_halo_map(int n_blocks, const int* blist, const SceneDev* sc, int ns, const int* page, int* rep,
+                            cudaStream_t s);
+// The ghost sum over those copies, in two launches: every copy's node sums
+// (momentum, its FP64 accumulators, and with `mass` the mass, body mask and
+// per-body masses) added into its representative, then the totals copied
+// back to every copy.
+template <class T>
+cudaError_t launch_halo_sum(int n_blocks, const int* rep, V4<T>* gp, V4<double>* gp64, T* gm, uint32_t* gmask,
+                            T* gmb, int max_bodies, int64_t n_nodes, bool mass, cudaStream_t s);
 // all64: take every node's momentum from the FP64 accumulators (after kModeMassV).
 template <class T>
 cudaError_t launch_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask, V4<T>* gp,

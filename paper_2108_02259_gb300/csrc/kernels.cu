@@ -1766,6 +1766,91 @@ cudaError_t launch_items(const IterParams<T>& p, int mode, int variant, bool ove
 #undef APIC_VARIANT
 }
 
+// ---- partitions of one scene: the ghost sum of shared grid blocks ----
+
+__global__ void k_halo_map(int n_blocks, const int* __restrict__ blist, const SceneDev* __restrict__ sc, int ns,
+                           const int* __restrict__ page, int* __restrict__ rep) {
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= n_blocks) return;
+  const long long pg = blist[cb];
+  const int s = scene_of_page(sc, ns, pg);
+  const Box b = sc[s].box;
+  const long long local = pg - sc[s].page_off;
+  const int gx = (int)(local % b.nx) + b.ox, gy = (int)((local / b.nx) % b.ny) + b.oy,
+            gz = (int)(local / ((long long)b.nx * b.ny)) + b.oz;
+  int r = -1;
+  for (int s2 = 0; s2 < s && r < 0; ++s2) {
+    const Box b2 = sc[s2].box;
+    const int lx = gx - b2.ox, ly = gy - b2.oy, lz = gz - b2.oz;
+    if (lx < 0 || ly < 0 || lz < 0 || lx >= b2.nx || ly >= b2.ny || lz >= b2.nz) continue;
+    r = page[sc[s2].page_off + ((long long)lz * b2.ny + ly) * b2.nx + lx];
+  }
+  rep[cb] = r;
+}
+
+template <class T>
+__global__ void k_halo_add(int n_blocks, const int* __restrict__ rep, V4<T>* gp, V4<double>* gp64, T* gm,
+                           uint32_t* gmask, T* gmb, int max_bodies, int64_t n_nodes, int mass) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n_blocks * kNodesPerBlock) return;
+  const int r = rep[t / kNodesPerBlock];
+  if (r < 0) return;
+  const int64_t i = t, j = (int64_t)r * kNodesPerBlock + t % kNodesPerBlock;
+  const V4<T> q = gp[i];
+  atomicAdd(&gp[j].x, q.x);
+  atomicAdd(&gp[j].y, q.y);
+  atomicAdd(&gp[j].z, q.z);
+  if (gp64) {
+    const V4<double> d = gp64[i];
+    atomicAdd(&gp64[j].x, d.x);
+    atomicAdd(&gp64[j].y, d.y);
+    atomicAdd(&gp64[j].z, d.z);
+  }
+  if (mass) {
+    atomicAdd(&gm[j], gm[i]);
+    atomicOr(&gmask[j], gmask[i]);
+    if (gmb)
+      for (int b = 0; b < max_bodies; ++b) atomicAdd(&gmb[b * n_nodes + j], gmb[b * n_nodes + i]);
+  }
+}
+
+template <class T>
+__global__ void k_halo_copy(int n_blocks, const int* __restrict__ rep, V4<T>* gp, V4<double>* gp64, T* gm,
+                            uint32_t* gmask, T* gmb, int max_bodies, int64_t n_nodes, int mass) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n_blocks * kNodesPerBlock) return;
+  const int r = rep[t / kNodesPerBlock];
+  if (r < 0) return;
+  const int64_t i = t, j = (int64_t)r * kNodesPerBlock + t % kNodesPerBlock;
+  gp[i] = gp[j];
+  if (gp64) gp64[i] = gp64[j];
+  if (mass) {
+    gm[i] = gm[j];
+    gmask[i] = gmask[j];
+    if (gmb)
+      for (int b = 0; b < max_bodies; ++b) gmb[b * n_nodes + i] = gmb[b * n_nodes + j];
+  }
+}
+
+cudaError_t launch_halo_map(int n_blocks, const int* blist, const SceneDev* sc, int ns, const int* page, int* rep,
+                            cudaStream_t s) {
+  if (n_blocks <= 0) return cudaSuccess;
+  k_halo_map<<<(n_blocks + 255) / 256, 256, 0, s>>>(n_blocks, blist, sc, ns, page, rep);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_halo_sum(int n_blocks, const int* rep, V4<T>* gp, V4<double>* gp64, T* gm, uint32_t* gmask,
+                            T* gmb, int max_bodies, int64_t n_nodes, bool mass, cudaStream_t s) {
+  if (n_blocks <= 0) return cudaSuccess;
+  const int64_t n = (int64_t)n_blocks * kNodesPerBlock;
+  k_halo_add<T><<<grid_for(n, 256), 256, 0, s>>>(n_blocks, rep, gp, gp64, gm, gmask, gmb, max_bodies, n_nodes,
+                                                  mass ? 1 : 0);
+  k_halo_copy<T><<<grid_for(n, 256), 256, 0, s>>>(n_blocks, rep, gp, gp64, gm, gmask, gmb, max_bodies, n_nodes,
+                                                   mass ? 1 : 0);
+  return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_normalize(int64_t n_nodes, const T* gm, const uint32_t* gmask, V4<T>* gp,
                              V4<double>* gp64, V4<T>* gv, int all64, bool overlap, cudaStream_t s) {
@@ -2165,6 +2250,8 @@ cudaError_t launch_copy_table(CopyEntry* table, int n_entries, long long max_byt
   template cudaError_t launch_gather_v<T>(int64_t, const SceneDev*, int, const int*, V4<T>*, V4<T>*,     \
                                           int, cudaStream_t);                                                \
   template cudaError_t launch_items<T>(const IterParams<T>&, int, int, bool, cudaStream_t);             \
+  template cudaError_t launch_halo_sum<T>(int, const int*, V4<T>*, V4<double>*, T*, uint32_t*, T*, int,   \
+                                          int64_t, bool, cudaStream_t);                                 \
   template cudaError_t launch_normalize<T>(int64_t, const T*, const uint32_t*, V4<T>*, V4<double>*,     \
                                            V4<T>*, int, bool, cudaStream_t);                            \
   template cudaError_t launch_momentum<T>(int64_t, const double*, const T*, const T*, const T*, double, \

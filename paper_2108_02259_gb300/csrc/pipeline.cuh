@@ -38,7 +38,7 @@ enum Slot : int {
   kSlotSBbox, kSlotSMom, kSlotSCount, kSlotHX, kSlotHBody, kSlotHV, kSlotHC, kSlotHM, kSlotHN, kSlotHVo,
   kSlotHCo, kSlotDS, kSlotNrmAcc, kSlotNrmX, kSlotNrmTri, kSlotNrmOut, kSlotAugF, kSlotAugAm, kSlotAugVbar,
   kSlotAugVhat, kSlotAugChat, kSlotAugNrm, kSlotAugOut, kSlotRunCnt, kSlotRunOffs, kSlotRunEnd, kSlotFxMax,
-  kSlotFxErr, kSlotGmbFx, kSlotTicket, kSlotCount
+  kSlotFxErr, kSlotGmbFx, kSlotTicket, kSlotHaloRep, kSlotCount
 };
 
 constexpr int kMaxBodies = 32;
@@ -211,6 +211,8 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   const bool det = (flags & APIC_DETERMINISTIC) != 0;
   const bool mnrm = normals_only || (flags & APIC_MASS_NORMALS) != 0;
   const int check = (flags & APIC_CHECK) ? 1 : 0;
+  // partitions of one scene: their grids are summed where they share blocks
+  const bool parts = (flags & APIC_PARTITIONED) != 0 && ns > 1;
   const int N = scenes[0].n_iter;
   if (normals_only && (host || stats)) return pfail(APIC_ERR_INVALID_ARG, "normals: device pointers, no statistics");
   if (det && sizeof(T) != 4)
@@ -550,6 +552,8 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   P_TRY(env.take(kSlotGv, n_nodes, &gv, "grid velocity"));
   unsigned* ticket = nullptr;
   P_TRY(env.take(kSlotTicket, 1, &ticket, "item tickets"));
+  int* halo_rep = nullptr;
+  if (parts) P_TRY(env.take(kSlotHaloRep, std::max(n_blocks, 1), &halo_rep, "shared-block map"));
   if (sizeof(T) == 4) P_TRY(env.take(kSlotGp64, n_nodes, &gp64, "FP64 node momentum"));
   unsigned* fx_max = nullptr;
   int* fx_err = nullptr;
@@ -581,7 +585,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   struct PassKey {
     IterParams<T> p;
     T* mup;
-    int n_iter, any_mu, variant, split_v, split_n, mnrm, normals_only;
+    int n_iter, any_mu, variant, split_v, split_n, mnrm, normals_only, parts;
   };
   PassKey key;
   std::memset(&key, 0, sizeof(key));  // padding bytes take part in the comparison
@@ -627,6 +631,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   key.split_n = split_n ? 1 : 0;
   key.mnrm = mnrm ? 1 : 0;
   key.normals_only = normals_only ? 1 : 0;
+  key.parts = parts ? 1 : 0;
 
   auto series = [&](cudaStream_t q) -> apic_status {
     IterParams<T> pp = key.p;
@@ -638,6 +643,12 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     P_CUDA(cudaMemsetAsync(gm, 0, n_nodes * sizeof(T), q));
     P_CUDA(cudaMemsetAsync(gmask, 0, n_nodes * sizeof(uint32_t), q));
     P_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), q));
+    if (parts) P_LAUNCH(env, launch_halo_map(n_blocks, blist, sc, ns, page, halo_rep, q));
+    // the ghost sum over grid blocks that several partitions share, after a
+    // particle-to-grid transfer and before the normalisation
+    auto halo = [&](bool mass) -> cudaError_t {
+      return launch_halo_sum<T>(n_blocks, halo_rep, gp, gp64, gm, gmask, gmb, max_bodies, n_nodes, mass, q);
+    };
     P_CUDA(cudaMemsetAsync(gp, 0, n_nodes * sizeof(V4<T>), q));
     if (gp64) P_CUDA(cudaMemsetAsync(gp64, 0, n_nodes * sizeof(V4<double>), q));
     if (gmb) P_CUDA(cudaMemsetAsync(gmb, 0, (size_t)max_bodies * n_nodes * sizeof(T), q));
@@ -661,6 +672,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     };
     if (normals_only) P_CUDA(cudaMemsetAsync(V, 0, 3 * n * sizeof(V4<T>), q));  // (the mass pass reads V)
     P_LAUNCH(env, launch_items<T>(pp, kModeMassV, var, false, q));
+    if (parts) P_LAUNCH(env, halo(true));
     if (any_mu) {
       P_LAUNCH(env, launch_items<T>(pp, kModeMu, var, ov, q));
       pp.mup = mup;
@@ -705,6 +717,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
         typename Env::Span span_pass(env, q, 2);
         P_LAUNCH(env, launch_items<T>(pp, mode, var, ov && !(pass == 0 && split_n), q));
       }
+      if (pass < N && parts) P_LAUNCH(env, halo(false));
       if (pass < N) P_LAUNCH(env, normalize(1 + pass, 0));
     }
     return APIC_OK;

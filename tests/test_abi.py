@@ -44,7 +44,7 @@ def test_flags_match_header():
 
     hdr = open(os.path.join(ROOT, "include", "apiccontact.h")).read()
     for name in ("APIC_FP64", "APIC_HOST_PTRS", "APIC_VARIANT_PIC", "APIC_VARIANT_SEP23", "APIC_AUGURY_INIT",
-                 "APIC_DETERMINISTIC", "APIC_CHECK"):
+                 "APIC_DETERMINISTIC", "APIC_CHECK", "APIC_MASS_NORMALS", "APIC_PARTITIONED"):
         m = re.search(rf"#define {name} \(1u << (\d+)\)", hdr)
         assert m, name
         assert getattr(apic, name) == 1 << int(m.group(1))
