@@ -437,6 +437,7 @@ def main():
             "ms_per_step": b["ms_per_step"], "kernel_variant": b["kernel_variant"], "e2e": b["e2e"],
             "plain_single_scene": b["plain_single_scene"], "roofline": b["roofline"],
             "gpu_launches": b["gpu_launches"], "momentum_check": b["momentum_check"]}
+        line["partitioned2"] = partitioned_measure(args, apic, ctx, sc[0], dev, stream, flush, m["ms_per_step"])
         ctx.close()
         ctx = None
         line["served"] = served_measure(args, seconds=3.0, squeezed=False)
@@ -448,6 +449,53 @@ def main():
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def partitioned_measure(args, apic, ctx, s, dev, stream, flush, whole_ms):
+    """The scene as two partitions (halves along x) in one APIC_PARTITIONED
+    batched call: each keeps its own grid and the blocks both reach are
+    summed across them after every particle-to-grid transfer, the exchange a
+    split of one scene over two devices needs (here both on one GPU).  Times
+    the step like the main leg and checks the outputs against one call on
+    the whole scene."""
+    import torch
+
+    f = s.astype(np.float32)
+    xm = float(np.median(s.x[:, 0]))
+    parts = [np.flatnonzero(s.x[:, 0] < xm), np.flatnonzero(s.x[:, 0] >= xm)]
+
+    def t(a, d):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=d).to(dev)
+
+    batch = [apic.BatchScene(t(f.x[ix], torch.float64), t(f.v[ix], torch.float32), t(f.C[ix], torch.float32),
+                             t(f.m[ix], torch.float32), t(f.nrm[ix], torch.float32), t(f.body[ix], torch.int32),
+                             s.h, s.mu, n_bodies=s.n_bodies, mu_pair=s.mu_pair) for ix in parts]
+    N = s.n_iter
+    for _ in range(max(args.warmup, 3)):
+        apic.contact_step_batched(ctx, batch, N, stream=stream, flags=apic.APIC_PARTITIONED)
+    torch.cuda.synchronize(dev)
+    steps = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush.fill_(1.0)
+        a.record(stream)
+        apic.contact_step_batched(ctx, batch, N, stream=stream, flags=apic.APIC_PARTITIONED)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    whole = apic.contact_step(ctx, t(f.x, torch.float64), t(f.v, torch.float32), t(f.C, torch.float32),
+                              t(f.m, torch.float32), t(f.nrm, torch.float32), t(f.body, torch.int32), s.h, s.mu, N,
+                              n_bodies=s.n_bodies, mu_pair=s.mu_pair, stream=stream)
+    torch.cuda.synchronize(dev)
+    v = np.zeros((s.n, 3), np.float32)
+    for ix, b in zip(parts, batch):
+        v[ix] = b.v_out.cpu().numpy().reshape(-1, 3)
+    dv = float(np.abs(v - whole.v.cpu().numpy()).max() / np.abs(s.v).max())
+    return {"what": "the same scene as two partitions (halves along x), each with its own grid, summed where "
+                    "they share grid blocks after every particle-to-grid transfer (APIC_PARTITIONED)",
+            "partitions": [int(len(ix)) for ix in parts], "value": s.n * (N + 1) / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms, "vs_whole_scene_step": ms / whole_ms,
+            "max_dv_vs_whole_scene": dv, "l2": "flushed before every timed step"}
 
 
 def measure(args, apic, ctx, sc, dt, batched, dev, stream, flush, ws, with_e2e=True, with_clocks=True):
