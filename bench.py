@@ -360,6 +360,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="eight_bodies",
                     choices=["four_bodies", "two_cubes", "eight_bodies", "batched64", "served"])
+    ap.add_argument("--served-workers", type=int, default=2, help="served workload: server worker threads")
+    ap.add_argument("--served-batch", type=int, default=64, help="served workload: most requests per batch")
     ap.add_argument("--served-seconds", type=float, default=6.0,
                     help="open-loop seconds per offered load (the served workload; 3 s in the default line's leg)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -726,7 +728,8 @@ def served_measure(args, seconds=6.0, squeezed=True):
 
     build.build()
     sims = scenes.served_simulations()
-    srv = apic.Server(0, hbm_budget_bytes=80 << 30, n_workers=2, max_batch_scenes=64)
+    workers, batch = getattr(args, "served_workers", 2), getattr(args, "served_batch", 64)
+    srv = apic.Server(0, hbm_budget_bytes=80 << 30, n_workers=workers, max_batch_scenes=batch)
     srv.set_policy(args.variant, not args.no_graphs)
     hs = []
     for s in sims:
@@ -795,7 +798,7 @@ def served_measure(args, seconds=6.0, squeezed=True):
     out = {"config": {"workload": f"served: {len(sims)} resident simulations, {P} FE nodes in total (2k-1M per "
                                   f"simulation, each size drawn on its own, 2-8 bodies, mu in [0, 0.5], "
                                   f"N = {sims[0].n_iter}), Poisson step requests, each step advects x by "
-                                  "0.1 h / max|v|, 80 GiB budget, 2 workers",
+                                  f"0.1 h / max|v|, 80 GiB budget, {workers} workers, at most {batch} requests a batch",
                       "launch_policy": {"variant": args.variant, "graphs": not args.no_graphs},
                       "particles": P, "simulations": len(sims), "seconds_per_load": seconds,
                       "l2": f"working set far above L2 ({P / 1e6:.1f}M nodes)"},
