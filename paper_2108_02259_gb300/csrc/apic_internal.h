@@ -158,6 +158,11 @@ struct IterParams {
   int fx_stride;
   int fx_slot;
   int fx_attempt;
+  // FP32 default path: the first transfer pass computes each particle's
+  // per-pair friction blend itself (from the node masks it fetches with its
+  // tile) and writes it to mup_out for the later passes, instead of a
+  // separate blend pass before it.
+  int fold_mu;
   // Persistent grids: a counter of item tickets, 0 between launches (the
   // launch draws exactly n_items tickets and atomicInc wraps it back to 0).
   unsigned* ticket;

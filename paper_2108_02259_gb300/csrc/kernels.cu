@@ -471,6 +471,39 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
     return nd >= 0 && !APIC_DBG_CHECK(nd < p.n_nodes, kDbgTileNode) ? -1 : nd;
   };
   const int n = p.n_particles;
+  // R9 friction blend of one particle at tile cell `base` from the tile's
+  // node masks: mu_p = sum_{b' != b} mu(b,b') M_b'p / sum_{b' != b} M_b'p with
+  // M_b'p = sum_i N_ip m_{b',i}; mu(b,b) when no other body is near.
+  auto friction_blend = [&](const uint32_t* masks, const V4<T>& pt, int base, int body, const SceneDev& S,
+                            float fxSm) -> T {
+    T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4];
+    bspline(pt.x, wx, dx);
+    bspline(pt.y, wy, dy);
+    bspline(pt.z, wz, dz);
+    T num = T(0), den = T(0);
+    const uint32_t own = 1u << body;
+#pragma unroll 1
+    for (int q = 0; q < 64; ++q) {
+      const int kx = q & 3, ky = (q >> 2) & 3, kz = q >> 4;
+      const int tq = base + kz * (kTile * kTile) + ky * kTile + kx;
+      uint32_t other = masks[tq] & ~own;
+      if (!other) continue;
+      const int node = node_of(tq);
+      T wxk = kx == 0 ? wx[0] : kx == 1 ? wx[1] : kx == 2 ? wx[2] : wx[3];
+      T wyk = ky == 0 ? wy[0] : ky == 1 ? wy[1] : ky == 2 ? wy[2] : wy[3];
+      T wzk = kz == 0 ? wz[0] : kz == 1 ? wz[1] : kz == 2 ? wz[2] : wz[3];
+      const T w = wxk * wyk * wzk;
+      while (other) {
+        const int bo = __ffs(other) - 1;
+        other &= other - 1;
+        const T M = DET ? (T)from_fx(p.gmb_fx[(int64_t)bo * p.n_nodes + node], 1.f / fxSm)
+                        : p.gmb[(int64_t)bo * p.n_nodes + node];
+        num += w * p.mu_table[S.mu_off + body * S.n_bodies + bo] * M;
+        den += w * M;
+      }
+    }
+    return den > T(0) ? num / den : p.mu_table[S.mu_off + body * S.n_bodies + body];
+  };
   if (item >= p.n_items) {
     grid_dep_wait();
     return;
@@ -582,6 +615,17 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
     }
     __syncthreads();
   }
+  // the first pass with the friction blend folded in: does any other body
+  // reach this item's tile? (uniform over the CTA)
+  bool fold_other = false;
+  if constexpr (kMaskPre && MODE == kModeFirst) {
+    if (p.fold_mu && S.mu_off >= 0) {
+      const uint32_t own = 1u << body;
+      int o = 0;
+      for (int t = t_lo + tid; t < t_hi; t += CHUNK) o |= (smk[t] & ~own) != 0u;
+      fold_other = __syncthreads_or(o) != 0;
+    }
+  }
   if (MODE == kModeNormals) {
     for (int t = t_lo + tid; t < t_hi; t += CHUNK) {
       const int node = node_of(t);
@@ -631,35 +675,7 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
       if (MODE == kModeMu && S.mu_off < 0) {
         p.mup_out[s] = (T)S.mu;  // a scene with one scalar mu
       } else if (MODE == kModeMu) {
-        // mu_p = sum_{b' != b} mu(b,b') M_b'p / sum_{b' != b} M_b'p with
-        // M_b'p = sum_i N_ip m_{b',i}; mu(b,b) when no other body is near.
-        T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4];
-        bspline(pt.x, wx, dx);
-        bspline(pt.y, wy, dy);
-        bspline(pt.z, wz, dz);
-        T num = T(0), den = T(0);
-        const uint32_t own = 1u << body;
-#pragma unroll 1
-        for (int q = 0; q < 64; ++q) {
-          const int kx = q & 3, ky = (q >> 2) & 3, kz = q >> 4;
-          const int tq = base + kz * (kTile * kTile) + ky * kTile + kx;
-          uint32_t other = smask[tq] & ~own;
-          if (!other) continue;
-          const int node = node_of(tq);
-          T wxk = kx == 0 ? wx[0] : kx == 1 ? wx[1] : kx == 2 ? wx[2] : wx[3];
-          T wyk = ky == 0 ? wy[0] : ky == 1 ? wy[1] : ky == 2 ? wy[2] : wy[3];
-          T wzk = kz == 0 ? wz[0] : kz == 1 ? wz[1] : kz == 2 ? wz[2] : wz[3];
-          const T w = wxk * wyk * wzk;
-          while (other) {
-            const int bo = __ffs(other) - 1;
-            other &= other - 1;
-            const T M = DET ? (T)from_fx(p.gmb_fx[(int64_t)bo * p.n_nodes + node], 1.f / fxSm)
-                            : p.gmb[(int64_t)bo * p.n_nodes + node];
-            num += w * p.mu_table[S.mu_off + body * S.n_bodies + bo] * M;
-            den += w * M;
-          }
-        }
-        p.mup_out[s] = den > T(0) ? num / den : p.mu_table[S.mu_off + body * S.n_bodies + body];
+        p.mup_out[s] = friction_blend(smask, pt, base, body, S, fxSm);
       } else if (MODE == kModeNormals) {
         // rho = sum N m_b and g = sum grad N m_b (cell units) over the body's
         // own node masses, sum-factorised; n = -g/|g| on the surface, else 0
@@ -746,7 +762,19 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
         else
           g2p_tile<T, true>(sv, base, wx, dx, wy, dy, wz, dz, hv, hC);
         const T nrm[3] = {pn.x, pn.y, pn.z};
-        const T mu = p.mup ? p.mup[s] : (T)S.mu;
+        T mu;
+        if (kMaskPre && MODE == kModeFirst && p.fold_mu) {
+          if constexpr (kMaskPre) {
+            mu = S.mu_off < 0 ? (T)S.mu
+                 : fold_other ? friction_blend(smk, pt, base, body, S, fxSm)
+                              : p.mu_table[S.mu_off + body * S.n_bodies + body];
+          } else {
+            mu = (T)S.mu;
+          }
+          p.mup_out[s] = mu;  // for the passes after this one
+        } else {
+          mu = p.mup ? p.mup[s] : (T)S.mu;
+        }
         T dv[3], dC[9];
         bool out = false;
         if (MODE == kModeFirst || MODE == kModeOnly) {

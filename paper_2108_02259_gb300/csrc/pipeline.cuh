@@ -622,6 +622,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   p.fx_err = fx_err;
   p.gmb_fx = gmb_fx;
   p.fx_stride = fx_stride;
+  p.fold_mu = 0;
   p.ticket = ticket;
   key.mup = mup;
   key.n_iter = N;
@@ -673,7 +674,11 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     if (normals_only) P_CUDA(cudaMemsetAsync(V, 0, 3 * n * sizeof(V4<T>), q));  // (the mass pass reads V)
     P_LAUNCH(env, launch_items<T>(pp, kModeMassV, var, false, q));
     if (parts) P_LAUNCH(env, halo(true));
-    if (any_mu) {
+    // the per-pair friction blend: a pass of its own, or (FP32 default path
+    // with transfer passes) computed by the first pass from the node masks it
+    // fetches with its tile and written for the passes after it
+    const bool fold_mu = any_mu && sizeof(T) == 4 && !det && N > 0;
+    if (any_mu && !fold_mu) {
       P_LAUNCH(env, launch_items<T>(pp, kModeMu, var, ov, q));
       pp.mup = mup;
     }
@@ -713,6 +718,8 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     for (int pass = 0; pass <= N; ++pass) {
       const int mode = N == 0 ? kModeOnly : pass == 0 ? kModeFirst : pass == N ? kModeLast : kModeMid;
       pp.fx_slot = 1 + pass;  // bound of the W this pass scatters, measured by the pass before
+      pp.fold_mu = fold_mu && pass == 0 ? 1 : 0;
+      if (fold_mu && pass == 1) pp.mup = mup;  // written by the first pass
       {
         typename Env::Span span_pass(env, q, 2);
         P_LAUNCH(env, launch_items<T>(pp, mode, var, ov && !(pass == 0 && split_n), q));
