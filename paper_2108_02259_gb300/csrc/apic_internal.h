@@ -176,16 +176,20 @@ constexpr int kFxRetryHeadLog2 = 24;
 // Cells, validation, per-scene bounding boxes of particle blocks (sbbox[6 s]).
 template <class T>
 // check: also validate v, C and the normals (APIC_CHECK).
-cudaError_t launch_cells(int64_t n, const SceneDev* sc, int ns, int4* cellb, int* sbbox, int* err, int check,
-                         cudaStream_t s);
+// ptc (FP32 path, else NULL): each particle's offset in its cell and mass,
+// (t_x, t_y, t_z, m) in caller order, for the gather.
+cudaError_t launch_cells(int64_t n, const SceneDev* sc, int ns, int4* cellb, V4<T>* ptc, int* sbbox, int* err,
+                         int check, cudaStream_t s);
 template <class K>
 cudaError_t launch_keys(int64_t n, const SceneDev* sc, int ns, const int4* cellb, int max_bodies, K* keys,
                         int* vals, int* err, cudaStream_t s);
 // V == nullptr: pt and pn's cell bits only (launch_gather_v fills the
 // normals and V later).
 template <class T>
-cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm, const int4* cellb, V4<T>* pt,
-                          V4<T>* pn, V4<T>* V, cudaStream_t s);
+// With ptc, pt comes from it and the cell-in-block bits from the sorted keys
+// (key_bytes 4 or 8); without (FP64 path), both are recomputed from x.
+cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm, const V4<T>* ptc, const void* skeys,
+                          int key_bytes, V4<T>* pt, V4<T>* pn, V4<T>* V, cudaStream_t s);
 // what: 1 the V planes, 2 the normals, 3 both.
 template <class T>
 cudaError_t launch_gather_v(int64_t n, const SceneDev* sc, int ns, const int* perm, V4<T>* pn, V4<T>* V,

@@ -1231,8 +1231,8 @@ __global__ void k_fx_prep(int64_t n, const SceneDev* __restrict__ sc, int ns, co
 // one scene reduces the box in shared memory and adds it with one set of
 // atomics; CTAs that straddle scenes add per particle.
 template <class T>
-__global__ void k_cells(int64_t n, const SceneDev* __restrict__ sc, int ns, int4* cellb, int* sbbox, int* errp,
-                        int check) {
+__global__ void k_cells(int64_t n, const SceneDev* __restrict__ sc, int ns, int4* cellb, V4<T>* ptc, int* sbbox,
+                        int* errp, int check) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t p_first = blockIdx.x * (int64_t)blockDim.x;
   const int64_t p_last = min(p_first + blockDim.x, n) - 1;
@@ -1251,18 +1251,24 @@ __global__ void k_cells(int64_t n, const SceneDev* __restrict__ sc, int ns, int4
     const int64_t i = p - S.part_off;
     int c[3];
 #pragma unroll
+    float t[3];
     for (int d = 0; d < 3; ++d) {
+      // x (2^32 / h) is x / h scaled exactly, so its floor as a 64-bit
+      // integer holds floor(x / h) above bit 32 and the offset in the cell's
+      // first 32 bits below: two FP64-pipe instructions an axis, the pipe
+      // being narrow on this GPU.  |x/h| < 2^29 keeps cells, blocks and their
+      // margins inside int32; the test reads the exponent bits (also false
+      // for inf and NaN).
       const double xs = S.x[3 * i + d] * S.inv_h;
-      // |x/h| < 2^29 keeps cells, blocks and their margins inside int32; the
-      // test reads the exponent bits (also false for inf and NaN), and the
-      // floor is the rounding mode of the conversion: two FP64-pipe
-      // instructions an axis, the pipe being narrow on this GPU
       const int bexp = (int)((__double_as_longlong(xs) >> 52) & 0x7ff);
       if (bexp >= 1023 + 29) {
         err |= kErrPos;
         c[d] = 0;
+        t[d] = 0.f;
       } else {
-        c[d] = __double2int_rd(xs);
+        const long long q = __double2ll_rd(S.x[3 * i + d] * (S.inv_h * 4294967296.0));
+        c[d] = (int)(q >> 32);
+        t[d] = (float)(unsigned)(q & 0xffffffffll) * 0x1p-32f;
       }
       lo[d] = hi[d] = c[d] >> 2;
     }
@@ -1287,6 +1293,9 @@ __global__ void k_cells(int64_t n, const SceneDev* __restrict__ sc, int ns, int4
       if (!fin) err |= kErrFinite;
     }
     cellb[p] = make_int4(c[0], c[1], c[2], b);
+    // FP32 path: the offset in the cell and the mass, in caller order, for
+    // the gather (one aligned 16-byte record instead of x and m)
+    if (ptc) ptc[p] = V4<T>{(T)t[0], (T)t[1], (T)t[2], static_cast<const T*>(S.m)[i]};
     if (uniform_scene < 0) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -1376,38 +1385,35 @@ __global__ void k_keys(int64_t n, const SceneDev* __restrict__ sc, int ns, const
 // and V = (v, h C) in three float4 planes.
 template <class T>
 __global__ void k_gather(int64_t n, const SceneDev* __restrict__ sc, int ns, const int* __restrict__ perm,
-                         const int4* __restrict__ cellb, V4<T>* pt, V4<T>* pn, V4<T>* V) {
+                         const V4<T>* __restrict__ ptc, const void* __restrict__ skeys, int key_bytes, V4<T>* pt,
+                         V4<T>* pn, V4<T>* V) {
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int64_t g = perm[s];
   if (!APIC_DBG_CHECK(g >= 0 && g < n, kDbgPerm)) return;
   const SceneDev& S = sc[scene_of_particle(sc, ns, g)];
   const int64_t i = g - S.part_off;
-  // the cell again from x (one gathered read fewer than loading it), and the
-  // offset in the cell: x (2^32 / h) is x / h scaled exactly, so its floor
-  // as a 64-bit integer holds floor(x / h) (k_cells' integer) above bit 32
-  // and the offset's first 32 bits below (two FP64-pipe instructions an axis)
-  // (The FP64 path keeps the exact FP64 difference x / h - floor(x / h).)
-  const double* x = S.x;
-  const double s32 = S.inv_h * 4294967296.0;
-  int cc[3];
-  T tt[3];
+  uint32_t loc;
+  if (ptc != nullptr) {
+    // FP32 path: offset and mass from the cell kernel's record, the cell in
+    // the block from the sorted key's low six bits
+    pt[s] = ptc[g];
+    loc = key_bytes == 8 ? (uint32_t)(static_cast<const uint64_t*>(skeys)[s] & 63u)
+                         : static_cast<const uint32_t*>(skeys)[s] & 63u;
+  } else {
+    // FP64 path: the exact FP64 difference x / h - floor(x / h)
+    const double* x = S.x;
+    int cc[3];
+    T tt[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    if constexpr (sizeof(T) == 4) {
-      const long long q = __double2ll_rd(x[3 * i + d] * s32);
-      cc[d] = (int)(q >> 32);
-      tt[d] = (T)((float)(unsigned)(q & 0xffffffffll) * 0x1p-32f);
-    } else {
+    for (int d = 0; d < 3; ++d) {
       const double xs = x[3 * i + d] * S.inv_h;
       cc[d] = __double2int_rd(xs);
       tt[d] = (T)(xs - (double)cc[d]);
     }
+    pt[s] = V4<T>{tt[0], tt[1], tt[2], static_cast<const T*>(S.m)[i]};
+    loc = (uint32_t)(((cc[2] & 3) << 4) | ((cc[1] & 3) << 2) | (cc[0] & 3));
   }
-  const int3 c = make_int3(cc[0], cc[1], cc[2]);
-  const T tx = tt[0], ty = tt[1], tz = tt[2];
-  pt[s] = V4<T>{tx, ty, tz, static_cast<const T*>(S.m)[i]};
-  const uint32_t loc = (uint32_t)(((c.z & 3) << 4) | ((c.y & 3) << 2) | (c.x & 3));
   if (V == nullptr) {  // normals and V planes gathered later (k_gather_v)
     pn[s] = V4<T>{T(0), T(0), T(0), bits_to(T(0), loc)};
     return;
@@ -1632,10 +1638,10 @@ inline unsigned grid_for(int64_t n, int threads) {
 }  // namespace
 
 template <class T>
-cudaError_t launch_cells(int64_t n, const SceneDev* sc, int ns, int4* cellb, int* sbbox, int* err, int check,
-                         cudaStream_t s) {
+cudaError_t launch_cells(int64_t n, const SceneDev* sc, int ns, int4* cellb, V4<T>* ptc, int* sbbox, int* err,
+                         int check, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_cells<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, cellb, sbbox, err, check);
+  k_cells<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, cellb, ptc, sbbox, err, check);
   return cudaGetLastError();
 }
 
@@ -1648,10 +1654,10 @@ cudaError_t launch_keys(int64_t n, const SceneDev* sc, int ns, const int4* cellb
 }
 
 template <class T>
-cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm, const int4* cellb, V4<T>* pt,
-                          V4<T>* pn, V4<T>* V, cudaStream_t s) {
+cudaError_t launch_gather(int64_t n, const SceneDev* sc, int ns, const int* perm, const V4<T>* ptc, const void* skeys,
+                          int key_bytes, V4<T>* pt, V4<T>* pn, V4<T>* V, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_gather<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, perm, cellb, pt, pn, V);
+  k_gather<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, perm, ptc, skeys, key_bytes, pt, pn, V);
   return cudaGetLastError();
 }
 
@@ -2272,9 +2278,10 @@ cudaError_t launch_copy_table(CopyEntry* table, int n_entries, long long max_byt
 }
 
 #define APIC_INST_T(T)                                                                                  \
-  template cudaError_t launch_cells<T>(int64_t, const SceneDev*, int, int4*, int*, int*, int, cudaStream_t); \
-  template cudaError_t launch_gather<T>(int64_t, const SceneDev*, int, const int*, const int4*, V4<T>*,  \
-                                        V4<T>*, V4<T>*, cudaStream_t);                                  \
+  template cudaError_t launch_cells<T>(int64_t, const SceneDev*, int, int4*, V4<T>*, int*, int*, int,     \
+                                       cudaStream_t);                                                   \
+  template cudaError_t launch_gather<T>(int64_t, const SceneDev*, int, const int*, const V4<T>*,         \
+                                        const void*, int, V4<T>*, V4<T>*, V4<T>*, cudaStream_t);         \
   template cudaError_t launch_gather_v<T>(int64_t, const SceneDev*, int, const int*, V4<T>*, V4<T>*,     \
                                           int, cudaStream_t);                                                \
   template cudaError_t launch_items<T>(const IterParams<T>&, int, int, bool, cudaStream_t);             \

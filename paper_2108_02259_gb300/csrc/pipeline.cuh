@@ -38,7 +38,7 @@ enum Slot : int {
   kSlotSBbox, kSlotSMom, kSlotSCount, kSlotHX, kSlotHBody, kSlotHV, kSlotHC, kSlotHM, kSlotHN, kSlotHVo,
   kSlotHCo, kSlotDS, kSlotNrmAcc, kSlotNrmX, kSlotNrmTri, kSlotNrmOut, kSlotAugF, kSlotAugAm, kSlotAugVbar,
   kSlotAugVhat, kSlotAugChat, kSlotAugNrm, kSlotAugOut, kSlotRunCnt, kSlotRunOffs, kSlotRunEnd, kSlotFxMax,
-  kSlotFxErr, kSlotGmbFx, kSlotTicket, kSlotHaloRep, kSlotCount
+  kSlotFxErr, kSlotGmbFx, kSlotTicket, kSlotHaloRep, kSlotPtc, kSlotCount
 };
 
 constexpr int kMaxBodies = 32;
@@ -375,6 +375,8 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
   P_TRY(env.take(kSlotScenes, ns, &sc, "scene table"));
   P_TRY(env.take(kSlotSBbox, 6 * ns, &sbbox, "scene boxes"));
   P_TRY(env.take(kSlotCells, n, &cellb, "cells"));
+  V4<T>* ptc = nullptr;  // FP32 path: offsets and masses for the gather
+  if (sizeof(T) == 4) P_TRY(env.take(kSlotPtc, n, &ptc, "cell offsets"));
   int* hbbox = env.host_bbox(ns);
   Box* boxes = env.box_cache(ns);  // persistent per-scene boxes (or scratch)
 
@@ -389,7 +391,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     if (with_cells) {
       P_CUDA(cudaMemcpyAsync(ds, hs, sizeof(DevScalars), cudaMemcpyHostToDevice, q));
       P_CUDA(cudaMemcpyAsync(sc, hsc, ns * sizeof(SceneDev), cudaMemcpyHostToDevice, q));
-      P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, sbbox, &ds->err, check, q));
+      P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, ptc, sbbox, &ds->err, check, q));
     }
     // 3. keys and one radix sort over all scenes.
     if (sb.k64)
@@ -398,7 +400,8 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       P_TRY((sort_keys<uint32_t>(env, n, sc, ns, cellb, max_bodies, &ds->err, sb, q)));
     // 4. sorted SoA (normals and V planes later when they are still in
     //    transit).
-    P_LAUNCH(env, launch_gather<T>(n, sc, ns, sb.perm, cellb, pt, pn, (split_v || normals_only) ? nullptr : V, q));
+    P_LAUNCH(env, launch_gather<T>(n, sc, ns, sb.perm, ptc, sb.kb, sb.k64 ? 8 : 4, pt, pn,
+                                   (split_v || normals_only) ? nullptr : V, q));
     // 5. work items: runs of equal (grid block, body), each split into
     //    equal items of at most `chunk` particles (the variant's CTA size).
     if (sb.k64) {
@@ -471,7 +474,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       P_CUDA(cudaMemcpyAsync(sbbox, hbbox, 6 * ns * sizeof(int), cudaMemcpyHostToDevice, s));
       P_CUDA(cudaMemcpyAsync(ds, hs, sizeof(DevScalars), cudaMemcpyHostToDevice, s));
       P_CUDA(cudaMemcpyAsync(sc, hsc, ns * sizeof(SceneDev), cudaMemcpyHostToDevice, s));
-      P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, sbbox, &ds->err, check, s));
+      P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, ptc, sbbox, &ds->err, check, s));
       // 2. page-table boxes: one block of stencil margin plus kBoxSlack
       //    blocks of room for motion in later steps; laid end to end.
       P_CUDA(cudaMemcpyAsync(hbbox, sbbox, 6 * ns * sizeof(int), cudaMemcpyDeviceToHost, s));
