@@ -177,9 +177,11 @@ constexpr int kFxRetryHeadLog2 = 24;
 template <class T>
 // check: also validate v, C and the normals (APIC_CHECK).
 // ptc (FP32 path, else NULL): each particle's offset in its cell and mass,
-// (t_x, t_y, t_z, m) in caller order, for the gather.
+// (t_x, t_y, t_z, m) in caller order, for the gather.  keys (NULL, or with
+// every scene's page-table box already in sc): the sort keys of k_keys
+// (key_bytes 4 or 8) instead of the cells, so that k_keys is not needed.
 cudaError_t launch_cells(int64_t n, const SceneDev* sc, int ns, int4* cellb, V4<T>* ptc, int* sbbox, int* err,
-                         int check, cudaStream_t s);
+                         int check, void* keys, int key_bytes, int max_bodies, cudaStream_t s);
 template <class K>
 cudaError_t launch_keys(int64_t n, const SceneDev* sc, int ns, const int4* cellb, int max_bodies, K* keys,
                         int* vals, int* err, cudaStream_t s);

@@ -1232,7 +1232,7 @@ __global__ void k_fx_prep(int64_t n, const SceneDev* __restrict__ sc, int ns, co
 // atomics; CTAs that straddle scenes add per particle.
 template <class T>
 __global__ void k_cells(int64_t n, const SceneDev* __restrict__ sc, int ns, int4* cellb, V4<T>* ptc, int* sbbox,
-                        int* errp, int check) {
+                        int* errp, int check, void* keys, int key_bytes, int max_bodies) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t p_first = blockIdx.x * (int64_t)blockDim.x;
   const int64_t p_last = min(p_first + blockDim.x, n) - 1;
@@ -1292,7 +1292,25 @@ __global__ void k_cells(int64_t n, const SceneDev* __restrict__ sc, int ns, int4
       }
       if (!fin) err |= kErrFinite;
     }
-    cellb[p] = make_int4(c[0], c[1], c[2], b);
+    if (keys != nullptr) {
+      // the scene's page-table box is known (reused from the step before):
+      // the sort key here, as k_keys computes it from the cell
+      const Box box = S.box;
+      int bx = (c[0] >> 2) - box.ox, by = (c[1] >> 2) - box.oy, bz = (c[2] >> 2) - box.oz;
+      if (bx < 1 || by < 1 || bz < 1 || bx > box.nx - 2 || by > box.ny - 2 || bz > box.nz - 2) {
+        err |= kErrBox;  // a block left the reused box: the host sizes fresh boxes
+        bx = min(max(bx, 1), box.nx - 2);
+        by = min(max(by, 1), box.ny - 2);
+        bz = min(max(bz, 1), box.nz - 2);
+      }
+      const int64_t gpage = S.page_off + ((int64_t)bz * box.ny + by) * box.nx + bx;
+      const uint32_t loc = (uint32_t)(((c[2] & 3) << 4) | ((c[1] & 3) << 2) | (c[0] & 3));
+      const uint64_t key = (((uint64_t)gpage * (uint64_t)max_bodies + (uint64_t)(b < 0 ? 0 : b)) << 6) | loc;
+      if (key_bytes == 8) static_cast<uint64_t*>(keys)[p] = key;
+      else static_cast<uint32_t*>(keys)[p] = (uint32_t)key;
+    } else {
+      cellb[p] = make_int4(c[0], c[1], c[2], b);
+    }
     // FP32 path: the offset in the cell and the mass, in caller order, for
     // the gather (one aligned 16-byte record instead of x and m)
     if (ptc) ptc[p] = V4<T>{(T)t[0], (T)t[1], (T)t[2], static_cast<const T*>(S.m)[i]};
@@ -1639,9 +1657,10 @@ inline unsigned grid_for(int64_t n, int threads) {
 
 template <class T>
 cudaError_t launch_cells(int64_t n, const SceneDev* sc, int ns, int4* cellb, V4<T>* ptc, int* sbbox, int* err,
-                         int check, cudaStream_t s) {
+                         int check, void* keys, int key_bytes, int max_bodies, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_cells<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, cellb, ptc, sbbox, err, check);
+  k_cells<T><<<grid_for(n, 256), 256, 0, s>>>(n, sc, ns, cellb, ptc, sbbox, err, check, keys, key_bytes,
+                                               max_bodies);
   return cudaGetLastError();
 }
 
@@ -2279,7 +2298,7 @@ cudaError_t launch_copy_table(CopyEntry* table, int n_entries, long long max_byt
 
 #define APIC_INST_T(T)                                                                                  \
   template cudaError_t launch_cells<T>(int64_t, const SceneDev*, int, int4*, V4<T>*, int*, int*, int,     \
-                                       cudaStream_t);                                                   \
+                                       void*, int, int, cudaStream_t);                                  \
   template cudaError_t launch_gather<T>(int64_t, const SceneDev*, int, const int*, const V4<T>*,         \
                                         const void*, int, V4<T>*, V4<T>*, V4<T>*, cudaStream_t);         \
   template cudaError_t launch_gather_v<T>(int64_t, const SceneDev*, int, const int*, V4<T>*, V4<T>*,     \

@@ -174,15 +174,19 @@ apic_status plan_sizing(Env& env, int64_t n, int64_t NB, int max_bodies, SizingB
 // Keys of every particle, then the radix sort; the sorted keys land in kb
 // and the permutation in perm (the keys start in the buffer that makes the
 // last pass end there).
+// The buffer the keys start in (so that the last pass ends in kb).
+inline void* first_keys(const SizingBufs& b) { return radix_passes(b.end_bit) % 2 == 1 ? b.ka : b.kb; }
+
+// keys_ready: the cell kernel has already written the keys (reused boxes).
 template <class K, class Env>
 apic_status sort_keys(Env& env, int64_t n, const SceneDev* sc, int ns, const int4* cellb, int max_bodies,
-                      int* err, const SizingBufs& b, cudaStream_t s) {
+                      int* err, const SizingBufs& b, bool keys_ready, cudaStream_t s) {
   const bool odd = radix_passes(b.end_bit) % 2 == 1;
-  K* k0 = static_cast<K*>(odd ? b.ka : b.kb);
+  K* k0 = static_cast<K*>(first_keys(b));
   K* k1 = static_cast<K*>(odd ? b.kb : b.ka);
   int* v0 = odd ? b.va : b.perm;
   int* v1 = odd ? b.perm : b.va;
-  P_LAUNCH(env, launch_keys<K>(n, sc, ns, cellb, max_bodies, k0, v0, err, s));
+  if (!keys_ready) P_LAUNCH(env, launch_keys<K>(n, sc, ns, cellb, max_bodies, k0, v0, err, s));
   P_CUDA(launch_radix_sort<K>(k0, v0, k1, v1, n, b.end_bit, true, b.tmp, err, s));
   env.sorted();
   return APIC_OK;
@@ -391,13 +395,15 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
     if (with_cells) {
       P_CUDA(cudaMemcpyAsync(ds, hs, sizeof(DevScalars), cudaMemcpyHostToDevice, q));
       P_CUDA(cudaMemcpyAsync(sc, hsc, ns * sizeof(SceneDev), cudaMemcpyHostToDevice, q));
-      P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, ptc, sbbox, &ds->err, check, q));
+      // the boxes are reused: the cell kernel writes the sort keys too
+      P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, ptc, sbbox, &ds->err, check, first_keys(sb), sb.k64 ? 8 : 4,
+                                    max_bodies, q));
     }
     // 3. keys and one radix sort over all scenes.
     if (sb.k64)
-      P_TRY((sort_keys<uint64_t>(env, n, sc, ns, cellb, max_bodies, &ds->err, sb, q)));
+      P_TRY((sort_keys<uint64_t>(env, n, sc, ns, cellb, max_bodies, &ds->err, sb, with_cells, q)));
     else
-      P_TRY((sort_keys<uint32_t>(env, n, sc, ns, cellb, max_bodies, &ds->err, sb, q)));
+      P_TRY((sort_keys<uint32_t>(env, n, sc, ns, cellb, max_bodies, &ds->err, sb, with_cells, q)));
     // 4. sorted SoA (normals and V planes later when they are still in
     //    transit).
     P_LAUNCH(env, launch_gather<T>(n, sc, ns, sb.perm, ptc, sb.kb, sb.k64 ? 8 : 4, pt, pn,
@@ -474,7 +480,7 @@ apic_status run_batch(Env& env, const apic_step_args* scenes, int ns, cudaStream
       P_CUDA(cudaMemcpyAsync(sbbox, hbbox, 6 * ns * sizeof(int), cudaMemcpyHostToDevice, s));
       P_CUDA(cudaMemcpyAsync(ds, hs, sizeof(DevScalars), cudaMemcpyHostToDevice, s));
       P_CUDA(cudaMemcpyAsync(sc, hsc, ns * sizeof(SceneDev), cudaMemcpyHostToDevice, s));
-      P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, ptc, sbbox, &ds->err, check, s));
+      P_LAUNCH(env, launch_cells<T>(n, sc, ns, cellb, ptc, sbbox, &ds->err, check, nullptr, 0, max_bodies, s));
       // 2. page-table boxes: one block of stencil margin plus kBoxSlack
       //    blocks of room for motion in later steps; laid end to end.
       P_CUDA(cudaMemcpyAsync(hbbox, sbbox, 6 * ns * sizeof(int), cudaMemcpyDeviceToHost, s));
