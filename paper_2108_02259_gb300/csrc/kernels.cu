@@ -110,9 +110,19 @@ __device__ __forceinline__ void undesirable(const T dv[3], const T dC[9], const 
     T vt[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) vt[a] = dv[a] - dn * n[a];
-    const T nt = sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
-    const T s = fmin(nt, -mu * dn);
-    const T keep = nt > T(0) ? s / nt : T(0);
+    // the admissible tangential part keeps min(|vt|, -mu dn) / |vt| of vt
+    T keep;
+    if constexpr (sizeof(T) == 4) {
+      // FP32: min(1, -mu dn / |vt|) with the reciprocal square root
+      // (rsqrtf: no IEEE square root and divide, whose slow paths branch);
+      // |vt|^2 below the smallest normal float is taken at that floor
+      const float nt2 = vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2];
+      keep = nt2 > 0.f ? fminf(1.f, -mu * dn * rsqrtf(fmaxf(nt2, 1.17549435e-38f))) : 0.f;
+    } else {
+      const T nt = sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
+      const T s = fmin(nt, -mu * dn);
+      keep = nt > T(0) ? s / nt : T(0);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) wv[a] = vt[a] - keep * vt[a];
   } else {
@@ -746,9 +756,10 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
         }
         stash[4][sidx(j)] = V4<T>{wx[0], wx[1], wx[2], wx[3]};
         stash[5][sidx(j)] = V4<T>{wx[0] * dx[0], wx[1] * dx[1], wx[2] * dx[2], wx[3] * dx[3]};
-        stash[1][sidx(j)] = q0;
-        stash[2][sidx(j)] = q1;
-        stash[3][sidx(j)] = q2;
+        // W = V, in phase 2's record layout (below)
+        stash[1][sidx(j)] = V4<T>{q0.x, q0.y, q1.x, q1.w};
+        stash[2][sidx(j)] = V4<T>{q1.y, q2.x, q0.w, q1.z};
+        stash[3][sidx(j)] = V4<T>{q0.z, q2.z, q2.w, q2.y};
       } else {
         T wx[4], dx[4], wy[4], dy[4], wz[4], dz[4];
         bspline(pt.x, wx, dx);
@@ -837,9 +848,10 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
           } else {
             stash[0][sidx(j)] = pt;
           }
-          stash[1][sidx(j)] = V4<T>{u[0], u[1], u[2], uC[0]};
-          stash[2][sidx(j)] = V4<T>{uC[1], uC[2], uC[3], uC[4]};
-          stash[3][sidx(j)] = V4<T>{uC[5], uC[6], uC[7], uC[8]};
+          // W = (u, uC) in phase 2's record layout (below)
+          stash[1][sidx(j)] = V4<T>{u[0], u[1], uC[1], uC[4]};
+          stash[2][sidx(j)] = V4<T>{uC[2], uC[5], uC[0], uC[3]};
+          stash[3][sidx(j)] = V4<T>{u[2], uC[7], uC[8], uC[6]};
           stash[4][sidx(j)] = V4<T>{wx[0], wx[1], wx[2], wx[3]};
           stash[5][sidx(j)] = V4<T>{wx[0] * dx[0], wx[1] * dx[1], wx[2] * dx[2], wx[3] * dx[3]};
         }
@@ -865,11 +877,13 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
     // (each one-dimensional App. B weight is at most 1/2).  With B < 2^k,
     // T = 2^(33 - k) keeps them below 2^30 in magnitude.
     fx_nonfinite = !(B <= 3.0e38f);
-    int k = 0;
-    if (!fx_nonfinite && B > 0.f) (void)frexpf(B, &k);
+    // B = f 2^k with f in [0.5, 1): k is B's biased exponent - 126 (a zero or
+    // subnormal B gives k = -126, and the cap e = 126 applies); T and 1/T are
+    // built from their exponent bits
+    const int k = (int)((__float_as_uint(B) >> 23) & 0xffu) - 126;
     const int e = fx_nonfinite ? 0 : min(33 - k, 126);
-    fxT = ldexpf(1.f, e);
-    fxInvT = ldexpf(1.f, -e);
+    fxT = __uint_as_float((unsigned)(e + 127) << 23);
+    fxInvT = __uint_as_float((unsigned)(127 - e) << 23);
   } else {
     __syncwarp();
   }
@@ -896,7 +910,6 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
       acc[k].zero();
       macc[k].zero();
     }
-    int cur = -1;
     const int j0 = grp * 16, j1 = min(j0 + 16, count);
     auto flush = [&](int base) {
 #pragma unroll
@@ -925,23 +938,22 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
         macc[kk].zero();
       }
     };
-    for (int j = j0; j < j1; ++j) {
-      const int base = sloc[j];
-      if (base != cur) {
-        if (cur >= 0) flush(cur);
-        cur = base;
-      }
-      const V4<T> X = stash[4][sidx(j)], XD = stash[5][sidx(j)];
+    // stash row index sidx(j) = j + (j >> 4); j >> 4 is fixed over a group's 16
+    const int jofs = j0 >> 4;
+    // phase 2 for stashed particle j: this lane's rows of its 4^3 stencil
+    auto accumulate = [&](const int j) {
+      const int sj = j + jofs;
+      const V4<T> X = stash[4][sj], XD = stash[5][sj];
       T wyzm[RPL], ty = T(0), tz = T(0);
       if constexpr (ROWTAB) {
         // this lane's row weights m N_y(ky) N_z(kz), from the stashed factors
         // (the particle's own offset is already folded into u)
-        const T wym = reinterpret_cast<const T*>(&stash[0][sidx(j)])[ky];
+        const T wym = reinterpret_cast<const T*>(&stash[0][sj])[ky];
 #pragma unroll
         for (int k = 0; k < RPL; ++k)
-          wyzm[k] = wym * reinterpret_cast<const T*>(&stash[ROWTAB ? 6 : 0][sidx(j)])[kzr[k]];
+          wyzm[k] = wym * reinterpret_cast<const T*>(&stash[ROWTAB ? 6 : 0][sj])[kzr[k]];
       } else {
-        const V4<T> a = stash[0][sidx(j)];
+        const V4<T> a = stash[0][sj];
         const T wym = a.w * (cy0 + a.y * (cy1 + a.y * cy2));
 #pragma unroll
         for (int k = 0; k < RPL; ++k) wyzm[k] = wym * (cz0[k] + a.z * (cz1[k] + a.z * cz2[k]));
@@ -956,33 +968,73 @@ __device__ __forceinline__ void items_body(const IterParams<T>& p, const int ite
         }
       }
       {
-        const V4<T> w0 = stash[1][sidx(j)], w1 = stash[2][sidx(j)], w2 = stash[3][sidx(j)];
-        // W = (u, Ch); Ch rows (w0.w w1.x w1.y) (w1.z w1.w w2.x) (w2.y w2.z w2.w).
+        // W = (u, Ch) as the records w0 = (u_0, u_1, Ch_01, Ch_11),
+        // w1 = (Ch_02, Ch_12, Ch_00, Ch_10), w2 = (u_2, Ch_21, Ch_22, Ch_20), so
+        // that components 0 and 1 pair up for the paired FP32 operations.
         // Node k of a row gets wx_k A + wx_k dx_k B with
         //   A_c = m wy wz (u_c + Ch_c1 dy + Ch_c2 dz),  B_c = m wy wz Ch_c0.
+        const V4<T> w0 = stash[1][sj], w1 = stash[2][sj], w2 = stash[3][sj];
         const T dy = oy - ty;
 #pragma unroll
         for (int k = 0; k < RPL; ++k) {
           const T dz = oz[k] - tz;
           T A[3], B[3];
           if (aff) {
-            A[0] = wyzm[k] * (w0.x + w1.x * dy + w1.y * dz);
-            A[1] = wyzm[k] * (w0.y + w1.w * dy + w2.x * dz);
-            A[2] = wyzm[k] * (w0.z + w2.z * dy + w2.w * dz);
-            B[0] = wyzm[k] * w0.w;
-            B[1] = wyzm[k] * w1.z;
-            B[2] = wyzm[k] * w2.y;
+            if constexpr (sizeof(T) == 4) {
+              const float2 m2 = make_float2(wyzm[k], wyzm[k]);
+              float2 a01 = __ffma2_rn(make_float2(w0.z, w0.w), make_float2(dy, dy), make_float2(w0.x, w0.y));
+              a01 = __fmul2_rn(__ffma2_rn(make_float2(w1.x, w1.y), make_float2(dz, dz), a01), m2);
+              const float2 b01 = __fmul2_rn(make_float2(w1.z, w1.w), m2);
+              A[0] = a01.x;
+              A[1] = a01.y;
+              B[0] = b01.x;
+              B[1] = b01.y;
+            } else {
+              A[0] = wyzm[k] * (w0.x + w0.z * dy + w1.x * dz);
+              A[1] = wyzm[k] * (w0.y + w0.w * dy + w1.y * dz);
+              B[0] = wyzm[k] * w1.z;
+              B[1] = wyzm[k] * w1.w;
+            }
+            A[2] = wyzm[k] * (w2.x + w2.y * dy + w2.z * dz);
+            B[2] = wyzm[k] * w2.w;
             acc[k].add(X, XD, A, B);
           } else {
             A[0] = wyzm[k] * w0.x;
             A[1] = wyzm[k] * w0.y;
-            A[2] = wyzm[k] * w0.z;
+            A[2] = wyzm[k] * w2.x;
             acc[k].add(X, XD, A, nullptr);
           }
         }
       }
+    };
+    if constexpr (RPL == 1) {
+      // Runs of equal cells from a warp ballot of the run heads (phase-1 slot
+      // j is thread j's, in this warp): a group walks each run without
+      // checking for a change of cell and flushes once at its end.
+      const bool head = tid < count && ((tid & 15) == 0 || sloc[tid] != sloc[tid - 1]);
+      const unsigned heads = __ballot_sync(0xffffffffu, head);
+      const unsigned hm = (heads >> (j0 & 31)) & 0xffffu;  // this group's 16 slots
+      int a = j0;
+      while (a < j1) {
+        const unsigned later = hm & ~((2u << (a - j0)) - 1u);  // heads after slot a
+        const int b = later ? min(j0 + __ffs(later) - 1, j1) : j1;
+        const int base = sloc[a];
+        for (int j = a; j < b; ++j) accumulate(j);
+        flush(base);
+        a = b;
+      }
+    } else {
+      int cur = -1;
+      for (int j = j0; j < j1; ++j) {
+        const int base = sloc[j];
+        if (base != cur) {
+          if (cur >= 0) flush(cur);
+          cur = base;
+        }
+        accumulate(j);
+      }
+      if (cur >= 0) flush(cur);
     }
-    if (cur >= 0) flush(cur);
   }
   __syncthreads();
 
