@@ -505,3 +505,33 @@ def test_planted_mistakes(tmp_path):
             else:
                 failures += np.abs(vo - sc.v).max() > 1e-10
         assert failures > 0, f"planted mistake not caught: {new}"
+
+
+def test_separation_rule_is_a_step_and_the_cone_rule_is_continuous():
+    """Sec. 2.3's separation rule switches W between 0 and Delta at dn = 0, and
+    the series drives the particles of an active contact there; Sec. 2.4's cone
+    projection is continuous.  So under seeded relative changes of v and C the
+    oracle's output moves in proportion to the change with the cone rule (ten
+    times the change, ten times the effect), but jumps with the separation rule
+    at a change of only 1e-8.  The GPU tests compare the separation rule beyond
+    the oracle's own envelope for this reason (tests/discontinuity.py)."""
+    import discontinuity
+
+    s = scenes.four_bodies(scale=0.02)
+    vs = np.abs(s.v).max()
+    moved = {}
+    for flags in (0, oracle.FLAG_SEP23):
+        def run(v, C, flags=flags):
+            return oracle.contact_step(s.x, v, C, s.m, s.nrm, s.body, s.h, s.mu, s.n_iter, n_bodies=s.n_bodies,
+                                       flags=flags)[:2]
+        for eps in (1e-8, 1e-7):
+            for seed in range(3):
+                ev = discontinuity.envelope(run, s.v, s.C, eps=eps, trials=1, seed=seed)[2]
+                moved[flags, eps, seed] = ev.max() / vs
+    for seed in range(3):  # cone rule: linear in the change, to 10%
+        ratio = moved[0, 1e-7, seed] / moved[0, 1e-8, seed]
+        assert 9.0 < ratio < 11.0, (seed, ratio)
+        assert moved[0, 1e-8, seed] < 1e-7
+    cone = max(moved[0, 1e-8, k] for k in range(3))
+    step = max(moved[oracle.FLAG_SEP23, 1e-8, k] for k in range(3))
+    assert step > 10 * cone, (step, cone)
