@@ -1278,6 +1278,30 @@ __global__ void k_fx_prep(int64_t n, const SceneDev* __restrict__ sc, int ns, co
   }
 }
 
+// floor(x 2^k) for a double x, from its bits with integer instructions only:
+// |x| 2^k = mant 2^sh exactly, so the floor is a shift, less one for a
+// negative x whose shifted-out bits are not all zero.  The caller keeps the
+// result inside +-2^62 (sh <= 9 here).
+__device__ __forceinline__ long long floor_pow2_scaled(double x, int k) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7ff);
+  const unsigned long long mant = (u & 0xfffffffffffffull) | (e != 0 ? (1ull << 52) : 0ull);
+  const int sh = (e != 0 ? e : 1) - 1075 + k;
+  unsigned long long a;
+  bool frac;
+  if (sh >= 0) {
+    a = mant << sh;
+    frac = false;
+  } else if (sh > -64) {
+    a = mant >> -sh;
+    frac = (mant & ((1ull << -sh) - 1ull)) != 0;
+  } else {
+    a = 0;
+    frac = mant != 0;
+  }
+  return (u >> 63) ? -(long long)(a + (frac ? 1ull : 0ull)) : (long long)a;
+}
+
 // Cell of every particle (x/h in FP64, floor), validation, and the bounding
 // box of each scene's particle blocks.  A CTA whose particles all belong to
 // one scene reduces the box in shared memory and adds it with one set of
@@ -1302,23 +1326,39 @@ __global__ void k_cells(int64_t n, const SceneDev* __restrict__ sc, int ns, int4
     const SceneDev& S = sc[scene];
     const int64_t i = p - S.part_off;
     int c[3];
-#pragma unroll
     float t[3];
+    // 1/h a power of two 2^lg (h = 1/512 and the like): x / h is exact and
+    // its scaled floor comes from the bits of x with integer instructions
+    const unsigned long long hb = (unsigned long long)__double_as_longlong(S.inv_h);
+    const int he = (int)((hb >> 52) & 0x7ff);
+    const bool pow2 = (hb & 0xfffffffffffffull) == 0 && he != 0 && he != 0x7ff;
+    const int lg = he - 1023;
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
-      // x (2^32 / h) is x / h scaled exactly, so its floor as a 64-bit
-      // integer holds floor(x / h) above bit 32 and the offset in the cell's
-      // first 32 bits below: two FP64-pipe instructions an axis, the pipe
-      // being narrow on this GPU.  |x/h| < 2^29 keeps cells, blocks and their
-      // margins inside int32; the test reads the exponent bits (also false
-      // for inf and NaN).
-      const double xs = S.x[3 * i + d] * S.inv_h;
-      const int bexp = (int)((__double_as_longlong(xs) >> 52) & 0x7ff);
-      if (bexp >= 1023 + 29) {
+      // floor(x 2^32 / h) as a 64-bit integer holds floor(x / h) above bit 32
+      // and the offset in the cell's first 32 bits below.  x 2^32 / h is x / h
+      // scaled exactly, so its exponent is that of x / h plus 32.  |x/h| < 2^29
+      // keeps cells, blocks and their margins inside int32; the tests read
+      // exponent bits (and refuse inf and NaN).  The FP64 pipe is narrow on
+      // this GPU: the general path takes two FP64 instructions an axis, the
+      // power-of-two path none.
+      const double xd = S.x[3 * i + d];
+      bool bad;
+      long long q = 0;
+      if (pow2) {
+        const int e = (int)((__double_as_longlong(xd) >> 52) & 0x7ff);
+        bad = e == 0x7ff || e - 1023 + lg >= 29;
+        if (!bad) q = floor_pow2_scaled(xd, lg + 32);
+      } else {
+        const double xs = xd * (S.inv_h * 4294967296.0);
+        bad = (int)((__double_as_longlong(xs) >> 52) & 0x7ff) >= 1023 + 29 + 32;
+        if (!bad) q = __double2ll_rd(xs);
+      }
+      if (bad) {
         err |= kErrPos;
         c[d] = 0;
         t[d] = 0.f;
       } else {
-        const long long q = __double2ll_rd(S.x[3 * i + d] * (S.inv_h * 4294967296.0));
         c[d] = (int)(q >> 32);
         t[d] = (float)(unsigned)(q & 0xffffffffll) * 0x1p-32f;
       }
