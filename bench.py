@@ -356,7 +356,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 200; 20 for --impl reference, whose steps are host-bound)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="eight_bodies",
                     choices=["four_bodies", "two_cubes", "eight_bodies", "batched64", "served"])
@@ -377,6 +378,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip every measurement beside the workload's own (normals, augury, batched and served legs)")
     args = ap.parse_args()
+    if args.steps is None:
+        # about a second of timed device work on the 4M-node scene, so that the
+        # clock samples taken during it are several
+        args.steps = 20 if args.impl == "reference" else 200
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)

@@ -1305,7 +1305,9 @@ __device__ __forceinline__ long long floor_pow2_scaled(double x, int k) {
 // Cell of every particle (x/h in FP64, floor), validation, and the bounding
 // box of each scene's particle blocks.  A CTA whose particles all belong to
 // one scene reduces the box in shared memory and adds it with one set of
-// atomics; CTAs that straddle scenes add per particle.
+// atomics; CTAs that straddle scenes add per particle.  With keys (the boxes
+// reused from the step before) the kernel writes the sort keys instead and
+// skips the box.
 template <class T>
 __global__ void k_cells(int64_t n, const SceneDev* __restrict__ sc, int ns, int4* cellb, V4<T>* ptc, int* sbbox,
                         int* errp, int check, void* keys, int key_bytes, int max_bodies) {
@@ -1406,13 +1408,18 @@ __global__ void k_cells(int64_t n, const SceneDev* __restrict__ sc, int ns, int4
     // FP32 path: the offset in the cell and the mass, in caller order, for
     // the gather (one aligned 16-byte record instead of x and m)
     if (ptc) ptc[p] = V4<T>{(T)t[0], (T)t[1], (T)t[2], static_cast<const T*>(S.m)[i]};
-    if (uniform_scene < 0) {
+    if (uniform_scene < 0 && keys == nullptr) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         atomicMin(&sbbox[6 * scene + d], lo[d]);
         atomicMax(&sbbox[6 * scene + 3 + d], hi[d]);
       }
     }
+  }
+  if (keys != nullptr) {
+    // the boxes are reused and known: no box reduction, only errors
+    if (err) atomicOr(errp, err);
+    return;
   }
   if (uniform_scene < 0) {
     if (err) atomicOr(errp, err);
