@@ -493,18 +493,24 @@ int64_t radix_temp_ints(int64_t n, int end_bit) {
   return (int64_t)passes * kRadixBins + 32 + (int64_t)passes * tiles * kRadixBins;
 }
 
-// One pass of k_onesweep with ITEMS keys a thread; the staged tile's dynamic
-// shared memory is allowed once per instantiation.
+// One pass of k_onesweep with ITEMS keys a thread.  Its shared memory (static
+// plus the staged tile) can exceed 48 KB, which each device allows once per
+// instantiation (the flag is per device ordinal; beyond kAttrDevices the
+// attribute is set on every launch).
+constexpr int kAttrDevices = 64;
 template <class K, int ITEMS>
 cudaError_t launch_onesweep(int64_t tiles, const K* kin, const int* vin, K* kout, int* vout, int64_t n, int shift,
                             int bits, const int* counts, unsigned* status, int* tile_ctr, int* err, cudaStream_t s) {
-  static std::atomic<bool> attr_set{false};
+  static std::atomic<bool> attr_set[kAttrDevices];
   const size_t dyn = (size_t)SortTile<K, ITEMS>::kTile * (sizeof(K) + sizeof(int));
-  if (!attr_set.load()) {
-    const cudaError_t e = cudaFuncSetAttribute(k_onesweep<K, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)dyn);
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool known = dev >= 0 && dev < kAttrDevices;
+  if (!known || !attr_set[dev].load()) {
+    e = cudaFuncSetAttribute(k_onesweep<K, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
-    attr_set.store(true);
+    if (known) attr_set[dev].store(true);
   }
   k_onesweep<K, ITEMS><<<(unsigned)tiles, kSortThreads, dyn, s>>>(kin, vin, kout, vout, n, shift, bits, counts, status,
                                                                    tile_ctr, err);
